@@ -1,0 +1,224 @@
+"""CPU FP64 oracle for the meshless molecular ray-caster.
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` are the only callers.  The product renderer
+never imports this package and this package never imports the renderer; the
+two read the same seeded arrays from ``paper_2501_12750_gb300.scenes`` and
+share nothing else.
+
+The arithmetic lives in ``vtx_oracle.c`` (plain C, FP64, OpenMP, built with
+``-ffp-contract=off``).  This module only compiles it, marshals arrays and
+chains its steps: hits -> shading -> SSAO (fetching the depths the SSAO
+samples need by computing those pixels too).
+
+Parity unpinned (constants the paper does not state): the Blinn-Phong
+coefficients and the SSAO kernel, radius and bias.  They are fixed by
+definition here and in the renderer.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "vtx_oracle.c")
+_SO = os.path.join(_HERE, "_vtx_oracle.so")
+
+CFLAGS = ["-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+
+FLAG_TIE, FLAG_GRAZE, FLAG_NEAR, FLAG_SPLIT = 1, 2, 4, 16
+FLAG_GRID, FLAG_MARGIN, FLAG_FETCH = 32, 64, 128
+FLAG_CUTOFF, FLAG_ORDER, FLAG_STOP, FLAG_CLAMP = 256, 512, 1024, 2048
+ID_FLAGS = FLAG_TIE | FLAG_GRAZE | FLAG_NEAR
+NO_ID = 0xFFFFFFFF
+
+TIE_TOL = 1e-4      # A: pixels whose two nearest depths differ by less are id-ambiguous
+GRAZE_TOL = 1e-6    # A: distance to a silhouette/rim/near-plane decision
+GRID_TOL = 1e-3     # px: SSAO sample distance to a pixel-grid line
+MARGIN_TOL = 1e-4   # A: SSAO occlusion-test margin
+
+SHADE_DEFAULTS = dict(ka=0.2, kd=0.7, ks=0.3, shininess=32.0,
+                      light_dir=(0.25, 0.5, 1.0), background=(1.0, 1.0, 1.0))
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle library next to its source (gcc, no GPU needed)."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + ".%d.tmp" % os.getpid()
+        subprocess.check_call(["gcc", *CFLAGS, _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_SO)
+        P = ctypes.c_void_p
+        i64, i32, f32, f64 = ctypes.c_int64, ctypes.c_int32, ctypes.c_float, ctypes.c_double
+        L.orc_hits.argtypes = [P, i64, P, i64, i32, f32, f32, P, P, i64, f64, f64, P, P, P, P, P, P, i32]
+        L.orc_hits.restype = i32
+        L.orc_shade.argtypes = [P, P, i64, P, P, P, i64, P, P, P, P, f64, f64, f64, f64, P, P]
+        L.orc_ssao_project.argtypes = [P, P, i64, P, P, P, P, i32, f64, f64, P, P, P]
+        L.orc_ssao_resolve.argtypes = [i64, i32, P, P, P, P, P, f64, f64, f64, P, P]
+        L.orc_soft_forward.argtypes = [P, i64, P, f64, P, i64, f64, P, P, P, P, P, P, i32]
+        L.orc_soft_vjp.argtypes = [P, i64, P, f64, P, i64, P, P, P, P, i32]
+        _lib = L
+    return _lib
+
+
+def _p(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _cam(cam) -> np.ndarray:
+    rec = cam.record() if hasattr(cam, "record") else np.asarray(cam)
+    return np.array(rec).reshape(1)
+
+
+def all_pixels(width: int, height: int) -> np.ndarray:
+    ys, xs = np.mgrid[0:height, 0:width]
+    return np.ascontiguousarray(np.stack([xs.ravel(), ys.ravel()], axis=1).astype(np.int32))
+
+
+@dataclass
+class Hits:
+    pix: np.ndarray
+    depth: np.ndarray
+    id: np.ndarray
+    normal: np.ndarray
+    gap: np.ndarray
+    flags: np.ndarray
+    side: np.ndarray
+    rgb: Optional[np.ndarray] = None
+    ao: Optional[np.ndarray] = None
+    rgb_final: Optional[np.ndarray] = None
+
+
+def hits(xyzr, cam, pix, bonds=None, mode=0, ball_radius=0.4, bond_radius=0.15,
+         tie_tol=TIE_TOL, graze_tol=GRAZE_TOL, threads=0) -> Hits:
+    """Nearest hit per listed pixel by brute force over all primitives (FP64)."""
+    xyzr = np.ascontiguousarray(xyzr, dtype=np.float32)
+    pix = np.ascontiguousarray(pix, dtype=np.int32).reshape(-1, 2)
+    nb = 0 if bonds is None else int(bonds.shape[0])
+    b = None if bonds is None else np.ascontiguousarray(bonds, dtype=np.uint32)
+    P = pix.shape[0]
+    out = Hits(pix=pix, depth=np.empty(P), id=np.empty(P, np.uint32), normal=np.empty((P, 3)),
+               gap=np.empty(P), flags=np.empty(P, np.int32), side=np.empty(P, np.int32))
+    c = _cam(cam)
+    lib().orc_hits(_p(xyzr), xyzr.shape[0], _p(b), nb, mode, ball_radius, bond_radius, _p(c), _p(pix), P,
+                   tie_tol, graze_tol, _p(out.depth), _p(out.id), _p(out.normal), _p(out.gap), _p(out.flags),
+                   _p(out.side), threads)
+    return out
+
+
+def shade(h: Hits, elem, palette, n_atoms, cam, bonds=None, **kw) -> np.ndarray:
+    s = dict(SHADE_DEFAULTS)
+    s.update(kw)
+    P = h.pix.shape[0]
+    rgb = np.empty((P, 3))
+    light = np.asarray(s["light_dir"], np.float32)
+    bg = np.asarray(s["background"], np.float32)
+    b = None if bonds is None else np.ascontiguousarray(bonds, dtype=np.uint32)
+    lib().orc_shade(_p(np.ascontiguousarray(elem, np.uint8)), _p(np.ascontiguousarray(palette, np.float32)),
+                    n_atoms, _p(b), _p(_cam(cam)), _p(h.pix), P, _p(h.id), _p(h.normal), _p(h.side), _p(light),
+                    s["ka"], s["kd"], s["ks"], s["shininess"], _p(bg), _p(rgb))
+    return rgb
+
+
+def ssao(h: Hits, xyzr, cam, kernel, radius=2.0, bias=0.025, bonds=None, mode=0, ball_radius=0.4,
+         bond_radius=0.15, grid_tol=GRID_TOL, margin_tol=MARGIN_TOL, threads=0):
+    """AO per listed pixel; flags gain GRID / MARGIN / FETCH bits.  Fetched pixels are ray-cast on demand."""
+    kernel = np.ascontiguousarray(kernel, np.float32).reshape(-1, 3)
+    ns = kernel.shape[0]
+    P = h.pix.shape[0]
+    fetch = np.empty((P, ns, 2), np.int32)
+    sdepth = np.empty((P, ns))
+    c = _cam(cam)
+    lib().orc_ssao_project(_p(c), _p(h.pix), P, _p(h.depth), _p(h.id), _p(h.normal), _p(kernel), ns, radius,
+                           grid_tol, _p(fetch), _p(sdepth), _p(h.flags))
+    W = int(c["width"][0])
+    lin = np.where(fetch[..., 0] >= 0, fetch[..., 1].astype(np.int64) * W + fetch[..., 0], -1)
+    own = h.pix[:, 1].astype(np.int64) * W + h.pix[:, 0]
+    need = np.unique(lin[lin >= 0])
+    known = dict(zip(own.tolist(), range(P)))
+    missing = np.array([q for q in need.tolist() if q not in known], dtype=np.int64)
+    zf = np.full((P, ns), np.inf)
+    famb = np.zeros((P, ns), np.int32)
+    depth_of, amb_of = {}, {}
+    for q, k in known.items():
+        depth_of[q] = h.depth[k]
+        amb_of[q] = int(h.flags[k] & ID_FLAGS)
+    if missing.size:
+        mp = np.stack([missing % W, missing // W], axis=1).astype(np.int32)
+        hm = hits(xyzr, cam, mp, bonds=bonds, mode=mode, ball_radius=ball_radius, bond_radius=bond_radius,
+                  threads=threads)
+        for k, q in enumerate(missing.tolist()):
+            depth_of[q] = hm.depth[k]
+            amb_of[q] = int(hm.flags[k] & ID_FLAGS)
+    valid = lin >= 0
+    flat = lin[valid].tolist()
+    zf[valid] = np.array([depth_of[q] for q in flat]) if flat else []
+    famb[valid] = np.array([amb_of[q] for q in flat], dtype=np.int32) if flat else []
+    ao = np.empty(P)
+    lib().orc_ssao_resolve(P, ns, _p(h.depth), _p(h.id), _p(sdepth), _p(np.ascontiguousarray(zf)),
+                           _p(np.ascontiguousarray(famb)), radius, bias, margin_tol, _p(ao), _p(h.flags))
+    return ao
+
+
+def render_pixels(scene, cam_index, pix, kernel=None, threads=0, **shade_kw) -> Hits:
+    """Hits, shading and (when ``kernel`` is given) SSAO at the listed pixels of a scene view."""
+    cam = scene.cameras[cam_index]
+    kw = dict(bonds=scene.bonds, mode=scene.mode)
+    h = hits(scene.xyzr, cam, pix, threads=threads, **kw)
+    h.rgb = shade(h, scene.elem, scene.palette, scene.xyzr.shape[0], cam, bonds=scene.bonds, **shade_kw)
+    if kernel is not None:
+        h.ao = ssao(h, scene.xyzr, cam, kernel, threads=threads, **kw)
+        h.rgb_final = h.rgb * h.ao[:, None]
+    else:
+        h.ao = np.ones(h.pix.shape[0])
+        h.rgb_final = h.rgb
+    return h
+
+
+# --------------------------------------------------------------- soft form --
+
+@dataclass
+class Soft:
+    A: np.ndarray
+    D: np.ndarray
+    N: np.ndarray
+    n_used: np.ndarray
+    T_final: np.ndarray
+    flags: np.ndarray
+
+
+def soft_forward(xyzr64, cam, pix, sigma=0.5, amb_tol=1e-6, threads=0) -> Soft:
+    x = np.ascontiguousarray(xyzr64, np.float64).reshape(-1, 4)
+    pix = np.ascontiguousarray(pix, np.int32).reshape(-1, 2)
+    P = pix.shape[0]
+    o = Soft(np.empty(P), np.empty(P), np.empty((P, 3)), np.empty(P, np.int32), np.empty(P), np.empty(P, np.int32))
+    lib().orc_soft_forward(_p(x), x.shape[0], _p(_cam(cam)), sigma, _p(pix), P, amb_tol, _p(o.A), _p(o.D),
+                           _p(o.N), _p(o.n_used), _p(o.T_final), _p(o.flags), threads)
+    return o
+
+
+def soft_vjp(xyzr64, cam, pix, gA, gD, gN, sigma=0.5, threads=0) -> np.ndarray:
+    """d/d(x,y,z,r) of sum(gA A + gD D + gN . N) over the listed pixels (FP64, analytic)."""
+    x = np.ascontiguousarray(xyzr64, np.float64).reshape(-1, 4)
+    pix = np.ascontiguousarray(pix, np.int32).reshape(-1, 2)
+    P = pix.shape[0]
+    grad = np.zeros((x.shape[0], 4))
+    lib().orc_soft_vjp(_p(x), x.shape[0], _p(_cam(cam)), sigma, _p(pix), P,
+                       _p(np.ascontiguousarray(gA, np.float64)), _p(np.ascontiguousarray(gD, np.float64)),
+                       _p(np.ascontiguousarray(gN, np.float64).reshape(-1, 3)), _p(grad), threads)
+    return grad
