@@ -1,0 +1,393 @@
+#!/usr/bin/env python3
+"""Benchmark of the meshless ray-caster on the whole-cell-scale frame.
+
+Workload (default, "cell4k"): 100,000,000 atoms (20,000 protein-like blobs in
+a 12,000 A cube), 3840x2160, van der Waals spheres, Blinn-Phong, 16-sample
+SSAO, overview camera 36,000 A away.  One step = one full frame: cull,
+precise setup + direct splat, tile binning, tile ray-cast, resolve, shading,
+SSAO.  Inputs (1.6 GB of atom records) are larger than L2, so no flush is
+needed between steps.
+
+Also measured in the same run (keys under "extra", skipped with --no-extra):
+the batched trajectory (500,000 atoms x 256 frames x 4 views at 1280x720,
+one graph launch) against the plain per-frame loop, and the soft-edge
+renderer's forward+backward time (20,000 atoms, 16 views at 512x512).
+
+--impl reference times the CPU FP64 oracle (the only reference there is) on
+a bounded sample of the same frame on the host cores.
+
+Prints ONE JSON line (rank 0).  Multi-GPU runs are replicas: every rank
+renders the same frame (weak scaling), value = frames of all ranks / time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+KERNELS_PER_FRAME = 10  # init, cull, finalize, setup, scan x3, scatter, raster, resolve
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="vtx", choices=["vtx", "reference"])
+    ap.add_argument("--no-extra", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--clusters", type=int, default=20000, help="blobs of 5,000 atoms (20,000 = 1e8 atoms)")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while active."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def oracle_baseline(scene, kernel, cam_index, target_s, max_pixels=4096):
+    """Time the oracle on a bounded random pixel sample of the frame; frames/s extrapolated to W*H pixels."""
+    import oracle
+    cam = scene.cameras[cam_index]
+    W, H = cam.width, cam.height
+    rng = np.random.default_rng(99)
+    threads = os.cpu_count() or 1
+    n = 8
+    while True:
+        pix = np.stack([rng.integers(0, W, n), rng.integers(0, H, n)], 1).astype(np.int32)
+        t0 = time.perf_counter()
+        oracle.render_pixels(scene, cam_index, pix, kernel=kernel, threads=threads)
+        dt = time.perf_counter() - t0
+        if dt >= 0.5 * target_s or n >= max_pixels:
+            break
+        n = int(min(max_pixels, max(2 * n, n * target_s / max(dt, 1e-3))))
+    per_pixel = dt / n
+    fps = 1.0 / (per_pixel * W * H)
+    return {"value": fps, "unit": "frames/s", "cores": threads, "kind": "oracle",
+            "sample": "%d random pixels of the %dx%d frame, brute force over all %d atoms incl. SSAO fetches, "
+                      "%.1f s; frames/s extrapolated to %d pixels" % (n, W, H, scene.xyzr.shape[0], dt, W * H),
+            "seconds": dt}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    from paper_2501_12750_gb300 import scenes
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        s = scenes.config3(n_clusters=args.clusters)
+        k = scenes.ssao_kernel()
+        # each step is one bounded sample of the same frame
+        vals = []
+        cb = None
+        for i in range(max(1, args.warmup // 5) + args.steps):
+            cb = oracle_baseline(s, k, 0, max(1.0, args.cpu_seconds / max(1, args.steps)), max_pixels=512)
+            if i >= max(1, args.warmup // 5):
+                vals.append(cb["value"])
+        v = float(np.median(vals))
+        cb["value"] = v
+        line = {"impl": "reference", "metric": "frames/s", "value": v, "unit": "frames/s", "n_gpus": 1,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "cell4k: 1e8-atom whole-cell stand-in, 3840x2160, vdW + SSAO16, view V1",
+                           "atoms": int(s.xyzr.shape[0]), "width": 3840, "height": 2160},
+                "cpu_baseline": cb, "e2e": {"value": v, "unit": "frames/s", "h2d_bytes_per_step": 0,
+                                            "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    import paper_2501_12750_gb300 as vtx
+
+    t_gen = time.time()
+    s = scenes.config3(n_clusters=args.clusters)
+    gen_s = time.time() - t_gen
+    cam = s.cameras[0]
+    W, H = cam.width, cam.height
+    N = s.xyzr.shape[0]
+    k = scenes.ssao_kernel()
+    r = vtx.Renderer(dev.index)
+    xyzr = torch.from_numpy(s.xyzr).to(dev)
+    elem = torch.from_numpy(s.elem).to(dev)
+    r.upload_atoms(xyzr, elem, s.palette)
+    r.set_camera(cam)
+    out = r.alloc_outputs(W, H)
+    warm = vtx.default_settings(ssao_kernel=k, flags=vtx.FLAG_SYNC)
+    timed = vtx.default_settings(ssao_kernel=k, flags=vtx.FLAG_PROFILE)
+    for _ in range(max(3, args.warmup)):
+        r.render_frame(warm, out=out)
+    r.sync_status()
+    try:
+        r.stage_times()
+    except vtx.VtxError:
+        pass
+    stream = r.stream
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(dev.index if world == 1 else local)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        r.render_frame(timed, out=out)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    stages = r.stage_times()
+    r.sync_status()  # raises on a capacity overflow inside the timed region
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    ms_per_step = elapsed_ms / args.steps
+    fps = world * args.steps / (elapsed_ms / 1e3)
+
+    peak, peak_kind = measured_peaks()
+    cull_ms = stages["cull"]
+    alg_bytes = 16.0 * N
+    achieved = alg_bytes / (cull_ms * 1e-3) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        try:
+            tj = json.load(open(prof))
+            if tj.get("kernel") == "k_cull_atoms" and tj.get("atoms") == N:
+                traffic = tj.get("bytes_per_launch")
+        except (OSError, ValueError):
+            traffic = None
+
+    # end to end through the host-buffer entry point (copies inside the timed region)
+    host_x = torch.from_numpy(s.xyzr).pin_memory()
+    host_e = torch.from_numpy(s.elem).pin_memory()
+    ho = {"depth": torch.empty((H, W), dtype=torch.float32).pin_memory(),
+          "id": torch.empty((H, W), dtype=torch.int32).pin_memory(),
+          "normal": torch.empty((3, H, W), dtype=torch.float32).pin_memory(),
+          "rgb": torch.empty((3, H, W), dtype=torch.float32).pin_memory(),
+          "ao": torch.empty((H, W), dtype=torch.float32).pin_memory()}
+    hon = {kk: v.numpy() for kk, v in ho.items()}
+    he = vtx.default_settings(ssao_kernel=k)
+    r.render_frame_host(host_x.numpy(), host_e.numpy(), cam, he, hon, s.palette)
+    n_e2e = max(2, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        r.render_frame_host(host_x.numpy(), host_e.numpy(), cam, he, hon, s.palette)
+    e2e_s = (time.perf_counter() - t0) / n_e2e
+    h2d = 17 * N
+    d2h = 4 * 9 * W * H
+
+    extra = {}
+    if not args.no_extra:
+        extra = run_extras(vtx, torch, dev, r)
+
+    cpu = None
+    if rank == 0 and world == 1:
+        cpu = oracle_baseline(s, k, 0, args.cpu_seconds)
+
+    line = {
+        "metric": "frames/s", "value": fps, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "cell4k: 1e8-atom whole-cell stand-in (20,000 protein-like blobs in a 12,000 A cube), "
+                               "3840x2160, vdW spheres + Blinn-Phong + SSAO16, view V1 at 36,000 A",
+                   "atoms": int(N), "width": W, "height": H, "l2": "inputs (1.6 GB) larger than L2; no flush",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "gatoms_per_s": fps * N / 1e9,
+        "roofline": {"bound": "hbm", "kernel": "k_cull_atoms", "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": cull_ms},
+        "stages_ms": {kk: v for kk, v in stages.items() if kk != "runs"},
+        "e2e": {"value": 1.0 / e2e_s, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "api": "vtx_render_frame_host (pinned host buffers)"},
+        "gpu_launches": KERNELS_PER_FRAME * args.steps,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+        "gen_seconds": gen_s,
+        "extra": extra,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    r.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_extras(vtx, torch, dev, r):
+    from paper_2501_12750_gb300 import scenes
+    res = {}
+    # batched trajectory: 256 frames x 4 views, one graph launch, against the per-frame loop
+    s4 = scenes.config4()
+    frames = torch.from_numpy(s4.frames).to(dev)
+    F, N4 = s4.frames.shape[0], s4.frames.shape[1]
+    cams = s4.cameras
+    k = scenes.ssao_kernel()
+    st = vtx.default_settings(ssao_kernel=k)
+    out = r.alloc_outputs(cams[0].width, cams[0].height, F * len(cams))
+    elem = torch.from_numpy(s4.elem).to(dev)
+    r.upload_atoms(frames[0], elem, s4.palette)
+    counts = [N4] * F
+    r.render_batch(frames, counts, cams, vtx.default_settings(ssao_kernel=k, flags=vtx.FLAG_SYNC), out=out)
+    r.render_batch(frames, counts, cams, st, out=out, use_graph=True)
+    torch.cuda.synchronize()
+    reps = 3
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(r.stream)
+    for _ in range(reps):
+        r.render_batch(frames, counts, cams, st, out=out, use_graph=True)
+    e1.record(r.stream)
+    torch.cuda.synchronize()
+    r.sync_status()
+    batch_ms = e0.elapsed_time(e1) / reps
+    # plain per-frame loop on the same images (one render_frame per image)
+    single = r.alloc_outputs(cams[0].width, cams[0].height)
+    loop_frames = 32
+    for f in range(2):
+        r.upload_atoms(frames[f], elem, s4.palette)
+        r.set_camera(cams[0])
+        r.render_frame(vtx.default_settings(ssao_kernel=k, flags=vtx.FLAG_SYNC), out=single)
+    torch.cuda.synchronize()
+    e0.record(r.stream)
+    for f in range(loop_frames):
+        r.upload_atoms(frames[f], elem, s4.palette)
+        for c in cams:
+            r.set_camera(c)
+            r.render_frame(st, out=single)
+    e1.record(r.stream)
+    torch.cuda.synchronize()
+    loop_ms = e0.elapsed_time(e1) / (loop_frames * len(cams))
+    res["batched_traj"] = {"workload": "500,000 atoms x 256 frames x 4 views, 1280x720, SSAO16",
+                           "images_per_s": F * len(cams) / (batch_ms / 1e3), "batch_ms": batch_ms,
+                           "per_frame_loop_images_per_s": 1e3 / loop_ms, "graph": True}
+    del out, frames
+    torch.cuda.empty_cache()
+    # soft forward + backward
+    s5 = scenes.config5()
+    x = torch.from_numpy(s5.xyzr).to(dev)
+    tgt = torch.from_numpy(s5.extra["target"]).to(dev)
+    with torch.no_grad():
+        A_t, D_t, N_t = r.render_soft_fwd(tgt, s5.cameras)
+    for _ in range(2):
+        A, D, Nn = r.render_soft_fwd(x, s5.cameras)
+        gA, gD, gN = 2 * (A - A_t), 0.2 * (D - D_t), 2 * (Nn - N_t)
+        r.render_soft_bwd(x, s5.cameras, gA, gD, gN)
+    torch.cuda.synchronize()
+    reps = 5
+    e0.record(r.stream)
+    for _ in range(reps):
+        A, D, Nn = r.render_soft_fwd(x, s5.cameras)
+    e1.record(r.stream)
+    torch.cuda.synchronize()
+    fwd_ms = e0.elapsed_time(e1) / reps
+    e0.record(r.stream)
+    for _ in range(reps):
+        r.render_soft_bwd(x, s5.cameras, gA, gD, gN)
+    e1.record(r.stream)
+    torch.cuda.synchronize()
+    bwd_ms = e0.elapsed_time(e1) / reps
+    # hard renderer on the same 16 views
+    r.upload_atoms(x, torch.from_numpy(s5.elem).to(dev), s5.palette)
+    hs = vtx.default_settings()
+    ho = r.alloc_outputs(512, 512)
+    for c in s5.cameras[:2]:
+        r.set_camera(c)
+        r.render_frame(vtx.default_settings(flags=vtx.FLAG_SYNC), out=ho)
+    torch.cuda.synchronize()
+    e0.record(r.stream)
+    for c in s5.cameras:
+        r.set_camera(c)
+        r.render_frame(hs, out=ho)
+    e1.record(r.stream)
+    torch.cuda.synchronize()
+    hard_ms = e0.elapsed_time(e1)
+    res["soft"] = {"workload": "20,000 atoms, 16 views at 512x512, sigma 0.5 px", "fwd_ms": fwd_ms,
+                   "bwd_ms": bwd_ms, "fwd_bwd_ms": fwd_ms + bwd_ms, "hard_16_views_ms": hard_ms,
+                   "note": "fwd and bwd each rebuild their tile lists (cull, setup, scan, scatter)"}
+    return res
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,248 @@
+/*
+ * vtx.h -- C ABI of the GB300 meshless molecular ray-caster.
+ *
+ * The paper (VTX, Methods: "Meshless Representations", "High Quality
+ * Rendering") draws a molecule -- atom positions, radii and connectivity --
+ * without triangle meshes: every primitive (a van der Waals sphere, or the
+ * spheres and bond cylinders of ball-and-stick) is ray-cast against its
+ * implicit surface so that each pixel shows the nearest hit, and lighting is
+ * deferred: shading and screen-space ambient occlusion run on the per-pixel
+ * hit record.  This library computes that per-frame path on one GPU with
+ * hand-written CUDA kernels for sm_103a:
+ *
+ *   cull -> precise setup / direct splat -> tile binning + per-tile depth
+ *   sort -> tile ray-cast -> resolve (depth, id, normal) -> Blinn-Phong
+ *   shading -> SSAO,
+ *
+ * plus a batched form for molecular-dynamics trajectories (many frames x
+ * views per call, optionally replayed as one CUDA graph) and a soft-edge
+ * differentiable form with a hand-written backward pass.
+ *
+ * Conventions (shared by every entry point):
+ *   - Atoms are float4 records (x, y, z, r) in Angstrom, world space.
+ *   - Camera: float32 eye and basis used exactly as passed (not
+ *     re-normalised).  Pixel (px, py), row 0 at the TOP, has its ray through
+ *     the pixel centre: slope a = (px + 0.5 - W/2)/f, b = (H/2 - py - 0.5)/f
+ *     with f = H / (2 tan_half_fovy).  Depth is the distance along the
+ *     forward axis; a hit is accepted only when its entry point lies at or
+ *     beyond znear (an entry point in front of znear skips the primitive).
+ *   - Normals are reported in the right-handed view frame (x right, y up,
+ *     z toward the viewer).
+ *   - Output planes are caller-owned DEVICE buffers laid out [H][W]
+ *     (normal and rgb: [3][H][W], one plane per component).
+ *   - Background pixels: depth +inf, id 0xFFFFFFFF, normal 0, rgb =
+ *     settings.background, ao 1.
+ *   - Primitive ids: atoms 0..n_atoms-1; bond b (ball-and-stick) is
+ *     n_atoms + b.  Equal depths resolve to the smaller id.
+ *
+ * Ownership and asynchrony: device pointers given to vtx_upload_* are
+ * recorded, not copied; the caller keeps them alive and unchanged until the
+ * next upload or vtx_destroy.  Every render call only enqueues work on the
+ * context's stream and returns; results are ready after the caller
+ * synchronises that stream.  The context owns and grows its scratch memory.
+ *
+ * Errors: every call returns a vtx_status; vtx_last_error() gives the text
+ * of the most recent failure.  Argument errors are detected on the host
+ * before anything is enqueued.  Capacity overflows of the scratch arena are
+ * detected on the device (the kernels stop writing past a capacity and
+ * record the size they needed); the next vtx_sync_status() (or a render
+ * call with VTX_FLAG_SYNC) reports VTX_ERR_CAPACITY once and grows the arena
+ * so that re-rendering succeeds.  No kernel in this library waits on another
+ * block, so no device-side wait can hang.
+ */
+#ifndef VTX_H_
+#define VTX_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vtx_ctx vtx_ctx;
+
+typedef enum {
+  VTX_OK = 0,
+  VTX_ERR_INVALID_ARG = 1, /* a null pointer, a size out of range, an unsupported mode */
+  VTX_ERR_CUDA = 2,        /* a CUDA runtime call failed (text in vtx_last_error) */
+  VTX_ERR_OOM = 3,         /* device allocation of scratch memory failed */
+  VTX_ERR_CAPACITY = 4,    /* a previous frame overflowed the scratch arena (now grown: render again) */
+  VTX_ERR_TIMEOUT = 5,     /* reserved: no entry point of this version waits on the device */
+  VTX_ERR_BOUNDS = 6,      /* a device-side bounds check failed (debug builds) */
+  VTX_ERR_STATE = 7        /* call order: no atoms uploaded, no camera set */
+} vtx_status;
+
+enum {
+  VTX_MODE_VDW = 0,            /* spheres of radius xyzr.w */
+  VTX_MODE_BALL_AND_STICK = 1  /* spheres of radius ball_radius + bond cylinders of radius bond_radius */
+};
+
+enum {
+  VTX_FLAG_SYNC = 1u,     /* synchronise at the end of the call and report device-side errors */
+  VTX_FLAG_PROFILE = 2u,  /* record per-stage CUDA events (read with vtx_stage_times) */
+  VTX_FLAG_NO_SSAO = 4u   /* skip ambient occlusion even if ssao_samples > 0 */
+};
+
+/* Pinhole camera, 64 bytes.  forward/right/up: the view basis (float32 as passed). */
+typedef struct {
+  float eye[3];
+  float forward[3];
+  float right[3];
+  float up[3];
+  float tan_half_fovy; /* tan of half the VERTICAL field of view */
+  float znear;         /* near plane depth, > 0 */
+  int32_t width;       /* pixels, 1..16384 */
+  int32_t height;      /* pixels, 1..16384 */
+} vtx_camera;
+
+#define VTX_MAX_SSAO_SAMPLES 64
+#define VTX_MAX_ELEMENTS 32
+#define VTX_MAX_VIEWS 16
+
+/*
+ * Rendering settings.  vtx_default_settings() fills the values used by the
+ * tests: Blinn-Phong ka 0.2, kd 0.7, ks 0.3, shininess 32, light (0.25, 0.5, 1)
+ * in view space, white background, no SSAO, 16x16 tiles, direct splat up to
+ * 16 candidate pixels.  The paper names the techniques (glossy shading,
+ * screen-space ambient occlusion) but not these constants.
+ */
+typedef struct {
+  int32_t mode;          /* VTX_MODE_* */
+  float ball_radius;     /* ball-and-stick sphere radius (A) */
+  float bond_radius;     /* ball-and-stick cylinder radius (A) */
+  float ka, kd, ks, shininess;
+  float light_dir[3];    /* view space; normalised by the library */
+  float background[3];
+  int32_t ssao_samples;  /* 0 = off, else 1..VTX_MAX_SSAO_SAMPLES */
+  float ssao_radius;     /* A */
+  float ssao_bias;       /* A */
+  float ssao_kernel[VTX_MAX_SSAO_SAMPLES][3]; /* hemisphere offsets (unit-ball scale), z along the normal */
+  int32_t tile_w, tile_h; /* 0 = library default; supported: 16x16, 32x8, 8x8 */
+  int32_t splat_max_px;  /* primitives whose candidate pixel box is <= this are splatted directly (0 = default) */
+  uint32_t flags;        /* VTX_FLAG_* */
+} vtx_settings;
+
+/* Output planes (device pointers, caller-owned).  ao may be NULL. */
+typedef struct {
+  float *depth;     /* [H][W] depth of the visible hit, +inf for background */
+  uint32_t *id;     /* [H][W] primitive id, 0xFFFFFFFF for background */
+  float *normal;    /* [3][H][W] unit normal, right-handed view frame */
+  float *rgb;       /* [3][H][W] shaded colour times ambient occlusion, in [0,1] */
+  float *ao;        /* [H][W] ambient occlusion factor in [0,1] (1 when SSAO is off) */
+} vtx_outputs;
+
+/* Version string of the library. */
+const char *vtx_version(void);
+
+/* Fill *s with the defaults listed above. */
+vtx_status vtx_default_settings(vtx_settings *s);
+
+/*
+ * Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * owned by the caller (NULL = the legacy default stream).  Allocates only a
+ * few small host-pinned and device buffers; scratch grows on first use.
+ */
+vtx_status vtx_create(vtx_ctx **out, int32_t device, void *cuda_stream);
+vtx_status vtx_destroy(vtx_ctx *ctx);
+vtx_status vtx_set_stream(vtx_ctx *ctx, void *cuda_stream);
+
+/*
+ * Record the atom set (the molecule of the paper's Methods: positions, radii).
+ * xyzr: device float4 [n_atoms]; elem: device uint8 [n_atoms] element index
+ * (< n_elem), may be NULL (element 0); palette_rgb: HOST float [n_elem][3]
+ * element colours (copied).  n_atoms in 0..2^31-1, n_elem in 1..32.
+ */
+vtx_status vtx_upload_atoms(vtx_ctx *ctx, const float *xyzr, const uint8_t *elem, const float *palette_rgb,
+                            int32_t n_elem, int64_t n_atoms);
+
+/*
+ * Record the connectivity (the paper's "connectivity"; drawn as capped
+ * cylinders in ball-and-stick).  pairs: device uint32 [n_bonds][2], i < j <
+ * n_atoms, endpoints at least 1e-3 A apart.  n_bonds = 0 clears them.
+ */
+vtx_status vtx_upload_bonds(vtx_ctx *ctx, const uint32_t *pairs, int64_t n_bonds);
+
+/* Set the camera for vtx_render_frame (copied). */
+vtx_status vtx_set_camera(vtx_ctx *ctx, const vtx_camera *cam);
+
+/*
+ * Render one frame of the recorded atoms from the current camera: the
+ * nearest hit per pixel (ids exact), its depth and normal, Blinn-Phong
+ * shading and, when settings->ssao_samples > 0, SSAO.  Enqueued on the
+ * context's stream.
+ */
+vtx_status vtx_render_frame(vtx_ctx *ctx, const vtx_settings *s, const vtx_outputs *out);
+
+/*
+ * Same as vtx_render_frame, with HOST inputs and outputs: copies xyzr and
+ * elem (host, pinned recommended) to context-owned device memory, renders,
+ * and copies every output plane back into host buffers (same layout as
+ * vtx_outputs).  Synchronises before returning.  Used to measure end to end
+ * throughput including host<->device traffic.
+ */
+vtx_status vtx_render_frame_host(vtx_ctx *ctx, const float *xyzr_host, const uint8_t *elem_host,
+                                 const float *palette_rgb, int32_t n_elem, int64_t n_atoms,
+                                 const vtx_camera *cam, const vtx_settings *s, const vtx_outputs *out_host);
+
+/*
+ * Batched trajectory rendering (the paper: trajectories re-rendered every
+ * frame, ambient occlusion included).  frames_xyzr: device float4
+ * [n_frames][frame_stride] (frame f uses its first atom_counts[f] records);
+ * atom_counts: HOST int64 [n_frames], uneven allowed, each <= frame_stride;
+ * the element array of vtx_upload_atoms is indexed by atom (must cover
+ * frame_stride atoms, or be NULL).  cams: HOST [n_views] cameras, all with
+ * the same width and height, n_views <= VTX_MAX_VIEWS.  out: ONE vtx_outputs
+ * whose planes hold n_frames*n_views images back to back, image index
+ * f*n_views + v (plane stride H*W, normal/rgb 3*H*W per image).
+ * VTX_MODE_VDW only.  use_graph != 0 captures the whole batch into a CUDA
+ * graph on first use and replays it on later calls with identical
+ * arguments (one cudaGraphLaunch per call).
+ */
+vtx_status vtx_render_batch(vtx_ctx *ctx, const float *frames_xyzr, int64_t frame_stride,
+                            const int64_t *atom_counts, int32_t n_frames, const vtx_camera *cams,
+                            int32_t n_views, const vtx_settings *s, const vtx_outputs *out, int32_t use_graph);
+
+/*
+ * Soft-edge (differentiable) renderer, forward.  Per pixel, over the spheres
+ * whose signed pixel distance to the silhouette is >= -4 px, ordered by
+ * centre depth (ties: smaller id), front-to-back composite of
+ * alpha = min(0.99, sigmoid(delta_px / sigma_px)), stopping once the
+ * transmittance falls below 1e-4.  Outputs per view v: coverage [V][H][W],
+ * depth [V][H][W] (sum of w_i t_i), normal [V][3][H][W] (sum of w_i n_i, view
+ * frame).  xyzr: device float4 [n]; cams: HOST [n_views], equal sizes.
+ */
+vtx_status vtx_render_soft_fwd(vtx_ctx *ctx, const float *xyzr, int64_t n, const vtx_camera *cams,
+                               int32_t n_views, float sigma_px, float *cov, float *depth, float *normal);
+
+/*
+ * Soft-edge renderer, backward: grad_xyzr (device float4 [n], OVERWRITTEN)
+ * = d/d(x,y,z,r) of sum over views and pixels of
+ *   g_cov*cov + g_depth*depth + g_normal . normal.
+ * Tile lists are rebuilt (not stored by the forward call).  Gradient
+ * planes have the layout of the forward outputs; any may be NULL (zero).
+ */
+vtx_status vtx_render_soft_bwd(vtx_ctx *ctx, const float *xyzr, int64_t n, const vtx_camera *cams,
+                               int32_t n_views, float sigma_px, const float *g_cov, const float *g_depth,
+                               const float *g_normal, float *grad_xyzr);
+
+/* Synchronise the context's stream and report (once) any device-side error. */
+vtx_status vtx_sync_status(vtx_ctx *ctx);
+
+/*
+ * Per-stage GPU times (ms), averaged over every pipeline run made with
+ * VTX_FLAG_PROFILE since the previous call, measured with CUDA events
+ * recorded on the context's stream between the stages (clear, cull, setup,
+ * scan, scatter, raster, resolve).  names/ms: arrays of *n entries (in:
+ * capacity; out: stages written); *runs (may be NULL) receives the number of
+ * runs averaged.  Waits for the last profiled run, then forgets the runs.
+ */
+vtx_status vtx_stage_times(vtx_ctx *ctx, const char **names, float *ms, int32_t *n, int32_t *runs);
+
+/* Text of the most recent error on this context ("" if none). */
+const char *vtx_last_error(const vtx_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VTX_H_ */

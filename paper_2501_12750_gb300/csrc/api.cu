@@ -1,0 +1,765 @@
+// api.cu -- C ABI of the renderer (declared in include/vtx.h): context,
+// scratch arena, argument checks, per-frame / batched / soft entry points,
+// CUDA-graph capture of batches and per-stage CUDA-event profiling.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/vtx.h"
+#include "vtx_internal.h"
+
+using namespace vtx;
+
+namespace {
+
+struct Buf {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+
+struct GraphEntry {
+  std::vector<unsigned char> key;
+  cudaGraphExec_t exec = nullptr;
+  long long *d_counts = nullptr;
+};
+
+const char *kStageNames[7] = {"clear", "cull", "setup", "scan", "scatter", "raster", "resolve"};
+
+}  // namespace
+
+struct vtx_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  // scene
+  const float4 *xyzr = nullptr;
+  const uint8_t *elem = nullptr;
+  long long n_atoms = 0;
+  float palette[kMaxElem][3];
+  int n_elem = 1;
+  const uint2 *bonds = nullptr;
+  long long n_bonds = 0;
+  vtx_camera cam;
+  bool has_cam = false;
+  // scratch
+  Buf keys, surv, state, tcount, tstart, tcursor, bsums, recs, recimg, recof, entries, status, counts, hostin_x,
+      hostin_e, hostout;
+  uint32_t cap_rec = 0;
+  unsigned long long cap_entries = 0;
+  Status *h_status = nullptr;
+  long long *h_counts = nullptr;
+  int h_counts_cap = 0;
+  cudaEvent_t counts_done = nullptr;
+  // profiling: one set of 8 events per profiled pipeline run since the last read
+  std::vector<cudaEvent_t *> ev_sets;
+  size_t ev_used = 0;
+  // graphs
+  std::vector<GraphEntry> graphs;
+  std::string err;
+};
+
+static vtx_status fail(vtx_ctx *c, vtx_status s, const std::string &msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+static vtx_status cuda_fail(vtx_ctx *c, cudaError_t e, const char *where) {
+  return fail(c, VTX_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+static vtx_status ensure(vtx_ctx *c, Buf &b, size_t bytes, const char *what) {
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return VTX_OK;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  size_t want = bytes + bytes / 8;
+  cudaError_t e = cudaMalloc(&b.p, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      b.p = nullptr;
+      return fail(c, VTX_ERR_OOM, std::string("cudaMalloc failed for ") + what);
+    }
+    want = bytes;
+  }
+  b.bytes = want;
+  return VTX_OK;
+}
+
+static void drop_graphs(vtx_ctx *c) {
+  for (auto &g : c->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.d_counts) cudaFree(g.d_counts);
+  }
+  c->graphs.clear();
+}
+
+static ViewParams make_view(const vtx_camera &cam) {
+  ViewParams v;
+  for (int k = 0; k < 3; ++k) {
+    v.eye[k] = cam.eye[k];
+    v.R[k] = cam.right[k];
+    v.U[k] = cam.up[k];
+    v.F[k] = cam.forward[k];
+  }
+  double f = (double)cam.height / (2.0 * (double)cam.tan_half_fovy);
+  v.f_hi = (float)f;
+  v.f_lo = (float)(f - (double)v.f_hi);
+  v.f = v.f_hi;
+  v.inv_f = (float)(1.0 / f);
+  v.cx = 0.5f * (float)cam.width;
+  v.cy = 0.5f * (float)cam.height;
+  v.znear = cam.znear;
+  v.pad0 = 0.0f;
+  return v;
+}
+
+static bool cam_ok(const vtx_camera *c) {
+  if (!c) return false;
+  if (c->width < 1 || c->height < 1 || c->width > 16384 || c->height > 16384) return false;
+  if (!(c->tan_half_fovy > 0.0f) || !std::isfinite(c->tan_half_fovy)) return false;
+  if (!(c->znear > 0.0f) || !std::isfinite(c->znear)) return false;
+  for (int k = 0; k < 3; ++k)
+    if (!std::isfinite(c->eye[k]) || !std::isfinite(c->forward[k]) || !std::isfinite(c->right[k]) ||
+        !std::isfinite(c->up[k]))
+      return false;
+  return true;
+}
+
+static vtx_status settings_ok(vtx_ctx *c, const vtx_settings *s) {
+  if (!s) return fail(c, VTX_ERR_INVALID_ARG, "settings is NULL");
+  if (s->mode != VTX_MODE_VDW && s->mode != VTX_MODE_BALL_AND_STICK) return fail(c, VTX_ERR_INVALID_ARG, "bad mode");
+  if (s->ssao_samples < 0 || s->ssao_samples > VTX_MAX_SSAO_SAMPLES)
+    return fail(c, VTX_ERR_INVALID_ARG, "ssao_samples out of range");
+  int tw = s->tile_w ? s->tile_w : 16, th = s->tile_h ? s->tile_h : 16;
+  if (!((tw == 16 && th == 16) || (tw == 32 && th == 8) || (tw == 8 && th == 8)))
+    return fail(c, VTX_ERR_INVALID_ARG, "unsupported tile size");
+  if (s->splat_max_px < 0) return fail(c, VTX_ERR_INVALID_ARG, "splat_max_px < 0");
+  if (s->mode == VTX_MODE_BALL_AND_STICK && (!(s->ball_radius >= 0.0f) || !(s->bond_radius > 0.0f)))
+    return fail(c, VTX_ERR_INVALID_ARG, "ball-and-stick radii");
+  return VTX_OK;
+}
+
+static ShadeParams make_shade(const vtx_ctx *c, const vtx_settings *s) {
+  ShadeParams sh;
+  memset(&sh, 0, sizeof(sh));
+  sh.ka = s->ka;
+  sh.kd = s->kd;
+  sh.ks = s->ks;
+  sh.shin = s->shininess;
+  double L[3] = {s->light_dir[0], s->light_dir[1], s->light_dir[2]};
+  double ln = std::sqrt(L[0] * L[0] + L[1] * L[1] + L[2] * L[2]);
+  if (!(ln > 0.0)) ln = 1.0;
+  for (int k = 0; k < 3; ++k) {
+    sh.L[k] = (float)(L[k] / ln);
+    sh.bg[k] = s->background[k];
+  }
+  for (int e = 0; e < kMaxElem; ++e)
+    for (int k = 0; k < 3; ++k) sh.palette[e][k] = c->palette[e][k];
+  sh.n_elem = c->n_elem;
+  sh.ssao_n = (s->flags & VTX_FLAG_NO_SSAO) ? 0 : s->ssao_samples;
+  sh.ssao_radius = s->ssao_radius;
+  sh.ssao_bias = s->ssao_bias;
+  for (int j = 0; j < VTX_MAX_SSAO_SAMPLES; ++j)
+    for (int k = 0; k < 3; ++k) sh.kernel[j][k] = s->ssao_kernel[j][k];
+  return sh;
+}
+
+static void base_geometry(Geometry &g, const vtx_camera *cams, int n_views, int tile_w, int tile_h) {
+  memset(&g, 0, sizeof(g));
+  for (int v = 0; v < n_views; ++v) g.views[v] = make_view(cams[v]);
+  g.n_views = n_views;
+  g.W = cams[0].width;
+  g.H = cams[0].height;
+  g.tile_w = tile_w;
+  g.tile_h = tile_h;
+  g.tiles_x = (g.W + tile_w - 1) / tile_w;
+  g.tiles_y = (g.H + tile_h - 1) / tile_h;
+  g.tiles_per_img = g.tiles_x * g.tiles_y;
+  g.pix_per_img = (long long)g.W * g.H;
+}
+
+// Size the arena for a launch; records/entries grow only through overflow reports.
+static vtx_status prepare(vtx_ctx *c, const Geometry &g, bool soft, long long stride_for_recof) {
+  const long long n_img = g.n_img;
+  const long long n_tiles = n_img * g.tiles_per_img;
+  vtx_status st;
+  if (!soft && (st = ensure(c, c->keys, sizeof(unsigned long long) * (size_t)(n_img * g.pix_per_img), "keys")))
+    return st;
+  if ((st = ensure(c, c->surv, sizeof(uint32_t) * (size_t)(n_img * g.surv_cap), "survivors"))) return st;
+  if ((st = ensure(c, c->state, sizeof(ImageState) * (size_t)n_img, "image state"))) return st;
+  if ((st = ensure(c, c->tcount, sizeof(uint32_t) * (size_t)(n_tiles + 1), "tile counts"))) return st;
+  if ((st = ensure(c, c->tstart, sizeof(uint32_t) * (size_t)(n_tiles + 1), "tile starts"))) return st;
+  if ((st = ensure(c, c->tcursor, sizeof(uint32_t) * (size_t)(n_tiles + 1), "tile cursors"))) return st;
+  if ((st = ensure(c, c->bsums, sizeof(unsigned long long) * (size_t)(n_tiles / 4096 + 4), "scan blocks"))) return st;
+  if (c->cap_rec == 0) {
+    long long est = n_img * g.stride / 8;
+    est = est < (1 << 16) ? (1 << 16) : (est > (1 << 22) ? (1 << 22) : est);
+    c->cap_rec = (uint32_t)est;
+    c->cap_entries = 4ull * est;
+  }
+  if ((st = ensure(c, c->recs, sizeof(PrimRec) * (size_t)c->cap_rec, "records"))) return st;
+  if ((st = ensure(c, c->recimg, sizeof(uint32_t) * (size_t)c->cap_rec, "record images"))) return st;
+  if ((st = ensure(c, c->entries, sizeof(unsigned long long) * (size_t)c->cap_entries, "entries"))) return st;
+  if (soft && (st = ensure(c, c->recof, sizeof(uint32_t) * (size_t)(n_img * stride_for_recof), "record map")))
+    return st;
+  if (!c->status.p) {
+    if ((st = ensure(c, c->status, sizeof(Status), "status"))) return st;
+    cudaMemsetAsync(c->status.p, 0, sizeof(Status), c->stream);
+  }
+  return VTX_OK;
+}
+
+static Scratch scratch_of(vtx_ctx *c) {
+  Scratch s;
+  s.keys = (unsigned long long *)c->keys.p;
+  s.surv = (uint32_t *)c->surv.p;
+  s.state = (ImageState *)c->state.p;
+  s.tile_count = (uint32_t *)c->tcount.p;
+  s.tile_start = (uint32_t *)c->tstart.p;
+  s.tile_cursor = (uint32_t *)c->tcursor.p;
+  s.block_sums = (uint32_t *)c->bsums.p;
+  s.recs = (PrimRec *)c->recs.p;
+  s.rec_img = (uint32_t *)c->recimg.p;
+  s.rec_of = (uint32_t *)c->recof.p;
+  s.entries = (unsigned long long *)c->entries.p;
+  s.status = (Status *)c->status.p;
+  s.cap_rec = c->cap_rec;
+  s.cap_entries = c->cap_entries;
+  return s;
+}
+
+// Read the device status; on overflow grow the arena and clear the flags.
+static vtx_status check_status(vtx_ctx *c) {
+  cudaError_t e = cudaMemcpyAsync(c->h_status, c->status.p, sizeof(Status), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "device error");
+  Status s = *c->h_status;
+  if (s.overflow == 0u) return VTX_OK;
+  std::string msg = "scratch capacity exceeded:";
+  if (s.overflow & 2u) {
+    unsigned long long need = (unsigned long long)s.n_rec;
+    unsigned long long cap = need + need / 2 + 1024;
+    if (cap > 0xfffffff0ull) cap = 0xfffffff0ull;
+    if (cap > c->cap_rec) c->cap_rec = (uint32_t)cap;
+    msg += " records";
+  }
+  if (s.overflow & 4u) {
+    unsigned long long need = s.n_entries;
+    unsigned long long cap = need + need / 2 + 4096;
+    if (cap > 0xfffffff0ull) cap = 0xfffffff0ull;
+    if (cap > c->cap_entries) c->cap_entries = cap;
+    msg += " tile entries";
+  }
+  if (s.overflow & 8u) msg += " soft tile list longer than 4096";
+  cudaMemsetAsync(c->status.p, 0, sizeof(Status), c->stream);
+  drop_graphs(c);
+  vtx_status st;
+  if ((st = ensure(c, c->recs, sizeof(PrimRec) * (size_t)c->cap_rec, "records"))) return st;
+  if ((st = ensure(c, c->recimg, sizeof(uint32_t) * (size_t)c->cap_rec, "record images"))) return st;
+  if ((st = ensure(c, c->entries, sizeof(unsigned long long) * (size_t)c->cap_entries, "entries"))) return st;
+  if (s.overflow & 8u) return fail(c, VTX_ERR_CAPACITY, msg);
+  return fail(c, VTX_ERR_CAPACITY, msg + " (arena grown; render again)");
+}
+
+static StageEvents *events_for(vtx_ctx *c, const vtx_settings *s, StageEvents &ev) {
+  if (!(s && (s->flags & VTX_FLAG_PROFILE))) return nullptr;
+  if (c->ev_used == c->ev_sets.size()) {
+    cudaEvent_t *set = new cudaEvent_t[8];
+    for (int i = 0; i < 8; ++i) cudaEventCreate(&set[i]);
+    c->ev_sets.push_back(set);
+  }
+  cudaEvent_t *set = c->ev_sets[c->ev_used++];
+  cudaEventRecord(set[7], c->stream);
+  ev.ev = set;
+  ev.n = 7;
+  return &ev;
+}
+
+extern "C" {
+
+const char *vtx_version(void) { return "vtx-gb300 0.1 (sm_103a)"; }
+
+vtx_status vtx_default_settings(vtx_settings *s) {
+  if (!s) return VTX_ERR_INVALID_ARG;
+  memset(s, 0, sizeof(*s));
+  s->mode = VTX_MODE_VDW;
+  s->ball_radius = 0.4f;
+  s->bond_radius = 0.15f;
+  s->ka = 0.2f;
+  s->kd = 0.7f;
+  s->ks = 0.3f;
+  s->shininess = 32.0f;
+  s->light_dir[0] = 0.25f;
+  s->light_dir[1] = 0.5f;
+  s->light_dir[2] = 1.0f;
+  s->background[0] = s->background[1] = s->background[2] = 1.0f;
+  s->ssao_samples = 0;
+  s->ssao_radius = 2.0f;
+  s->ssao_bias = 0.025f;
+  s->tile_w = 16;
+  s->tile_h = 16;
+  s->splat_max_px = 16;
+  return VTX_OK;
+}
+
+vtx_status vtx_create(vtx_ctx **out, int32_t device, void *cuda_stream) {
+  if (!out) return VTX_ERR_INVALID_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    return VTX_ERR_INVALID_ARG;
+  }
+  vtx_ctx *c = new vtx_ctx();
+  c->device = device;
+  cudaSetDevice(device);
+  c->stream = (cudaStream_t)cuda_stream;
+  for (int e = 0; e < kMaxElem; ++e) c->palette[e][0] = c->palette[e][1] = c->palette[e][2] = 0.5f;
+  if (cudaMallocHost((void **)&c->h_status, sizeof(Status)) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return VTX_ERR_OOM;
+  }
+  memset(c->h_status, 0, sizeof(Status));
+  cudaEventCreateWithFlags(&c->counts_done, cudaEventDisableTiming);
+  *out = c;
+  return VTX_OK;
+}
+
+vtx_status vtx_destroy(vtx_ctx *c) {
+  if (!c) return VTX_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  drop_graphs(c);
+  Buf *bufs[] = {&c->keys,   &c->surv,   &c->state,  &c->tcount,   &c->tstart,   &c->tcursor,
+                 &c->bsums,  &c->recs,   &c->recimg, &c->recof,    &c->entries,  &c->status,
+                 &c->counts, &c->hostin_x, &c->hostin_e, &c->hostout};
+  for (Buf *b : bufs)
+    if (b->p) cudaFree(b->p);
+  if (c->h_status) cudaFreeHost(c->h_status);
+  if (c->h_counts) cudaFreeHost(c->h_counts);
+  if (c->counts_done) cudaEventDestroy(c->counts_done);
+  for (cudaEvent_t *set : c->ev_sets) {
+    for (int i = 0; i < 8; ++i) cudaEventDestroy(set[i]);
+    delete[] set;
+  }
+  delete c;
+  return VTX_OK;
+}
+
+vtx_status vtx_set_stream(vtx_ctx *c, void *cuda_stream) {
+  if (!c) return VTX_ERR_INVALID_ARG;
+  c->stream = (cudaStream_t)cuda_stream;
+  drop_graphs(c);
+  return VTX_OK;
+}
+
+vtx_status vtx_upload_atoms(vtx_ctx *c, const float *xyzr, const uint8_t *elem, const float *palette_rgb,
+                            int32_t n_elem, int64_t n_atoms) {
+  if (!c) return VTX_ERR_INVALID_ARG;
+  if (n_atoms < 0 || n_atoms > 2147483647LL) return fail(c, VTX_ERR_INVALID_ARG, "n_atoms out of range");
+  if (n_atoms > 0 && !xyzr) return fail(c, VTX_ERR_INVALID_ARG, "xyzr is NULL");
+  if (((uintptr_t)xyzr & 15u) != 0) return fail(c, VTX_ERR_INVALID_ARG, "xyzr must be 16-byte aligned");
+  if (n_elem < 1 || n_elem > VTX_MAX_ELEMENTS || !palette_rgb)
+    return fail(c, VTX_ERR_INVALID_ARG, "palette: need 1..32 elements");
+  c->xyzr = (const float4 *)xyzr;
+  c->elem = elem;
+  c->n_atoms = n_atoms;
+  c->n_elem = n_elem;
+  for (int e = 0; e < n_elem; ++e)
+    for (int k = 0; k < 3; ++k) c->palette[e][k] = palette_rgb[3 * e + k];
+  c->bonds = nullptr;
+  c->n_bonds = 0;
+  drop_graphs(c);
+  return VTX_OK;
+}
+
+vtx_status vtx_upload_bonds(vtx_ctx *c, const uint32_t *pairs, int64_t n_bonds) {
+  if (!c) return VTX_ERR_INVALID_ARG;
+  if (n_bonds < 0 || c->n_atoms + n_bonds > 4294967040LL) return fail(c, VTX_ERR_INVALID_ARG, "n_bonds out of range");
+  if (n_bonds > 0 && !pairs) return fail(c, VTX_ERR_INVALID_ARG, "pairs is NULL");
+  if (((uintptr_t)pairs & 7u) != 0) return fail(c, VTX_ERR_INVALID_ARG, "pairs must be 8-byte aligned");
+  c->bonds = n_bonds > 0 ? (const uint2 *)pairs : nullptr;
+  c->n_bonds = n_bonds;
+  drop_graphs(c);
+  return VTX_OK;
+}
+
+vtx_status vtx_set_camera(vtx_ctx *c, const vtx_camera *cam) {
+  if (!c) return VTX_ERR_INVALID_ARG;
+  if (!cam_ok(cam)) return fail(c, VTX_ERR_INVALID_ARG, "invalid camera");
+  c->cam = *cam;
+  c->has_cam = true;
+  return VTX_OK;
+}
+
+static vtx_status render_once(vtx_ctx *c, const vtx_settings *s, const vtx_outputs *out, StageEvents *ev) {
+  Geometry g;
+  int tw = s->tile_w ? s->tile_w : 16, th = s->tile_h ? s->tile_h : 16;
+  base_geometry(g, &c->cam, 1, tw, th);
+  g.n_frames = 1;
+  g.n_img = 1;
+  g.mode = s->mode;
+  g.ball_radius = s->ball_radius;
+  g.bond_radius = s->bond_radius;
+  g.splat_max = s->splat_max_px ? s->splat_max_px : 16;
+  g.soft = 0;
+  g.stride = c->n_atoms;
+  g.n_atoms = c->n_atoms;
+  g.n_bonds = s->mode == VTX_MODE_BALL_AND_STICK ? c->n_bonds : 0;
+  g.surv_cap = c->n_atoms + g.n_bonds;
+  vtx_status st = prepare(c, g, false, 0);
+  if (st) return st;
+  Scene sc{c->xyzr, nullptr, c->elem, g.n_bonds ? c->bonds : nullptr};
+  Outputs o{out->depth, out->id, out->normal, out->rgb, out->ao};
+  ShadeParams sh = make_shade(c, s);
+  cudaError_t e = run_frame_pipeline(g, sh, sc, scratch_of(c), o, sh.ssao_n > 0, c->stream, ev);
+  if (e != cudaSuccess) return cuda_fail(c, e, "render_frame launch");
+  return VTX_OK;
+}
+
+vtx_status vtx_render_frame(vtx_ctx *c, const vtx_settings *s, const vtx_outputs *out) {
+  if (!c) return VTX_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
+  vtx_status st = settings_ok(c, s);
+  if (st) return st;
+  if (!out || !out->depth || !out->id || !out->normal || !out->rgb)
+    return fail(c, VTX_ERR_INVALID_ARG, "outputs: depth, id, normal and rgb are required");
+  if (!c->has_cam) return fail(c, VTX_ERR_STATE, "no camera set");
+  if (c->n_atoms > 0 && !c->xyzr) return fail(c, VTX_ERR_STATE, "no atoms uploaded");
+  if (s->mode == VTX_MODE_BALL_AND_STICK && c->n_bonds > 0 && c->n_atoms == 0)
+    return fail(c, VTX_ERR_STATE, "bonds without atoms");
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    StageEvents ev;
+    st = render_once(c, s, out, events_for(c, s, ev));
+    if (st) return st;
+    if (!(s->flags & VTX_FLAG_SYNC)) return VTX_OK;
+    st = check_status(c);
+    if (st != VTX_ERR_CAPACITY) return st;
+    c->err.clear();
+  }
+  return st;
+}
+
+vtx_status vtx_render_frame_host(vtx_ctx *c, const float *xyzr_host, const uint8_t *elem_host,
+                                 const float *palette_rgb, int32_t n_elem, int64_t n_atoms, const vtx_camera *cam,
+                                 const vtx_settings *s, const vtx_outputs *oh) {
+  if (!c) return VTX_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
+  if (n_atoms < 0 || (n_atoms > 0 && !xyzr_host) || !oh || !oh->depth || !oh->id || !oh->normal || !oh->rgb)
+    return fail(c, VTX_ERR_INVALID_ARG, "host render: bad pointers");
+  vtx_status st;
+  if ((st = ensure(c, c->hostin_x, sizeof(float4) * (size_t)(n_atoms > 0 ? n_atoms : 1), "host atoms"))) return st;
+  if (elem_host && (st = ensure(c, c->hostin_e, (size_t)(n_atoms > 0 ? n_atoms : 1), "host elements"))) return st;
+  cudaError_t e = cudaMemcpyAsync(c->hostin_x.p, xyzr_host, sizeof(float4) * (size_t)n_atoms,
+                                  cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess && elem_host)
+    e = cudaMemcpyAsync(c->hostin_e.p, elem_host, (size_t)n_atoms, cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "host render upload");
+  if ((st = vtx_upload_atoms(c, (const float *)c->hostin_x.p, elem_host ? (const uint8_t *)c->hostin_e.p : nullptr,
+                             palette_rgb, n_elem, n_atoms)))
+    return st;
+  if ((st = vtx_set_camera(c, cam))) return st;
+  const long long ppi = (long long)cam->width * cam->height;
+  size_t need = sizeof(float) * (size_t)ppi * 9;
+  if ((st = ensure(c, c->hostout, need, "host outputs"))) return st;
+  float *base = (float *)c->hostout.p;
+  vtx_outputs od{base, (uint32_t *)(base + ppi), base + 2 * ppi, base + 5 * ppi, oh->ao ? base + 8 * ppi : nullptr};
+  vtx_settings s2 = *s;
+  s2.flags &= ~VTX_FLAG_SYNC;
+  if ((st = vtx_render_frame(c, &s2, &od))) return st;
+  e = cudaMemcpyAsync(oh->depth, od.depth, sizeof(float) * ppi, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(oh->id, od.id, sizeof(uint32_t) * ppi, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(oh->normal, od.normal, sizeof(float) * 3 * ppi, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(oh->rgb, od.rgb, sizeof(float) * 3 * ppi, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess && oh->ao)
+    e = cudaMemcpyAsync(oh->ao, od.ao, sizeof(float) * ppi, cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "host render download");
+  return check_status(c);
+}
+
+static vtx_status batch_once(vtx_ctx *c, const float *frames, int64_t stride, const long long *d_counts,
+                             int32_t f0, int32_t nf, const vtx_camera *cams, int32_t n_views, const vtx_settings *s,
+                             const vtx_outputs *out, StageEvents *ev) {
+  Geometry g;
+  int tw = s->tile_w ? s->tile_w : 16, th = s->tile_h ? s->tile_h : 16;
+  base_geometry(g, cams, n_views, tw, th);
+  g.n_frames = nf;
+  g.n_img = nf * n_views;
+  g.mode = VTX_MODE_VDW;
+  g.splat_max = s->splat_max_px ? s->splat_max_px : 16;
+  g.stride = stride;
+  g.n_atoms = stride;
+  g.surv_cap = stride;
+  vtx_status st = prepare(c, g, false, 0);
+  if (st) return st;
+  const long long ppi = g.pix_per_img;
+  const long long img0 = (long long)f0 * n_views;
+  Scene sc{(const float4 *)frames + (long long)f0 * stride, d_counts + f0, c->elem, nullptr};
+  Outputs o{out->depth + img0 * ppi, out->id + img0 * ppi, out->normal + img0 * 3 * ppi, out->rgb + img0 * 3 * ppi,
+            out->ao ? out->ao + img0 * ppi : nullptr};
+  ShadeParams sh = make_shade(c, s);
+  cudaError_t e = run_frame_pipeline(g, sh, sc, scratch_of(c), o, sh.ssao_n > 0, c->stream, ev);
+  if (e != cudaSuccess) return cuda_fail(c, e, "render_batch launch");
+  return VTX_OK;
+}
+
+// Frames per pipeline pass: bounded so the per-image scratch stays near 8 GB.
+static int batch_chunk(const vtx_camera *cams, int n_views, long long stride, int n_frames) {
+  double per_frame = (double)n_views * ((double)cams[0].width * cams[0].height * 8.0 + (double)stride * 4.0);
+  int fc = (int)(8e9 / (per_frame > 1.0 ? per_frame : 1.0));
+  if (fc < 1) fc = 1;
+  if (fc > n_frames) fc = n_frames;
+  return fc;
+}
+
+static vtx_status batch_all(vtx_ctx *c, const float *frames, int64_t stride, const long long *d_counts, int32_t nf,
+                            const vtx_camera *cams, int32_t n_views, const vtx_settings *s, const vtx_outputs *out,
+                            StageEvents *ev) {
+  const int fc = batch_chunk(cams, n_views, stride, nf);
+  for (int f0 = 0; f0 < nf; f0 += fc) {
+    int n = nf - f0 < fc ? nf - f0 : fc;
+    vtx_status st = batch_once(c, frames, stride, d_counts, f0, n, cams, n_views, s, out, f0 == 0 ? ev : nullptr);
+    if (st) return st;
+  }
+  return VTX_OK;
+}
+
+vtx_status vtx_render_batch(vtx_ctx *c, const float *frames_xyzr, int64_t frame_stride, const int64_t *atom_counts,
+                            int32_t n_frames, const vtx_camera *cams, int32_t n_views, const vtx_settings *s,
+                            const vtx_outputs *out, int32_t use_graph) {
+  if (!c) return VTX_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
+  vtx_status st = settings_ok(c, s);
+  if (st) return st;
+  if (s->mode != VTX_MODE_VDW) return fail(c, VTX_ERR_INVALID_ARG, "batch: van der Waals mode only");
+  if (!frames_xyzr || ((uintptr_t)frames_xyzr & 15u)) return fail(c, VTX_ERR_INVALID_ARG, "frames: NULL or unaligned");
+  if (n_frames < 1 || n_views < 1 || n_views > VTX_MAX_VIEWS || !cams || !atom_counts)
+    return fail(c, VTX_ERR_INVALID_ARG, "batch: bad frame/view counts");
+  if (frame_stride < 1 || frame_stride > 2147483647LL) return fail(c, VTX_ERR_INVALID_ARG, "frame_stride");
+  for (int v = 0; v < n_views; ++v) {
+    if (!cam_ok(cams + v)) return fail(c, VTX_ERR_INVALID_ARG, "invalid camera");
+    if (cams[v].width != cams[0].width || cams[v].height != cams[0].height)
+      return fail(c, VTX_ERR_INVALID_ARG, "batch cameras must share one size");
+  }
+  for (int f = 0; f < n_frames; ++f)
+    if (atom_counts[f] < 0 || atom_counts[f] > frame_stride) return fail(c, VTX_ERR_INVALID_ARG, "atom_counts");
+  if (!out || !out->depth || !out->id || !out->normal || !out->rgb)
+    return fail(c, VTX_ERR_INVALID_ARG, "outputs: depth, id, normal and rgb are required");
+  // graph cache lookup
+  std::vector<unsigned char> key;
+  auto push = [&key](const void *p, size_t n) {
+    const unsigned char *b = (const unsigned char *)p;
+    key.insert(key.end(), b, b + n);
+  };
+  if (use_graph) {
+    push(&frames_xyzr, sizeof(void *));
+    push(&frame_stride, sizeof(frame_stride));
+    push(&n_frames, sizeof(n_frames));
+    push(atom_counts, sizeof(int64_t) * (size_t)n_frames);
+    push(cams, sizeof(vtx_camera) * (size_t)n_views);
+    push(s, sizeof(vtx_settings));
+    push(out, sizeof(vtx_outputs));
+    push(&c->elem, sizeof(void *));
+    for (auto &ge : c->graphs)
+      if (ge.key == key) {
+        cudaError_t e = cudaGraphLaunch(ge.exec, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphLaunch");
+        return VTX_OK;
+      }
+  }
+  // per-frame atom counts on the device
+  if (n_frames > c->h_counts_cap) {
+    if (c->h_counts) {
+      cudaEventSynchronize(c->counts_done);
+      cudaFreeHost(c->h_counts);
+    }
+    c->h_counts = nullptr;
+    if (cudaMallocHost((void **)&c->h_counts, sizeof(long long) * (size_t)n_frames) != cudaSuccess) {
+      cudaGetLastError();
+      c->h_counts_cap = 0;
+      return fail(c, VTX_ERR_OOM, "pinned counts");
+    }
+    c->h_counts_cap = n_frames;
+  }
+  cudaEventSynchronize(c->counts_done);
+  for (int f = 0; f < n_frames; ++f) c->h_counts[f] = atom_counts[f];
+  if ((st = ensure(c, c->counts, sizeof(long long) * (size_t)n_frames, "counts"))) return st;
+  cudaError_t e =
+      cudaMemcpyAsync(c->counts.p, c->h_counts, sizeof(long long) * (size_t)n_frames, cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "counts upload");
+  cudaEventRecord(c->counts_done, c->stream);
+  const long long *d_counts = (const long long *)c->counts.p;
+  if (!use_graph) {
+    for (int attempt = 0; attempt < 4; ++attempt) {
+      StageEvents ev;
+      st = batch_all(c, frames_xyzr, frame_stride, d_counts, n_frames, cams, n_views, s, out, events_for(c, s, ev));
+      if (st) return st;
+      if (!(s->flags & VTX_FLAG_SYNC)) return VTX_OK;
+      st = check_status(c);
+      if (st != VTX_ERR_CAPACITY) return st;
+      c->err.clear();
+    }
+    return st;
+  }
+  // first use: size the arena with a synchronous run, then capture
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    st = batch_all(c, frames_xyzr, frame_stride, d_counts, n_frames, cams, n_views, s, out, nullptr);
+    if (st) return st;
+    st = check_status(c);
+    if (st != VTX_ERR_CAPACITY) break;
+    c->err.clear();
+  }
+  if (st) return st;
+  GraphEntry ge;
+  ge.key = key;
+  if (cudaMalloc((void **)&ge.d_counts, sizeof(long long) * (size_t)n_frames) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, VTX_ERR_OOM, "graph counts");
+  }
+  cudaMemcpyAsync(ge.d_counts, d_counts, sizeof(long long) * (size_t)n_frames, cudaMemcpyDeviceToDevice, c->stream);
+  cudaStreamSynchronize(c->stream);
+  cudaStream_t cap = c->stream;
+  bool own = false;
+  if (cap == nullptr) {  // the legacy default stream cannot be captured
+    cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    own = true;
+  }
+  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    if (own) cudaStreamDestroy(cap);
+    cudaFree(ge.d_counts);
+    return cuda_fail(c, e, "cudaStreamBeginCapture");
+  }
+  cudaStream_t saved = c->stream;
+  c->stream = cap;
+  st = batch_all(c, frames_xyzr, frame_stride, ge.d_counts, n_frames, cams, n_views, s, out, nullptr);
+  c->stream = saved;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+  if (own) cudaStreamDestroy(cap);
+  if (st || e2 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaFree(ge.d_counts);
+    return st ? st : cuda_fail(c, e2, "cudaStreamEndCapture");
+  }
+  e = cudaGraphInstantiate(&ge.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    cudaFree(ge.d_counts);
+    return cuda_fail(c, e, "cudaGraphInstantiate");
+  }
+  c->graphs.push_back(ge);
+  e = cudaGraphLaunch(ge.exec, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphLaunch");
+  return VTX_OK;
+}
+
+static vtx_status soft_common(vtx_ctx *c, const float *xyzr, int64_t n, const vtx_camera *cams, int32_t n_views,
+                              float sigma, Geometry &g) {
+  if (!xyzr || ((uintptr_t)xyzr & 15u)) return fail(c, VTX_ERR_INVALID_ARG, "xyzr: NULL or unaligned");
+  if (n < 1 || n > 2147483647LL) return fail(c, VTX_ERR_INVALID_ARG, "n out of range");
+  if (!cams || n_views < 1 || n_views > VTX_MAX_VIEWS) return fail(c, VTX_ERR_INVALID_ARG, "views");
+  if (!(sigma > 0.0f)) return fail(c, VTX_ERR_INVALID_ARG, "sigma_px must be > 0");
+  for (int v = 0; v < n_views; ++v) {
+    if (!cam_ok(cams + v)) return fail(c, VTX_ERR_INVALID_ARG, "invalid camera");
+    if (cams[v].width != cams[0].width || cams[v].height != cams[0].height)
+      return fail(c, VTX_ERR_INVALID_ARG, "soft cameras must share one size");
+  }
+  base_geometry(g, cams, n_views, 16, 16);
+  g.n_frames = 1;
+  g.n_img = n_views;
+  g.mode = VTX_MODE_VDW;
+  g.soft = 1;
+  g.sigma = sigma;
+  g.stride = n;
+  g.n_atoms = n;
+  g.surv_cap = n;
+  return prepare(c, g, true, n);
+}
+
+static vtx_status soft_run(vtx_ctx *c, const float *xyzr, int64_t n, const vtx_camera *cams, int32_t n_views,
+                           float sigma, float *cov, float *depth, float *normal, const float *gc, const float *gd,
+                           const float *gn, float *grad) {
+  if (!c) return VTX_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
+  vtx_status st = VTX_OK;
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    Geometry g;
+    st = soft_common(c, xyzr, n, cams, n_views, sigma, g);
+    if (st) return st;
+    Scene sc{(const float4 *)xyzr, nullptr, nullptr, nullptr};
+    cudaError_t e =
+        run_soft_pipeline(g, sc, scratch_of(c), cov, depth, normal, gc, gd, gn, grad, c->stream, nullptr);
+    if (e != cudaSuccess) return cuda_fail(c, e, "soft launch");
+    st = check_status(c);
+    if (st != VTX_ERR_CAPACITY) return st;
+    if (c->h_status->overflow & 8u) return st;
+    c->err.clear();
+  }
+  return st;
+}
+
+vtx_status vtx_render_soft_fwd(vtx_ctx *c, const float *xyzr, int64_t n, const vtx_camera *cams, int32_t n_views,
+                               float sigma_px, float *cov, float *depth, float *normal) {
+  if (!cov || !depth || !normal) return fail(c, VTX_ERR_INVALID_ARG, "soft outputs are required");
+  return soft_run(c, xyzr, n, cams, n_views, sigma_px, cov, depth, normal, nullptr, nullptr, nullptr, nullptr);
+}
+
+vtx_status vtx_render_soft_bwd(vtx_ctx *c, const float *xyzr, int64_t n, const vtx_camera *cams, int32_t n_views,
+                               float sigma_px, const float *g_cov, const float *g_depth, const float *g_normal,
+                               float *grad_xyzr) {
+  if (!grad_xyzr || ((uintptr_t)grad_xyzr & 15u)) return fail(c, VTX_ERR_INVALID_ARG, "grad_xyzr: NULL or unaligned");
+  return soft_run(c, xyzr, n, cams, n_views, sigma_px, nullptr, nullptr, nullptr, g_cov, g_depth, g_normal, grad_xyzr);
+}
+
+vtx_status vtx_sync_status(vtx_ctx *c) {
+  if (!c) return VTX_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
+  if (!c->status.p) {
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    return e == cudaSuccess ? VTX_OK : cuda_fail(c, e, "device error");
+  }
+  return check_status(c);
+}
+
+vtx_status vtx_stage_times(vtx_ctx *c, const char **names, float *ms, int32_t *n, int32_t *runs) {
+  if (!c || !n) return VTX_ERR_INVALID_ARG;
+  if (c->ev_used == 0) {
+    *n = 0;
+    if (runs) *runs = 0;
+    return fail(c, VTX_ERR_STATE, "no profiled render since the last read");
+  }
+  cudaError_t e = cudaEventSynchronize(c->ev_sets[c->ev_used - 1][6]);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stage events");
+  int cap = *n < 7 ? *n : 7;
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (size_t r = 0; r < c->ev_used; ++r) {
+    cudaEvent_t *set = c->ev_sets[r];
+    cudaEvent_t prev = set[7];
+    for (int i = 0; i < 7; ++i) {
+      float t = 0.0f;
+      cudaEventElapsedTime(&t, prev, set[i]);
+      acc[i] += t;
+      prev = set[i];
+    }
+  }
+  for (int i = 0; i < cap; ++i) {
+    if (names) names[i] = kStageNames[i];
+    if (ms) ms[i] = (float)(acc[i] / (double)c->ev_used);
+  }
+  *n = cap;
+  if (runs) *runs = (int32_t)c->ev_used;
+  c->ev_used = 0;
+  return VTX_OK;
+}
+
+const char *vtx_last_error(const vtx_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+}  // extern "C"

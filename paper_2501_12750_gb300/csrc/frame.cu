@@ -1,0 +1,821 @@
+// frame.cu -- per-frame hard-edge path of the meshless ray-caster.
+//
+// The paper rasterises one impostor quad per primitive and ray-casts the
+// implicit surface in a fragment shader (Methods, "Meshless
+// Representations"), then shades a G-buffer and runs screen-space ambient
+// occlusion ("High Quality Rendering").  Here the same per-pixel result --
+// the nearest ray/primitive hit -- is computed without a graphics API:
+//
+//   k_cull_atoms / k_cull_bonds  stream every record once (16-byte vector
+//        loads), reject what cannot cover a pixel centre, append survivors
+//        (block-aggregated, one global atomic per 2,048 atoms per view);
+//   k_finalize   fixes each image's depth-key range from the survivors;
+//   k_setup      precise double-float setup per survivor; footprints of at
+//        most splat_max candidate pixels are ray-cast right there and
+//        merged with a 64-bit atomicMin of (depth key << 32 | id); larger
+//        ones become 64-byte records counted per screen tile;
+//   k_scan_*     exclusive scan of the per-tile counts (counting sort by tile);
+//   k_scatter    writes (min depth key << 32 | record) entries per tile;
+//   k_raster     one CTA per tile: depth-sorts its entries in shared memory
+//        (bitonic), stages records chunk by chunk, ray-casts every pixel,
+//        and stops once every pixel's hit is nearer than the next entry's
+//        nearest possible depth (__syncthreads_and);
+//   k_resolve    decodes id, recomputes the hit -> depth, normal, Blinn-Phong
+//        colour, SSAO from neighbouring depth keys; writes every plane once.
+#include <cstdio>
+
+#include "vtx_internal.h"
+
+namespace vtx {
+
+constexpr int kCullThreads = 256;
+constexpr int kCullPer = 8;
+constexpr int kCullTile = kCullThreads * kCullPer;
+constexpr int kScanItems = 4096;  // tiles per scan block (1024 threads x 4)
+
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 132;
+  }
+  return n;
+}
+
+// ----------------------------------------------------------------- init --
+
+__global__ void k_init_state(ImageState *st, int n_img, Status *status) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n_img) {
+    ImageState s;
+    s.zlo_bits = 0x7f800000u;
+    s.zhi_bits = 0u;
+    s.n_surv = 0u;
+    s.valid = 0u;
+    s.zlo = 0.0f;
+    s.S = 0.0f;
+    s.invS = 0.0f;
+    s.pad = 0.0f;
+    st[i] = s;
+  }
+  if (i == 0) {
+    status->n_rec = 0u;
+    status->n_entries = 0ull;
+  }
+}
+
+// ----------------------------------------------------------------- cull --
+
+// Radius used for binning.  Soft mode dilates by 4 px at the centre depth
+// (primitives contribute while their signed pixel distance is >= -4 px).
+__device__ __forceinline__ float cull_radius(const Geometry &g, const ViewParams &v, float r, float z) {
+  if (g.soft) return r + 4.0f * fmaxf(z, 0.0f) * v.inv_f * 1.0001f + 1e-6f;
+  return r;
+}
+
+__device__ __forceinline__ void warp_minmax(float &lo, float &hi) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+}
+
+// Every atom record of frame blockIdx.y is read once and tested against all
+// views of that frame.
+__global__ __launch_bounds__(kCullThreads) void k_cull_atoms(Geometry g, const float4 *__restrict__ frames,
+                                                             const long long *__restrict__ counts, ImageState *st,
+                                                             uint32_t *__restrict__ surv) {
+  __shared__ uint32_t s_idx[kCullTile];
+  __shared__ int s_cnt;
+  __shared__ unsigned int s_base;
+  __shared__ unsigned int s_zlo[kMaxViews], s_zhi[kMaxViews];
+  const int frame = blockIdx.y;
+  const long long n = counts ? counts[frame] : g.n_atoms;
+  const float4 *X = frames + (long long)frame * g.stride;
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x < kMaxViews) {
+    s_zlo[threadIdx.x] = 0x7f800000u;
+    s_zhi[threadIdx.x] = 0u;
+  }
+  __syncthreads();
+  for (long long base = (long long)blockIdx.x * kCullTile; base < n; base += (long long)gridDim.x * kCullTile) {
+    float4 a[kCullPer];
+#pragma unroll
+    for (int j = 0; j < kCullPer; ++j) {
+      long long i = base + (long long)j * kCullThreads + threadIdx.x;
+      a[j] = i < n ? __ldcs(X + i) : make_float4(0.0f, 0.0f, 0.0f, -1.0f);
+    }
+    for (int v = 0; v < g.n_views; ++v) {
+      const ViewParams &vp = g.views[v];
+      if (threadIdx.x == 0) s_cnt = 0;
+      __syncthreads();
+      float zlo = __int_as_float(0x7f800000), zhi = 0.0f;
+#pragma unroll
+      for (int j = 0; j < kCullPer; ++j) {
+        bool keep = false;
+        if (a[j].w >= 0.0f) {
+          float r = g.mode == 1 ? g.ball_radius : a[j].w;
+          float vx, vy, vz, err;
+          view_f32(vp, a[j].x, a[j].y, a[j].z, vx, vy, vz, err);
+          float R = cull_radius(g, vp, r, vz);
+          PixBox b;
+          keep = sphere_box(vp, g.W, g.H, vx, vy, vz, R, err, b);
+          if (g.soft && !(vz > vp.znear)) keep = false;
+          if (keep) {
+            zlo = fminf(zlo, vz - R - err);
+            zhi = fmaxf(zhi, vz + R + err);
+          }
+        }
+        unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (m) {
+          int leader = __ffs(m) - 1;
+          int pos = 0;
+          if (lane == leader) pos = atomicAdd(&s_cnt, __popc(m));
+          pos = __shfl_sync(0xffffffffu, pos, leader);
+          if (keep)
+            s_idx[pos + __popc(m & ((1u << lane) - 1u))] = (uint32_t)(base + (long long)j * kCullThreads + threadIdx.x);
+        }
+      }
+      warp_minmax(zlo, zhi);
+      if (lane == 0 && zhi > 0.0f) {
+        atomicMin(&s_zlo[v], __float_as_uint(fmaxf(zlo, 0.0f)));
+        atomicMax(&s_zhi[v], __float_as_uint(zhi));
+      }
+      __syncthreads();
+      const int cnt = s_cnt;
+      if (cnt > 0) {
+        const int img = frame * g.n_views + v;
+        if (threadIdx.x == 0) s_base = atomicAdd(&st[img].n_surv, (unsigned)cnt);
+        __syncthreads();
+        uint32_t *dst = surv + (long long)img * g.surv_cap + s_base;
+        for (int k = threadIdx.x; k < cnt; k += kCullThreads) dst[k] = s_idx[k];
+      }
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x < g.n_views && s_zhi[threadIdx.x] != 0u) {
+    const int img = frame * g.n_views + threadIdx.x;
+    atomicMin(&st[img].zlo_bits, s_zlo[threadIdx.x]);
+    atomicMax(&st[img].zhi_bits, s_zhi[threadIdx.x]);
+  }
+}
+
+// Bond cylinders (ball-and-stick, single frame, single view): the bounding
+// sphere of each capped cylinder is culled like an atom.
+__global__ __launch_bounds__(kCullThreads) void k_cull_bonds(Geometry g, const float4 *__restrict__ X,
+                                                             const uint2 *__restrict__ pairs, ImageState *st,
+                                                             uint32_t *__restrict__ surv) {
+  __shared__ uint32_t s_idx[kCullThreads];
+  __shared__ int s_cnt;
+  __shared__ unsigned int s_base;
+  const ViewParams &vp = g.views[0];
+  const int lane = threadIdx.x & 31;
+  float zlo = __int_as_float(0x7f800000), zhi = 0.0f;
+  for (long long base = (long long)blockIdx.x * kCullThreads; base < g.n_bonds;
+       base += (long long)gridDim.x * kCullThreads) {
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    long long b = base + threadIdx.x;
+    bool keep = false;
+    if (b < g.n_bonds) {
+      uint2 p = pairs[b];
+      float4 A = X[p.x], B = X[p.y];
+      float mx = 0.5f * (A.x + B.x), my = 0.5f * (A.y + B.y), mz = 0.5f * (A.z + B.z);
+      float dx = B.x - A.x, dy = B.y - A.y, dz = B.z - A.z;
+      float hl = 0.5f * sqrtf(dx * dx + dy * dy + dz * dz);
+      float Rb = sqrtf(hl * hl + g.bond_radius * g.bond_radius) * 1.00001f;
+      float vx, vy, vz, err;
+      view_f32(vp, mx, my, mz, vx, vy, vz, err);
+      err += 1.2e-7f * (fabsf(mx) + fabsf(my) + fabsf(mz)) + 1e-6f;
+      PixBox bx;
+      keep = sphere_box(vp, g.W, g.H, vx, vy, vz, Rb, err, bx);
+      if (keep) {
+        zlo = fminf(zlo, vz - Rb - err);
+        zhi = fmaxf(zhi, vz + Rb + err);
+      }
+    }
+    unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (m) {
+      int leader = __ffs(m) - 1;
+      int pos = 0;
+      if (lane == leader) pos = atomicAdd(&s_cnt, __popc(m));
+      pos = __shfl_sync(0xffffffffu, pos, leader);
+      if (keep) s_idx[pos + __popc(m & ((1u << lane) - 1u))] = (uint32_t)(g.n_atoms + b);
+    }
+    __syncthreads();
+    const int cnt = s_cnt;
+    if (cnt > 0) {
+      if (threadIdx.x == 0) s_base = atomicAdd(&st[0].n_surv, (unsigned)cnt);
+      __syncthreads();
+      for (int k = threadIdx.x; k < cnt; k += kCullThreads) surv[s_base + k] = s_idx[k];
+    }
+    __syncthreads();
+  }
+  warp_minmax(zlo, zhi);
+  if (lane == 0 && zhi > 0.0f) {
+    atomicMin(&st[0].zlo_bits, __float_as_uint(fmaxf(zlo, 0.0f)));
+    atomicMax(&st[0].zhi_bits, __float_as_uint(zhi));
+  }
+}
+
+// Depth-key range per image: [zlo, zhi] of the survivors, widened past the
+// FP32 error of the cull and clamped to half the near plane.
+__global__ void k_finalize(Geometry g, ImageState *st) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.n_img) return;
+  ImageState s = st[i];
+  if (s.n_surv == 0u || s.zhi_bits == 0u) {
+    st[i].valid = 0u;
+    return;
+  }
+  const ViewParams &v = g.views[i % g.n_views];
+  float lo = __uint_as_float(s.zlo_bits), hi = __uint_as_float(s.zhi_bits);
+  lo = fmaxf(lo - 4e-6f * fabsf(lo) - 1e-4f, 0.5f * v.znear);
+  hi = hi + 4e-6f * fabsf(hi) + 1e-4f;
+  if (!(hi > lo)) hi = lo + 1.0f;
+  st[i].zlo = lo;
+  st[i].S = kKeySpanF / (hi - lo);
+  st[i].invS = (hi - lo) / kKeySpanF;
+  st[i].valid = 1u;
+}
+
+// ---------------------------------------------------------------- setup --
+
+struct PrimGeom {
+  Setup su;
+  float rad;       // sphere radius or cylinder radius
+  float3 A;        // cylinder axis (internal frame)
+  float hl;        // cylinder half length (0 for spheres)
+  float Rb;        // bounding radius
+  float vx, vy, vz, err;  // FP32 view centre for the conservative box
+};
+
+// Precise setup of primitive `id` of image `img` (sphere or bond cylinder).
+__device__ __forceinline__ PrimGeom prim_geom(const Geometry &g, const ViewParams &v, const float4 *X, const uint2 *bonds,
+                                              uint32_t id, float zlo, float S, bool use_box_r) {
+  PrimGeom p;
+  if ((long long)id < g.n_atoms || bonds == nullptr) {
+    float4 a = X[id];
+    float r = g.mode == 1 ? g.ball_radius : a.w;
+    p.rad = r;
+    p.hl = 0.0f;
+    p.A = make_float3(0.0f, 0.0f, 0.0f);
+    p.Rb = r;
+    df dx, dy, dz;
+    eye_offset(v, a, dx, dy, dz);
+    p.su = precise_setup(v, dx, dy, dz, r, zlo, S);
+    if (use_box_r) view_f32(v, a.x, a.y, a.z, p.vx, p.vy, p.vz, p.err);
+  } else {
+    uint2 pr = bonds[(long long)id - g.n_atoms];
+    float4 A = X[pr.x], B = X[pr.y];
+    df ax, ay, az, bx, by, bz;
+    eye_offset(v, A, ax, ay, az);
+    eye_offset(v, B, bx, by, bz);
+    df mx = df_add(ax, bx), my = df_add(ay, by), mz = df_add(az, bz);
+    mx.hi *= 0.5f; mx.lo *= 0.5f;
+    my.hi *= 0.5f; my.lo *= 0.5f;
+    mz.hi *= 0.5f; mz.lo *= 0.5f;
+    float dx = B.x - A.x, dy = B.y - A.y, dz = B.z - A.z;
+    float L = sqrtf(dx * dx + dy * dy + dz * dz);
+    float inv = 1.0f / L;
+    p.A = make_float3((v.R[0] * dx + v.R[1] * dy + v.R[2] * dz) * inv, (v.U[0] * dx + v.U[1] * dy + v.U[2] * dz) * inv,
+                      (v.F[0] * dx + v.F[1] * dy + v.F[2] * dz) * inv);
+    p.hl = 0.5f * L;
+    p.rad = g.bond_radius;
+    p.Rb = sqrtf(p.hl * p.hl + p.rad * p.rad) * 1.00001f;
+    p.su = precise_setup(v, mx, my, mz, p.Rb, zlo, S);
+    if (use_box_r) {
+      float cx = 0.5f * (A.x + B.x), cy = 0.5f * (A.y + B.y), cz = 0.5f * (A.z + B.z);
+      view_f32(v, cx, cy, cz, p.vx, p.vy, p.vz, p.err);
+      p.err += 1.2e-7f * (fabsf(cx) + fabsf(cy) + fabsf(cz)) + 1e-6f;
+    }
+  }
+  return p;
+}
+
+// Ray-cast primitive p at one pixel; s is relative to the reference depth.
+__device__ __forceinline__ bool prim_hit(const PrimGeom &p, float3 o, const PixRay &r, float &s, int &kind,
+                                         float &axial) {
+  if (p.hl == 0.0f) {
+    kind = 0;
+    axial = 0.0f;
+    return sphere_local(o, r, p.rad, s);
+  }
+  return cylinder_local(o, r, p.A, p.hl, p.rad, s, kind, axial);
+}
+
+template <bool SOFT>
+__global__ __launch_bounds__(256) void k_setup(Geometry g, const float4 *__restrict__ frames,
+                                               const uint2 *__restrict__ bonds, const ImageState *__restrict__ st,
+                                               const uint32_t *__restrict__ surv, unsigned long long *keys,
+                                               PrimRec *recs, uint32_t *rec_img, uint32_t *rec_of,
+                                               uint32_t *tile_count, Status *status, uint32_t cap_rec) {
+  const int img = blockIdx.y;
+  const ImageState s = st[img];
+  if (!s.valid) return;
+  const ViewParams &v = g.views[img % g.n_views];
+  const int frame = img / g.n_views;
+  const float4 *X = frames + (long long)frame * g.stride;
+  const long long n = min((long long)s.n_surv, g.surv_cap);
+  const uint32_t *sv = surv + (long long)img * g.surv_cap;
+  unsigned long long *K = keys + (long long)img * g.pix_per_img;
+  const int lane = threadIdx.x & 31;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long n_pad = (n + 31) & ~31LL;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n_pad; k += stride) {
+    bool binned = false;
+    PrimRec rec;
+    PixBox box;
+    if (k < n) {
+      const uint32_t id = sv[k];
+      PrimGeom p = prim_geom(g, v, X, bonds, id, s.zlo, s.S, true);
+      float Rbox = p.hl == 0.0f ? cull_radius(g, v, p.rad, p.vz) : p.Rb;
+      bool any = sphere_box(v, g.W, g.H, p.vx, p.vy, p.vz, Rbox, p.err, box);
+      if (any) {
+        const long long npx = (long long)(box.x1 - box.x0 + 1) * (long long)(box.y1 - box.y0 + 1);
+        if (!SOFT && npx <= g.splat_max) {
+          for (int py = box.y0; py <= box.y1; ++py)
+            for (int px = box.x0; px <= box.x1; ++px) {
+              PixRay r = pix_ray(v, px, py);
+              float3 o = local_o(p.su.u0.hi, p.su.u0.lo, p.su.v0.hi, p.su.v0.lo, p.su.k, p.su.dz, r);
+              float sh;
+              int kind;
+              float axial;
+              if (prim_hit(p, o, r, sh, kind, axial) && p.su.zr + sh >= v.znear)
+                atomicMin(K + (long long)py * g.W + px, pack_key(p.su.keyc, sh, s.S, id));
+            }
+        } else {
+          binned = true;
+          rec.u0h = p.su.u0.hi;
+          rec.u0l = p.su.u0.lo;
+          rec.v0h = p.su.v0.hi;
+          rec.v0l = p.su.v0.lo;
+          rec.zr = p.su.zr;
+          rec.k = p.su.k;
+          rec.dz = p.su.dz;
+          rec.rad = p.rad;
+          long long kc = p.su.keyc;
+          if (SOFT) {
+            // soft order key: the centre depth
+            kc = kc - llrintf(p.su.dz * s.S);
+          }
+          rec.keyc = (int)(kc < -2147483647LL ? -2147483647LL : (kc > 2147483647LL ? 2147483647LL : kc));
+          if (SOFT) rec.keyc = (int)(uint32_t)(kc < 0 ? 0 : (kc > kKeySpan ? kKeySpan : kc));
+          rec.id = id;
+          int tx0 = box.x0 / g.tile_w, tx1 = box.x1 / g.tile_w, ty0 = box.y0 / g.tile_h, ty1 = box.y1 / g.tile_h;
+          rec.box_lo = (uint32_t)tx0 | ((uint32_t)ty0 << 16);
+          rec.box_hi = (uint32_t)tx1 | ((uint32_t)ty1 << 16);
+          rec.ax = p.A.x;
+          rec.ay = p.A.y;
+          rec.az = p.A.z;
+          rec.hl = p.hl;
+        }
+      }
+    }
+    unsigned m = __ballot_sync(0xffffffffu, binned);
+    if (m) {
+      int leader = __ffs(m) - 1;
+      unsigned base = 0;
+      if (lane == leader) base = atomicAdd(&status->n_rec, (unsigned)__popc(m));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (binned) {
+        unsigned slot = base + __popc(m & ((1u << lane) - 1u));
+        if (slot < cap_rec) {
+          recs[slot] = rec;
+          rec_img[slot] = (uint32_t)img;
+          if (SOFT) rec_of[(long long)img * g.n_atoms + rec.id] = slot;
+          int tx0 = rec.box_lo & 0xffff, ty0 = rec.box_lo >> 16, tx1 = rec.box_hi & 0xffff, ty1 = rec.box_hi >> 16;
+          uint32_t *tc = tile_count + (long long)img * g.tiles_per_img;
+          for (int ty = ty0; ty <= ty1; ++ty)
+            for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(tc + ty * g.tiles_x + tx, 1u);
+        } else {
+          atomicOr(&status->overflow, 2u);
+        }
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------- scan --
+
+__device__ __forceinline__ unsigned long long block_exclusive_scan_1024(unsigned long long v,
+                                                                         unsigned long long *s_warp,
+                                                                         unsigned long long &total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned long long x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    unsigned long long w = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0ull;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    s_warp[lane] = w;
+  }
+  __syncthreads();
+  unsigned long long off = wid > 0 ? s_warp[wid - 1] : 0ull;
+  total = s_warp[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return off + x - v;
+}
+
+// Per-block exclusive scan of 4,096 tile counts; block totals to block_sums.
+__global__ __launch_bounds__(1024) void k_scan_blocks(const uint32_t *__restrict__ cnt, long long n,
+                                                      uint32_t *__restrict__ start, unsigned long long *block_sums) {
+  __shared__ unsigned long long s_warp[32];
+  const long long base = (long long)blockIdx.x * kScanItems + (long long)threadIdx.x * 4;
+  uint32_t c[4];
+  unsigned long long sum = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    c[j] = base + j < n ? cnt[base + j] : 0u;
+    sum += c[j];
+  }
+  unsigned long long total;
+  unsigned long long ex = block_exclusive_scan_1024(sum, s_warp, total);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (base + j < n) start[base + j] = (uint32_t)(ex > 0xffffffffull ? 0xffffffffull : ex);
+    ex += c[j];
+  }
+  if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
+// Scan of the block totals (one CTA, loops when there are more than 1,024 blocks).
+__global__ __launch_bounds__(1024) void k_scan_top(unsigned long long *block_sums, int nb, Status *status,
+                                                   unsigned long long cap_entries) {
+  __shared__ unsigned long long s_warp[32];
+  unsigned long long carry = 0;
+  for (int b0 = 0; b0 < nb; b0 += 1024) {
+    int i = b0 + threadIdx.x;
+    unsigned long long v = i < nb ? block_sums[i] : 0ull;
+    unsigned long long total;
+    unsigned long long ex = block_exclusive_scan_1024(v, s_warp, total);
+    if (i < nb) block_sums[i] = carry + ex;
+    carry += total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    block_sums[nb] = carry;
+    status->n_entries = carry;
+    if (carry > cap_entries) atomicOr(&status->overflow, 4u);
+  }
+}
+
+__global__ __launch_bounds__(1024) void k_scan_add(uint32_t *__restrict__ start, uint32_t *__restrict__ cursor,
+                                                   long long n, const unsigned long long *__restrict__ block_sums,
+                                                   unsigned long long cap_entries) {
+  const long long base = (long long)blockIdx.x * kScanItems + (long long)threadIdx.x * 4;
+  const unsigned long long off = block_sums[blockIdx.x];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    long long i = base + j;
+    if (i < n) {
+      unsigned long long v = off + start[i];
+      uint32_t w = (uint32_t)(v > cap_entries ? cap_entries : v);
+      start[i] = w;
+      cursor[i] = w;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    unsigned long long tot = block_sums[gridDim.x];
+    start[n] = (uint32_t)(tot > cap_entries ? cap_entries : tot);
+  }
+}
+
+// -------------------------------------------------------------- scatter --
+
+template <bool SOFT>
+__global__ __launch_bounds__(256) void k_scatter(Geometry g, const PrimRec *__restrict__ recs,
+                                                 const uint32_t *__restrict__ rec_img,
+                                                 const ImageState *__restrict__ st, const Status *__restrict__ status,
+                                                 uint32_t cap_rec, uint32_t *tile_cursor,
+                                                 unsigned long long *entries, unsigned long long cap_entries) {
+  const uint32_t n = min(status->n_rec, cap_rec);
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    const PrimRec &q = recs[r];
+    const int img = (int)rec_img[r];
+    unsigned long long key;
+    if (SOFT) {
+      key = ((unsigned long long)(uint32_t)q.keyc << 32) | (unsigned long long)q.id;
+    } else {
+      const float S = st[img].S;
+      float Rb = q.hl == 0.0f ? q.rad : sqrtf(q.hl * q.hl + q.rad * q.rad);
+      long long kmin = (long long)q.keyc - (long long)ceilf((Rb + fabsf(q.dz)) * S * 1.000001f) - 2;
+      kmin = kmin < 0 ? 0 : (kmin > kKeySpan ? kKeySpan : kmin);
+      key = ((unsigned long long)kmin << 32) | (unsigned long long)r;
+    }
+    int tx0 = q.box_lo & 0xffff, ty0 = q.box_lo >> 16, tx1 = q.box_hi & 0xffff, ty1 = q.box_hi >> 16;
+    uint32_t *cur = tile_cursor + (long long)img * g.tiles_per_img;
+    for (int ty = ty0; ty <= ty1; ++ty)
+      for (int tx = tx0; tx <= tx1; ++tx) {
+        unsigned pos = atomicAdd(cur + ty * g.tiles_x + tx, 1u);
+        if (pos < cap_entries) entries[pos] = key;
+      }
+  }
+}
+
+// --------------------------------------------------------------- raster --
+
+template <int NT>
+__device__ __forceinline__ void bitonic_sort_u64(unsigned long long *s, int n2) {
+  for (int k = 2; k <= n2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < n2; i += NT) {
+        int ixj = i ^ j;
+        if (ixj > i) {
+          unsigned long long a = s[i], b = s[ixj];
+          bool up = (i & k) == 0;
+          if ((a > b) == up) {
+            s[i] = b;
+            s[ixj] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+constexpr int kListCap = 2048;
+
+template <int TW, int TH>
+__global__ __launch_bounds__(TW *TH) void k_raster(Geometry g, const PrimRec *__restrict__ recs,
+                                                   const unsigned long long *__restrict__ entries,
+                                                   unsigned long long cap_entries,
+                                                   const uint32_t *__restrict__ tile_count,
+                                                   const uint32_t *__restrict__ tile_start,
+                                                   const ImageState *__restrict__ st, unsigned long long *keys,
+                                                   Status *status) {
+  constexpr int NT = TW * TH;
+  __shared__ unsigned long long s_e[kListCap];
+  __shared__ PrimRec s_r[NT];
+  const long long gt = blockIdx.x;
+  const int img = (int)(gt / g.tiles_per_img);
+  const int t = (int)(gt % g.tiles_per_img);
+  uint32_t cnt = tile_count[gt];
+  if (cnt == 0u) return;
+  const uint32_t start = tile_start[gt];
+  if ((unsigned long long)start >= cap_entries) return;
+  if ((unsigned long long)start + cnt > cap_entries) cnt = (uint32_t)(cap_entries - start);
+  const ViewParams &v = g.views[img % g.n_views];
+  const float S = st[img].S;
+  const int tx = t % g.tiles_x, ty = t / g.tiles_x;
+  const int px = tx * TW + (threadIdx.x % TW), py = ty * TH + (threadIdx.x / TW);
+  const bool inside = px < g.W && py < g.H;
+  const PixRay r = pix_ray(v, px, py);
+  unsigned long long *K = keys + (long long)img * g.pix_per_img + (long long)py * g.W + px;
+  unsigned long long best = inside ? *K : kBgKey;
+  if (threadIdx.x == 0) atomicMax(&status->max_list, cnt);
+  for (uint32_t seg = 0; seg < cnt; seg += kListCap) {
+    const int m = (int)min((uint32_t)kListCap, cnt - seg);
+    int n2 = 1;
+    while (n2 < m) n2 <<= 1;
+    for (int i = threadIdx.x; i < n2; i += NT) s_e[i] = i < m ? entries[start + seg + i] : ~0ull;
+    __syncthreads();
+    bitonic_sort_u64<NT>(s_e, n2);
+    for (int c0 = 0; c0 < m; c0 += NT) {
+      const uint32_t kmin = (uint32_t)(s_e[c0] >> 32);
+      const bool done = !inside || (uint32_t)(best >> 32) < kmin;
+      if (__syncthreads_and(done)) break;
+      const int j = c0 + threadIdx.x;
+      if (j < m) s_r[threadIdx.x] = recs[(uint32_t)s_e[j]];
+      __syncthreads();
+      const int nj = min(NT, m - c0);
+      if (!done) {
+        for (int q = 0; q < nj; ++q) {
+          const PrimRec &p = s_r[q];
+          float3 o = local_o(p.u0h, p.u0l, p.v0h, p.v0l, p.k, p.dz, r);
+          float s;
+          bool hit;
+          if (p.hl == 0.0f) {
+            hit = sphere_local(o, r, p.rad, s);
+          } else {
+            int kind;
+            float axial;
+            hit = cylinder_local(o, r, make_float3(p.ax, p.ay, p.az), p.hl, p.rad, s, kind, axial);
+          }
+          if (hit && p.zr + s >= v.znear) {
+            unsigned long long key = pack_key(p.keyc, s, S, p.id);
+            best = key < best ? key : best;
+          }
+        }
+      }
+      __syncthreads();
+    }
+    __syncthreads();
+  }
+  if (inside) *K = best;
+}
+
+// -------------------------------------------------------------- resolve --
+
+__global__ __launch_bounds__(256) void k_resolve(Geometry g, ShadeParams sh, const float4 *__restrict__ frames,
+                                                 const uint8_t *__restrict__ elem, const uint2 *__restrict__ bonds,
+                                                 const ImageState *__restrict__ st,
+                                                 const unsigned long long *__restrict__ keys, Outputs out,
+                                                 int do_ssao) {
+  const long long ppi = g.pix_per_img;
+  const long long total = ppi * g.n_img;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int img = (int)(q / ppi);
+    const long long p = q - (long long)img * ppi;
+    const int py = (int)(p / g.W), px = (int)(p - (long long)py * g.W);
+    const unsigned long long key = keys[q];
+    const uint32_t id = (uint32_t)key;
+    float *nrm = out.normal + (long long)img * 3 * ppi + p;
+    float *rgb = out.rgb + (long long)img * 3 * ppi + p;
+    if (id == kNoId) {
+      out.depth[q] = __int_as_float(0x7f800000);
+      out.id[q] = kNoId;
+      nrm[0] = nrm[ppi] = nrm[2 * ppi] = 0.0f;
+      rgb[0] = sh.bg[0];
+      rgb[ppi] = sh.bg[1];
+      rgb[2 * ppi] = sh.bg[2];
+      if (out.ao) out.ao[q] = 1.0f;
+      continue;
+    }
+    const ViewParams &v = g.views[img % g.n_views];
+    const ImageState s = st[img];
+    const float4 *X = frames + (long long)(img / g.n_views) * g.stride;
+    PrimGeom pg = prim_geom(g, v, X, bonds, id, s.zlo, s.S, false);
+    const PixRay r = pix_ray(v, px, py);
+    float3 o = local_o(pg.su.u0.hi, pg.su.u0.lo, pg.su.v0.hi, pg.su.v0.lo, pg.su.k, pg.su.dz, r);
+    float sh_s = 0.0f, axial = 0.0f;
+    int kind = 0;
+    float3 ni;
+    uint32_t atom = id;
+    if (pg.hl == 0.0f) {
+      float ou = fmaf(o.x, r.a, fmaf(o.y, r.b, o.z));
+      float oo = fmaf(o.x, o.x, fmaf(o.y, o.y, o.z * o.z));
+      float disc = fmaxf(fmaf(ou, ou, -r.uu * (oo - pg.rad * pg.rad)), 0.0f);
+      sh_s = (-ou - sqrtf(disc)) / r.uu;
+      float inv = 1.0f / pg.rad;
+      ni = make_float3((o.x + sh_s * r.a) * inv, (o.y + sh_s * r.b) * inv, (o.z + sh_s) * inv);
+    } else {
+      cylinder_local(o, r, pg.A, pg.hl, pg.rad, sh_s, kind, axial);
+      if (kind == 1) {
+        float ua = fmaf(r.a, pg.A.x, fmaf(r.b, pg.A.y, pg.A.z));
+        float oa = fmaf(o.x, pg.A.x, fmaf(o.y, pg.A.y, o.z * pg.A.z));
+        float ax = oa + sh_s * ua;
+        float inv = 1.0f / pg.rad;
+        ni = make_float3((o.x + sh_s * r.a - ax * pg.A.x) * inv, (o.y + sh_s * r.b - ax * pg.A.y) * inv,
+                         (o.z + sh_s - ax * pg.A.z) * inv);
+      } else {
+        float sg = kind == 2 ? 1.0f : -1.0f;
+        ni = make_float3(sg * pg.A.x, sg * pg.A.y, sg * pg.A.z);
+      }
+      uint2 pr = bonds[(long long)id - g.n_atoms];
+      atom = axial <= 0.0f ? pr.x : pr.y;
+    }
+    const float t = pg.su.zr + sh_s;
+    const float3 n = make_float3(ni.x, ni.y, -ni.z);  // right-handed view frame
+    const int e = elem ? (int)elem[atom] : 0;
+    const float3 alb = make_float3(sh.palette[e][0], sh.palette[e][1], sh.palette[e][2]);
+    float3 c = blinn_phong(sh, n, r, alb);
+    float aof = 1.0f;
+    if (do_ssao && sh.ssao_n > 0) {
+      // tangent frame
+      float3 a0 = fabsf(n.y) > 0.9f ? make_float3(1.0f, 0.0f, 0.0f) : make_float3(0.0f, 1.0f, 0.0f);
+      float3 T = make_float3(n.y * a0.z - n.z * a0.y, n.z * a0.x - n.x * a0.z, n.x * a0.y - n.y * a0.x);
+      float tinv = 1.0f / sqrtf(T.x * T.x + T.y * T.y + T.z * T.z);
+      T.x *= tinv;
+      T.y *= tinv;
+      T.z *= tinv;
+      float3 B = make_float3(n.y * T.z - n.z * T.y, n.z * T.x - n.x * T.z, n.x * T.y - n.y * T.x);
+      const unsigned long long *Kimg = keys + (long long)img * ppi;
+      const long long kP = (long long)(key >> 32);
+      float occ = 0.0f;
+      const float R = sh.ssao_radius;
+      for (int j = 0; j < sh.ssao_n; ++j) {
+        const float kx = sh.kernel[j][0], ky = sh.kernel[j][1], kz = sh.kernel[j][2];
+        float dx = R * (kx * T.x + ky * B.x + kz * n.x);
+        float dy = R * (kx * T.y + ky * B.y + kz * n.y);
+        float dzv = R * (kx * T.z + ky * B.z + kz * n.z);
+        float dl = -dzv;  // depth offset of the sample
+        float den = t + dl;
+        if (!(den > 0.0f)) continue;
+        float offx = v.f * (dx - r.a * dl) / den;
+        float offy = -v.f * (dy - r.b * dl) / den;
+        int ix = px + (int)floorf(0.5f + offx);
+        int iy = py + (int)floorf(0.5f + offy);
+        if (ix < 0 || iy < 0 || ix >= g.W || iy >= g.H) continue;
+        unsigned long long kf = Kimg[(long long)iy * g.W + ix];
+        if ((uint32_t)kf == kNoId) continue;
+        float dzf = (float)((long long)(kf >> 32) - kP) * s.invS;  // z_f - t
+        if (dzf <= dl - sh.ssao_bias) {
+          float adz = fabsf(dzf);
+          occ += adz <= R ? 1.0f : R / adz;
+        }
+      }
+      aof = 1.0f - occ / (float)sh.ssao_n;
+    }
+    out.depth[q] = t;
+    out.id[q] = id;
+    nrm[0] = n.x;
+    nrm[ppi] = n.y;
+    nrm[2 * ppi] = n.z;
+    rgb[0] = c.x * aof;
+    rgb[ppi] = c.y * aof;
+    rgb[2 * ppi] = c.z * aof;
+    if (out.ao) out.ao[q] = aof;
+  }
+}
+
+// ------------------------------------------------------------ launchers --
+
+static inline void ev_rec(StageEvents *e, int i, cudaStream_t st) {
+  if (e && e->ev && i < e->n) cudaEventRecord(e->ev[i], st);
+}
+
+// Shared binning front end: init, cull, finalize, setup (+splat), scan, scatter.
+cudaError_t run_binning(const Geometry &g, const Scene &sc, const Scratch &s, cudaStream_t st, StageEvents *evs,
+                        bool soft) {
+  const int sms = sm_count();
+  const long long n_tiles = (long long)g.n_img * g.tiles_per_img;
+  k_init_state<<<(g.n_img + 255) / 256, 256, 0, st>>>(s.state, g.n_img, s.status);
+  cudaMemsetAsync(s.tile_count, 0, sizeof(uint32_t) * (size_t)n_tiles, st);
+  if (!soft) cudaMemsetAsync(s.keys, 0xff, sizeof(unsigned long long) * (size_t)g.pix_per_img * g.n_img, st);
+  ev_rec(evs, 0, st);
+  {
+    long long per_frame = sc.counts ? g.stride : g.n_atoms;
+    long long blocks = (per_frame + kCullTile - 1) / kCullTile;
+    int bx = (int)(blocks < 4LL * sms ? (blocks > 0 ? blocks : 1) : 4LL * sms);
+    if (g.n_frames > 1) bx = (int)(blocks < 2LL * sms ? (blocks > 0 ? blocks : 1) : 2LL * sms);
+    dim3 grid(bx, g.n_frames);
+    k_cull_atoms<<<grid, kCullThreads, 0, st>>>(g, sc.frames, sc.counts, s.state, s.surv);
+    if (g.mode == 1 && g.n_bonds > 0 && sc.bonds) {
+      long long bb = (g.n_bonds + kCullThreads - 1) / kCullThreads;
+      int gb = (int)(bb < 8LL * sms ? bb : 8LL * sms);
+      k_cull_bonds<<<gb, kCullThreads, 0, st>>>(g, sc.frames, sc.bonds, s.state, s.surv);
+    }
+  }
+  ev_rec(evs, 1, st);
+  k_finalize<<<(g.n_img + 127) / 128, 128, 0, st>>>(g, s.state);
+  {
+    int bx = g.n_img >= 64 ? 8 : (4 * sms + g.n_img - 1) / g.n_img;
+    dim3 grid(bx, g.n_img);
+    if (soft)
+      k_setup<true><<<grid, 256, 0, st>>>(g, sc.frames, sc.bonds, s.state, s.surv, s.keys, s.recs, s.rec_img,
+                                          s.rec_of, s.tile_count, s.status, s.cap_rec);
+    else
+      k_setup<false><<<grid, 256, 0, st>>>(g, sc.frames, sc.bonds, s.state, s.surv, s.keys, s.recs, s.rec_img,
+                                           s.rec_of, s.tile_count, s.status, s.cap_rec);
+  }
+  ev_rec(evs, 2, st);
+  {
+    int nb = (int)((n_tiles + kScanItems - 1) / kScanItems);
+    unsigned long long *bs = reinterpret_cast<unsigned long long *>(s.block_sums);
+    k_scan_blocks<<<nb, 1024, 0, st>>>(s.tile_count, n_tiles, s.tile_start, bs);
+    k_scan_top<<<1, 1024, 0, st>>>(bs, nb, s.status, s.cap_entries);
+    k_scan_add<<<nb, 1024, 0, st>>>(s.tile_start, s.tile_cursor, n_tiles, bs, s.cap_entries);
+  }
+  ev_rec(evs, 3, st);
+  if (soft)
+    k_scatter<true><<<4 * sms, 256, 0, st>>>(g, s.recs, s.rec_img, s.state, s.status, s.cap_rec, s.tile_cursor,
+                                             s.entries, s.cap_entries);
+  else
+    k_scatter<false><<<4 * sms, 256, 0, st>>>(g, s.recs, s.rec_img, s.state, s.status, s.cap_rec, s.tile_cursor,
+                                              s.entries, s.cap_entries);
+  ev_rec(evs, 4, st);
+  return cudaGetLastError();
+}
+
+cudaError_t run_frame_pipeline(const Geometry &g, const ShadeParams &sh, const Scene &sc, const Scratch &s,
+                               const Outputs &out, bool ssao, cudaStream_t st, StageEvents *evs) {
+  cudaError_t e = run_binning(g, sc, s, st, evs, false);
+  if (e != cudaSuccess) return e;
+  const long long n_tiles = (long long)g.n_img * g.tiles_per_img;
+  if (g.tile_w == 16 && g.tile_h == 16)
+    k_raster<16, 16><<<(unsigned)n_tiles, 256, 0, st>>>(g, s.recs, s.entries, s.cap_entries, s.tile_count,
+                                                        s.tile_start, s.state, s.keys, s.status);
+  else if (g.tile_w == 32 && g.tile_h == 8)
+    k_raster<32, 8><<<(unsigned)n_tiles, 256, 0, st>>>(g, s.recs, s.entries, s.cap_entries, s.tile_count,
+                                                       s.tile_start, s.state, s.keys, s.status);
+  else
+    k_raster<8, 8><<<(unsigned)n_tiles, 64, 0, st>>>(g, s.recs, s.entries, s.cap_entries, s.tile_count,
+                                                     s.tile_start, s.state, s.keys, s.status);
+  ev_rec(evs, 5, st);
+  {
+    const int sms = sm_count();
+    long long total = g.pix_per_img * g.n_img;
+    long long blocks = (total + 255) / 256;
+    int gb = (int)(blocks < 16LL * sms ? blocks : 16LL * sms);
+    k_resolve<<<gb, 256, 0, st>>>(g, sh, sc.frames, sc.elem, sc.bonds, s.state, s.keys, out, ssao ? 1 : 0);
+  }
+  ev_rec(evs, 6, st);
+  return cudaGetLastError();
+}
+
+}  // namespace vtx

@@ -1,0 +1,366 @@
+// vtx_device.cuh -- device-side math of the meshless ray-caster (sm_103a).
+//
+// Every primitive the paper draws without a mesh (Methods, "Meshless
+// Representations": spheres for van der Waals / ball-and-stick atoms,
+// cylinders for bonds) is ray-cast against its implicit surface.  Doing that
+// in FP32 directly fails far from the eye: at 36,000 A an FP32 ulp is
+// 4e-3 A, which flips silhouette pixels and ruins normals.  So each
+// primitive gets a PRECISE SETUP in double-float arithmetic (pairs of FP32
+// numbers; TwoSum after Knuth, TwoProduct via FMA after Dekker 1971): its
+// projected reference point (u0, v0) in pixels, its reference depth and a
+// 32-bit fixed-point depth key.  Per pixel the ray is then expressed
+// relative to the primitive (every FP32 quantity is Angstrom-scale), which
+// keeps depth and normal errors near 1e-7 A.  FP64 is avoided: GB300 runs it
+// at a small fraction of its FP32 rate.
+//
+// Frames: the INTERNAL view frame used by the kernels is x right, y up,
+// z = depth (forward); pixel rays are u = (a, b, 1).  Reported normals are
+// in the right-handed view frame (x right, y up, z toward the viewer), i.e.
+// the internal normal with z negated.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace vtx {
+
+constexpr uint32_t kNoId = 0xFFFFFFFFu;
+constexpr unsigned long long kBgKey = ~0ull;
+constexpr long long kKeySpan = 4294966784LL;  // 2^32 - 512: object keys stay below the background key
+constexpr float kKeySpanF = 4294966784.0f;
+constexpr int kMaxViews = 16;
+constexpr int kMaxSsao = 64;
+constexpr int kMaxElem = 32;
+
+// ------------------------------------------------------------ parameters --
+
+// Per-camera constants, computed on the host in FP64 and stored as FP32.
+struct ViewParams {
+  float eye[3];
+  float R[3], U[3], F[3];  // right, up, forward exactly as passed
+  float f;                 // H / (2 tan_half_fovy): pixels per unit slope (FP32 rounding)
+  float f_hi, f_lo;        // f as a double-float
+  float inv_f;
+  float cx, cy;            // W/2, H/2
+  float znear;
+  float pad0;
+};
+
+// Launch-wide geometry shared by every stage of a frame or batch.
+struct Geometry {
+  ViewParams views[kMaxViews];
+  int n_views, n_frames, n_img;
+  int W, H;
+  int tile_w, tile_h, tiles_x, tiles_y, tiles_per_img;
+  int mode;              // 0 = vdW spheres, 1 = ball-and-stick
+  float ball_radius, bond_radius;
+  int splat_max;         // max candidate pixels for the direct splat path
+  int soft;              // 1 = soft-edge binning (dilated bounds, no splat, every survivor binned)
+  float sigma;           // soft: sigmoid width in pixels
+  long long stride;      // atom records per frame slot
+  long long n_atoms;     // atoms of frame 0 (single frame) -- primitive ids of bonds start here
+  long long n_bonds;
+  long long surv_cap;    // survivor slots per image
+  long long pix_per_img;
+};
+
+struct ShadeParams {
+  float ka, kd, ks, shin;
+  float L[3];            // normalised light direction (right-handed view frame)
+  float bg[3];
+  float palette[kMaxElem][3];
+  int n_elem;
+  int ssao_n;
+  float ssao_radius, ssao_bias;
+  float kernel[kMaxSsao][3];
+};
+
+// Per-image mutable state (device memory).
+struct ImageState {
+  unsigned int zlo_bits;  // atomicMin of max(z - R, 0) over survivors (float bits)
+  unsigned int zhi_bits;  // atomicMax of z + R over survivors
+  unsigned int n_surv;    // survivors appended (may exceed the capacity)
+  unsigned int valid;     // set by finalize when there is at least one survivor
+  float zlo, S, invS;     // key = (depth - zlo) * S
+  float pad;
+};
+
+// Launch-wide status (device memory, read back by the host).
+struct Status {
+  unsigned int n_rec;           // binned records requested
+  unsigned int overflow;        // bit 0 survivors, 1 records, 2 entries, 3 soft tile list too long
+  unsigned long long n_entries; // binned (tile, primitive) entries requested
+  unsigned int max_list;        // longest tile list seen by the raster stage
+  unsigned int pad;
+};
+
+// A binned primitive staged through shared memory (64 bytes).
+struct __align__(16) PrimRec {
+  float u0h, u0l, v0h, v0l;  // projected reference point (pixels), double-float
+  float zr, k, dz, rad;      // reference depth, A per pixel at zr, zr - centre depth, radius
+  int keyc;                  // depth key of zr (may be negative when zr < zlo)
+  uint32_t id;               // primitive id
+  uint32_t box_lo, box_hi;   // tile box: x | y << 16
+  float ax, ay, az, hl;      // cylinder axis (internal frame) and half length; hl = 0 for spheres
+};
+
+// ------------------------------------------------------ double-float ops --
+// Knuth TwoSum and Dekker/FMA TwoProduct; explicit round-to-nearest
+// intrinsics keep the compiler from fusing or reassociating them.
+
+struct df {
+  float hi, lo;
+};
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+
+__device__ __forceinline__ df df_norm(float hi, float lo) { return two_sum(hi, lo); }
+
+__device__ __forceinline__ df df_add(df a, df b) {
+  df s = two_sum(a.hi, b.hi);
+  return df_norm(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ df df_add_f(df a, float b) {
+  df s = two_sum(a.hi, b);
+  return df_norm(s.hi, __fadd_rn(s.lo, a.lo));
+}
+
+__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
+
+__device__ __forceinline__ df df_mul_f(df a, float b) {
+  float p = __fmul_rn(a.hi, b);
+  float e = __fmaf_rn(a.hi, b, -p);
+  e = __fmaf_rn(a.lo, b, e);
+  return df_norm(p, e);
+}
+
+__device__ __forceinline__ df df_mul(df a, df b) {
+  float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return df_norm(p, e);
+}
+
+__device__ __forceinline__ df df_div(df a, df b) {
+  float q1 = __fdiv_rn(a.hi, b.hi);
+  df r = df_add(a, df_neg(df_mul_f(b, q1)));
+  float q2 = __fdiv_rn(r.hi, b.hi);
+  return df_norm(q1, q2);
+}
+
+__device__ __forceinline__ df df_dot3(const float *w, df x, df y, df z) {
+  return df_add(df_add(df_mul_f(x, w[0]), df_mul_f(y, w[1])), df_mul_f(z, w[2]));
+}
+
+// ------------------------------------------------------------ per pixel --
+
+struct PixRay {
+  float pxc, pyc;  // pixel-centre coordinates (px + 0.5, py + 0.5), exact
+  float a, b;      // slopes of the ray u = (a, b, 1)
+  float uu;        // |u|^2
+};
+
+__device__ __forceinline__ PixRay pix_ray(const ViewParams &v, int px, int py) {
+  PixRay r;
+  r.pxc = (float)px + 0.5f;
+  r.pyc = (float)py + 0.5f;
+  r.a = (r.pxc - v.cx) * v.inv_f;
+  r.b = (v.cy - r.pyc) * v.inv_f;
+  r.uu = fmaf(r.a, r.a, fmaf(r.b, r.b, 1.0f));
+  return r;
+}
+
+// ---------------------------------------------------------- precise setup --
+
+struct Setup {
+  df u0, v0;   // projection of the reference point (pixels)
+  float zr;    // reference depth (FP32)
+  float dz;    // zr - centre depth (0 unless the primitive reaches the eye plane)
+  float k;     // zr / f: Angstrom per pixel at the reference depth
+  float zc;    // centre depth (FP32)
+  long long keyc;
+};
+
+__device__ __forceinline__ long long key_of(df z, float zlo, float S) {
+  df m = df_mul_f(df_add_f(z, -zlo), S);
+  float h = rintf(m.hi);
+  float fr = __fadd_rn(__fsub_rn(m.hi, h), m.lo);
+  return (long long)h + (long long)rintf(fr);
+}
+
+// d = X - eye as double-floats (exact for float32 inputs).
+// Rb: bounding radius (the reference depth is pushed to Rb + znear for a
+// primitive that reaches the eye plane, so the projection stays finite).
+__device__ __forceinline__ Setup precise_setup(const ViewParams &v, df dx, df dy, df dzw, float Rb, float zlo,
+                                               float S) {
+  df vx = df_dot3(v.R, dx, dy, dzw);
+  df vy = df_dot3(v.U, dx, dy, dzw);
+  df z = df_dot3(v.F, dx, dy, dzw);
+  Setup o;
+  float zmin = Rb + v.znear;
+  df zr = z;
+  o.dz = 0.0f;
+  if (z.hi < zmin) {
+    zr = df{zmin, 0.0f};
+    df dd = df_add(zr, df_neg(z));
+    o.dz = dd.hi + dd.lo;
+  }
+  df fdf{v.f_hi, v.f_lo};
+  df qx = df_div(vx, zr), qy = df_div(vy, zr);
+  o.u0 = df_add_f(df_mul(qx, fdf), v.cx);
+  o.v0 = df_add_f(df_neg(df_mul(qy, fdf)), v.cy);
+  o.zr = zr.hi;
+  o.zc = z.hi + z.lo;
+  o.k = zr.hi * v.inv_f;
+  o.keyc = key_of(zr, zlo, S);
+  return o;
+}
+
+__device__ __forceinline__ void eye_offset(const ViewParams &v, float4 X, df &dx, df &dy, df &dz) {
+  dx = two_sum(X.x, -v.eye[0]);
+  dy = two_sum(X.y, -v.eye[1]);
+  dz = two_sum(X.z, -v.eye[2]);
+}
+
+// Vector from the primitive's reference point to the pixel ray's point at
+// the reference depth (internal frame).  Every component is Angstrom-scale.
+__device__ __forceinline__ float3 local_o(float u0h, float u0l, float v0h, float v0l, float k, float dz,
+                                          const PixRay &r) {
+  float ox = __fsub_rn(__fsub_rn(r.pxc, u0h), u0l);
+  float oy = __fsub_rn(__fsub_rn(r.pyc, v0h), v0l);
+  return make_float3(k * ox, -k * oy, dz);
+}
+
+// Entry parameter s (depth = zr + s) of the ray o + s u into a sphere of radius rad at the origin.
+__device__ __forceinline__ bool sphere_local(float3 o, const PixRay &r, float rad, float &s) {
+  float ou = fmaf(o.x, r.a, fmaf(o.y, r.b, o.z));
+  float oo = fmaf(o.x, o.x, fmaf(o.y, o.y, o.z * o.z));
+  float disc = fmaf(ou, ou, -r.uu * (oo - rad * rad));
+  if (!(disc >= 0.0f)) return false;
+  s = (-ou - sqrtf(disc)) / r.uu;
+  return true;
+}
+
+// Entry into a capped cylinder (axis A through the origin, half length hl,
+// radius rb).  kind: 1 side, 2 cap at +hl, 3 cap at -hl.
+__device__ __forceinline__ bool cylinder_local(float3 o, const PixRay &r, float3 A, float hl, float rb, float &s,
+                                               int &kind, float &axial) {
+  float ua = fmaf(r.a, A.x, fmaf(r.b, A.y, A.z));
+  float oa = fmaf(o.x, A.x, fmaf(o.y, A.y, o.z * A.z));
+  float3 up = make_float3(r.a - ua * A.x, r.b - ua * A.y, 1.0f - ua * A.z);
+  float3 op = make_float3(o.x - oa * A.x, o.y - oa * A.y, o.z - oa * A.z);
+  float a2 = fmaf(up.x, up.x, fmaf(up.y, up.y, up.z * up.z));
+  float b2 = fmaf(op.x, up.x, fmaf(op.y, up.y, op.z * up.z));
+  float c2 = fmaf(op.x, op.x, fmaf(op.y, op.y, op.z * op.z)) - rb * rb;
+  float best = __int_as_float(0x7f800000);
+  kind = 0;
+  if (a2 > 1e-12f) {
+    float disc = fmaf(b2, b2, -a2 * c2);
+    if (disc >= 0.0f) {
+      float s1 = (-b2 - sqrtf(disc)) / a2;
+      float ax = fmaf(s1, ua, oa);
+      if (fabsf(ax) <= hl) {
+        best = s1;
+        kind = 1;
+      }
+    }
+  }
+  if (fabsf(ua) > 1e-12f) {
+#pragma unroll
+    for (int sg = 0; sg < 2; ++sg) {
+      float tgt = sg == 0 ? hl : -hl;
+      float sc = (tgt - oa) / ua;
+      float qx = fmaf(sc, up.x, op.x), qy = fmaf(sc, up.y, op.y), qz = fmaf(sc, up.z, op.z);
+      float rad2 = fmaf(qx, qx, fmaf(qy, qy, qz * qz));
+      if (rad2 <= rb * rb && sc < best) {
+        best = sc;
+        kind = sg == 0 ? 2 : 3;
+      }
+    }
+  }
+  if (kind == 0) return false;
+  s = best;
+  axial = fmaf(s, ua, oa);
+  return true;
+}
+
+__device__ __forceinline__ unsigned long long pack_key(long long keyc, float s, float S, uint32_t id) {
+  long long k = keyc + llrintf(fminf(fmaxf(s * S, -4.0e18f), 4.0e18f));
+  k = k < 0 ? 0 : (k > kKeySpan ? kKeySpan : k);
+  return ((unsigned long long)k << 32) | (unsigned long long)id;
+}
+
+// --------------------------------------------------- conservative bounds --
+
+struct PixBox {
+  int x0, x1, y0, y1;  // inclusive pixel-index ranges; empty when x0 > x1 or y0 > y1
+};
+
+// Pixel centres that a sphere (FP32 view centre vx, vy, depth z; radius R,
+// centre error bound errR) can cover.  Exact per-axis tangent-slope bounds
+// of the perspective projection, widened by an FP32 error margin.  Returns
+// false when the sphere cannot produce an accepted hit.
+__device__ __forceinline__ bool sphere_box(const ViewParams &v, int W, int H, float vx, float vy, float z, float R,
+                                           float errR, PixBox &b) {
+  float Rm = R + errR;
+  if (z + Rm < v.znear) return false;
+  if (z <= Rm * 1.01f) {  // reaches the eye plane: any pixel
+    b.x0 = 0;
+    b.x1 = W - 1;
+    b.y0 = 0;
+    b.y1 = H - 1;
+    return true;
+  }
+  float zm = z - Rm, zp = z + Rm;
+  float den = zm * zp;
+  float sx = sqrtf(fmaf(vx, vx, den)), sy = sqrtf(fmaf(vy, vy, den));
+  float mx0 = (vx * z - Rm * sx) / den, mx1 = (vx * z + Rm * sx) / den;
+  float my0 = (vy * z - Rm * sy) / den, my1 = (vy * z + Rm * sy) / den;
+  float mmax = fmaxf(fmaxf(fabsf(mx0), fabsf(mx1)), fmaxf(fabsf(my0), fabsf(my1)));
+  float mpx = 1e-4f + v.f * (mmax + 1.0f) * (1e-6f + 4e-7f * z / zm);
+  float X0 = v.cx + v.f * mx0 - mpx, X1 = v.cx + v.f * mx1 + mpx;
+  float Y0 = v.cy - v.f * my1 - mpx, Y1 = v.cy - v.f * my0 + mpx;
+  X0 = fmaxf(X0, -2.0f);
+  Y0 = fmaxf(Y0, -2.0f);
+  X1 = fminf(X1, (float)W + 2.0f);
+  Y1 = fminf(Y1, (float)H + 2.0f);
+  b.x0 = max((int)ceilf(X0 - 0.5f), 0);
+  b.x1 = min((int)floorf(X1 - 0.5f), W - 1);
+  b.y0 = max((int)ceilf(Y0 - 0.5f), 0);
+  b.y1 = min((int)floorf(Y1 - 0.5f), H - 1);
+  return b.x0 <= b.x1 && b.y0 <= b.y1;
+}
+
+// FP32 view coordinates of a world point and the bound on their error.
+__device__ __forceinline__ void view_f32(const ViewParams &v, float x, float y, float z, float &vx, float &vy,
+                                         float &vz, float &err) {
+  float dx = x - v.eye[0], dy = y - v.eye[1], dz = z - v.eye[2];
+  vx = fmaf(v.R[0], dx, fmaf(v.R[1], dy, v.R[2] * dz));
+  vy = fmaf(v.U[0], dx, fmaf(v.U[1], dy, v.U[2] * dz));
+  vz = fmaf(v.F[0], dx, fmaf(v.F[1], dy, v.F[2] * dz));
+  err = 4e-7f * (fabsf(dx) + fabsf(dy) + fabsf(dz));
+}
+
+// ------------------------------------------------------------- shading --
+
+__device__ __forceinline__ float3 blinn_phong(const ShadeParams &sh, float3 n, const PixRay &r, float3 alb) {
+  float inv = 1.0f / sqrtf(r.uu);
+  float3 V = make_float3(-r.a * inv, -r.b * inv, inv);
+  float3 Hv = make_float3(sh.L[0] + V.x, sh.L[1] + V.y, sh.L[2] + V.z);
+  float hinv = 1.0f / sqrtf(Hv.x * Hv.x + Hv.y * Hv.y + Hv.z * Hv.z);
+  float nl = n.x * sh.L[0] + n.y * sh.L[1] + n.z * sh.L[2];
+  float nh = (n.x * Hv.x + n.y * Hv.y + n.z * Hv.z) * hinv;
+  float diff = sh.ka + sh.kd * fmaxf(nl, 0.0f);
+  float spec = nl > 0.0f ? sh.ks * powf(fmaxf(nh, 0.0f), sh.shin) : 0.0f;
+  return make_float3(fminf(fmaxf(alb.x * diff + spec, 0.0f), 1.0f), fminf(fmaxf(alb.y * diff + spec, 0.0f), 1.0f),
+                     fminf(fmaxf(alb.z * diff + spec, 0.0f), 1.0f));
+}
+
+}  // namespace vtx

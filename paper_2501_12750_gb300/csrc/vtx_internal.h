@@ -1,0 +1,60 @@
+// vtx_internal.h -- host-side declarations shared by the renderer's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "vtx_device.cuh"
+
+namespace vtx {
+
+// Device buffers of one pipeline run (all owned by the context).
+struct Scratch {
+  unsigned long long *keys;   // [n_img][H][W] packed (depth key << 32 | id)
+  uint32_t *surv;             // [n_img][surv_cap] survivor primitive ids
+  ImageState *state;          // [n_img]
+  uint32_t *tile_count;       // [n_tiles]
+  uint32_t *tile_start;       // [n_tiles + 1] exclusive prefix (tile_start[n_tiles] = total, clamped)
+  uint32_t *tile_cursor;      // [n_tiles]
+  uint32_t *block_sums;       // [ceil(n_tiles / 4096) + 1]
+  PrimRec *recs;              // [cap_rec]
+  uint32_t *rec_img;          // [cap_rec] image of each record
+  uint32_t *rec_of;           // soft: [n_img][n_atoms] record of each atom
+  unsigned long long *entries;  // [cap_entries] (sort key << 32 | record or id)
+  Status *status;
+  uint32_t cap_rec;
+  unsigned long long cap_entries;
+};
+
+struct Scene {
+  const float4 *frames;       // [n_frames][stride]
+  const long long *counts;    // device [n_frames] atom counts, or null (all = n_atoms)
+  const uint8_t *elem;        // [stride] or null
+  const uint2 *bonds;         // [n_bonds] or null
+};
+
+struct Outputs {
+  float *depth;
+  uint32_t *id;
+  float *normal;
+  float *rgb;
+  float *ao;
+};
+
+struct StageEvents {
+  cudaEvent_t *ev;  // array of events, one recorded after each stage (may be null)
+  int n;
+};
+
+// Hard-edge pipeline: cull .. resolve.  Returns the first launch error.
+cudaError_t run_frame_pipeline(const Geometry &g, const ShadeParams &sh, const Scene &sc, const Scratch &s,
+                               const Outputs &out, bool ssao, cudaStream_t st, StageEvents *evs);
+
+// Soft-edge pipeline (binning shared with the hard path); backward when grad != null.
+cudaError_t run_soft_pipeline(const Geometry &g, const Scene &sc, const Scratch &s, float *cov, float *depth,
+                              float *normal, const float *g_cov, const float *g_depth, const float *g_normal,
+                              float *grad, cudaStream_t st, StageEvents *evs);
+
+int sm_count();
+
+}  // namespace vtx
