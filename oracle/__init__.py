@@ -34,13 +34,16 @@ CFLAGS = ["-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", 
 FLAG_TIE, FLAG_GRAZE, FLAG_NEAR, FLAG_SPLIT = 1, 2, 4, 16
 FLAG_GRID, FLAG_MARGIN, FLAG_FETCH = 32, 64, 128
 FLAG_CUTOFF, FLAG_ORDER, FLAG_STOP, FLAG_CLAMP = 256, 512, 1024, 2048
+FLAG_SILH = 4096    # SSAO: the pixel's hit lies within SIL_TOL (relative) of its surface's silhouette
 ID_FLAGS = FLAG_TIE | FLAG_GRAZE | FLAG_NEAR
 NO_ID = 0xFFFFFFFF
 
 TIE_TOL = 1e-4      # A: pixels whose two nearest depths differ by less are id-ambiguous
 GRAZE_TOL = 1e-6    # A: distance to a silhouette/rim/near-plane decision
-GRID_TOL = 1e-3     # px: SSAO sample distance to a pixel-grid line
-MARGIN_TOL = 1e-4   # A: SSAO occlusion-test margin
+GRID_ABS = 1e-5     # px: SSAO sample distance to a pixel-grid line ...
+GRID_LEN = 1e-5     # A: ... plus the projected size of this displacement of the sample
+MARGIN_TOL = 5e-5   # A: SSAO occlusion-test margin
+SIL_TOL = 1e-4      # relative: (R^2 - rho^2)/(2 R^2) below this makes an FP32 normal ill-conditioned
 
 SHADE_DEFAULTS = dict(ka=0.2, kd=0.7, ks=0.3, shininess=32.0,
                       light_dir=(0.25, 0.5, 1.0), background=(1.0, 1.0, 1.0))
@@ -65,10 +68,10 @@ def lib():
         L = ctypes.CDLL(_SO)
         P = ctypes.c_void_p
         i64, i32, f32, f64 = ctypes.c_int64, ctypes.c_int32, ctypes.c_float, ctypes.c_double
-        L.orc_hits.argtypes = [P, i64, P, i64, i32, f32, f32, P, P, i64, f64, f64, P, P, P, P, P, P, i32]
+        L.orc_hits.argtypes = [P, i64, P, i64, i32, f32, f32, P, P, i64, f64, f64, P, P, P, P, P, P, P, i32]
         L.orc_hits.restype = i32
         L.orc_shade.argtypes = [P, P, i64, P, P, P, i64, P, P, P, P, f64, f64, f64, f64, P, P]
-        L.orc_ssao_project.argtypes = [P, P, i64, P, P, P, P, i32, f64, f64, P, P, P]
+        L.orc_ssao_project.argtypes = [P, P, i64, P, P, P, P, i32, f64, f64, f64, P, P, P]
         L.orc_ssao_resolve.argtypes = [i64, i32, P, P, P, P, P, f64, f64, f64, P, P]
         L.orc_soft_forward.argtypes = [P, i64, P, f64, P, i64, f64, P, P, P, P, P, P, i32]
         L.orc_soft_vjp.argtypes = [P, i64, P, f64, P, i64, P, P, P, P, i32]
@@ -99,6 +102,7 @@ class Hits:
     gap: np.ndarray
     flags: np.ndarray
     side: np.ndarray
+    sil: np.ndarray
     rgb: Optional[np.ndarray] = None
     ao: Optional[np.ndarray] = None
     rgb_final: Optional[np.ndarray] = None
@@ -113,11 +117,11 @@ def hits(xyzr, cam, pix, bonds=None, mode=0, ball_radius=0.4, bond_radius=0.15,
     b = None if bonds is None else np.ascontiguousarray(bonds, dtype=np.uint32)
     P = pix.shape[0]
     out = Hits(pix=pix, depth=np.empty(P), id=np.empty(P, np.uint32), normal=np.empty((P, 3)),
-               gap=np.empty(P), flags=np.empty(P, np.int32), side=np.empty(P, np.int32))
+               gap=np.empty(P), flags=np.empty(P, np.int32), side=np.empty(P, np.int32), sil=np.empty(P))
     c = _cam(cam)
     lib().orc_hits(_p(xyzr), xyzr.shape[0], _p(b), nb, mode, ball_radius, bond_radius, _p(c), _p(pix), P,
                    tie_tol, graze_tol, _p(out.depth), _p(out.id), _p(out.normal), _p(out.gap), _p(out.flags),
-                   _p(out.side), threads)
+                   _p(out.side), _p(out.sil), threads)
     return out
 
 
@@ -136,16 +140,18 @@ def shade(h: Hits, elem, palette, n_atoms, cam, bonds=None, **kw) -> np.ndarray:
 
 
 def ssao(h: Hits, xyzr, cam, kernel, radius=2.0, bias=0.025, bonds=None, mode=0, ball_radius=0.4,
-         bond_radius=0.15, grid_tol=GRID_TOL, margin_tol=MARGIN_TOL, threads=0):
-    """AO per listed pixel; flags gain GRID / MARGIN / FETCH bits.  Fetched pixels are ray-cast on demand."""
+         bond_radius=0.15, grid_abs=GRID_ABS, grid_len=GRID_LEN, margin_tol=MARGIN_TOL, sil_tol=SIL_TOL,
+         threads=0):
+    """AO per listed pixel; flags gain GRID / MARGIN / FETCH / SILH bits.  Fetched pixels are ray-cast on demand."""
     kernel = np.ascontiguousarray(kernel, np.float32).reshape(-1, 3)
     ns = kernel.shape[0]
     P = h.pix.shape[0]
     fetch = np.empty((P, ns, 2), np.int32)
     sdepth = np.empty((P, ns))
     c = _cam(cam)
+    h.flags[(h.id != NO_ID) & (h.sil < sil_tol)] |= FLAG_SILH
     lib().orc_ssao_project(_p(c), _p(h.pix), P, _p(h.depth), _p(h.id), _p(h.normal), _p(kernel), ns, radius,
-                           grid_tol, _p(fetch), _p(sdepth), _p(h.flags))
+                           grid_abs, grid_len, _p(fetch), _p(sdepth), _p(h.flags))
     W = int(c["width"][0])
     lin = np.where(fetch[..., 0] >= 0, fetch[..., 1].astype(np.int64) * W + fetch[..., 0], -1)
     own = h.pix[:, 1].astype(np.int64) * W + h.pix[:, 0]

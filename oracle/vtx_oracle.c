@@ -187,7 +187,7 @@ static inline primhit sphere_hit(const double *C, double r, const double *u, dou
  * Works relative to the midpoint M so that nothing cancels far from the eye.
  * Optional outputs: surface normal (view space) and axial coordinate of the hit. */
 static inline primhit cylinder_hit(const double *Ci, const double *Cj, double rb, const double *u, double uu,
-                                   double znear, double graze_tol, double *normal, double *axial) {
+                                   double znear, double graze_tol, double *normal, double *axial, double *sil) {
   primhit h = {0, INFINITY, INFINITY, 0};
   double M[3] = {0.5 * (Ci[0] + Cj[0]), 0.5 * (Ci[1] + Cj[1]), 0.5 * (Ci[2] + Cj[2])};
   double Av[3] = {Cj[0] - Ci[0], Cj[1] - Ci[1], Cj[2] - Ci[2]};
@@ -240,6 +240,15 @@ static inline primhit cylinder_hit(const double *Ci, const double *Cj, double rb
   if (t < znear) return h;
   h.hit = 1;
   h.t = t;
+  if (sil) {
+    /* relative distance of the hit to the silhouette of the surface it lies on */
+    if (kind == 1) {
+      *sil = (b2 * b2 - a2 * c2) / a2 / (2.0 * rb * rb);
+    } else {
+      double qv[3] = {op[0] + best * up[0], op[1] + best * up[1], op[2] + best * up[2]};
+      *sil = (rb * rb - dot3(qv, qv)) / (2.0 * rb * rb);
+    }
+  }
   if (normal) {
     if (kind == 1) {
       for (int k = 0; k < 3; ++k) normal[k] = (op[k] + best * up[k]) / rb;
@@ -263,12 +272,14 @@ static inline double sphere_radius(int mode, float ball_radius, const float *rec
  * Outputs per pixel: depth (INFINITY for background), id (0xFFFFFFFF for
  * background), normal[3] (view space, 0 for background), gap = second minus
  * first depth, flags (ORC_FLAG_*), side (bonds: 0 when the hit lies on atom
- * i's half, 1 on atom j's; -1 otherwise).
+ * i's half, 1 on atom j's; -1 otherwise), sil = (R^2 - rho^2) / (2 R^2): how
+ * far, relative to the radius R of the surface hit, the ray passes inside
+ * that surface's silhouette (rho: ray-to-centre or ray-to-axis distance).
  */
 int orc_hits(const float *xyzr, int64_t n_atoms, const uint32_t *bonds, int64_t n_bonds, int32_t mode,
              float ball_radius, float bond_radius, const orc_camera *camera, const int32_t *pix, int64_t n_pix,
              double tie_tol, double graze_tol, double *depth, uint32_t *id, double *normal, double *gap,
-             int32_t *flags, int32_t *side, int32_t n_threads) {
+             int32_t *flags, int32_t *side, double *sil, int32_t n_threads) {
   ocam c;
   cam_load(camera, &c);
   if (mode != 1) n_bonds = 0;
@@ -315,7 +326,8 @@ int orc_hits(const float *xyzr, int64_t n_atoms, const uint32_t *bonds, int64_t 
           to_view_f(&c, xyzr + 4 * (int64_t)bonds[2 * b], Ci);
           to_view_f(&c, xyzr + 4 * (int64_t)bonds[2 * b + 1], Cj);
           for (int64_t p = p0; p < p1; ++p) {
-            primhit h = cylinder_hit(Ci, Cj, bond_radius, rays + 4 * p, rays[4 * p + 3], c.znear, graze_tol, 0, 0);
+            primhit h =
+                cylinder_hit(Ci, Cj, bond_radius, rays + 4 * p, rays[4 * p + 3], c.znear, graze_tol, 0, 0, 0);
             if (h.amb_t < my[p].tg) my[p].tg = h.amb_t;
             my[p].near |= h.near_amb;
             if (h.hit) hs_add(my + p, h.t, (uint32_t)k);
@@ -337,6 +349,7 @@ int orc_hits(const float *xyzr, int64_t n_atoms, const uint32_t *bonds, int64_t 
     id[p] = s.id1;
     gap[p] = s.t2 - s.t1;
     side[p] = -1;
+    sil[p] = 0.0;
     normal[3 * p] = normal[3 * p + 1] = normal[3 * p + 2] = 0.0;
     if (s.id1 != ORC_NO_ID) {
       double P[3] = {s.t1 * u[0], s.t1 * u[1], s.t1 * u[2]};
@@ -345,12 +358,15 @@ int orc_hits(const float *xyzr, int64_t n_atoms, const uint32_t *bonds, int64_t 
         to_view_f(&c, xyzr + 4 * (int64_t)s.id1, C);
         double r = sphere_radius(mode, ball_radius, xyzr + 4 * (int64_t)s.id1);
         for (int k = 0; k < 3; ++k) normal[3 * p + k] = (P[k] - C[k]) / r;
+        double tc = dot3(u, C) / u[3];
+        double q[3] = {C[0] - tc * u[0], C[1] - tc * u[1], C[2] - tc * u[2]};
+        sil[p] = (r * r - dot3(q, q)) / (2.0 * r * r);
       } else {
         int64_t b = (int64_t)s.id1 - n_atoms;
         double Ci[3], Cj[3], nrm[3], ax = 0.0;
         to_view_f(&c, xyzr + 4 * (int64_t)bonds[2 * b], Ci);
         to_view_f(&c, xyzr + 4 * (int64_t)bonds[2 * b + 1], Cj);
-        cylinder_hit(Ci, Cj, bond_radius, u, u[3], c.znear, graze_tol, nrm, &ax);
+        cylinder_hit(Ci, Cj, bond_radius, u, u[3], c.znear, graze_tol, nrm, &ax, sil + p);
         for (int k = 0; k < 3; ++k) normal[3 * p + k] = nrm[k];
         side[p] = ax <= 0.0 ? 0 : 1;
         if (fabs(ax) < graze_tol) fl |= ORC_FLAG_SPLIT;
@@ -420,11 +436,14 @@ void orc_shade(const uint8_t *elem, const float *palette, int64_t n_atoms, const
  * B = n x T.  Sample j is S_j = P + radius (k_x T + k_y B + k_z n), projected
  * to pixel coordinates and floored.  Output per (pixel, sample): the fetched
  * pixel (fx, fy) or (-1, -1) when off screen, and the sample's own depth.
- * A sample within grid_tol px of a grid line flags the pixel ORC_FLAG_GRID.
+ * A sample within grid_abs + grid_len f/depth(S) px of a grid line (the
+ * projected size of a grid_len Angstrom displacement) flags the pixel
+ * ORC_FLAG_GRID.
  */
 void orc_ssao_project(const orc_camera *camera, const int32_t *pix, int64_t n_pix, const double *depth,
                       const uint32_t *id, const double *normal, const float *kernel, int32_t n_samples,
-                      double radius, double grid_tol, int32_t *fetch, double *sample_depth, int32_t *flags) {
+                      double radius, double grid_abs, double grid_len, int32_t *fetch, double *sample_depth,
+                      int32_t *flags) {
   ocam c;
   cam_load(camera, &c);
   for (int64_t p = 0; p < n_pix; ++p) {
@@ -457,6 +476,7 @@ void orc_ssao_project(const orc_camera *camera, const int32_t *pix, int64_t n_pi
       if (ds <= 0.0) continue;
       double x = 0.5 * c.W * (1.0 + (S[0] / ds) / (c.th * c.aspect));
       double y = 0.5 * c.H * (1.0 - (S[1] / ds) / c.th);
+      double grid_tol = grid_abs + grid_len * c.f / ds;
       if (fabs(x - floor(x + 0.5)) < grid_tol || fabs(y - floor(y + 0.5)) < grid_tol) flags[p] |= ORC_FLAG_GRID;
       double fx = floor(x), fy = floor(y);
       if (fx < 0.0 || fy < 0.0 || fx >= c.W || fy >= c.H) continue;

@@ -43,7 +43,7 @@ struct vtx_ctx {
   vtx_camera cam;
   bool has_cam = false;
   // scratch
-  Buf keys, surv, state, tcount, tstart, tcursor, bsums, recs, recimg, recof, entries, status, counts, hostin_x,
+  Buf keys, surv, state, tcount, tstart, tcursor, bsums, recs, recimg, recbox, recof, entries, status, counts, hostin_x,
       hostin_e, hostout;
   uint32_t cap_rec = 0;
   unsigned long long cap_entries = 0;
@@ -204,8 +204,9 @@ static vtx_status prepare(vtx_ctx *c, const Geometry &g, bool soft, long long st
   }
   if ((st = ensure(c, c->recs, sizeof(PrimRec) * (size_t)c->cap_rec, "records"))) return st;
   if ((st = ensure(c, c->recimg, sizeof(uint32_t) * (size_t)c->cap_rec, "record images"))) return st;
+  if ((st = ensure(c, c->recbox, sizeof(uint2) * (size_t)c->cap_rec, "record boxes"))) return st;
   if ((st = ensure(c, c->entries, sizeof(unsigned long long) * (size_t)c->cap_entries, "entries"))) return st;
-  if (soft && (st = ensure(c, c->recof, sizeof(uint32_t) * (size_t)(n_img * stride_for_recof), "record map")))
+  if (soft &&(st = ensure(c, c->recof, sizeof(uint32_t) * (size_t)(n_img * stride_for_recof), "record map")))
     return st;
   if (!c->status.p) {
     if ((st = ensure(c, c->status, sizeof(Status), "status"))) return st;
@@ -225,6 +226,7 @@ static Scratch scratch_of(vtx_ctx *c) {
   s.block_sums = (uint32_t *)c->bsums.p;
   s.recs = (PrimRec *)c->recs.p;
   s.rec_img = (uint32_t *)c->recimg.p;
+  s.rec_box = (uint2 *)c->recbox.p;
   s.rec_of = (uint32_t *)c->recof.p;
   s.entries = (unsigned long long *)c->entries.p;
   s.status = (Status *)c->status.p;
@@ -261,6 +263,7 @@ static vtx_status check_status(vtx_ctx *c) {
   vtx_status st;
   if ((st = ensure(c, c->recs, sizeof(PrimRec) * (size_t)c->cap_rec, "records"))) return st;
   if ((st = ensure(c, c->recimg, sizeof(uint32_t) * (size_t)c->cap_rec, "record images"))) return st;
+  if ((st = ensure(c, c->recbox, sizeof(uint2) * (size_t)c->cap_rec, "record boxes"))) return st;
   if ((st = ensure(c, c->entries, sizeof(unsigned long long) * (size_t)c->cap_entries, "entries"))) return st;
   if (s.overflow & 8u) return fail(c, VTX_ERR_CAPACITY, msg);
   return fail(c, VTX_ERR_CAPACITY, msg + " (arena grown; render again)");
@@ -337,7 +340,7 @@ vtx_status vtx_destroy(vtx_ctx *c) {
   cudaStreamSynchronize(c->stream);
   drop_graphs(c);
   Buf *bufs[] = {&c->keys,   &c->surv,   &c->state,  &c->tcount,   &c->tstart,   &c->tcursor,
-                 &c->bsums,  &c->recs,   &c->recimg, &c->recof,    &c->entries,  &c->status,
+                 &c->bsums,  &c->recs,   &c->recimg, &c->recbox,   &c->recof,    &c->entries,  &c->status,
                  &c->counts, &c->hostin_x, &c->hostin_e, &c->hostout};
   for (Buf *b : bufs)
     if (b->p) cudaFree(b->p);

@@ -311,7 +311,7 @@ template <bool SOFT>
 __global__ __launch_bounds__(256) void k_setup(Geometry g, const float4 *__restrict__ frames,
                                                const uint2 *__restrict__ bonds, const ImageState *__restrict__ st,
                                                const uint32_t *__restrict__ surv, unsigned long long *keys,
-                                               PrimRec *recs, uint32_t *rec_img, uint32_t *rec_of,
+                                               PrimRec *recs, uint32_t *rec_img, uint2 *rec_box, uint32_t *rec_of,
                                                uint32_t *tile_count, Status *status, uint32_t cap_rec) {
   const int img = blockIdx.y;
   const ImageState s = st[img];
@@ -329,6 +329,7 @@ __global__ __launch_bounds__(256) void k_setup(Geometry g, const float4 *__restr
     bool binned = false;
     PrimRec rec;
     PixBox box;
+    uint2 rbox = make_uint2(0u, 0u);
     if (k < n) {
       const uint32_t id = sv[k];
       PrimGeom p = prim_geom(g, v, X, bonds, id, s.zlo, s.S, true);
@@ -359,19 +360,20 @@ __global__ __launch_bounds__(256) void k_setup(Geometry g, const float4 *__restr
           rec.rad = p.rad;
           long long kc = p.su.keyc;
           if (SOFT) {
-            // soft order key: the centre depth
+            // soft order key: the centre depth, clamped into the key range
             kc = kc - llrintf(p.su.dz * s.S);
+            kc = kc < 0 ? 0 : (kc > kKeySpan ? kKeySpan : kc);
           }
-          rec.keyc = (int)(kc < -2147483647LL ? -2147483647LL : (kc > 2147483647LL ? 2147483647LL : kc));
-          if (SOFT) rec.keyc = (int)(uint32_t)(kc < 0 ? 0 : (kc > kKeySpan ? kKeySpan : kc));
+          rec.key_lo = (uint32_t)((unsigned long long)kc & 0xffffffffull);
+          rec.key_hi = (int)(kc >> 32);
           rec.id = id;
-          int tx0 = box.x0 / g.tile_w, tx1 = box.x1 / g.tile_w, ty0 = box.y0 / g.tile_h, ty1 = box.y1 / g.tile_h;
-          rec.box_lo = (uint32_t)tx0 | ((uint32_t)ty0 << 16);
-          rec.box_hi = (uint32_t)tx1 | ((uint32_t)ty1 << 16);
+          rec.hl = p.hl;
           rec.ax = p.A.x;
           rec.ay = p.A.y;
           rec.az = p.A.z;
-          rec.hl = p.hl;
+          rec.pad = 0.0f;
+          int tx0 = box.x0 / g.tile_w, tx1 = box.x1 / g.tile_w, ty0 = box.y0 / g.tile_h, ty1 = box.y1 / g.tile_h;
+          rbox = make_uint2((uint32_t)tx0 | ((uint32_t)ty0 << 16), (uint32_t)tx1 | ((uint32_t)ty1 << 16));
         }
       }
     }
@@ -386,8 +388,9 @@ __global__ __launch_bounds__(256) void k_setup(Geometry g, const float4 *__restr
         if (slot < cap_rec) {
           recs[slot] = rec;
           rec_img[slot] = (uint32_t)img;
+          rec_box[slot] = rbox;
           if (SOFT) rec_of[(long long)img * g.n_atoms + rec.id] = slot;
-          int tx0 = rec.box_lo & 0xffff, ty0 = rec.box_lo >> 16, tx1 = rec.box_hi & 0xffff, ty1 = rec.box_hi >> 16;
+          int tx0 = rbox.x & 0xffff, ty0 = rbox.x >> 16, tx1 = rbox.y & 0xffff, ty1 = rbox.y >> 16;
           uint32_t *tc = tile_count + (long long)img * g.tiles_per_img;
           for (int ty = ty0; ty <= ty1; ++ty)
             for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(tc + ty * g.tiles_x + tx, 1u);
@@ -498,6 +501,7 @@ __global__ __launch_bounds__(1024) void k_scan_add(uint32_t *__restrict__ start,
 template <bool SOFT>
 __global__ __launch_bounds__(256) void k_scatter(Geometry g, const PrimRec *__restrict__ recs,
                                                  const uint32_t *__restrict__ rec_img,
+                                                 const uint2 *__restrict__ rec_box,
                                                  const ImageState *__restrict__ st, const Status *__restrict__ status,
                                                  uint32_t cap_rec, uint32_t *tile_cursor,
                                                  unsigned long long *entries, unsigned long long cap_entries) {
@@ -505,17 +509,18 @@ __global__ __launch_bounds__(256) void k_scatter(Geometry g, const PrimRec *__re
   for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
     const PrimRec &q = recs[r];
     const int img = (int)rec_img[r];
+    const uint2 bx = rec_box[r];
     unsigned long long key;
     if (SOFT) {
-      key = ((unsigned long long)(uint32_t)q.keyc << 32) | (unsigned long long)q.id;
+      key = ((unsigned long long)q.key_lo << 32) | (unsigned long long)q.id;
     } else {
       const float S = st[img].S;
       float Rb = q.hl == 0.0f ? q.rad : sqrtf(q.hl * q.hl + q.rad * q.rad);
-      long long kmin = (long long)q.keyc - (long long)ceilf((Rb + fabsf(q.dz)) * S * 1.000001f) - 2;
+      long long kmin = rec_key(q) - (long long)ceilf((Rb + fabsf(q.dz)) * S * 1.000001f) - 2;
       kmin = kmin < 0 ? 0 : (kmin > kKeySpan ? kKeySpan : kmin);
       key = ((unsigned long long)kmin << 32) | (unsigned long long)r;
     }
-    int tx0 = q.box_lo & 0xffff, ty0 = q.box_lo >> 16, tx1 = q.box_hi & 0xffff, ty1 = q.box_hi >> 16;
+    int tx0 = bx.x & 0xffff, ty0 = bx.x >> 16, tx1 = bx.y & 0xffff, ty1 = bx.y >> 16;
     uint32_t *cur = tile_cursor + (long long)img * g.tiles_per_img;
     for (int ty = ty0; ty <= ty1; ++ty)
       for (int tx = tx0; tx <= tx1; ++tx) {
@@ -606,7 +611,7 @@ __global__ __launch_bounds__(TW *TH) void k_raster(Geometry g, const PrimRec *__
             hit = cylinder_local(o, r, make_float3(p.ax, p.ay, p.az), p.hl, p.rad, s, kind, axial);
           }
           if (hit && p.zr + s >= v.znear) {
-            unsigned long long key = pack_key(p.keyc, s, S, p.id);
+            unsigned long long key = pack_key(rec_key(p), s, S, p.id);
             best = key < best ? key : best;
           }
         }
@@ -768,10 +773,10 @@ cudaError_t run_binning(const Geometry &g, const Scene &sc, const Scratch &s, cu
     dim3 grid(bx, g.n_img);
     if (soft)
       k_setup<true><<<grid, 256, 0, st>>>(g, sc.frames, sc.bonds, s.state, s.surv, s.keys, s.recs, s.rec_img,
-                                          s.rec_of, s.tile_count, s.status, s.cap_rec);
+                                          s.rec_box, s.rec_of, s.tile_count, s.status, s.cap_rec);
     else
       k_setup<false><<<grid, 256, 0, st>>>(g, sc.frames, sc.bonds, s.state, s.surv, s.keys, s.recs, s.rec_img,
-                                           s.rec_of, s.tile_count, s.status, s.cap_rec);
+                                           s.rec_box, s.rec_of, s.tile_count, s.status, s.cap_rec);
   }
   ev_rec(evs, 2, st);
   {
@@ -783,11 +788,11 @@ cudaError_t run_binning(const Geometry &g, const Scene &sc, const Scratch &s, cu
   }
   ev_rec(evs, 3, st);
   if (soft)
-    k_scatter<true><<<4 * sms, 256, 0, st>>>(g, s.recs, s.rec_img, s.state, s.status, s.cap_rec, s.tile_cursor,
-                                             s.entries, s.cap_entries);
+    k_scatter<true><<<4 * sms, 256, 0, st>>>(g, s.recs, s.rec_img, s.rec_box, s.state, s.status, s.cap_rec,
+                                             s.tile_cursor, s.entries, s.cap_entries);
   else
-    k_scatter<false><<<4 * sms, 256, 0, st>>>(g, s.recs, s.rec_img, s.state, s.status, s.cap_rec, s.tile_cursor,
-                                              s.entries, s.cap_entries);
+    k_scatter<false><<<4 * sms, 256, 0, st>>>(g, s.recs, s.rec_img, s.rec_box, s.state, s.status, s.cap_rec,
+                                              s.tile_cursor, s.entries, s.cap_entries);
   ev_rec(evs, 4, st);
   return cudaGetLastError();
 }

@@ -94,15 +94,21 @@ struct Status {
   unsigned int pad;
 };
 
-// A binned primitive staged through shared memory (64 bytes).
+// A binned primitive staged through shared memory (64 bytes).  Its tile box
+// lives in a separate array (only the scatter stage reads it).
 struct __align__(16) PrimRec {
   float u0h, u0l, v0h, v0l;  // projected reference point (pixels), double-float
   float zr, k, dz, rad;      // reference depth, A per pixel at zr, zr - centre depth, radius
-  int keyc;                  // depth key of zr (may be negative when zr < zlo)
+  uint32_t key_lo;           // depth key of zr, low word (soft: centre-depth sort key)
+  int key_hi;                // depth key of zr, high word (the key may leave [0, 2^32) for near-eye primitives)
   uint32_t id;               // primitive id
-  uint32_t box_lo, box_hi;   // tile box: x | y << 16
-  float ax, ay, az, hl;      // cylinder axis (internal frame) and half length; hl = 0 for spheres
+  float hl;                  // cylinder half length; 0 for spheres
+  float ax, ay, az, pad;     // cylinder axis (internal frame)
 };
+
+__device__ __forceinline__ long long rec_key(const PrimRec &p) {
+  return (long long)(((unsigned long long)(unsigned)p.key_hi << 32) | (unsigned long long)p.key_lo);
+}
 
 // ------------------------------------------------------ double-float ops --
 // Knuth TwoSum and Dekker/FMA TwoProduct; explicit round-to-nearest

@@ -19,6 +19,7 @@ struct Scratch {
   uint32_t *block_sums;       // [ceil(n_tiles / 4096) + 1]
   PrimRec *recs;              // [cap_rec]
   uint32_t *rec_img;          // [cap_rec] image of each record
+  uint2 *rec_box;             // [cap_rec] tile box of each record: (x0 | y0 << 16, x1 | y1 << 16)
   uint32_t *rec_of;           // soft: [n_img][n_atoms] record of each atom
   unsigned long long *entries;  // [cap_entries] (sort key << 32 | record or id)
   Status *status;

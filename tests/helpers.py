@@ -21,7 +21,7 @@ DEPTH_RTOL = 1e-5
 NORMAL_ATOL = 1e-4
 RGB_ATOL = 1.0 / 255.0
 AO_ATOL = 2.0 / 255.0
-SSAO_FLAGS = oracle.FLAG_GRID | oracle.FLAG_MARGIN | oracle.FLAG_FETCH
+SSAO_FLAGS = oracle.FLAG_GRID | oracle.FLAG_MARGIN | oracle.FLAG_FETCH | oracle.FLAG_SILH
 
 
 def gpu_render(scene, cam_index=0, ssao=None, mode=None, tile=(16, 16), splat_max=16, bonds=True, renderer=None):
@@ -89,7 +89,11 @@ def compare(res, h, ssao: bool, allow_excluded=0.005, label=""):
     assert cerr <= tol, "%s: rgb err %.3g" % (label, cerr)
     excl = amb | (~rgb_ok)
     frac = excl[covered].mean() if covered.any() else 0.0
-    assert frac <= allow_excluded, "%s: %.3f%% of covered pixels excluded" % (label, 100 * frac)
+    by_flag = {name: int(((h.flags & bit) != 0)[covered].sum()) for name, bit in
+               [("tie", oracle.FLAG_TIE), ("graze", oracle.FLAG_GRAZE), ("near", oracle.FLAG_NEAR),
+                ("split", oracle.FLAG_SPLIT), ("grid", oracle.FLAG_GRID), ("margin", oracle.FLAG_MARGIN),
+                ("fetch", oracle.FLAG_FETCH), ("silh", oracle.FLAG_SILH)]}
+    assert frac <= allow_excluded, "%s: %.3f%% of covered pixels excluded %s" % (label, 100 * frac, by_flag)
     return dict(pixels=n, covered=int(covered.sum()), excluded=int(excl.sum()), depth_rel=float(rel.max()),
                 normal=float(nerr), rgb=float(cerr), ao=float(aoerr))
 

@@ -43,8 +43,10 @@ def test_random_tiny_scenes(seed):
 
 def test_near_plane_and_eye_inside():
     """Spheres cut by the near plane, one enclosing the eye, one behind it."""
-    cam = scenes.look_at((0.0, 0.0, 0.35), (0.0, 0.0, 0.0), 97, 81, fovy_deg=150.0)
-    xyzr = np.array([[0, 0, 0, 0.32], [0.3, 0.1, 0.3, 0.5], [0, 0, 2.0, 1.0], [-0.5, -0.3, -1.0, 0.4]],
+    cam = scenes.look_at((0.0, 0.0, 1.0), (0.0, 0.0, 0.0), 97, 81, fovy_deg=90.0)
+    # front pole of the first sphere at depth 0.03 (< near 0.05), its rim beyond the near plane;
+    # the eye lies inside the second; the third is behind the eye
+    xyzr = np.array([[0, 0, 0, 0.97], [0.3, 0.1, 1.0, 0.5], [0, 0, 3.0, 1.0], [-0.6, -0.3, -1.0, 0.4]],
                     np.float32)
     s = scenes.Scene("near", xyzr, np.array([0, 1, 2, 3], np.uint8), [cam], ssao=False)
     res = gpu_render(s)
@@ -79,6 +81,21 @@ def test_config2_full_size_sampled_with_ssao():
     h = oracle.render_pixels(s, 0, pix, kernel=k)
     st = compare(res, h, ssao=True, label="config2")
     assert st["covered"] > 1500
+
+
+def test_config3_full_size_sampled():
+    """The benchmark frame itself: 1e8 atoms, 3840x2160, SSAO, overview view V1; sampled pixels vs the oracle."""
+    s = scenes.config3()
+    k = scenes.ssao_kernel()
+    res = gpu_render(s, ssao=k)
+    cov = res["id"] != oracle.NO_ID
+    assert cov.sum() > 100000
+    ys, xs = np.nonzero(cov)
+    j = len(xs) // 2
+    pix = sample_pixels(3840, 2160, 160, 11, windows=[(xs[j] - 6, ys[j] - 6, 12)], covered_mask=cov)
+    h = oracle.render_pixels(s, 0, pix, kernel=k)
+    st = compare(res, h, ssao=True, allow_excluded=0.01, label="config3 V1")
+    assert st["covered"] > 150
 
 
 def test_ball_and_stick_subset():
