@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="vtx", choices=["vtx", "reference"])
     ap.add_argument("--no-extra", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline (profiling runs)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--clusters", type=int, default=20000, help="blobs of 5,000 atoms (20,000 = 1e8 atoms)")
     return ap.parse_args()
@@ -264,7 +265,7 @@ def main():
         extra = run_extras(vtx, torch, dev, r)
 
     cpu = None
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and not args.no_cpu:
         cpu = oracle_baseline(s, k, 0, args.cpu_seconds)
 
     line = {

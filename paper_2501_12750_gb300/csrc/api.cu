@@ -242,6 +242,10 @@ static vtx_status check_status(vtx_ctx *c) {
   if (e != cudaSuccess) return cuda_fail(c, e, "device error");
   Status s = *c->h_status;
   if (s.overflow == 0u) return VTX_OK;
+  if (s.overflow & 16u) {
+    cudaMemsetAsync(c->status.p, 0, sizeof(Status), c->stream);
+    return fail(c, VTX_ERR_TIMEOUT, "a device-side wait for a bulk copy gave up; the frame is invalid");
+  }
   std::string msg = "scratch capacity exceeded:";
   if (s.overflow & 2u) {
     unsigned long long need = (unsigned long long)s.n_rec;

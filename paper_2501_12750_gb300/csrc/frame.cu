@@ -29,8 +29,11 @@
 namespace vtx {
 
 constexpr int kCullThreads = 256;
-constexpr int kCullPer = 8;
-constexpr int kCullTile = kCullThreads * kCullPer;
+constexpr int kStages = 4;                           // TMA pipeline depth of the cull
+constexpr int kChunk = 1024;                         // atoms per stage (16 KB)
+constexpr int kPerThread = kChunk / kCullThreads;
+constexpr size_t kCullSmem = (size_t)kStages * kChunk * sizeof(float4);
+constexpr uint32_t kWaitLimit = 1u << 24;            // polls before a wait is declared failed
 constexpr int kScanItems = 4096;  // tiles per scan block (1024 threads x 4)
 
 int sm_count() {
@@ -84,59 +87,92 @@ __device__ __forceinline__ void warp_minmax(float &lo, float &hi) {
 }
 
 // Every atom record of frame blockIdx.y is read once and tested against all
-// views of that frame.
-__global__ __launch_bounds__(kCullThreads) void k_cull_atoms(Geometry g, const float4 *__restrict__ frames,
-                                                             const long long *__restrict__ counts, ImageState *st,
-                                                             uint32_t *__restrict__ surv) {
-  __shared__ uint32_t s_idx[kCullTile];
-  __shared__ int s_cnt;
+// views of that frame.  The records stream through shared memory in
+// kStages x 16 KB stages filled by 1-D TMA bulk copies (cp.async.bulk,
+// completion on an mbarrier), so HBM reads overlap the tests of earlier
+// stages.  Survivors are compacted per view with warp ballots into shared
+// memory and appended with one global atomic per 1,024 atoms.
+__global__ __launch_bounds__(kCullThreads, 2) void k_cull_atoms(Geometry g, const float4 *__restrict__ frames,
+                                                                const long long *__restrict__ counts, ImageState *st,
+                                                                uint32_t *__restrict__ surv, Status *status) {
+  extern __shared__ __align__(128) unsigned char cull_smem[];
+  float4 *s_atoms = reinterpret_cast<float4 *>(cull_smem);
+  __shared__ __align__(8) uint64_t s_bar[kStages];
+  __shared__ uint32_t s_idx[2][kChunk];
+  __shared__ int s_cnt[2];
   __shared__ unsigned int s_base;
+  __shared__ int s_fail;
   __shared__ unsigned int s_zlo[kMaxViews], s_zhi[kMaxViews];
   const int frame = blockIdx.y;
   const long long n = counts ? counts[frame] : g.n_atoms;
   const float4 *X = frames + (long long)frame * g.stride;
+  const long long n_chunks = (n + kChunk - 1) / kChunk;
+  const long long mine = (long long)blockIdx.x < n_chunks ? (n_chunks - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int lane = threadIdx.x & 31;
   if (threadIdx.x < kMaxViews) {
     s_zlo[threadIdx.x] = 0x7f800000u;
     s_zhi[threadIdx.x] = 0u;
   }
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    s_cnt[0] = 0;
+    s_cnt[1] = 0;
+    for (int s = 0; s < kStages; ++s) mbar_init(&s_bar[s], 1u);
+    fence_mbar_init();
+  }
   __syncthreads();
-  for (long long base = (long long)blockIdx.x * kCullTile; base < n; base += (long long)gridDim.x * kCullTile) {
-    float4 a[kCullPer];
+  long long issued = 0;  // meaningful in thread 0 only
+  if (threadIdx.x == 0) {
+    for (; issued < mine && issued < kStages; ++issued) {
+      const long long a0 = ((long long)blockIdx.x + issued * gridDim.x) * kChunk;
+      const uint32_t bytes = (uint32_t)min((long long)kChunk, n - a0) * 16u;
+      const int stg = (int)(issued % kStages);
+      mbar_expect_tx(&s_bar[stg], bytes);
+      bulk_g2s(s_atoms + stg * kChunk, X + a0, bytes, &s_bar[stg]);
+    }
+  }
+  int buf = 0;
+  long long k = 0;
+  for (; k < mine; ++k) {
+    const int stg = (int)(k % kStages);
+    if (!mbar_wait_bounded(&s_bar[stg], (uint32_t)((k / kStages) & 1), kWaitLimit)) {
+      s_fail = 1;
+      atomicOr(&status->overflow, 16u);
+    }
+    const long long a0 = ((long long)blockIdx.x + k * gridDim.x) * kChunk;
+    const int cnt = (int)min((long long)kChunk, n - a0);
+    float4 a[kPerThread];
 #pragma unroll
-    for (int j = 0; j < kCullPer; ++j) {
-      long long i = base + (long long)j * kCullThreads + threadIdx.x;
-      a[j] = i < n ? __ldcs(X + i) : make_float4(0.0f, 0.0f, 0.0f, -1.0f);
+    for (int j = 0; j < kPerThread; ++j) {
+      const int i = j * kCullThreads + threadIdx.x;
+      a[j] = i < cnt ? s_atoms[stg * kChunk + i] : make_float4(0.0f, 0.0f, 0.0f, -1.0f);
     }
     for (int v = 0; v < g.n_views; ++v) {
       const ViewParams &vp = g.views[v];
-      if (threadIdx.x == 0) s_cnt = 0;
-      __syncthreads();
       float zlo = __int_as_float(0x7f800000), zhi = 0.0f;
 #pragma unroll
-      for (int j = 0; j < kCullPer; ++j) {
+      for (int j = 0; j < kPerThread; ++j) {
         bool keep = false;
         if (a[j].w >= 0.0f) {
-          float r = g.mode == 1 ? g.ball_radius : a[j].w;
+          const float r = g.mode == 1 ? g.ball_radius : a[j].w;
           float vx, vy, vz, err;
           view_f32(vp, a[j].x, a[j].y, a[j].z, vx, vy, vz, err);
-          float R = cull_radius(g, vp, r, vz);
-          PixBox b;
-          keep = sphere_box(vp, g.W, g.H, vx, vy, vz, R, err, b);
+          const float R = cull_radius(g, vp, r, vz);
+          keep = cull_fast(vp, g.W, g.H, vx, vy, vz, R, err);
           if (g.soft && !(vz > vp.znear)) keep = false;
           if (keep) {
             zlo = fminf(zlo, vz - R - err);
             zhi = fmaxf(zhi, vz + R + err);
           }
         }
-        unsigned m = __ballot_sync(0xffffffffu, keep);
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
         if (m) {
-          int leader = __ffs(m) - 1;
+          const int leader = __ffs(m) - 1;
           int pos = 0;
-          if (lane == leader) pos = atomicAdd(&s_cnt, __popc(m));
+          if (lane == leader) pos = atomicAdd(&s_cnt[buf], __popc(m));
           pos = __shfl_sync(0xffffffffu, pos, leader);
           if (keep)
-            s_idx[pos + __popc(m & ((1u << lane) - 1u))] = (uint32_t)(base + (long long)j * kCullThreads + threadIdx.x);
+            s_idx[buf][pos + __popc(m & ((1u << lane) - 1u))] = (uint32_t)(a0 + j * kCullThreads + threadIdx.x);
         }
       }
       warp_minmax(zlo, zhi);
@@ -144,18 +180,36 @@ __global__ __launch_bounds__(kCullThreads) void k_cull_atoms(Geometry g, const f
         atomicMin(&s_zlo[v], __float_as_uint(fmaxf(zlo, 0.0f)));
         atomicMax(&s_zhi[v], __float_as_uint(zhi));
       }
-      __syncthreads();
-      const int cnt = s_cnt;
-      if (cnt > 0) {
-        const int img = frame * g.n_views + v;
-        if (threadIdx.x == 0) s_base = atomicAdd(&st[img].n_surv, (unsigned)cnt);
-        __syncthreads();
-        uint32_t *dst = surv + (long long)img * g.surv_cap + s_base;
-        for (int k = threadIdx.x; k < cnt; k += kCullThreads) dst[k] = s_idx[k];
+      __syncthreads();  // survivors of this view collected; every thread holds its atoms in registers
+      const int img = frame * g.n_views + v;
+      if (threadIdx.x == 0) {
+        const int c = s_cnt[buf];
+        s_base = c ? atomicAdd(&st[img].n_surv, (unsigned)c) : 0u;
+        s_cnt[buf ^ 1] = 0;
+        if (v == 0 && issued < mine) {  // the stage is free again: refill it
+          fence_proxy_async();
+          const long long b0 = ((long long)blockIdx.x + issued * gridDim.x) * kChunk;
+          const uint32_t bytes = (uint32_t)min((long long)kChunk, n - b0) * 16u;
+          const int s2 = (int)(issued % kStages);
+          mbar_expect_tx(&s_bar[s2], bytes);
+          bulk_g2s(s_atoms + s2 * kChunk, X + b0, bytes, &s_bar[s2]);
+          ++issued;
+        }
       }
       __syncthreads();
+      const int c = s_cnt[buf];
+      uint32_t *dst = surv + (long long)img * g.surv_cap + s_base;
+      for (int i = threadIdx.x; i < c; i += kCullThreads) dst[i] = s_idx[buf][i];
+      buf ^= 1;
     }
+    if (s_fail) break;  // uniform: s_fail is only set before the first barrier of a chunk
   }
+  // drain copies still in flight (only after a failed wait)
+  if (threadIdx.x == 0) {
+    for (long long q = k; q < issued; ++q)
+      mbar_wait_bounded(&s_bar[q % kStages], (uint32_t)((q / kStages) & 1), kWaitLimit);
+  }
+  __syncthreads();
   if (threadIdx.x < g.n_views && s_zhi[threadIdx.x] != 0u) {
     const int img = frame * g.n_views + threadIdx.x;
     atomicMin(&st[img].zlo_bits, s_zlo[threadIdx.x]);
@@ -190,8 +244,7 @@ __global__ __launch_bounds__(kCullThreads) void k_cull_bonds(Geometry g, const f
       float vx, vy, vz, err;
       view_f32(vp, mx, my, mz, vx, vy, vz, err);
       err += 1.2e-7f * (fabsf(mx) + fabsf(my) + fabsf(mz)) + 1e-6f;
-      PixBox bx;
-      keep = sphere_box(vp, g.W, g.H, vx, vy, vz, Rb, err, bx);
+      keep = cull_fast(vp, g.W, g.H, vx, vy, vz, Rb, err);
       if (keep) {
         zlo = fminf(zlo, vz - Rb - err);
         zhi = fmaxf(zhi, vz + Rb + err);
@@ -754,12 +807,19 @@ cudaError_t run_binning(const Geometry &g, const Scene &sc, const Scratch &s, cu
   if (!soft) cudaMemsetAsync(s.keys, 0xff, sizeof(unsigned long long) * (size_t)g.pix_per_img * g.n_img, st);
   ev_rec(evs, 0, st);
   {
-    long long per_frame = sc.counts ? g.stride : g.n_atoms;
-    long long blocks = (per_frame + kCullTile - 1) / kCullTile;
-    int bx = (int)(blocks < 4LL * sms ? (blocks > 0 ? blocks : 1) : 4LL * sms);
-    if (g.n_frames > 1) bx = (int)(blocks < 2LL * sms ? (blocks > 0 ? blocks : 1) : 2LL * sms);
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_cull_atoms, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCullSmem);
+      attr = true;
+    }
+    // two resident CTAs per SM in total, spread over the frames of a batch
+    const long long per_frame = sc.counts ? g.stride : g.n_atoms;
+    const long long chunks = (per_frame + kChunk - 1) / kChunk;
+    long long want = (2LL * sms + g.n_frames - 1) / g.n_frames;
+    if (want < 1) want = 1;
+    int bx = (int)(chunks < want ? (chunks > 0 ? chunks : 1) : want);
     dim3 grid(bx, g.n_frames);
-    k_cull_atoms<<<grid, kCullThreads, 0, st>>>(g, sc.frames, sc.counts, s.state, s.surv);
+    k_cull_atoms<<<grid, kCullThreads, kCullSmem, st>>>(g, sc.frames, sc.counts, s.state, s.surv, s.status);
     if (g.mode == 1 && g.n_bonds > 0 && sc.bonds) {
       long long bb = (g.n_bonds + kCullThreads - 1) / kCullThreads;
       int gb = (int)(bb < 8LL * sms ? bb : 8LL * sms);

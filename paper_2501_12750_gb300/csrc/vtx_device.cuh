@@ -344,6 +344,76 @@ __device__ __forceinline__ bool sphere_box(const ViewParams &v, int W, int H, fl
   return b.x0 <= b.x1 && b.y0 <= b.y1;
 }
 
+// Cheap conservative streaming test: can the sphere (FP32 view centre, radius
+// R, centre error err) cover a pixel centre with an entry point at or beyond
+// the near plane?  One correctly rounded reciprocal and no division or square
+// root.  The exact x-extent of a projected sphere around the projected
+// centre m = vx/z is bounded by rho (|m| rho + sqrt(1 + m^2)) / (1 - rho^2),
+// rho = R/z (tangent lines in the x-z plane; same for y), which is relaxed
+// here to rho (1 + 2 rho^2)(|m| rho + 1 + m^2/2) for rho <= 1/8.  Larger or
+// nearer spheres always survive (the precise setup decides).  The box then
+// contains a pixel centre iff the nearest on-screen centre column and row do.
+__device__ __forceinline__ bool cull_fast(const ViewParams &v, int W, int H, float vx, float vy, float z, float R,
+                                          float err) {
+  const float Rm = R + err;
+  if (z + Rm < v.znear) return false;
+  if (!(z > 8.0f * Rm)) return true;
+  const float rz = __frcp_rn(z);
+  const float rho = Rm * rz;
+  const float mx = vx * rz, my = vy * rz;
+  const float k = rho * fmaf(2.0f * rho, rho, 1.0f);
+  const float hx = v.f * k * fmaf(fabsf(mx), rho, fmaf(0.5f * mx, mx, 1.0f));
+  const float hy = v.f * k * fmaf(fabsf(my), rho, fmaf(0.5f * my, my, 1.0f));
+  const float ux = fmaf(v.f, mx, v.cx - 0.5f), uy = fmaf(-v.f, my, v.cy - 0.5f);
+  // FP32 rounding of this test (reciprocal, products, the pixel coordinate itself)
+  const float ex = 1e-4f + 4e-6f * hx + 4e-7f * v.f * (fabsf(mx) + 1.0f) + 2.5e-7f * fabsf(ux);
+  const float ey = 1e-4f + 4e-6f * hy + 4e-7f * v.f * (fabsf(my) + 1.0f) + 2.5e-7f * fabsf(uy);
+  const float nx = fminf(fmaxf(rintf(ux), 0.0f), (float)(W - 1));
+  const float ny = fminf(fmaxf(rintf(uy), 0.0f), (float)(H - 1));
+  return fabsf(ux - nx) <= hx + ex && fabsf(uy - ny) <= hy + ey;
+}
+
+// ------------------------------------------------- TMA bulk copy helpers --
+// 1-D bulk copies global -> shared completed on an mbarrier (sm_90+ PTX).
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+
+// Bounded wait: gives up after `limit` polls (each poll may suspend briefly).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t limit) {
+  for (uint32_t i = 0; i < limit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
 // FP32 view coordinates of a world point and the bound on their error.
 __device__ __forceinline__ void view_f32(const ViewParams &v, float x, float y, float z, float &vx, float &vy,
                                          float &vz, float &err) {

@@ -89,7 +89,7 @@ def test_config3_full_size_sampled():
     k = scenes.ssao_kernel()
     res = gpu_render(s, ssao=k)
     cov = res["id"] != oracle.NO_ID
-    assert cov.sum() > 100000
+    assert cov.sum() > 50000
     ys, xs = np.nonzero(cov)
     j = len(xs) // 2
     pix = sample_pixels(3840, 2160, 160, 11, windows=[(xs[j] - 6, ys[j] - 6, 12)], covered_mask=cov)
