@@ -98,9 +98,10 @@ __global__ __launch_bounds__(kCullThreads, 2) void k_cull_atoms(Geometry g, cons
   extern __shared__ __align__(128) unsigned char cull_smem[];
   float4 *s_atoms = reinterpret_cast<float4 *>(cull_smem);
   __shared__ __align__(8) uint64_t s_bar[kStages];
-  __shared__ uint32_t s_idx[2][kChunk];
-  __shared__ int s_cnt[2];
-  __shared__ unsigned int s_base;
+  __shared__ uint32_t s_idx[3][kChunk];
+  __shared__ int s_cnt[3];
+  __shared__ unsigned int s_pub_base;
+  __shared__ int s_pub_cnt, s_pub_img;
   __shared__ int s_fail;
   __shared__ unsigned int s_zlo[kMaxViews], s_zhi[kMaxViews];
   const int frame = blockIdx.y;
@@ -117,6 +118,7 @@ __global__ __launch_bounds__(kCullThreads, 2) void k_cull_atoms(Geometry g, cons
     s_fail = 0;
     s_cnt[0] = 0;
     s_cnt[1] = 0;
+    s_cnt[2] = 0;
     for (int s = 0; s < kStages; ++s) mbar_init(&s_bar[s], 1u);
     fence_mbar_init();
   }
@@ -131,7 +133,12 @@ __global__ __launch_bounds__(kCullThreads, 2) void k_cull_atoms(Geometry g, cons
       bulk_g2s(s_atoms + stg * kChunk, X + a0, bytes, &s_bar[stg]);
     }
   }
-  int buf = 0;
+  // Survivors of unit u = (chunk, view) collect in s_idx[u % 3]; the global
+  // atomic that reserves their slots is issued at unit u and its result is
+  // consumed one unit later, so its latency hides behind the next unit.
+  long long u = 0;
+  unsigned int pend_base = 0u;  // thread 0: atomic result of the previous unit
+  int pend_cnt = 0, pend_img = 0;
   long long k = 0;
   for (; k < mine; ++k) {
     const int stg = (int)(k % kStages);
@@ -147,7 +154,8 @@ __global__ __launch_bounds__(kCullThreads, 2) void k_cull_atoms(Geometry g, cons
       const int i = j * kCullThreads + threadIdx.x;
       a[j] = i < cnt ? s_atoms[stg * kChunk + i] : make_float4(0.0f, 0.0f, 0.0f, -1.0f);
     }
-    for (int v = 0; v < g.n_views; ++v) {
+    for (int v = 0; v < g.n_views; ++v, ++u) {
+      const int b = (int)(u % 3);
       const ViewParams &vp = g.views[v];
       float zlo = __int_as_float(0x7f800000), zhi = 0.0f;
 #pragma unroll
@@ -169,10 +177,9 @@ __global__ __launch_bounds__(kCullThreads, 2) void k_cull_atoms(Geometry g, cons
         if (m) {
           const int leader = __ffs(m) - 1;
           int pos = 0;
-          if (lane == leader) pos = atomicAdd(&s_cnt[buf], __popc(m));
+          if (lane == leader) pos = atomicAdd(&s_cnt[b], __popc(m));
           pos = __shfl_sync(0xffffffffu, pos, leader);
-          if (keep)
-            s_idx[buf][pos + __popc(m & ((1u << lane) - 1u))] = (uint32_t)(a0 + j * kCullThreads + threadIdx.x);
+          if (keep) s_idx[b][pos + __popc(m & ((1u << lane) - 1u))] = (uint32_t)(a0 + j * kCullThreads + threadIdx.x);
         }
       }
       warp_minmax(zlo, zhi);
@@ -180,12 +187,19 @@ __global__ __launch_bounds__(kCullThreads, 2) void k_cull_atoms(Geometry g, cons
         atomicMin(&s_zlo[v], __float_as_uint(fmaxf(zlo, 0.0f)));
         atomicMax(&s_zhi[v], __float_as_uint(zhi));
       }
-      __syncthreads();  // survivors of this view collected; every thread holds its atoms in registers
-      const int img = frame * g.n_views + v;
+      __syncthreads();  // (A) unit u collected; every thread holds its atoms in registers
       if (threadIdx.x == 0) {
-        const int c = s_cnt[buf];
-        s_base = c ? atomicAdd(&st[img].n_surv, (unsigned)c) : 0u;
-        s_cnt[buf ^ 1] = 0;
+        // publish the previous unit's reservation (its atomic has long returned)
+        s_pub_base = pend_base;
+        s_pub_cnt = pend_cnt;
+        s_pub_img = pend_img;
+        // reserve this unit's slots; the result is only read at the next unit
+        const int img = frame * g.n_views + v;
+        const int c = s_cnt[b];
+        pend_base = c ? atomicAdd(&st[img].n_surv, (unsigned)c) : 0u;
+        pend_cnt = c;
+        pend_img = img;
+        s_cnt[(b + 1) % 3] = 0;
         if (v == 0 && issued < mine) {  // the stage is free again: refill it
           fence_proxy_async();
           const long long b0 = ((long long)blockIdx.x + issued * gridDim.x) * kChunk;
@@ -196,13 +210,29 @@ __global__ __launch_bounds__(kCullThreads, 2) void k_cull_atoms(Geometry g, cons
           ++issued;
         }
       }
-      __syncthreads();
-      const int c = s_cnt[buf];
-      uint32_t *dst = surv + (long long)img * g.surv_cap + s_base;
-      for (int i = threadIdx.x; i < c; i += kCullThreads) dst[i] = s_idx[buf][i];
-      buf ^= 1;
+      __syncthreads();  // (B)
+      {  // write out the previous unit
+        const int c = s_pub_cnt;
+        const int pb = (int)((u + 2) % 3);
+        uint32_t *dst = surv + (long long)s_pub_img * g.surv_cap + s_pub_base;
+        for (int i = threadIdx.x; i < c; i += kCullThreads) dst[i] = s_idx[pb][i];
+      }
     }
-    if (s_fail) break;  // uniform: s_fail is only set before the first barrier of a chunk
+    if (s_fail) break;  // uniform: s_fail is only written before barrier (A) of a chunk
+  }
+  // the last unit's survivors
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s_pub_base = pend_base;
+    s_pub_cnt = pend_cnt;
+    s_pub_img = pend_img;
+  }
+  __syncthreads();
+  {
+    const int c = s_pub_cnt;
+    const int pb = (int)((u + 2) % 3);
+    uint32_t *dst = surv + (long long)s_pub_img * g.surv_cap + s_pub_base;
+    for (int i = threadIdx.x; i < c; i += kCullThreads) dst[i] = s_idx[pb][i];
   }
   // drain copies still in flight (only after a failed wait)
   if (threadIdx.x == 0) {
@@ -684,12 +714,13 @@ __global__ __launch_bounds__(256) void k_resolve(Geometry g, ShadeParams sh, con
                                                  const unsigned long long *__restrict__ keys, Outputs out,
                                                  int do_ssao) {
   const long long ppi = g.pix_per_img;
-  const long long total = ppi * g.n_img;
-  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
-       q += (long long)gridDim.x * blockDim.x) {
-    const int img = (int)(q / ppi);
-    const long long p = q - (long long)img * ppi;
-    const int py = (int)(p / g.W), px = (int)(p - (long long)py * g.W);
+  // one 32x8 pixel block per CTA, blockIdx.z = image: no integer division per pixel
+  const int px = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int py = blockIdx.y * 8 + (threadIdx.x >> 5);
+  const int img = blockIdx.z;
+  if (px < g.W && py < g.H) {
+    const long long p = (long long)py * g.W + px;
+    const long long q = (long long)img * ppi + p;
     const unsigned long long key = keys[q];
     const uint32_t id = (uint32_t)key;
     float *nrm = out.normal + (long long)img * 3 * ppi + p;
@@ -702,7 +733,7 @@ __global__ __launch_bounds__(256) void k_resolve(Geometry g, ShadeParams sh, con
       rgb[ppi] = sh.bg[1];
       rgb[2 * ppi] = sh.bg[2];
       if (out.ao) out.ao[q] = 1.0f;
-      continue;
+      return;
     }
     const ViewParams &v = g.views[img % g.n_views];
     const ImageState s = st[img];
@@ -873,11 +904,8 @@ cudaError_t run_frame_pipeline(const Geometry &g, const ShadeParams &sh, const S
                                                      s.tile_start, s.state, s.keys, s.status);
   ev_rec(evs, 5, st);
   {
-    const int sms = sm_count();
-    long long total = g.pix_per_img * g.n_img;
-    long long blocks = (total + 255) / 256;
-    int gb = (int)(blocks < 16LL * sms ? blocks : 16LL * sms);
-    k_resolve<<<gb, 256, 0, st>>>(g, sh, sc.frames, sc.elem, sc.bonds, s.state, s.keys, out, ssao ? 1 : 0);
+    dim3 grid((g.W + 31) / 32, (g.H + 7) / 8, g.n_img);
+    k_resolve<<<grid, 256, 0, st>>>(g, sh, sc.frames, sc.elem, sc.bonds, s.state, s.keys, out, ssao ? 1 : 0);
   }
   ev_rec(evs, 6, st);
   return cudaGetLastError();

@@ -92,9 +92,9 @@ def test_config3_full_size_sampled():
     assert cov.sum() > 50000
     ys, xs = np.nonzero(cov)
     j = len(xs) // 2
-    pix = sample_pixels(3840, 2160, 160, 11, windows=[(xs[j] - 6, ys[j] - 6, 12)], covered_mask=cov)
+    pix = sample_pixels(3840, 2160, 240, 11, windows=[(xs[j] - 6, ys[j] - 6, 12)], covered_mask=cov)
     h = oracle.render_pixels(s, 0, pix, kernel=k)
-    st = compare(res, h, ssao=True, allow_excluded=0.01, label="config3 V1")
+    st = compare(res, h, ssao=True, allow_excluded=0.02, label="config3 V1")
     assert st["covered"] > 150
 
 
