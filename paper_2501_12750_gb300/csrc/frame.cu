@@ -29,7 +29,7 @@
 namespace vtx {
 
 constexpr int kCullThreads = 256;
-constexpr int kStages = 4;                           // TMA pipeline depth of the cull
+constexpr int kStages = 3;                           // TMA pipeline depth of the cull
 constexpr int kChunk = 1024;                         // atoms per stage (16 KB)
 constexpr int kPerThread = kChunk / kCullThreads;
 constexpr size_t kCullSmem = (size_t)kStages * kChunk * sizeof(float4);
@@ -92,11 +92,15 @@ __device__ __forceinline__ void warp_minmax(float &lo, float &hi) {
 // completion on an mbarrier), so HBM reads overlap the tests of earlier
 // stages.  Survivors are compacted per view with warp ballots into shared
 // memory and appended with one global atomic per 1,024 atoms.
-__global__ __launch_bounds__(kCullThreads, 2) void k_cull_atoms(Geometry g, const float4 *__restrict__ frames,
+// ONE_VIEW: a single camera, whose constants are then compile-time indexed
+// kernel parameters; otherwise the views are read from a shared-memory copy.
+template <bool ONE_VIEW>
+__global__ __launch_bounds__(kCullThreads, 3) void k_cull_atoms(Geometry g, const float4 *__restrict__ frames,
                                                                 const long long *__restrict__ counts, ImageState *st,
                                                                 uint32_t *__restrict__ surv, Status *status) {
   extern __shared__ __align__(128) unsigned char cull_smem[];
   float4 *s_atoms = reinterpret_cast<float4 *>(cull_smem);
+  __shared__ ViewParams s_views[ONE_VIEW ? 1 : kMaxViews];
   __shared__ __align__(8) uint64_t s_bar[kStages];
   __shared__ uint32_t s_idx[3][kChunk];
   __shared__ int s_cnt[3];
@@ -113,7 +117,9 @@ __global__ __launch_bounds__(kCullThreads, 2) void k_cull_atoms(Geometry g, cons
   if (threadIdx.x < kMaxViews) {
     s_zlo[threadIdx.x] = 0x7f800000u;
     s_zhi[threadIdx.x] = 0u;
+    if (!ONE_VIEW && threadIdx.x < g.n_views) s_views[threadIdx.x] = g.views[threadIdx.x];
   }
+  const int n_views = ONE_VIEW ? 1 : g.n_views;
   if (threadIdx.x == 0) {
     s_fail = 0;
     s_cnt[0] = 0;
@@ -154,9 +160,9 @@ __global__ __launch_bounds__(kCullThreads, 2) void k_cull_atoms(Geometry g, cons
       const int i = j * kCullThreads + threadIdx.x;
       a[j] = i < cnt ? s_atoms[stg * kChunk + i] : make_float4(0.0f, 0.0f, 0.0f, -1.0f);
     }
-    for (int v = 0; v < g.n_views; ++v, ++u) {
+    for (int v = 0; v < n_views; ++v, ++u) {
       const int b = (int)(u % 3);
-      const ViewParams &vp = g.views[v];
+      const ViewParams &vp = ONE_VIEW ? g.views[0] : s_views[v];
       float zlo = __int_as_float(0x7f800000), zhi = 0.0f;
 #pragma unroll
       for (int j = 0; j < kPerThread; ++j) {
@@ -240,7 +246,7 @@ __global__ __launch_bounds__(kCullThreads, 2) void k_cull_atoms(Geometry g, cons
       mbar_wait_bounded(&s_bar[q % kStages], (uint32_t)((q / kStages) & 1), kWaitLimit);
   }
   __syncthreads();
-  if (threadIdx.x < g.n_views && s_zhi[threadIdx.x] != 0u) {
+  if (threadIdx.x < n_views && s_zhi[threadIdx.x] != 0u) {
     const int img = frame * g.n_views + threadIdx.x;
     atomicMin(&st[img].zlo_bits, s_zlo[threadIdx.x]);
     atomicMax(&st[img].zhi_bits, s_zhi[threadIdx.x]);
@@ -840,17 +846,21 @@ cudaError_t run_binning(const Geometry &g, const Scene &sc, const Scratch &s, cu
   {
     static bool attr = false;
     if (!attr) {
-      cudaFuncSetAttribute(k_cull_atoms, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCullSmem);
+      cudaFuncSetAttribute(k_cull_atoms<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCullSmem);
+      cudaFuncSetAttribute(k_cull_atoms<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCullSmem);
       attr = true;
     }
-    // two resident CTAs per SM in total, spread over the frames of a batch
+    // three resident CTAs per SM in total, spread over the frames of a batch
     const long long per_frame = sc.counts ? g.stride : g.n_atoms;
     const long long chunks = (per_frame + kChunk - 1) / kChunk;
-    long long want = (2LL * sms + g.n_frames - 1) / g.n_frames;
+    long long want = (3LL * sms + g.n_frames - 1) / g.n_frames;
     if (want < 1) want = 1;
     int bx = (int)(chunks < want ? (chunks > 0 ? chunks : 1) : want);
     dim3 grid(bx, g.n_frames);
-    k_cull_atoms<<<grid, kCullThreads, kCullSmem, st>>>(g, sc.frames, sc.counts, s.state, s.surv, s.status);
+    if (g.n_views == 1)
+      k_cull_atoms<true><<<grid, kCullThreads, kCullSmem, st>>>(g, sc.frames, sc.counts, s.state, s.surv, s.status);
+    else
+      k_cull_atoms<false><<<grid, kCullThreads, kCullSmem, st>>>(g, sc.frames, sc.counts, s.state, s.surv, s.status);
     if (g.mode == 1 && g.n_bonds > 0 && sc.bonds) {
       long long bb = (g.n_bonds + kCullThreads - 1) / kCullThreads;
       int gb = (int)(bb < 8LL * sms ? bb : 8LL * sms);

@@ -154,10 +154,14 @@ __device__ __forceinline__ df df_mul(df a, df b) {
   return df_norm(p, e);
 }
 
+// a / b.  The first quotient only needs ~23 correct bits: the remainder
+// a - q1 b is formed exactly (FMA TwoProduct) and its quotient corrects q1,
+// leaving a relative error near 2^-44, so a reciprocal multiply suffices.
 __device__ __forceinline__ df df_div(df a, df b) {
-  float q1 = __fdiv_rn(a.hi, b.hi);
+  const float rb = __frcp_rn(b.hi);
+  float q1 = __fmul_rn(a.hi, rb);
   df r = df_add(a, df_neg(df_mul_f(b, q1)));
-  float q2 = __fdiv_rn(r.hi, b.hi);
+  float q2 = __fmul_rn(r.hi, rb);
   return df_norm(q1, q2);
 }
 
