@@ -115,6 +115,12 @@ static ViewParams make_view(const vtx_camera &cam) {
   v.cy = 0.5f * (float)cam.height;
   v.znear = cam.znear;
   v.pad0 = 0.0f;
+  v.hc = (float)(f * (1.0 + 4e-6));
+  v.e0 = (float)(1e-4 + 1e-6 * ((double)cam.width + (double)cam.height));
+  v.cxm = v.cx - 0.5f;
+  v.cym = v.cy - 0.5f;
+  v.wm1 = (float)(cam.width - 1);
+  v.hm1 = (float)(cam.height - 1);
   return v;
 }
 

@@ -142,13 +142,15 @@ __global__ __launch_bounds__(kCullThreads, 3) void k_cull_atoms(Geometry g, cons
   // Survivors of unit u = (chunk, view) collect in s_idx[u % 3]; the global
   // atomic that reserves their slots is issued at unit u and its result is
   // consumed one unit later, so its latency hides behind the next unit.
-  long long u = 0;
+  int ub = 0;  // buffer of the current unit: u % 3
+  int stg = 0;
+  uint32_t phase = 0u;
   unsigned int pend_base = 0u;  // thread 0: atomic result of the previous unit
   int pend_cnt = 0, pend_img = 0;
   long long k = 0;
   for (; k < mine; ++k) {
-    const int stg = (int)(k % kStages);
-    if (!mbar_wait_bounded(&s_bar[stg], (uint32_t)((k / kStages) & 1), kWaitLimit)) {
+    // stage k % kStages, parity (k / kStages) & 1
+    if (!mbar_wait_bounded(&s_bar[stg], phase, kWaitLimit)) {
       s_fail = 1;
       atomicOr(&status->overflow, 16u);
     }
@@ -160,8 +162,8 @@ __global__ __launch_bounds__(kCullThreads, 3) void k_cull_atoms(Geometry g, cons
       const int i = j * kCullThreads + threadIdx.x;
       a[j] = i < cnt ? s_atoms[stg * kChunk + i] : make_float4(0.0f, 0.0f, 0.0f, -1.0f);
     }
-    for (int v = 0; v < n_views; ++v, ++u) {
-      const int b = (int)(u % 3);
+    for (int v = 0; v < n_views; ++v, ub = ub == 2 ? 0 : ub + 1) {
+      const int b = ub;
       const ViewParams &vp = ONE_VIEW ? g.views[0] : s_views[v];
       float zlo = __int_as_float(0x7f800000), zhi = 0.0f;
 #pragma unroll
@@ -172,7 +174,7 @@ __global__ __launch_bounds__(kCullThreads, 3) void k_cull_atoms(Geometry g, cons
           float vx, vy, vz, err;
           view_f32(vp, a[j].x, a[j].y, a[j].z, vx, vy, vz, err);
           const float R = cull_radius(g, vp, r, vz);
-          keep = cull_fast(vp, g.W, g.H, vx, vy, vz, R, err);
+          keep = cull_lean(vp, vx, vy, vz, R + err);
           if (g.soft && !(vz > vp.znear)) keep = false;
           if (keep) {
             zlo = fminf(zlo, vz - R - err);
@@ -219,10 +221,14 @@ __global__ __launch_bounds__(kCullThreads, 3) void k_cull_atoms(Geometry g, cons
       __syncthreads();  // (B)
       {  // write out the previous unit
         const int c = s_pub_cnt;
-        const int pb = (int)((u + 2) % 3);
+        const int pb = b == 0 ? 2 : b - 1;
         uint32_t *dst = surv + (long long)s_pub_img * g.surv_cap + s_pub_base;
         for (int i = threadIdx.x; i < c; i += kCullThreads) dst[i] = s_idx[pb][i];
       }
+    }
+    if (++stg == kStages) {
+      stg = 0;
+      phase ^= 1u;
     }
     if (s_fail) break;  // uniform: s_fail is only written before barrier (A) of a chunk
   }
@@ -236,7 +242,7 @@ __global__ __launch_bounds__(kCullThreads, 3) void k_cull_atoms(Geometry g, cons
   __syncthreads();
   {
     const int c = s_pub_cnt;
-    const int pb = (int)((u + 2) % 3);
+    const int pb = ub == 0 ? 2 : ub - 1;
     uint32_t *dst = surv + (long long)s_pub_img * g.surv_cap + s_pub_base;
     for (int i = threadIdx.x; i < c; i += kCullThreads) dst[i] = s_idx[pb][i];
   }
@@ -280,7 +286,7 @@ __global__ __launch_bounds__(kCullThreads) void k_cull_bonds(Geometry g, const f
       float vx, vy, vz, err;
       view_f32(vp, mx, my, mz, vx, vy, vz, err);
       err += 1.2e-7f * (fabsf(mx) + fabsf(my) + fabsf(mz)) + 1e-6f;
-      keep = cull_fast(vp, g.W, g.H, vx, vy, vz, Rb, err);
+      keep = cull_lean(vp, vx, vy, vz, Rb + err);
       if (keep) {
         zlo = fminf(zlo, vz - Rb - err);
         zhi = fmaxf(zhi, vz + Rb + err);
@@ -397,7 +403,7 @@ __device__ __forceinline__ bool prim_hit(const PrimGeom &p, float3 o, const PixR
 }
 
 template <bool SOFT>
-__global__ __launch_bounds__(256) void k_setup(Geometry g, const float4 *__restrict__ frames,
+__global__ __launch_bounds__(256, 3) void k_setup(Geometry g, const float4 *__restrict__ frames,
                                                const uint2 *__restrict__ bonds, const ImageState *__restrict__ st,
                                                const uint32_t *__restrict__ surv, unsigned long long *keys,
                                                PrimRec *recs, uint32_t *rec_img, uint2 *rec_box, uint32_t *rec_of,
@@ -423,7 +429,7 @@ __global__ __launch_bounds__(256) void k_setup(Geometry g, const float4 *__restr
       const uint32_t id = sv[k];
       PrimGeom p = prim_geom(g, v, X, bonds, id, s.zlo, s.S, true);
       float Rbox = p.hl == 0.0f ? cull_radius(g, v, p.rad, p.vz) : p.Rb;
-      bool any = sphere_box(v, g.W, g.H, p.vx, p.vy, p.vz, Rbox, p.err, box);
+      bool any = lean_box(v, g.W, g.H, p.vx, p.vy, p.vz, Rbox + p.err, box);
       if (any) {
         const long long npx = (long long)(box.x1 - box.x0 + 1) * (long long)(box.y1 - box.y0 + 1);
         if (!SOFT && npx <= g.splat_max) {
@@ -714,7 +720,7 @@ __global__ __launch_bounds__(TW *TH) void k_raster(Geometry g, const PrimRec *__
 
 // -------------------------------------------------------------- resolve --
 
-__global__ __launch_bounds__(256) void k_resolve(Geometry g, ShadeParams sh, const float4 *__restrict__ frames,
+__global__ __launch_bounds__(256, 4) void k_resolve(Geometry g, ShadeParams sh, const float4 *__restrict__ frames,
                                                  const uint8_t *__restrict__ elem, const uint2 *__restrict__ bonds,
                                                  const ImageState *__restrict__ st,
                                                  const unsigned long long *__restrict__ keys, Outputs out,

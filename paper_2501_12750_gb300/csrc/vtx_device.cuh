@@ -44,6 +44,11 @@ struct ViewParams {
   float cx, cy;            // W/2, H/2
   float znear;
   float pad0;
+  // constants of the streaming cull test (cull_lean)
+  float hc;                // f * (1 + 4e-6): pixels per slope, inflated by the test's relative rounding
+  float e0;                // absolute pixel margin: 1e-4 + 1e-6 * (W + H)
+  float cxm, cym;          // cx - 0.5, cy - 0.5
+  float wm1, hm1;          // W - 1, H - 1
 };
 
 // Launch-wide geometry shared by every stage of a frame or batch.
@@ -375,6 +380,54 @@ __device__ __forceinline__ bool cull_fast(const ViewParams &v, int W, int H, flo
   const float nx = fminf(fmaxf(rintf(ux), 0.0f), (float)(W - 1));
   const float ny = fminf(fmaxf(rintf(uy), 0.0f), (float)(H - 1));
   return fabsf(ux - nx) <= hx + ex && fabsf(uy - ny) <= hy + ey;
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// The same test as cull_fast with its rounding margins folded into per-view
+// constants (ViewParams::hc, e0) and a 1-ulp approximate reciprocal:
+//   reciprocal and products: <= 3.6e-7 relative on the slopes, i.e. at most
+//   3.6e-7 (|u| + cx) px on the centre column u, and |u| <= W + h wherever
+//   the test can pass; FP32 rounding of f: 6e-8 relative; rounding of h:
+//   <= 7e-7 relative.  e0 = 1e-4 + 1e-6 (W + H) px and hc = f (1 + 4e-6)
+//   cover these.  Rm already includes the error of the FP32 view centre.
+__device__ __forceinline__ bool cull_lean(const ViewParams &v, float vx, float vy, float vz, float Rm) {
+  if (!(vz + Rm >= v.znear)) return false;
+  if (!(vz > 8.0f * Rm)) return true;
+  const float rz = rcp_approx(vz);
+  const float rho = Rm * rz;
+  const float mx = vx * rz, my = vy * rz;
+  const float t = v.hc * rho * fmaf(2.0f * rho, rho, 1.0f);
+  const float hx = fmaf(t, fmaf(fabsf(mx), rho, fmaf(0.5f * mx, mx, 1.0f)), v.e0);
+  const float hy = fmaf(t, fmaf(fabsf(my), rho, fmaf(0.5f * my, my, 1.0f)), v.e0);
+  const float ux = fmaf(v.f, mx, v.cxm), uy = fmaf(-v.f, my, v.cym);
+  const float nx = fminf(fmaxf(rintf(ux), 0.0f), v.wm1);
+  const float ny = fminf(fmaxf(rintf(uy), 0.0f), v.hm1);
+  return fabsf(ux - nx) <= hx && fabsf(uy - ny) <= hy;
+}
+
+// Candidate pixel box of a sphere from the cull_lean bound (the exact
+// tangent-slope box for spheres that come within 8 radii of the eye plane).
+__device__ __forceinline__ bool lean_box(const ViewParams &v, int W, int H, float vx, float vy, float vz, float Rm,
+                                         PixBox &b) {
+  if (!(vz + Rm >= v.znear)) return false;
+  if (!(vz > 8.0f * Rm)) return sphere_box(v, W, H, vx, vy, vz, Rm, 0.0f, b);
+  const float rz = rcp_approx(vz);
+  const float rho = Rm * rz;
+  const float mx = vx * rz, my = vy * rz;
+  const float t = v.hc * rho * fmaf(2.0f * rho, rho, 1.0f);
+  const float hx = fmaf(t, fmaf(fabsf(mx), rho, fmaf(0.5f * mx, mx, 1.0f)), v.e0);
+  const float hy = fmaf(t, fmaf(fabsf(my), rho, fmaf(0.5f * my, my, 1.0f)), v.e0);
+  const float ux = fmaf(v.f, mx, v.cxm), uy = fmaf(-v.f, my, v.cym);
+  b.x0 = (int)fminf(fmaxf(ceilf(ux - hx), 0.0f), (float)W);
+  b.x1 = (int)fmaxf(fminf(floorf(ux + hx), (float)(W - 1)), -1.0f);
+  b.y0 = (int)fminf(fmaxf(ceilf(uy - hy), 0.0f), (float)H);
+  b.y1 = (int)fmaxf(fminf(floorf(uy + hy), (float)(H - 1)), -1.0f);
+  return b.x0 <= b.x1 && b.y0 <= b.y1;
 }
 
 // ------------------------------------------------- TMA bulk copy helpers --
