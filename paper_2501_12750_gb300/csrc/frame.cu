@@ -29,7 +29,7 @@
 namespace vtx {
 
 constexpr int kCullThreads = 256;
-constexpr int kStages = 3;                           // TMA pipeline depth of the cull
+constexpr int kStages = 2;                           // TMA pipeline depth of the cull
 constexpr int kChunk = 1024;                         // atoms per stage (16 KB)
 constexpr int kPerThread = kChunk / kCullThreads;
 constexpr size_t kCullSmem = (size_t)kStages * kChunk * sizeof(float4);
@@ -95,7 +95,7 @@ __device__ __forceinline__ void warp_minmax(float &lo, float &hi) {
 // ONE_VIEW: a single camera, whose constants are then compile-time indexed
 // kernel parameters; otherwise the views are read from a shared-memory copy.
 template <bool ONE_VIEW>
-__global__ __launch_bounds__(kCullThreads, 3) void k_cull_atoms(Geometry g, const float4 *__restrict__ frames,
+__global__ __launch_bounds__(kCullThreads, 5) void k_cull_atoms(Geometry g, const float4 *__restrict__ frames,
                                                                 const long long *__restrict__ counts, ImageState *st,
                                                                 uint32_t *__restrict__ surv, Status *status) {
   extern __shared__ __align__(128) unsigned char cull_smem[];
@@ -349,11 +349,13 @@ struct PrimGeom {
 };
 
 // Precise setup of primitive `id` of image `img` (sphere or bond cylinder).
+// `pre` (when non-null) is the already loaded record of atom `id`.
 __device__ __forceinline__ PrimGeom prim_geom(const Geometry &g, const ViewParams &v, const float4 *X, const uint2 *bonds,
-                                              uint32_t id, float zlo, float S, bool use_box_r) {
+                                              uint32_t id, float zlo, float S, bool use_box_r,
+                                              const float4 *pre = nullptr) {
   PrimGeom p;
   if ((long long)id < g.n_atoms || bonds == nullptr) {
-    float4 a = X[id];
+    float4 a = pre ? *pre : X[id];
     float r = g.mode == 1 ? g.ball_radius : a.w;
     p.rad = r;
     p.hl = 0.0f;
@@ -420,14 +422,26 @@ __global__ __launch_bounds__(256, 3) void k_setup(Geometry g, const float4 *__re
   const int lane = threadIdx.x & 31;
   const long long stride = (long long)gridDim.x * blockDim.x;
   const long long n_pad = (n + 31) & ~31LL;
-  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n_pad; k += stride) {
+  // two-stage prefetch: the id two iterations ahead, the atom record one ahead
+  const long long k0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  uint32_t id_cur = k0 < n ? sv[k0] : 0u;
+  uint32_t id_nxt = k0 + stride < n ? sv[k0 + stride] : 0u;
+  float4 a_cur = (k0 < n && (long long)id_cur < g.n_atoms) ? X[id_cur] : zero4;
+  for (long long k = k0; k < n_pad; k += stride) {
+    const float4 a_nxt = (k + stride < n && (long long)id_nxt < g.n_atoms) ? X[id_nxt] : zero4;
+    const uint32_t id_nn = k + 2 * stride < n ? sv[k + 2 * stride] : 0u;
     bool binned = false;
     PrimRec rec;
     PixBox box;
     uint2 rbox = make_uint2(0u, 0u);
+    const uint32_t id = id_cur;
+    const float4 a_here = a_cur;
+    id_cur = id_nxt;
+    a_cur = a_nxt;
+    id_nxt = id_nn;
     if (k < n) {
-      const uint32_t id = sv[k];
-      PrimGeom p = prim_geom(g, v, X, bonds, id, s.zlo, s.S, true);
+      PrimGeom p = prim_geom(g, v, X, bonds, id, s.zlo, s.S, true, &a_here);
       float Rbox = p.hl == 0.0f ? cull_radius(g, v, p.rad, p.vz) : p.Rb;
       bool any = lean_box(v, g.W, g.H, p.vx, p.vy, p.vz, Rbox + p.err, box);
       if (any) {
@@ -720,20 +734,15 @@ __global__ __launch_bounds__(TW *TH) void k_raster(Geometry g, const PrimRec *__
 
 // -------------------------------------------------------------- resolve --
 
-__global__ __launch_bounds__(256, 4) void k_resolve(Geometry g, ShadeParams sh, const float4 *__restrict__ frames,
-                                                 const uint8_t *__restrict__ elem, const uint2 *__restrict__ bonds,
-                                                 const ImageState *__restrict__ st,
-                                                 const unsigned long long *__restrict__ keys, Outputs out,
-                                                 int do_ssao) {
+__device__ __forceinline__ void resolve_pixel(const Geometry &g, const ShadeParams &sh, const float4 *__restrict__ frames,
+                                              const uint8_t *__restrict__ elem, const uint2 *__restrict__ bonds,
+                                              const ImageState *__restrict__ st,
+                                              const unsigned long long *__restrict__ keys, const Outputs &out,
+                                              int do_ssao, int img, int px, int py, unsigned long long key) {
   const long long ppi = g.pix_per_img;
-  // one 32x8 pixel block per CTA, blockIdx.z = image: no integer division per pixel
-  const int px = blockIdx.x * 32 + (threadIdx.x & 31);
-  const int py = blockIdx.y * 8 + (threadIdx.x >> 5);
-  const int img = blockIdx.z;
-  if (px < g.W && py < g.H) {
+  {
     const long long p = (long long)py * g.W + px;
     const long long q = (long long)img * ppi + p;
-    const unsigned long long key = keys[q];
     const uint32_t id = (uint32_t)key;
     float *nrm = out.normal + (long long)img * 3 * ppi + p;
     float *rgb = out.rgb + (long long)img * 3 * ppi + p;
@@ -834,6 +843,31 @@ __global__ __launch_bounds__(256, 4) void k_resolve(Geometry g, ShadeParams sh, 
   }
 }
 
+// One 32x32 pixel block per CTA (4 rows per thread, keys loaded up front),
+// blockIdx.z = image: no integer division per pixel.
+__global__ __launch_bounds__(256, 4) void k_resolve(Geometry g, ShadeParams sh, const float4 *__restrict__ frames,
+                                                 const uint8_t *__restrict__ elem, const uint2 *__restrict__ bonds,
+                                                 const ImageState *__restrict__ st,
+                                                 const unsigned long long *__restrict__ keys, Outputs out,
+                                                 int do_ssao) {
+  const int px = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int py0 = blockIdx.y * 32 + (threadIdx.x >> 5);
+  const int img = blockIdx.z;
+  if (px >= g.W) return;
+  const unsigned long long *K = keys + (long long)img * g.pix_per_img;
+  unsigned long long kk[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int py = py0 + 8 * i;
+    kk[i] = py < g.H ? K[(long long)py * g.W + px] : kBgKey;
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int py = py0 + 8 * i;
+    if (py < g.H) resolve_pixel(g, sh, frames, elem, bonds, st, keys, out, do_ssao, img, px, py, kk[i]);
+  }
+}
+
 // ------------------------------------------------------------ launchers --
 
 static inline void ev_rec(StageEvents *e, int i, cudaStream_t st) {
@@ -856,10 +890,10 @@ cudaError_t run_binning(const Geometry &g, const Scene &sc, const Scratch &s, cu
       cudaFuncSetAttribute(k_cull_atoms<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCullSmem);
       attr = true;
     }
-    // three resident CTAs per SM in total, spread over the frames of a batch
+    // five resident CTAs per SM in total, spread over the frames of a batch
     const long long per_frame = sc.counts ? g.stride : g.n_atoms;
     const long long chunks = (per_frame + kChunk - 1) / kChunk;
-    long long want = (3LL * sms + g.n_frames - 1) / g.n_frames;
+    long long want = (5LL * sms + g.n_frames - 1) / g.n_frames;
     if (want < 1) want = 1;
     int bx = (int)(chunks < want ? (chunks > 0 ? chunks : 1) : want);
     dim3 grid(bx, g.n_frames);
@@ -920,7 +954,7 @@ cudaError_t run_frame_pipeline(const Geometry &g, const ShadeParams &sh, const S
                                                      s.tile_start, s.state, s.keys, s.status);
   ev_rec(evs, 5, st);
   {
-    dim3 grid((g.W + 31) / 32, (g.H + 7) / 8, g.n_img);
+    dim3 grid((g.W + 31) / 32, (g.H + 31) / 32, g.n_img);
     k_resolve<<<grid, 256, 0, st>>>(g, sh, sc.frames, sc.elem, sc.bonds, s.state, s.keys, out, ssao ? 1 : 0);
   }
   ev_rec(evs, 6, st);
