@@ -425,7 +425,7 @@ static vtx_status render_once(vtx_ctx *c, const vtx_settings *s, const vtx_outpu
   g.stride = c->n_atoms;
   g.n_atoms = c->n_atoms;
   g.n_bonds = s->mode == VTX_MODE_BALL_AND_STICK ? c->n_bonds : 0;
-  g.surv_cap = c->n_atoms + g.n_bonds;
+  g.surv_cap = c->n_atoms + g.n_bonds + cull_survivor_slack(c->n_atoms);
   vtx_status st = prepare(c, g, false, 0);
   if (st) return st;
   Scene sc{c->xyzr, nullptr, c->elem, g.n_bonds ? c->bonds : nullptr};

@@ -259,6 +259,149 @@ __global__ __launch_bounds__(kCullThreads, 5) void k_cull_atoms(Geometry g, cons
   }
 }
 
+constexpr int kSlab = 64;  // survivor slots a warp reserves at a time (single-view cull)
+
+// Single-view streaming cull.  As k_cull_atoms, but with no block-wide
+// barrier in the loop: every thread arrives on the stage's "empty" mbarrier
+// once its atoms are in registers and thread 0 refills the stage when all
+// have; survivors go straight to global memory through per-warp slabs of
+// kSlab slots (one global atomic per slab; a ballot that does not fit in the
+// current slab spills into the next one, so only each warp's last slab has
+// unused slots, which are filled with kNoId and skipped by the setup stage);
+// the depth range is kept in registers and reduced once at the end.
+__global__ __launch_bounds__(kCullThreads, 6) void k_cull_one(Geometry g, const float4 *__restrict__ X, ImageState *st,
+                                                              uint32_t *__restrict__ surv, Status *status) {
+  extern __shared__ __align__(128) unsigned char cull_smem[];
+  float4 *s_atoms = reinterpret_cast<float4 *>(cull_smem);
+  __shared__ __align__(8) uint64_t s_full[kStages];
+  __shared__ __align__(8) uint64_t s_empty[kStages];
+  const ViewParams &vp = g.views[0];
+  const long long n = g.n_atoms;
+  const long long n_chunks = (n + kChunk - 1) / kChunk;
+  const long long mine = (long long)blockIdx.x < n_chunks ? (n_chunks - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const long long cap = g.surv_cap;  // slots are reserved past it only if the host sized it wrongly
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&s_full[s], 1u);
+      mbar_init(&s_empty[s], kCullThreads);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+  long long issued = 0;  // thread 0 only
+  if (threadIdx.x == 0) {
+    for (; issued < mine && issued < kStages; ++issued) {
+      const long long a0 = ((long long)blockIdx.x + issued * gridDim.x) * kChunk;
+      const uint32_t bytes = (uint32_t)min((long long)kChunk, n - a0) * 16u;
+      mbar_expect_tx(&s_full[issued], bytes);
+      bulk_g2s(s_atoms + issued * kChunk, X + a0, bytes, &s_full[issued]);
+    }
+  }
+  uint32_t slab = kNoId;
+  int used = kSlab;
+  float zlo = __int_as_float(0x7f800000), zhi = 0.0f;
+  int stg = 0;
+  uint32_t phase = 0u;
+  long long k = 0;
+  for (; k < mine; ++k) {
+    const bool ok = mbar_wait_bounded(&s_full[stg], phase, kWaitLimit);
+    if (__any_sync(0xffffffffu, !ok)) {
+      if (lane == 0) atomicOr(&status->overflow, 16u);
+      break;
+    }
+    const long long a0 = ((long long)blockIdx.x + k * gridDim.x) * kChunk;
+    const int cnt = (int)min((long long)kChunk, n - a0);
+    float4 a[kPerThread];
+#pragma unroll
+    for (int j = 0; j < kPerThread; ++j) {
+      const int i = j * kCullThreads + threadIdx.x;
+      a[j] = i < cnt ? s_atoms[stg * kChunk + i] : make_float4(0.0f, 0.0f, 0.0f, -1.0f);
+    }
+    mbar_arrive(&s_empty[stg]);
+    if (threadIdx.x == 0 && issued < mine) {  // refill this stage once every thread has read it
+      if (!mbar_wait_bounded(&s_empty[stg], phase, kWaitLimit)) {
+        atomicOr(&status->overflow, 16u);
+      } else {
+        fence_proxy_async();
+        const long long b0 = ((long long)blockIdx.x + issued * gridDim.x) * kChunk;
+        const uint32_t bytes = (uint32_t)min((long long)kChunk, n - b0) * 16u;
+        mbar_expect_tx(&s_full[stg], bytes);
+        bulk_g2s(s_atoms + stg * kChunk, X + b0, bytes, &s_full[stg]);
+        ++issued;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kPerThread; ++j) {
+      bool keep = false;
+      if (a[j].w >= 0.0f) {
+        const float r = g.mode == 1 ? g.ball_radius : a[j].w;
+        float vx, vy, vz, err;
+        view_f32(vp, a[j].x, a[j].y, a[j].z, vx, vy, vz, err);
+        const float Rm = r + err;
+        keep = cull_lean(vp, vx, vy, vz, Rm);
+        if (keep) {
+          zlo = fminf(zlo, vz - Rm);
+          zhi = fmaxf(zhi, vz + Rm);
+        }
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, keep);
+      if (m) {
+        // slots [used, kSlab) of the current slab first, the rest in a fresh slab
+        const int c = __popc(m);
+        const int pos = used + __popc(m & lt);
+        uint32_t next = slab;
+        if (used + c > kSlab) {
+          unsigned nb = 0u;
+          if (lane == 0) nb = atomicAdd(&st[0].n_surv, (unsigned)kSlab);
+          next = __shfl_sync(0xffffffffu, nb, 0);
+        }
+        if (keep) {
+          const long long dst = pos < kSlab ? (long long)slab + pos : (long long)next + (pos - kSlab);
+          if (dst < cap) surv[dst] = (uint32_t)(a0 + j * kCullThreads + threadIdx.x);
+        }
+        if (used + c > kSlab) {
+          slab = next;
+          used = used + c - kSlab;
+        } else {
+          used += c;
+        }
+      }
+    }
+    if (++stg == kStages) {
+      stg = 0;
+      phase ^= 1u;
+    }
+  }
+  if (slab != kNoId)  // the final slab's unused slots become holes
+    for (int i = used + lane; i < kSlab; i += 32)
+      if ((long long)slab + i < cap) surv[slab + i] = kNoId;
+  warp_minmax(zlo, zhi);
+  if (lane == 0 && zhi > 0.0f) {
+    atomicMin(&st[0].zlo_bits, __float_as_uint(fmaxf(zlo, 0.0f)));
+    atomicMax(&st[0].zhi_bits, __float_as_uint(zhi));
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {  // copies still in flight (only after a failed wait)
+    uint32_t ph = phase;
+    int sg = stg;
+    for (long long q = k; q < issued; ++q) {
+      mbar_wait_bounded(&s_full[sg], ph, kWaitLimit);
+      if (++sg == kStages) {
+        sg = 0;
+        ph ^= 1u;
+      }
+    }
+  }
+}
+
+long long cull_survivor_slack(long long n_atoms) {
+  const long long chunks = (n_atoms + kChunk - 1) / kChunk;
+  const long long ctas = chunks < 6LL * sm_count() ? (chunks > 0 ? chunks : 1) : 6LL * sm_count();
+  return ctas * (kCullThreads / 32) * kSlab;
+}
+
 // Bond cylinders (ball-and-stick, single frame, single view): the bounding
 // sphere of each capped cylinder is culled like an atom.
 __global__ __launch_bounds__(kCullThreads) void k_cull_bonds(Geometry g, const float4 *__restrict__ X,
@@ -440,7 +583,7 @@ __global__ __launch_bounds__(256, 3) void k_setup(Geometry g, const float4 *__re
     id_cur = id_nxt;
     a_cur = a_nxt;
     id_nxt = id_nn;
-    if (k < n) {
+    if (k < n && id != kNoId) {
       PrimGeom p = prim_geom(g, v, X, bonds, id, s.zlo, s.S, true, &a_here);
       float Rbox = p.hl == 0.0f ? cull_radius(g, v, p.rad, p.vz) : p.Rb;
       bool any = lean_box(v, g.W, g.H, p.vx, p.vy, p.vz, Rbox + p.err, box);
@@ -843,7 +986,7 @@ __device__ __forceinline__ void resolve_pixel(const Geometry &g, const ShadePara
   }
 }
 
-// One 32x32 pixel block per CTA (4 rows per thread, keys loaded up front),
+// One 32x32 pixel block per CTA (4 rows per thread, the four keys loaded up front),
 // blockIdx.z = image: no integer division per pixel.
 __global__ __launch_bounds__(256, 4) void k_resolve(Geometry g, ShadeParams sh, const float4 *__restrict__ frames,
                                                  const uint8_t *__restrict__ elem, const uint2 *__restrict__ bonds,
@@ -855,16 +998,18 @@ __global__ __launch_bounds__(256, 4) void k_resolve(Geometry g, ShadeParams sh, 
   const int img = blockIdx.z;
   if (px >= g.W) return;
   const unsigned long long *K = keys + (long long)img * g.pix_per_img;
-  unsigned long long kk[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  unsigned long long k0 = py0 < g.H ? K[(long long)py0 * g.W + px] : kBgKey;
+  unsigned long long k1 = py0 + 8 < g.H ? K[(long long)(py0 + 8) * g.W + px] : kBgKey;
+  unsigned long long k2 = py0 + 16 < g.H ? K[(long long)(py0 + 16) * g.W + px] : kBgKey;
+  unsigned long long k3 = py0 + 24 < g.H ? K[(long long)(py0 + 24) * g.W + px] : kBgKey;
+#pragma unroll 1
+  for (int i = 0; i < 4; ++i) {  // one copy of the (large) pixel body: keys rotate through registers
+    const unsigned long long key = k0;
+    k0 = k1;
+    k1 = k2;
+    k2 = k3;
     const int py = py0 + 8 * i;
-    kk[i] = py < g.H ? K[(long long)py * g.W + px] : kBgKey;
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int py = py0 + 8 * i;
-    if (py < g.H) resolve_pixel(g, sh, frames, elem, bonds, st, keys, out, do_ssao, img, px, py, kk[i]);
+    if (py < g.H) resolve_pixel(g, sh, frames, elem, bonds, st, keys, out, do_ssao, img, px, py, key);
   }
 }
 
@@ -888,6 +1033,7 @@ cudaError_t run_binning(const Geometry &g, const Scene &sc, const Scratch &s, cu
     if (!attr) {
       cudaFuncSetAttribute(k_cull_atoms<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCullSmem);
       cudaFuncSetAttribute(k_cull_atoms<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCullSmem);
+      cudaFuncSetAttribute(k_cull_one, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCullSmem);
       attr = true;
     }
     // five resident CTAs per SM in total, spread over the frames of a batch
@@ -897,10 +1043,14 @@ cudaError_t run_binning(const Geometry &g, const Scene &sc, const Scratch &s, cu
     if (want < 1) want = 1;
     int bx = (int)(chunks < want ? (chunks > 0 ? chunks : 1) : want);
     dim3 grid(bx, g.n_frames);
-    if (g.n_views == 1)
+    if (g.n_views == 1 && g.n_frames == 1 && sc.counts == nullptr && !g.soft) {
+      const int b1 = (int)(chunks < 6LL * sms ? (chunks > 0 ? chunks : 1) : 6LL * sms);
+      k_cull_one<<<b1, kCullThreads, kCullSmem, st>>>(g, sc.frames, s.state, s.surv, s.status);
+    } else if (g.n_views == 1) {
       k_cull_atoms<true><<<grid, kCullThreads, kCullSmem, st>>>(g, sc.frames, sc.counts, s.state, s.surv, s.status);
-    else
+    } else {
       k_cull_atoms<false><<<grid, kCullThreads, kCullSmem, st>>>(g, sc.frames, sc.counts, s.state, s.surv, s.status);
+    }
     if (g.mode == 1 && g.n_bonds > 0 && sc.bonds) {
       long long bb = (g.n_bonds + kCullThreads - 1) / kCullThreads;
       int gb = (int)(bb < 8LL * sms ? bb : 8LL * sms);

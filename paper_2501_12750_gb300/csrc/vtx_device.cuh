@@ -471,6 +471,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
   return false;
 }
 
+// Plain (non-transaction) arrival of the calling thread.
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // FP32 view coordinates of a world point and the bound on their error.
 __device__ __forceinline__ void view_f32(const ViewParams &v, float x, float y, float z, float &vx, float &vy,
                                          float &vz, float &err) {

@@ -58,4 +58,7 @@ cudaError_t run_soft_pipeline(const Geometry &g, const Scene &sc, const Scratch 
 
 int sm_count();
 
+// Extra survivor slots the single-view cull may leave as holes (per-warp slabs).
+long long cull_survivor_slack(long long n_atoms);
+
 }  // namespace vtx
