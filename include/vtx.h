@@ -241,6 +241,33 @@ vtx_status vtx_stage_times(vtx_ctx *ctx, const char **names, float *ms, int32_t 
 /* Text of the most recent error on this context ("" if none). */
 const char *vtx_last_error(const vtx_ctx *ctx);
 
+/*
+ * Allocation-free visibility buffer.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory (code
+ * running inside an allocator or memory-pool callback, plug-ins of an
+ * application that owns every allocation on the device, real-time loops
+ * that must not trigger cudaMalloc's implicit synchronisation).  It renders
+ * the nearest atom id and its depth per pixel for van der Waals spheres
+ * (the same ids and depths as vtx_render_frame) using scratch held in a
+ * file-scope __device__ array of VTX_STATIC_MAX_PIXELS 64-bit depth keys
+ * (8 MiB, kept by every GPU that loads the library until the process exits).
+ * No cudaMalloc, cudaFree or other allocating routine is called.
+ *   xyzr: device float4 [n_atoms] (16-byte aligned); cam: host camera with
+ *   width*height <= VTX_STATIC_MAX_PIXELS; depth: device float [H][W]
+ *   (+inf for background); id: device uint32 [H][W] (0xFFFFFFFF for
+ *   background); cuda_stream: the stream to enqueue on (NULL = default).
+ * Returns VTX_ERR_CAPACITY for larger images, VTX_ERR_INVALID_ARG for bad
+ * arguments, VTX_ERR_CUDA if a launch fails.  Work is only enqueued.
+ * The first call on a device looks up the array's device address with that
+ * device current (cudaGetSymbolAddress), so make that first call before any
+ * stream capture.  Every call shares the one array and clears it first:
+ * calls whose work overlaps on the GPU (other streams, other threads) race
+ * on it and must be serialised by the caller.
+ */
+#define VTX_STATIC_MAX_PIXELS (1 << 20)
+vtx_status vtx_render_visibility_static(const float *xyzr, int64_t n_atoms, const vtx_camera *cam, float *depth,
+                                        uint32_t *id, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif
