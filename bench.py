@@ -34,7 +34,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-KERNELS_PER_FRAME = 10  # init, cull, finalize, setup, scan x3, scatter, raster, resolve
+KERNELS_PER_FRAME = 8  # init, cull, finalize, setup, scan, scatter, raster, resolve
 
 
 def parse():

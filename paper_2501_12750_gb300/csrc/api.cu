@@ -43,7 +43,7 @@ struct vtx_ctx {
   vtx_camera cam;
   bool has_cam = false;
   // scratch
-  Buf keys, surv, state, tcount, tstart, tcursor, bsums, recs, recimg, recbox, recof, entries, status, counts, hostin_x,
+  Buf keys, surv, state, tcount, tstart, tcursor, tlist, bsums, recs, recimg, recbox, recof, entries, status, counts, hostin_x,
       hostin_e, hostout;
   uint32_t cap_rec = 0;
   unsigned long long cap_entries = 0;
@@ -201,6 +201,7 @@ static vtx_status prepare(vtx_ctx *c, const Geometry &g, bool soft, long long st
   if ((st = ensure(c, c->tcount, sizeof(uint32_t) * (size_t)(n_tiles + 1), "tile counts"))) return st;
   if ((st = ensure(c, c->tstart, sizeof(uint32_t) * (size_t)(n_tiles + 1), "tile starts"))) return st;
   if ((st = ensure(c, c->tcursor, sizeof(uint32_t) * (size_t)(n_tiles + 1), "tile cursors"))) return st;
+  if ((st = ensure(c, c->tlist, sizeof(uint32_t) * (size_t)(n_tiles + 1), "tile list"))) return st;
   if ((st = ensure(c, c->bsums, sizeof(unsigned long long) * (size_t)(n_tiles / 4096 + 4), "scan blocks"))) return st;
   if (c->cap_rec == 0) {
     long long est = n_img * g.stride / 8;
@@ -230,6 +231,7 @@ static Scratch scratch_of(vtx_ctx *c) {
   s.tile_start = (uint32_t *)c->tstart.p;
   s.tile_cursor = (uint32_t *)c->tcursor.p;
   s.block_sums = (uint32_t *)c->bsums.p;
+  s.tile_list = (uint32_t *)c->tlist.p;
   s.recs = (PrimRec *)c->recs.p;
   s.rec_img = (uint32_t *)c->recimg.p;
   s.rec_box = (uint2 *)c->recbox.p;
@@ -349,7 +351,7 @@ vtx_status vtx_destroy(vtx_ctx *c) {
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
   drop_graphs(c);
-  Buf *bufs[] = {&c->keys,   &c->surv,   &c->state,  &c->tcount,   &c->tstart,   &c->tcursor,
+  Buf *bufs[] = {&c->keys,   &c->surv,   &c->state,  &c->tcount,   &c->tstart,   &c->tcursor,  &c->tlist,
                  &c->bsums,  &c->recs,   &c->recimg, &c->recbox,   &c->recof,    &c->entries,  &c->status,
                  &c->counts, &c->hostin_x, &c->hostin_e, &c->hostout};
   for (Buf *b : bufs)

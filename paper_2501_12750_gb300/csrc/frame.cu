@@ -66,6 +66,7 @@ __global__ void k_init_state(ImageState *st, int n_img, Status *status) {
   if (i == 0) {
     status->n_rec = 0u;
     status->n_entries = 0ull;
+    status->n_list = 0u;
   }
 }
 
@@ -706,6 +707,53 @@ __global__ __launch_bounds__(1024) void k_scan_blocks(const uint32_t *__restrict
   if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
 }
 
+constexpr long long kScanSingleMax = 65536;
+
+// Exclusive scan of every tile count in one CTA (up to kScanSingleMax tiles),
+// listing the non-empty tiles for the raster stage on the way.
+__global__ __launch_bounds__(1024) void k_scan_single(const uint32_t *__restrict__ cnt, long long n,
+                                                      uint32_t *__restrict__ start, uint32_t *__restrict__ cursor,
+                                                      uint32_t *__restrict__ list, Status *status,
+                                                      unsigned long long cap_entries) {
+  __shared__ unsigned long long s_warp[32];
+  __shared__ unsigned int s_n;
+  if (threadIdx.x == 0) s_n = 0u;
+  __syncthreads();
+  unsigned long long carry = 0;
+  for (long long b0 = 0; b0 < n; b0 += kScanItems) {
+    const long long base = b0 + (long long)threadIdx.x * 4;
+    uint32_t c[4];
+    unsigned long long sum = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      c[j] = base + j < n ? cnt[base + j] : 0u;
+      sum += c[j];
+    }
+    unsigned long long total;
+    unsigned long long ex = block_exclusive_scan_1024(sum, s_warp, total);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const long long i = base + j;
+      if (i < n) {
+        const unsigned long long v = carry + ex;
+        const uint32_t w = (uint32_t)(v > cap_entries ? cap_entries : v);
+        start[i] = w;
+        cursor[i] = w;
+        if (c[j] > 0u) list[atomicAdd(&s_n, 1u)] = (uint32_t)i;
+      }
+      ex += c[j];
+    }
+    carry += total;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    start[n] = (uint32_t)(carry > cap_entries ? cap_entries : carry);
+    status->n_entries = carry;
+    status->n_list = s_n;
+    if (carry > cap_entries) atomicOr(&status->overflow, 4u);
+  }
+}
+
 // Scan of the block totals (one CTA, loops when there are more than 1,024 blocks).
 __global__ __launch_bounds__(1024) void k_scan_top(unsigned long long *block_sums, int nb, Status *status,
                                                    unsigned long long cap_entries) {
@@ -729,17 +777,29 @@ __global__ __launch_bounds__(1024) void k_scan_top(unsigned long long *block_sum
 
 __global__ __launch_bounds__(1024) void k_scan_add(uint32_t *__restrict__ start, uint32_t *__restrict__ cursor,
                                                    long long n, const unsigned long long *__restrict__ block_sums,
-                                                   unsigned long long cap_entries) {
+                                                   unsigned long long cap_entries, const uint32_t *__restrict__ cnt,
+                                                   uint32_t *__restrict__ list, Status *status) {
   const long long base = (long long)blockIdx.x * kScanItems + (long long)threadIdx.x * 4;
   const unsigned long long off = block_sums[blockIdx.x];
+  const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     long long i = base + j;
+    bool ne = false;
     if (i < n) {
       unsigned long long v = off + start[i];
       uint32_t w = (uint32_t)(v > cap_entries ? cap_entries : v);
       start[i] = w;
       cursor[i] = w;
+      ne = cnt[i] > 0u;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, ne);
+    if (m) {
+      const int leader = __ffs(m) - 1;
+      unsigned b = 0u;
+      if (lane == leader) b = atomicAdd(&status->n_list, (unsigned)__popc(m));
+      b = __shfl_sync(0xffffffffu, b, leader);
+      if (ne) list[b + __popc(m & ((1u << lane) - 1u))] = (uint32_t)i;
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -813,17 +873,19 @@ __global__ __launch_bounds__(TW *TH) void k_raster(Geometry g, const PrimRec *__
                                                    const uint32_t *__restrict__ tile_count,
                                                    const uint32_t *__restrict__ tile_start,
                                                    const ImageState *__restrict__ st, unsigned long long *keys,
-                                                   Status *status) {
+                                                   const uint32_t *__restrict__ tile_list, Status *status) {
   constexpr int NT = TW * TH;
   __shared__ unsigned long long s_e[kListCap];
   __shared__ PrimRec s_r[NT];
-  const long long gt = blockIdx.x;
+  const uint32_t n_list = status->n_list;
+  for (uint32_t li = blockIdx.x; li < n_list; li += gridDim.x) {  // only the non-empty tiles
+  const long long gt = tile_list[li];
   const int img = (int)(gt / g.tiles_per_img);
   const int t = (int)(gt % g.tiles_per_img);
   uint32_t cnt = tile_count[gt];
-  if (cnt == 0u) return;
+  if (cnt == 0u) continue;
   const uint32_t start = tile_start[gt];
-  if ((unsigned long long)start >= cap_entries) return;
+  if ((unsigned long long)start >= cap_entries) continue;
   if ((unsigned long long)start + cnt > cap_entries) cnt = (uint32_t)(cap_entries - start);
   const ViewParams &v = g.views[img % g.n_views];
   const float S = st[img].S;
@@ -873,6 +935,7 @@ __global__ __launch_bounds__(TW *TH) void k_raster(Geometry g, const PrimRec *__
     __syncthreads();
   }
   if (inside) *K = best;
+  }
 }
 
 // -------------------------------------------------------------- resolve --
@@ -951,25 +1014,43 @@ __device__ __forceinline__ void resolve_pixel(const Geometry &g, const ShadePara
       const long long kP = (long long)(key >> 32);
       float occ = 0.0f;
       const float R = sh.ssao_radius;
-      for (int j = 0; j < sh.ssao_n; ++j) {
-        const float kx = sh.kernel[j][0], ky = sh.kernel[j][1], kz = sh.kernel[j][2];
-        float dx = R * (kx * T.x + ky * B.x + kz * n.x);
-        float dy = R * (kx * T.y + ky * B.y + kz * n.y);
-        float dzv = R * (kx * T.z + ky * B.z + kz * n.z);
-        float dl = -dzv;  // depth offset of the sample
-        float den = t + dl;
-        if (!(den > 0.0f)) continue;
-        float offx = v.f * (dx - r.a * dl) / den;
-        float offy = -v.f * (dy - r.b * dl) / den;
-        int ix = px + (int)floorf(0.5f + offx);
-        int iy = py + (int)floorf(0.5f + offy);
-        if (ix < 0 || iy < 0 || ix >= g.W || iy >= g.H) continue;
-        unsigned long long kf = Kimg[(long long)iy * g.W + ix];
-        if ((uint32_t)kf == kNoId) continue;
-        float dzf = (float)((long long)(kf >> 32) - kP) * s.invS;  // z_f - t
-        if (dzf <= dl - sh.ssao_bias) {
-          float adz = fabsf(dzf);
-          occ += adz <= R ? 1.0f : R / adz;
+      // samples in groups of four: the four neighbour-key loads are issued together
+      for (int j0 = 0; j0 < sh.ssao_n; j0 += 4) {
+        long long at[4];
+        float dls[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = j0 + u;
+          at[u] = -1;
+          dls[u] = 0.0f;
+          if (j < sh.ssao_n) {
+            const float kx = sh.kernel[j][0], ky = sh.kernel[j][1], kz = sh.kernel[j][2];
+            const float dx = R * (kx * T.x + ky * B.x + kz * n.x);
+            const float dy = R * (kx * T.y + ky * B.y + kz * n.y);
+            const float dzv = R * (kx * T.z + ky * B.z + kz * n.z);
+            const float dl = -dzv;  // depth offset of the sample
+            const float den = t + dl;
+            dls[u] = dl;
+            if (den > 0.0f) {
+              const float offx = v.f * (dx - r.a * dl) / den;
+              const float offy = -v.f * (dy - r.b * dl) / den;
+              const int ix = px + (int)floorf(0.5f + offx);
+              const int iy = py + (int)floorf(0.5f + offy);
+              if (ix >= 0 && iy >= 0 && ix < g.W && iy < g.H) at[u] = (long long)iy * g.W + ix;
+            }
+          }
+        }
+        unsigned long long kf[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) kf[u] = at[u] >= 0 ? Kimg[at[u]] : kBgKey;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if ((uint32_t)kf[u] == kNoId) continue;
+          const float dzf = (float)((long long)(kf[u] >> 32) - kP) * s.invS;  // z_f - t
+          if (dzf <= dls[u] - sh.ssao_bias) {
+            const float adz = fabsf(dzf);
+            occ += adz <= R ? 1.0f : R / adz;
+          }
         }
       }
       aof = 1.0f - occ / (float)sh.ssao_n;
@@ -1071,11 +1152,17 @@ cudaError_t run_binning(const Geometry &g, const Scene &sc, const Scratch &s, cu
   }
   ev_rec(evs, 2, st);
   {
-    int nb = (int)((n_tiles + kScanItems - 1) / kScanItems);
-    unsigned long long *bs = reinterpret_cast<unsigned long long *>(s.block_sums);
-    k_scan_blocks<<<nb, 1024, 0, st>>>(s.tile_count, n_tiles, s.tile_start, bs);
-    k_scan_top<<<1, 1024, 0, st>>>(bs, nb, s.status, s.cap_entries);
-    k_scan_add<<<nb, 1024, 0, st>>>(s.tile_start, s.tile_cursor, n_tiles, bs, s.cap_entries);
+    if (n_tiles <= kScanSingleMax) {
+      k_scan_single<<<1, 1024, 0, st>>>(s.tile_count, n_tiles, s.tile_start, s.tile_cursor, s.tile_list, s.status,
+                                        s.cap_entries);
+    } else {
+      int nb = (int)((n_tiles + kScanItems - 1) / kScanItems);
+      unsigned long long *bs = reinterpret_cast<unsigned long long *>(s.block_sums);
+      k_scan_blocks<<<nb, 1024, 0, st>>>(s.tile_count, n_tiles, s.tile_start, bs);
+      k_scan_top<<<1, 1024, 0, st>>>(bs, nb, s.status, s.cap_entries);
+      k_scan_add<<<nb, 1024, 0, st>>>(s.tile_start, s.tile_cursor, n_tiles, bs, s.cap_entries, s.tile_count,
+                                      s.tile_list, s.status);
+    }
   }
   ev_rec(evs, 3, st);
   if (soft)
@@ -1093,15 +1180,16 @@ cudaError_t run_frame_pipeline(const Geometry &g, const ShadeParams &sh, const S
   cudaError_t e = run_binning(g, sc, s, st, evs, false);
   if (e != cudaSuccess) return e;
   const long long n_tiles = (long long)g.n_img * g.tiles_per_img;
+  const unsigned rgrid = (unsigned)(n_tiles < 8LL * sm_count() ? n_tiles : 8LL * sm_count());
   if (g.tile_w == 16 && g.tile_h == 16)
-    k_raster<16, 16><<<(unsigned)n_tiles, 256, 0, st>>>(g, s.recs, s.entries, s.cap_entries, s.tile_count,
-                                                        s.tile_start, s.state, s.keys, s.status);
+    k_raster<16, 16><<<rgrid, 256, 0, st>>>(g, s.recs, s.entries, s.cap_entries, s.tile_count,
+                                                        s.tile_start, s.state, s.keys, s.tile_list, s.status);
   else if (g.tile_w == 32 && g.tile_h == 8)
-    k_raster<32, 8><<<(unsigned)n_tiles, 256, 0, st>>>(g, s.recs, s.entries, s.cap_entries, s.tile_count,
-                                                       s.tile_start, s.state, s.keys, s.status);
+    k_raster<32, 8><<<rgrid, 256, 0, st>>>(g, s.recs, s.entries, s.cap_entries, s.tile_count,
+                                                       s.tile_start, s.state, s.keys, s.tile_list, s.status);
   else
-    k_raster<8, 8><<<(unsigned)n_tiles, 64, 0, st>>>(g, s.recs, s.entries, s.cap_entries, s.tile_count,
-                                                     s.tile_start, s.state, s.keys, s.status);
+    k_raster<8, 8><<<rgrid, 64, 0, st>>>(g, s.recs, s.entries, s.cap_entries, s.tile_count,
+                                                     s.tile_start, s.state, s.keys, s.tile_list, s.status);
   ev_rec(evs, 5, st);
   {
     dim3 grid((g.W + 31) / 32, (g.H + 31) / 32, g.n_img);

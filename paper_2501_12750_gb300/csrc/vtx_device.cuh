@@ -96,7 +96,7 @@ struct Status {
   unsigned int overflow;        // bit 0 survivors, 1 records, 2 entries, 3 soft tile list too long
   unsigned long long n_entries; // binned (tile, primitive) entries requested
   unsigned int max_list;        // longest tile list seen by the raster stage
-  unsigned int pad;
+  unsigned int n_list;          // non-empty tiles listed by the scan (raster work list)
 };
 
 // A binned primitive staged through shared memory (64 bytes).  Its tile box

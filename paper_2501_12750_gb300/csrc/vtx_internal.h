@@ -17,6 +17,7 @@ struct Scratch {
   uint32_t *tile_start;       // [n_tiles + 1] exclusive prefix (tile_start[n_tiles] = total, clamped)
   uint32_t *tile_cursor;      // [n_tiles]
   uint32_t *block_sums;       // [ceil(n_tiles / 4096) + 1]
+  uint32_t *tile_list;        // [n_tiles] indices of the non-empty tiles
   PrimRec *recs;              // [cap_rec]
   uint32_t *rec_img;          // [cap_rec] image of each record
   uint2 *rec_box;             // [cap_rec] tile box of each record: (x0 | y0 << 16, x1 | y1 << 16)
