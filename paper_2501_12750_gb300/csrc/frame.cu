@@ -707,51 +707,79 @@ __global__ __launch_bounds__(1024) void k_scan_blocks(const uint32_t *__restrict
   if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
 }
 
-constexpr long long kScanSingleMax = 65536;
+constexpr int kScanRounds = 32;                                 // values per lane in the one-CTA scan
+constexpr long long kScanSingleMax = 32LL * 32 * kScanRounds;   // 32 warps x 32 lanes x rounds
 
 // Exclusive scan of every tile count in one CTA (up to kScanSingleMax tiles),
-// listing the non-empty tiles for the raster stage on the way.
+// listing the non-empty tiles for the raster stage on the way.  Warp w owns
+// the contiguous segment [w S, (w+1) S), S = 32 * kScanRounds; each lane loads
+// its kScanRounds values up front (coalesced rows of 32), warps scan their
+// rows with shuffles, and one pass over the 32 warp totals links the segments.
 __global__ __launch_bounds__(1024) void k_scan_single(const uint32_t *__restrict__ cnt, long long n,
                                                       uint32_t *__restrict__ start, uint32_t *__restrict__ cursor,
                                                       uint32_t *__restrict__ list, Status *status,
                                                       unsigned long long cap_entries) {
-  __shared__ unsigned long long s_warp[32];
+  __shared__ unsigned long long s_wsum[32];
   __shared__ unsigned int s_n;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const long long seg = (long long)wid * 32 * kScanRounds;
   if (threadIdx.x == 0) s_n = 0u;
+  uint32_t v[kScanRounds];
+  unsigned long long wsum = 0;
+#pragma unroll
+  for (int r = 0; r < kScanRounds; ++r) {
+    const long long i = seg + r * 32 + lane;
+    v[r] = i < n ? cnt[i] : 0u;
+  }
+#pragma unroll
+  for (int r = 0; r < kScanRounds; ++r) wsum += v[r];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
+  if (lane == 0) s_wsum[wid] = wsum;
   __syncthreads();
-  unsigned long long carry = 0;
-  for (long long b0 = 0; b0 < n; b0 += kScanItems) {
-    const long long base = b0 + (long long)threadIdx.x * 4;
-    uint32_t c[4];
-    unsigned long long sum = 0;
+  if (wid == 0) {
+    unsigned long long x = s_wsum[lane];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      c[j] = base + j < n ? cnt[base + j] : 0u;
-      sum += c[j];
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
     }
-    unsigned long long total;
-    unsigned long long ex = block_exclusive_scan_1024(sum, s_warp, total);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const long long i = base + j;
-      if (i < n) {
-        const unsigned long long v = carry + ex;
-        const uint32_t w = (uint32_t)(v > cap_entries ? cap_entries : v);
-        start[i] = w;
-        cursor[i] = w;
-        if (c[j] > 0u) list[atomicAdd(&s_n, 1u)] = (uint32_t)i;
-      }
-      ex += c[j];
+    s_wsum[lane] = x - s_wsum[lane];  // exclusive
+    if (lane == 31) {
+      status->n_entries = x;
+      start[n] = (uint32_t)(x > cap_entries ? cap_entries : x);
+      if (x > cap_entries) atomicOr(&status->overflow, 4u);
     }
-    carry += total;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    start[n] = (uint32_t)(carry > cap_entries ? cap_entries : carry);
-    status->n_entries = carry;
-    status->n_list = s_n;
-    if (carry > cap_entries) atomicOr(&status->overflow, 4u);
+  unsigned long long carry = s_wsum[wid];
+#pragma unroll
+  for (int r = 0; r < kScanRounds; ++r) {
+    unsigned long long x = v[r];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    const unsigned long long ex = carry + x - v[r];
+    const long long i = seg + r * 32 + lane;
+    const bool ne = i < n && v[r] > 0u;
+    if (i < n) {
+      const uint32_t w = (uint32_t)(ex > cap_entries ? cap_entries : ex);
+      start[i] = w;
+      cursor[i] = w;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, ne);
+    if (m) {
+      unsigned base = 0u;
+      if (lane == 0) base = atomicAdd(&s_n, (unsigned)__popc(m));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (ne) list[base + __popc(m & ((1u << lane) - 1u))] = (uint32_t)i;
+    }
+    carry += __shfl_sync(0xffffffffu, x, 31);
   }
+  __syncthreads();
+  if (threadIdx.x == 0) status->n_list = s_n;
 }
 
 // Scan of the block totals (one CTA, loops when there are more than 1,024 blocks).
@@ -940,6 +968,14 @@ __global__ __launch_bounds__(TW *TH) void k_raster(Geometry g, const PrimRec *__
 
 // -------------------------------------------------------------- resolve --
 
+#ifndef VTX_SSAO_GROUP
+#define VTX_SSAO_GROUP 4
+#endif
+#ifndef VTX_RESOLVE_MINB
+#define VTX_RESOLVE_MINB 4
+#endif
+constexpr int kSsaoGroup = VTX_SSAO_GROUP;  // SSAO samples whose neighbour keys are fetched together
+
 __device__ __forceinline__ void resolve_pixel(const Geometry &g, const ShadeParams &sh, const float4 *__restrict__ frames,
                                               const uint8_t *__restrict__ elem, const uint2 *__restrict__ bonds,
                                               const ImageState *__restrict__ st,
@@ -1014,12 +1050,12 @@ __device__ __forceinline__ void resolve_pixel(const Geometry &g, const ShadePara
       const long long kP = (long long)(key >> 32);
       float occ = 0.0f;
       const float R = sh.ssao_radius;
-      // samples in groups of four: the four neighbour-key loads are issued together
-      for (int j0 = 0; j0 < sh.ssao_n; j0 += 4) {
-        long long at[4];
-        float dls[4];
+      // samples in groups of kSsaoGroup: the group's neighbour-key loads are issued together
+      for (int j0 = 0; j0 < sh.ssao_n; j0 += kSsaoGroup) {
+        long long at[kSsaoGroup];
+        float dls[kSsaoGroup];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kSsaoGroup; ++u) {
           const int j = j0 + u;
           at[u] = -1;
           dls[u] = 0.0f;
@@ -1040,11 +1076,11 @@ __device__ __forceinline__ void resolve_pixel(const Geometry &g, const ShadePara
             }
           }
         }
-        unsigned long long kf[4];
+        unsigned long long kf[kSsaoGroup];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) kf[u] = at[u] >= 0 ? Kimg[at[u]] : kBgKey;
+        for (int u = 0; u < kSsaoGroup; ++u) kf[u] = at[u] >= 0 ? Kimg[at[u]] : kBgKey;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kSsaoGroup; ++u) {
           if ((uint32_t)kf[u] == kNoId) continue;
           const float dzf = (float)((long long)(kf[u] >> 32) - kP) * s.invS;  // z_f - t
           if (dzf <= dls[u] - sh.ssao_bias) {
@@ -1069,7 +1105,7 @@ __device__ __forceinline__ void resolve_pixel(const Geometry &g, const ShadePara
 
 // One 32x32 pixel block per CTA (4 rows per thread, the four keys loaded up front),
 // blockIdx.z = image: no integer division per pixel.
-__global__ __launch_bounds__(256, 4) void k_resolve(Geometry g, ShadeParams sh, const float4 *__restrict__ frames,
+__global__ __launch_bounds__(256, VTX_RESOLVE_MINB) void k_resolve(Geometry g, ShadeParams sh, const float4 *__restrict__ frames,
                                                  const uint8_t *__restrict__ elem, const uint2 *__restrict__ bonds,
                                                  const ImageState *__restrict__ st,
                                                  const unsigned long long *__restrict__ keys, Outputs out,

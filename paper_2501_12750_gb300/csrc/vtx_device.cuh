@@ -174,6 +174,54 @@ __device__ __forceinline__ df df_dot3(const float *w, df x, df y, df z) {
   return df_add(df_add(df_mul_f(x, w[0]), df_mul_f(y, w[1])), df_mul_f(z, w[2]));
 }
 
+// Dekker's FastTwoSum: exact when |a| >= |b| (otherwise still a faithful sum
+// whose error is below ulp(b), which is all the callers need).
+__device__ __forceinline__ df fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+// w . (x, y, z) for FP32 weights and double-float operands: the three products
+// of the high parts are exact (FMA TwoProduct), two TwoSums add them, and every
+// rounding error plus the low-part products are summed in FP32.  Absolute
+// error ~2^-46 of the largest product.
+__device__ __forceinline__ df df_dot3_lean(const float *w, df x, df y, df z) {
+  const float p0 = __fmul_rn(w[0], x.hi), p1 = __fmul_rn(w[1], y.hi), p2 = __fmul_rn(w[2], z.hi);
+  float e = __fmaf_rn(w[0], x.hi, -p0);
+  e = __fadd_rn(e, __fmaf_rn(w[1], y.hi, -p1));
+  e = __fadd_rn(e, __fmaf_rn(w[2], z.hi, -p2));
+  const df s01 = two_sum(p0, p1);
+  const df s = two_sum(s01.hi, p2);
+  e = __fadd_rn(e, __fadd_rn(s01.lo, s.lo));
+  e = __fmaf_rn(w[0], x.lo, e);
+  e = __fmaf_rn(w[1], y.lo, e);
+  e = __fmaf_rn(w[2], z.lo, e);
+  return fast_two_sum(s.hi, e);
+}
+
+// a / b with one exact remainder: q1 = a.hi / b.hi (to ~1 ulp), r = a - q1 b
+// where q1 * b.hi is split exactly by an FMA (a.hi - p is exact, Sterbenz),
+// then q = q1 + r / b.hi.  Relative error ~2^-44.
+__device__ __forceinline__ df df_div_lean(df a, df b) {
+  const float rb = __frcp_rn(b.hi);
+  const float q1 = __fmul_rn(a.hi, rb);
+  const float p = __fmul_rn(q1, b.hi);
+  const float pe = __fmaf_rn(q1, b.hi, -p);
+  float r = __fsub_rn(a.hi, p);
+  r = __fsub_rn(r, pe);
+  r = __fadd_rn(r, a.lo);
+  r = __fmaf_rn(-q1, b.lo, r);
+  return fast_two_sum(q1, __fmul_rn(r, rb));
+}
+
+__device__ __forceinline__ df df_mul_lean(df a, df b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return fast_two_sum(p, e);
+}
+
 // ------------------------------------------------------------ per pixel --
 
 struct PixRay {
@@ -215,9 +263,9 @@ __device__ __forceinline__ long long key_of(df z, float zlo, float S) {
 // primitive that reaches the eye plane, so the projection stays finite).
 __device__ __forceinline__ Setup precise_setup(const ViewParams &v, df dx, df dy, df dzw, float Rb, float zlo,
                                                float S) {
-  df vx = df_dot3(v.R, dx, dy, dzw);
-  df vy = df_dot3(v.U, dx, dy, dzw);
-  df z = df_dot3(v.F, dx, dy, dzw);
+  df vx = df_dot3_lean(v.R, dx, dy, dzw);
+  df vy = df_dot3_lean(v.U, dx, dy, dzw);
+  df z = df_dot3_lean(v.F, dx, dy, dzw);
   Setup o;
   float zmin = Rb + v.znear;
   df zr = z;
@@ -228,9 +276,9 @@ __device__ __forceinline__ Setup precise_setup(const ViewParams &v, df dx, df dy
     o.dz = dd.hi + dd.lo;
   }
   df fdf{v.f_hi, v.f_lo};
-  df qx = df_div(vx, zr), qy = df_div(vy, zr);
-  o.u0 = df_add_f(df_mul(qx, fdf), v.cx);
-  o.v0 = df_add_f(df_neg(df_mul(qy, fdf)), v.cy);
+  df qx = df_div_lean(vx, zr), qy = df_div_lean(vy, zr);
+  o.u0 = df_add_f(df_mul_lean(qx, fdf), v.cx);
+  o.v0 = df_add_f(df_neg(df_mul_lean(qy, fdf)), v.cy);
   o.zr = zr.hi;
   o.zc = z.hi + z.lo;
   o.k = zr.hi * v.inv_f;
