@@ -112,6 +112,16 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def aggregate_replicas(elapsed_ms, steps, world, device):
+    """Whole-job timing of N replicas: the slowest rank's time (MAX all-reduce) and all ranks' frames/s."""
+    if world > 1:
+        import torch
+        t = torch.tensor([float(elapsed_ms)], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    return elapsed_ms, world * steps / (elapsed_ms / 1e3)
+
+
 def oracle_baseline(scene, kernel, cam_index, target_s, max_pixels=4096):
     """Time the oracle on a bounded random pixel sample of the frame; frames/s extrapolated to W*H pixels."""
     import oracle
@@ -220,12 +230,8 @@ def main():
     elapsed_ms = ev0.elapsed_time(ev1)
     stages = r.stage_times()
     r.sync_status()  # raises on a capacity overflow inside the timed region
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    ms_per_step = elapsed_ms / args.steps
-    fps = world * args.steps / (elapsed_ms / 1e3)
+    ms_total, fps = aggregate_replicas(elapsed_ms, args.steps, world, dev)
+    ms_per_step = ms_total / args.steps
 
     peak, peak_kind = measured_peaks()
     cull_ms = stages["cull"]

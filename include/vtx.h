@@ -47,8 +47,9 @@
  * detected on the device (the kernels stop writing past a capacity and
  * record the size they needed); the next vtx_sync_status() (or a render
  * call with VTX_FLAG_SYNC) reports VTX_ERR_CAPACITY once and grows the arena
- * so that re-rendering succeeds.  No kernel in this library waits on another
- * block, so no device-side wait can hang.
+ * so that re-rendering succeeds.  No kernel waits on another block or launch;
+ * the only device-side waits are bounded polls on the completion of the
+ * kernel's own bulk copies (VTX_ERR_TIMEOUT if one ever gives up).
  */
 #ifndef VTX_H_
 #define VTX_H_
@@ -67,7 +68,7 @@ typedef enum {
   VTX_ERR_CUDA = 2,        /* a CUDA runtime call failed (text in vtx_last_error) */
   VTX_ERR_OOM = 3,         /* device allocation of scratch memory failed */
   VTX_ERR_CAPACITY = 4,    /* a previous frame overflowed the scratch arena (now grown: render again) */
-  VTX_ERR_TIMEOUT = 5,     /* reserved: no entry point of this version waits on the device */
+  VTX_ERR_TIMEOUT = 5,     /* a bounded device-side wait for a bulk copy gave up; the frame is invalid */
   VTX_ERR_BOUNDS = 6,      /* a device-side bounds check failed (debug builds) */
   VTX_ERR_STATE = 7        /* call order: no atoms uploaded, no camera set */
 } vtx_status;
@@ -103,8 +104,9 @@ typedef struct {
  * Rendering settings.  vtx_default_settings() fills the values used by the
  * tests: Blinn-Phong ka 0.2, kd 0.7, ks 0.3, shininess 32, light (0.25, 0.5, 1)
  * in view space, white background, no SSAO, 16x16 tiles, direct splat up to
- * 16 candidate pixels.  The paper names the techniques (glossy shading,
- * screen-space ambient occlusion) but not these constants.
+ * 16 candidate pixels (tile_w = 0 lets the library autotune both).  The
+ * paper names the techniques (glossy shading, screen-space ambient
+ * occlusion) but not these constants.
  */
 typedef struct {
   int32_t mode;          /* VTX_MODE_* */
@@ -117,8 +119,8 @@ typedef struct {
   float ssao_radius;     /* A */
   float ssao_bias;       /* A */
   float ssao_kernel[VTX_MAX_SSAO_SAMPLES][3]; /* hemisphere offsets (unit-ball scale), z along the normal */
-  int32_t tile_w, tile_h; /* 0 = library default; supported: 16x16, 32x8, 8x8 */
-  int32_t splat_max_px;  /* primitives whose candidate pixel box is <= this are splatted directly (0 = default) */
+  int32_t tile_w, tile_h; /* 16x16, 32x8 or 8x8; tile_w = 0: autotune tile shape AND splat_max_px (below) */
+  int32_t splat_max_px;  /* primitives whose candidate pixel box is <= this are splatted directly (0 = 16) */
   uint32_t flags;        /* VTX_FLAG_* */
 } vtx_settings;
 
@@ -237,6 +239,17 @@ vtx_status vtx_sync_status(vtx_ctx *ctx);
  * runs averaged.  Waits for the last profiled run, then forgets the runs.
  */
 vtx_status vtx_stage_times(vtx_ctx *ctx, const char **names, float *ms, int32_t *n, int32_t *runs);
+
+/*
+ * The tile shape and direct-splat threshold chosen by the autotuner for the
+ * most recent render call made with settings.tile_w = 0.  The tuner times all
+ * nine combinations of tile shape (16x16, 32x8, 8x8) and threshold (4, 16, 64
+ * candidate pixels) on the caller's own frame (a batch: its first four
+ * frames) once per class (image size, views, log2 of the primitive count,
+ * mode) and reuses the fastest.  The output never depends on the choice.
+ * Returns VTX_ERR_STATE before any tuned call.
+ */
+vtx_status vtx_tuned_settings(const vtx_ctx *ctx, int32_t *tile_w, int32_t *tile_h, int32_t *splat_max_px);
 
 /* Text of the most recent error on this context ("" if none). */
 const char *vtx_last_error(const vtx_ctx *ctx);

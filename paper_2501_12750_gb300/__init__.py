@@ -210,6 +210,12 @@ class Renderer:
                                                  _ptr(gc), _ptr(gd), _ptr(gn), _ptr(grad)))
         return grad
 
+    def tuned_settings(self):
+        """(tile_w, tile_h, splat_max_px) picked by the autotuner for the last call with tile_w = 0."""
+        tw, th, sp = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        self._check(self.lib.vtx_tuned_settings(self.ctx, ctypes.byref(tw), ctypes.byref(th), ctypes.byref(sp)))
+        return tw.value, th.value, sp.value
+
     def sync_status(self):
         self._check(self.lib.vtx_sync_status(self.ctx))
 

@@ -115,6 +115,7 @@ SIGNATURES = {
     "vtx_stage_times": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
     "vtx_last_error": ([c_void_p], ctypes.c_char_p),
     "vtx_render_visibility_static": ([c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
+    "vtx_tuned_settings": ([c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
 }
 
 _lib = None

@@ -1,6 +1,7 @@
 // api.cu -- C ABI of the renderer (declared in include/vtx.h): context,
 // scratch arena, argument checks, per-frame / batched / soft entry points,
 // CUDA-graph capture of batches and per-stage CUDA-event profiling.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -56,6 +57,13 @@ struct vtx_ctx {
   size_t ev_used = 0;
   // graphs
   std::vector<GraphEntry> graphs;
+  // autotuning results: key -> (tile_w, tile_h, splat_max)
+  struct Tune {
+    long long key[6];
+    int tw, th, splat;
+  };
+  std::vector<Tune> tunes;
+  int last_tw = 0, last_th = 0, last_splat = 0;
   std::string err;
 };
 
@@ -141,9 +149,11 @@ static vtx_status settings_ok(vtx_ctx *c, const vtx_settings *s) {
   if (s->mode != VTX_MODE_VDW && s->mode != VTX_MODE_BALL_AND_STICK) return fail(c, VTX_ERR_INVALID_ARG, "bad mode");
   if (s->ssao_samples < 0 || s->ssao_samples > VTX_MAX_SSAO_SAMPLES)
     return fail(c, VTX_ERR_INVALID_ARG, "ssao_samples out of range");
-  int tw = s->tile_w ? s->tile_w : 16, th = s->tile_h ? s->tile_h : 16;
-  if (!((tw == 16 && th == 16) || (tw == 32 && th == 8) || (tw == 8 && th == 8)))
-    return fail(c, VTX_ERR_INVALID_ARG, "unsupported tile size");
+  if (s->tile_w != 0) {
+    int tw = s->tile_w, th = s->tile_h;
+    if (!((tw == 16 && th == 16) || (tw == 32 && th == 8) || (tw == 8 && th == 8)))
+      return fail(c, VTX_ERR_INVALID_ARG, "unsupported tile size");
+  }
   if (s->splat_max_px < 0) return fail(c, VTX_ERR_INVALID_ARG, "splat_max_px < 0");
   if (s->mode == VTX_MODE_BALL_AND_STICK && (!(s->ball_radius >= 0.0f) || !(s->bond_radius > 0.0f)))
     return fail(c, VTX_ERR_INVALID_ARG, "ball-and-stick radii");
@@ -438,6 +448,93 @@ static vtx_status render_once(vtx_ctx *c, const vtx_settings *s, const vtx_outpu
   return VTX_OK;
 }
 
+}  // extern "C"
+
+// ------------------------------------------------------------ autotuner --
+// Tile shape x direct-splat threshold, chosen by timing every candidate on
+// the caller's own frame (or first frames of a batch) once per problem class.
+static const int kTuneShapes[3][2] = {{16, 16}, {32, 8}, {8, 8}};
+static const int kTuneSplat[3] = {4, 16, 64};
+
+static int ilog2ll(long long v) {
+  int r = 0;
+  while (v > 1) {
+    v >>= 1;
+    ++r;
+  }
+  return r;
+}
+
+// fn(settings) enqueues one run; returns the milliseconds it took (after a sync), or < 0 on error.
+template <class Fn>
+static vtx_status tune(vtx_ctx *c, const long long key[6], const vtx_settings *s, vtx_settings *chosen, Fn run) {
+  *chosen = *s;
+  for (auto &t : c->tunes)
+    if (std::equal(t.key, t.key + 6, key)) {
+      chosen->tile_w = t.tw;
+      chosen->tile_h = t.th;
+      chosen->splat_max_px = t.splat;
+      c->last_tw = t.tw;
+      c->last_th = t.th;
+      c->last_splat = t.splat;
+      return VTX_OK;
+    }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 3.4e38f;
+  int bi = 0, bj = 1;
+  vtx_status st = VTX_OK;
+  for (int i = 0; i < 3 && !st; ++i)
+    for (int j = 0; j < 3 && !st; ++j) {
+      vtx_settings cand = *s;
+      cand.tile_w = kTuneShapes[i][0];
+      cand.tile_h = kTuneShapes[i][1];
+      cand.splat_max_px = kTuneSplat[j];
+      cand.flags &= ~(uint32_t)(VTX_FLAG_SYNC | VTX_FLAG_PROFILE);
+      // warm-up (also grows the arena), then one timed run
+      for (int attempt = 0; attempt < 4; ++attempt) {
+        st = run(&cand);
+        if (st) break;
+        st = check_status(c);
+        if (st != VTX_ERR_CAPACITY) break;
+        c->err.clear();
+        st = VTX_OK;
+      }
+      if (st) break;
+      cudaEventRecord(e0, c->stream);
+      st = run(&cand);
+      cudaEventRecord(e1, c->stream);
+      if (st) break;
+      cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        bi = i;
+        bj = j;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st) return st;
+  vtx_ctx::Tune t;
+  std::copy(key, key + 6, t.key);
+  t.tw = kTuneShapes[bi][0];
+  t.th = kTuneShapes[bi][1];
+  t.splat = kTuneSplat[bj];
+  c->tunes.push_back(t);
+  chosen->tile_w = t.tw;
+  chosen->tile_h = t.th;
+  chosen->splat_max_px = t.splat;
+  c->last_tw = t.tw;
+  c->last_th = t.th;
+  c->last_splat = t.splat;
+  return VTX_OK;
+}
+
+extern "C" {
+
 vtx_status vtx_render_frame(vtx_ctx *c, const vtx_settings *s, const vtx_outputs *out) {
   if (!c) return VTX_ERR_INVALID_ARG;
   cudaSetDevice(c->device);
@@ -449,6 +546,13 @@ vtx_status vtx_render_frame(vtx_ctx *c, const vtx_settings *s, const vtx_outputs
   if (c->n_atoms > 0 && !c->xyzr) return fail(c, VTX_ERR_STATE, "no atoms uploaded");
   if (s->mode == VTX_MODE_BALL_AND_STICK && c->n_bonds > 0 && c->n_atoms == 0)
     return fail(c, VTX_ERR_STATE, "bonds without atoms");
+  vtx_settings tuned;
+  if (s->tile_w == 0) {
+    const long long key[6] = {0, c->cam.width, c->cam.height, 1, ilog2ll(c->n_atoms + c->n_bonds + 1), s->mode};
+    st = tune(c, key, s, &tuned, [&](const vtx_settings *cand) { return render_once(c, cand, out, nullptr); });
+    if (st) return st;
+    s = &tuned;
+  }
   for (int attempt = 0; attempt < 4; ++attempt) {
     StageEvents ev;
     st = render_once(c, s, out, events_for(c, s, ev));
@@ -611,6 +715,16 @@ vtx_status vtx_render_batch(vtx_ctx *c, const float *frames_xyzr, int64_t frame_
   if (e != cudaSuccess) return cuda_fail(c, e, "counts upload");
   cudaEventRecord(c->counts_done, c->stream);
   const long long *d_counts = (const long long *)c->counts.p;
+  vtx_settings tuned;
+  if (s->tile_w == 0) {  // tune on the first (up to) four frames
+    const long long key[6] = {1, cams[0].width, cams[0].height, n_views, ilog2ll(frame_stride + 1), s->mode};
+    const int nf = n_frames < 4 ? n_frames : 4;
+    st = tune(c, key, s, &tuned, [&](const vtx_settings *cand) {
+      return batch_all(c, frames_xyzr, frame_stride, d_counts, nf, cams, n_views, cand, out, nullptr);
+    });
+    if (st) return st;
+    s = &tuned;
+  }
   if (!use_graph) {
     for (int attempt = 0; attempt < 4; ++attempt) {
       StageEvents ev;
@@ -772,6 +886,15 @@ vtx_status vtx_stage_times(vtx_ctx *c, const char **names, float *ms, int32_t *n
   *n = cap;
   if (runs) *runs = (int32_t)c->ev_used;
   c->ev_used = 0;
+  return VTX_OK;
+}
+
+vtx_status vtx_tuned_settings(const vtx_ctx *c, int32_t *tile_w, int32_t *tile_h, int32_t *splat_max_px) {
+  if (!c || !tile_w || !tile_h || !splat_max_px) return VTX_ERR_INVALID_ARG;
+  if (c->last_tw == 0) return VTX_ERR_STATE;
+  *tile_w = c->last_tw;
+  *tile_h = c->last_th;
+  *splat_max_px = c->last_splat;
   return VTX_OK;
 }
 

@@ -125,3 +125,31 @@ def test_permutation_relabels_ids():
     h = oracle.hits(s.xyzr, s.cameras[0], oracle.all_pixels(64, 48))
     ok = ((h.flags & oracle.ID_FLAGS) == 0).reshape(48, 64)
     assert np.array_equal(mapped[ok], r0["id"][ok])
+
+
+def test_autotuner_choice_and_config_independence():
+    """tile_w = 0 autotunes; every tile shape / splat threshold gives bit-identical planes."""
+    import torch
+
+    import paper_2501_12750_gb300 as vtx
+    s = scenes.config2(n=30000, width=640, height=360)
+    k = scenes.ssao_kernel()
+    r = vtx.Renderer()
+    r.upload_atoms(torch.from_numpy(s.xyzr).cuda(), torch.from_numpy(s.elem).cuda(), s.palette)
+    r.set_camera(s.cameras[0])
+    outs = {}
+    auto = r.render_frame(vtx.default_settings(ssao_kernel=k, tile_w=0, tile_h=0, flags=vtx.FLAG_SYNC),
+                          width=640, height=360)
+    tw, th, sp = r.tuned_settings()
+    assert (tw, th) in [(16, 16), (32, 8), (8, 8)] and sp in (4, 16, 64)
+    outs["auto"] = {key: v.cpu().numpy() for key, v in auto.items()}
+    for tile in [(16, 16), (32, 8), (8, 8)]:
+        for splat in (0, 4, 64):
+            o = r.render_frame(vtx.default_settings(ssao_kernel=k, tile_w=tile[0], tile_h=tile[1],
+                                                    splat_max_px=splat, flags=vtx.FLAG_SYNC), width=640, height=360)
+            outs[(tile, splat)] = {key: v.cpu().numpy() for key, v in o.items()}
+    ref = outs["auto"]
+    assert (ref["id"] != -1).sum() > 5000
+    for name, o in outs.items():
+        for key in ref:
+            assert np.array_equal(o[key], ref[key], equal_nan=True), (name, key)
