@@ -73,9 +73,20 @@ typedef enum {
   VTX_ERR_STATE = 7        /* call order: no atoms uploaded, no camera set */
 } vtx_status;
 
+/* Representations (the paper's meshless list, Methods "Meshless Representations"). */
 enum {
-  VTX_MODE_VDW = 0,            /* spheres of radius xyzr.w */
-  VTX_MODE_BALL_AND_STICK = 1  /* spheres of radius ball_radius + bond cylinders of radius bond_radius */
+  VTX_MODE_VDW = 0,             /* van der Waals: spheres of radius xyzr.w */
+  VTX_MODE_BALL_AND_STICK = 1,  /* spheres of radius ball_radius + bond cylinders of radius bond_radius */
+  VTX_MODE_STICKS = 2,          /* spheres and bond cylinders, all of radius bond_radius */
+  VTX_MODE_SAS = 3              /* solvent accessible surface: spheres of radius xyzr.w + probe_radius */
+};
+
+/* Shading models (the paper's list, "High Quality Rendering": flat, matte, glossy, toon). */
+enum {
+  VTX_SHADE_GLOSSY = 0,  /* Blinn-Phong: albedo (ka + kd max(n.L,0)) + ks [n.L>0] max(n.H,0)^shininess */
+  VTX_SHADE_FLAT = 1,    /* albedo */
+  VTX_SHADE_MATTE = 2,   /* albedo (ka + kd max(n.L,0)) */
+  VTX_SHADE_TOON = 3     /* albedo (ka + kd b), b = min(floor(max(n.L,0) L), L-1) / (L-1), L = toon_levels */
 };
 
 enum {
@@ -102,11 +113,12 @@ typedef struct {
 
 /*
  * Rendering settings.  vtx_default_settings() fills the values used by the
- * tests: Blinn-Phong ka 0.2, kd 0.7, ks 0.3, shininess 32, light (0.25, 0.5, 1)
- * in view space, white background, no SSAO, 16x16 tiles, direct splat up to
- * 16 candidate pixels (tile_w = 0 lets the library autotune both).  The
- * paper names the techniques (glossy shading, screen-space ambient
- * occlusion) but not these constants.
+ * tests: glossy (Blinn-Phong) ka 0.2, kd 0.7, ks 0.3, shininess 32, light
+ * (0.25, 0.5, 1) in view space, white background, no SSAO, 16x16 tiles,
+ * direct splat up to 16 candidate pixels (tile_w = 0 lets the library
+ * autotune both), 4 toon bands, SAS probe 1.4 A, no clipping, fog or outline.
+ * The paper names these techniques but not their constants.  Order of the
+ * per-pixel operations: shade, times AO, outline (replaces the colour), fog.
  */
 typedef struct {
   int32_t mode;          /* VTX_MODE_* */
@@ -122,6 +134,17 @@ typedef struct {
   int32_t tile_w, tile_h; /* 16x16, 32x8 or 8x8; tile_w = 0: autotune tile shape AND splat_max_px (below) */
   int32_t splat_max_px;  /* primitives whose candidate pixel box is <= this are splatted directly (0 = 16) */
   uint32_t flags;        /* VTX_FLAG_* */
+  /* post-processes and variants (the paper's list: shading modes, fog, outline; Fig. 1C clipping) */
+  int32_t shading;       /* VTX_SHADE_* */
+  int32_t toon_levels;   /* VTX_SHADE_TOON: number of diffuse bands, 2..16 */
+  float probe_radius;    /* VTX_MODE_SAS: added to every atom radius (A) */
+  float clip_plane[4];   /* (nx, ny, nz, d), world space: atoms with n.x + d < 0 are removed (bonds with
+                            either atom removed too); n = 0 disables */
+  float fog_near, fog_far; /* linear fog over this depth range (A) toward the background colour */
+  float fog_density;     /* fog weight at fog_far and beyond, in [0,1]; 0 disables */
+  float outline_depth;   /* A: a covered pixel whose 4-neighbour is background or deeper by more than this
+                            takes outline_color; 0 disables */
+  float outline_color[3];
 } vtx_settings;
 
 /* Output planes (device pointers, caller-owned).  ao may be NULL. */

@@ -35,6 +35,8 @@ FLAG_TIE, FLAG_GRAZE, FLAG_NEAR, FLAG_SPLIT = 1, 2, 4, 16
 FLAG_GRID, FLAG_MARGIN, FLAG_FETCH = 32, 64, 128
 FLAG_CUTOFF, FLAG_ORDER, FLAG_STOP, FLAG_CLAMP = 256, 512, 1024, 2048
 FLAG_SILH = 4096    # SSAO: the pixel's hit lies within SIL_TOL (relative) of its surface's silhouette
+FLAG_BAND = 8192    # toon shading: the diffuse term lies within BAND_TOL of a band boundary
+FLAG_EDGE = 16384   # outline: a neighbour's depth step lies within EDGE_ABS + EDGE_REL * depth of the threshold
 ID_FLAGS = FLAG_TIE | FLAG_GRAZE | FLAG_NEAR
 NO_ID = 0xFFFFFFFF
 
@@ -44,6 +46,9 @@ GRID_ABS = 1e-5     # px: SSAO sample distance to a pixel-grid line ...
 GRID_LEN = 1e-5     # A: ... plus the projected size of this displacement of the sample
 MARGIN_TOL = 5e-5   # A: SSAO occlusion-test margin
 SIL_TOL = 1e-4      # relative: (R^2 - rho^2)/(2 R^2) below this makes an FP32 normal ill-conditioned
+BAND_TOL = 1e-3     # toon: |n.L * levels - boundary| (an FP32 normal is good to 1e-4 per component)
+EDGE_ABS = 1e-4     # A: outline depth-step decision ...
+EDGE_REL = 2e-5     # ... plus this fraction of the pixel's depth (FP32 depth keys)
 
 SHADE_DEFAULTS = dict(ka=0.2, kd=0.7, ks=0.3, shininess=32.0,
                       light_dir=(0.25, 0.5, 1.0), background=(1.0, 1.0, 1.0))
@@ -68,9 +73,11 @@ def lib():
         L = ctypes.CDLL(_SO)
         P = ctypes.c_void_p
         i64, i32, f32, f64 = ctypes.c_int64, ctypes.c_int32, ctypes.c_float, ctypes.c_double
-        L.orc_hits.argtypes = [P, i64, P, i64, i32, f32, f32, P, P, i64, f64, f64, P, P, P, P, P, P, P, i32]
+        L.orc_hits.argtypes = [P, i64, P, i64, i32, f32, f32, f32, P, P, P, i64, f64, f64, P, P, P, P, P, P, P,
+                               i32]
         L.orc_hits.restype = i32
-        L.orc_shade.argtypes = [P, P, i64, P, P, P, i64, P, P, P, P, f64, f64, f64, f64, P, P]
+        L.orc_shade.argtypes = [P, P, i64, P, P, P, i64, P, P, P, P, f64, f64, f64, f64, P, i32, i32, f64, P, P]
+        L.orc_post.argtypes = [i64, P, P, P, P, f64, P, f64, f64, f64, P, f64, f64, P, P]
         L.orc_ssao_project.argtypes = [P, P, i64, P, P, P, P, i32, f64, f64, f64, P, P, P]
         L.orc_ssao_resolve.argtypes = [i64, i32, P, P, P, P, P, f64, f64, f64, P, P]
         L.orc_soft_forward.argtypes = [P, i64, P, f64, P, i64, f64, P, P, P, P, P, P, i32]
@@ -108,9 +115,13 @@ class Hits:
     rgb_final: Optional[np.ndarray] = None
 
 
-def hits(xyzr, cam, pix, bonds=None, mode=0, ball_radius=0.4, bond_radius=0.15,
+def hits(xyzr, cam, pix, bonds=None, mode=0, ball_radius=0.4, bond_radius=0.15, probe=1.4, clip=None,
          tie_tol=TIE_TOL, graze_tol=GRAZE_TOL, threads=0) -> Hits:
-    """Nearest hit per listed pixel by brute force over all primitives (FP64)."""
+    """Nearest hit per listed pixel by brute force over all primitives (FP64).
+
+    mode 0 van der Waals, 1 ball-and-stick, 2 sticks, 3 solvent accessible surface (r + probe);
+    clip = (nx, ny, nz, d) keeps atoms with n.X + d >= 0 (a bond needs both of its atoms).
+    """
     xyzr = np.ascontiguousarray(xyzr, dtype=np.float32)
     pix = np.ascontiguousarray(pix, dtype=np.int32).reshape(-1, 2)
     nb = 0 if bonds is None else int(bonds.shape[0])
@@ -119,13 +130,17 @@ def hits(xyzr, cam, pix, bonds=None, mode=0, ball_radius=0.4, bond_radius=0.15,
     out = Hits(pix=pix, depth=np.empty(P), id=np.empty(P, np.uint32), normal=np.empty((P, 3)),
                gap=np.empty(P), flags=np.empty(P, np.int32), side=np.empty(P, np.int32), sil=np.empty(P))
     c = _cam(cam)
-    lib().orc_hits(_p(xyzr), xyzr.shape[0], _p(b), nb, mode, ball_radius, bond_radius, _p(c), _p(pix), P,
+    cl = None if clip is None else np.ascontiguousarray(clip, np.float32).reshape(4)
+    lib().orc_hits(_p(xyzr), xyzr.shape[0], _p(b), nb, mode, ball_radius, bond_radius, probe, _p(cl), _p(c),
+                   _p(pix), P,
                    tie_tol, graze_tol, _p(out.depth), _p(out.id), _p(out.normal), _p(out.gap), _p(out.flags),
                    _p(out.side), _p(out.sil), threads)
     return out
 
 
-def shade(h: Hits, elem, palette, n_atoms, cam, bonds=None, **kw) -> np.ndarray:
+def shade(h: Hits, elem, palette, n_atoms, cam, bonds=None, model=0, toon_levels=4, band_tol=BAND_TOL,
+          **kw) -> np.ndarray:
+    """Colour per hit: model 0 Blinn-Phong, 1 flat albedo, 2 matte (no specular), 3 toon bands."""
     s = dict(SHADE_DEFAULTS)
     s.update(kw)
     P = h.pix.shape[0]
@@ -135,12 +150,13 @@ def shade(h: Hits, elem, palette, n_atoms, cam, bonds=None, **kw) -> np.ndarray:
     b = None if bonds is None else np.ascontiguousarray(bonds, dtype=np.uint32)
     lib().orc_shade(_p(np.ascontiguousarray(elem, np.uint8)), _p(np.ascontiguousarray(palette, np.float32)),
                     n_atoms, _p(b), _p(_cam(cam)), _p(h.pix), P, _p(h.id), _p(h.normal), _p(h.side), _p(light),
-                    s["ka"], s["kd"], s["ks"], s["shininess"], _p(bg), _p(rgb))
+                    s["ka"], s["kd"], s["ks"], s["shininess"], _p(bg), model, toon_levels, band_tol, _p(rgb),
+                    _p(h.flags))
     return rgb
 
 
 def ssao(h: Hits, xyzr, cam, kernel, radius=2.0, bias=0.025, bonds=None, mode=0, ball_radius=0.4,
-         bond_radius=0.15, grid_abs=GRID_ABS, grid_len=GRID_LEN, margin_tol=MARGIN_TOL, sil_tol=SIL_TOL,
+         bond_radius=0.15, probe=1.4, clip=None, grid_abs=GRID_ABS, grid_len=GRID_LEN, margin_tol=MARGIN_TOL, sil_tol=SIL_TOL,
          threads=0):
     """AO per listed pixel; flags gain GRID / MARGIN / FETCH / SILH bits.  Fetched pixels are ray-cast on demand."""
     kernel = np.ascontiguousarray(kernel, np.float32).reshape(-1, 3)
@@ -167,7 +183,7 @@ def ssao(h: Hits, xyzr, cam, kernel, radius=2.0, bias=0.025, bonds=None, mode=0,
     if missing.size:
         mp = np.stack([missing % W, missing // W], axis=1).astype(np.int32)
         hm = hits(xyzr, cam, mp, bonds=bonds, mode=mode, ball_radius=ball_radius, bond_radius=bond_radius,
-                  threads=threads)
+                  probe=probe, clip=clip, threads=threads)
         for k, q in enumerate(missing.tolist()):
             depth_of[q] = hm.depth[k]
             amb_of[q] = int(hm.flags[k] & ID_FLAGS)
@@ -181,18 +197,66 @@ def ssao(h: Hits, xyzr, cam, kernel, radius=2.0, bias=0.025, bonds=None, mode=0,
     return ao
 
 
-def render_pixels(scene, cam_index, pix, kernel=None, threads=0, **shade_kw) -> Hits:
-    """Hits, shading and (when ``kernel`` is given) SSAO at the listed pixels of a scene view."""
+def post(h: Hits, xyzr, cam, rgb, outline_depth=0.0, outline_color=(0.0, 0.0, 0.0), fog_near=0.0, fog_far=0.0,
+         fog_density=0.0, background=SHADE_DEFAULTS["background"], rep=None, threads=0) -> np.ndarray:
+    """Outline, then fog, on colours `rgb` (after shading and AO); 4-neighbour depths are ray-cast on demand."""
+    rep = rep or {}
+    P = h.pix.shape[0]
+    out = np.ascontiguousarray(rgb, np.float64).copy()
+    W, H = int(_cam(cam)["width"][0]), int(_cam(cam)["height"][0])
+    nd = np.full((P, 4), np.nan)
+    na = np.zeros((P, 4), np.int32)
+    if outline_depth > 0.0:
+        off = np.array([[-1, 0], [1, 0], [0, -1], [0, 1]], np.int64)
+        q = h.pix[:, None, :].astype(np.int64) + off[None]
+        inside = (q[..., 0] >= 0) & (q[..., 0] < W) & (q[..., 1] >= 0) & (q[..., 1] < H)
+        lin = q[..., 1] * W + q[..., 0]
+        own = dict(zip((h.pix[:, 1].astype(np.int64) * W + h.pix[:, 0]).tolist(), range(P)))
+        need = np.unique(lin[inside])
+        missing = np.array([v for v in need.tolist() if v not in own], np.int64)
+        depth_of = {v: h.depth[k] for v, k in own.items()}
+        amb_of = {v: int(h.flags[k] & ID_FLAGS) for v, k in own.items()}
+        if missing.size:
+            mp = np.stack([missing % W, missing // W], 1).astype(np.int32)
+            hm = hits(xyzr, cam, mp, threads=threads, **rep)
+            for k, v in enumerate(missing.tolist()):
+                depth_of[v] = hm.depth[k]
+                amb_of[v] = int(hm.flags[k] & ID_FLAGS)
+        flat = lin[inside].tolist()
+        nd[inside] = np.array([depth_of[v] for v in flat]) if flat else []
+        na[inside] = np.array([amb_of[v] for v in flat], np.int32) if flat else []
+    lib().orc_post(P, _p(h.depth), _p(h.id), _p(np.ascontiguousarray(nd)), _p(np.ascontiguousarray(na)),
+                   outline_depth, _p(np.asarray(outline_color, np.float32)), fog_near, fog_far, fog_density,
+                   _p(np.asarray(background, np.float32)), EDGE_ABS, EDGE_REL, _p(out), _p(h.flags))
+    return out
+
+
+REP_KEYS = ("mode", "ball_radius", "bond_radius", "probe", "clip")
+POST_KEYS = ("outline_depth", "outline_color", "fog_near", "fog_far", "fog_density")
+
+
+def render_pixels(scene, cam_index, pix, kernel=None, threads=0, **kw) -> Hits:
+    """Hits, shading, (when ``kernel`` is given) SSAO, then outline and fog at the listed pixels of a scene view.
+
+    Keyword arguments go to the step that takes them: representation (mode, ball_radius, bond_radius, probe,
+    clip), shading (model, toon_levels, ka, kd, ks, shininess, light_dir, background) and post-processing
+    (outline_depth, outline_color, fog_near, fog_far, fog_density).
+    """
     cam = scene.cameras[cam_index]
-    kw = dict(bonds=scene.bonds, mode=scene.mode)
-    h = hits(scene.xyzr, cam, pix, threads=threads, **kw)
-    h.rgb = shade(h, scene.elem, scene.palette, scene.xyzr.shape[0], cam, bonds=scene.bonds, **shade_kw)
+    rep = dict(bonds=scene.bonds, mode=scene.mode)
+    rep.update({k: kw.pop(k) for k in REP_KEYS if k in kw})
+    pk = {k: kw.pop(k) for k in POST_KEYS if k in kw}
+    h = hits(scene.xyzr, cam, pix, threads=threads, **rep)
+    h.rgb = shade(h, scene.elem, scene.palette, scene.xyzr.shape[0], cam, bonds=scene.bonds, **kw)
     if kernel is not None:
-        h.ao = ssao(h, scene.xyzr, cam, kernel, threads=threads, **kw)
+        h.ao = ssao(h, scene.xyzr, cam, kernel, threads=threads, **rep)
         h.rgb_final = h.rgb * h.ao[:, None]
     else:
         h.ao = np.ones(h.pix.shape[0])
         h.rgb_final = h.rgb
+    if pk:
+        h.rgb_final = post(h, scene.xyzr, cam, h.rgb_final, background=kw.get("background",
+                           SHADE_DEFAULTS["background"]), rep=rep, threads=threads, **pk)
     return h
 
 

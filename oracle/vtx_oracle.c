@@ -63,7 +63,9 @@ enum {
   ORC_FLAG_CUTOFF = 256, /* soft: a primitive within tol of the -4 px cutoff */
   ORC_FLAG_ORDER = 512,  /* soft: two contributors' centre depths within tol */
   ORC_FLAG_STOP = 1024,  /* soft: transmittance within tol of the stop threshold */
-  ORC_FLAG_CLAMP = 2048  /* soft: opacity within tol of the 0.99 clamp */
+  ORC_FLAG_CLAMP = 2048, /* soft: opacity within tol of the 0.99 clamp */
+  ORC_FLAG_BAND = 8192,  /* toon: diffuse term within tol of a band boundary */
+  ORC_FLAG_EDGE = 16384  /* outline: a neighbour's depth step within tol of the threshold */
 };
 
 #define ORC_NO_ID 0xFFFFFFFFu
@@ -261,8 +263,23 @@ static inline primhit cylinder_hit(const double *Ci, const double *Cj, double rb
   return h;
 }
 
-static inline double sphere_radius(int mode, float ball_radius, const float *rec) {
-  return mode == 1 ? (double)ball_radius : (double)rec[3];
+/* Sphere radius per representation: 0 van der Waals (r), 1 ball-and-stick (ball radius),
+ * 2 sticks (bond radius), 3 solvent accessible surface (r + probe, summed in float32 as stored). */
+static inline double sphere_radius(int mode, float ball_radius, float bond_radius, float probe, const float *rec) {
+  if (mode == 1) return (double)ball_radius;
+  if (mode == 2) return (double)bond_radius;
+  if (mode == 3) {
+    float r = rec[3] + probe;
+    return (double)r;
+  }
+  return (double)rec[3];
+}
+
+/* Clipping (Fig. 1C): an atom is kept when n.X + d >= 0; plane NULL or n = 0 keeps everything. */
+static inline int clip_keep(const float *plane, const float *X) {
+  if (!plane || (plane[0] == 0.0f && plane[1] == 0.0f && plane[2] == 0.0f)) return 1;
+  double v = (double)plane[0] * X[0] + (double)plane[1] * X[1] + (double)plane[2] * X[2] + (double)plane[3];
+  return v >= 0.0;
 }
 
 /*
@@ -277,12 +294,12 @@ static inline double sphere_radius(int mode, float ball_radius, const float *rec
  * that surface's silhouette (rho: ray-to-centre or ray-to-axis distance).
  */
 int orc_hits(const float *xyzr, int64_t n_atoms, const uint32_t *bonds, int64_t n_bonds, int32_t mode,
-             float ball_radius, float bond_radius, const orc_camera *camera, const int32_t *pix, int64_t n_pix,
-             double tie_tol, double graze_tol, double *depth, uint32_t *id, double *normal, double *gap,
-             int32_t *flags, int32_t *side, double *sil, int32_t n_threads) {
+             float ball_radius, float bond_radius, float probe, const float *clip, const orc_camera *camera,
+             const int32_t *pix, int64_t n_pix, double tie_tol, double graze_tol, double *depth, uint32_t *id,
+             double *normal, double *gap, int32_t *flags, int32_t *side, double *sil, int32_t n_threads) {
   ocam c;
   cam_load(camera, &c);
-  if (mode != 1) n_bonds = 0;
+  if (mode != 1 && mode != 2) n_bonds = 0;
   double *rays = (double *)malloc(sizeof(double) * 4 * (size_t)(n_pix > 0 ? n_pix : 1));
   for (int64_t p = 0; p < n_pix; ++p) {
     pixel_ray(&c, pix[2 * p], pix[2 * p + 1], rays + 4 * p);
@@ -311,9 +328,10 @@ int orc_hits(const float *xyzr, int64_t n_atoms, const uint32_t *bonds, int64_t 
       int64_t p1 = p0 + PB < n_pix ? p0 + PB : n_pix;
       for (int64_t k = lo; k < hi; ++k) {
         if (k < n_atoms) {
+          if (!clip_keep(clip, xyzr + 4 * k)) continue;
           double C[3];
           to_view_f(&c, xyzr + 4 * k, C);
-          double r = sphere_radius(mode, ball_radius, xyzr + 4 * k);
+          double r = sphere_radius(mode, ball_radius, bond_radius, probe, xyzr + 4 * k);
           for (int64_t p = p0; p < p1; ++p) {
             primhit h = sphere_hit(C, r, rays + 4 * p, rays[4 * p + 3], c.znear, graze_tol);
             if (h.amb_t < my[p].tg) my[p].tg = h.amb_t;
@@ -322,6 +340,8 @@ int orc_hits(const float *xyzr, int64_t n_atoms, const uint32_t *bonds, int64_t 
           }
         } else {
           int64_t b = k - n_atoms;
+          if (!clip_keep(clip, xyzr + 4 * (int64_t)bonds[2 * b]) || !clip_keep(clip, xyzr + 4 * (int64_t)bonds[2 * b + 1]))
+            continue;
           double Ci[3], Cj[3];
           to_view_f(&c, xyzr + 4 * (int64_t)bonds[2 * b], Ci);
           to_view_f(&c, xyzr + 4 * (int64_t)bonds[2 * b + 1], Cj);
@@ -356,7 +376,7 @@ int orc_hits(const float *xyzr, int64_t n_atoms, const uint32_t *bonds, int64_t 
       if ((int64_t)s.id1 < n_atoms) {
         double C[3];
         to_view_f(&c, xyzr + 4 * (int64_t)s.id1, C);
-        double r = sphere_radius(mode, ball_radius, xyzr + 4 * (int64_t)s.id1);
+        double r = sphere_radius(mode, ball_radius, bond_radius, probe, xyzr + 4 * (int64_t)s.id1);
         for (int k = 0; k < 3; ++k) normal[3 * p + k] = (P[k] - C[k]) / r;
         double tc = dot3(u, C) / u[3];
         double q[3] = {C[0] - tc * u[0], C[1] - tc * u[1], C[2] - tc * u[2]};
@@ -392,7 +412,8 @@ int orc_hits(const float *xyzr, int64_t n_atoms, const uint32_t *bonds, int64_t 
 void orc_shade(const uint8_t *elem, const float *palette, int64_t n_atoms, const uint32_t *bonds,
                const orc_camera *camera, const int32_t *pix, int64_t n_pix, const uint32_t *id, const double *normal,
                const int32_t *side, const float *light_dir, double ka, double kd, double ks, double shininess,
-               const float *background, double *rgb) {
+               const float *background, int32_t model, int32_t toon_levels, double band_tol, double *rgb,
+               int32_t *flags) {
   ocam c;
   cam_load(camera, &c);
   double L[3] = {light_dir[0], light_dir[1], light_dir[2]};
@@ -418,8 +439,19 @@ void orc_shade(const uint8_t *elem, const float *palette, int64_t n_atoms, const
     for (int k = 0; k < 3; ++k) Hh[k] /= hn;
     const double *n = normal + 3 * p;
     double nl = dot3(n, L), nh = dot3(n, Hh);
-    double diff = ka + kd * (nl > 0.0 ? nl : 0.0);
-    double spec = nl > 0.0 ? ks * pow(nh > 0.0 ? nh : 0.0, shininess) : 0.0;
+    double d = nl > 0.0 ? nl : 0.0;
+    double diff = ka + kd * d, spec = 0.0;
+    if (model == 0) {
+      spec = nl > 0.0 ? ks * pow(nh > 0.0 ? nh : 0.0, shininess) : 0.0;
+    } else if (model == 1) {
+      diff = 1.0;
+    } else if (model == 3) {
+      double x = d * toon_levels;
+      double band = floor(x);
+      if (band > toon_levels - 1) band = toon_levels - 1;
+      if (fabs(x - floor(x + 0.5)) < band_tol && x > 0.5 && x < toon_levels - 0.5) flags[p] |= ORC_FLAG_BAND;
+      diff = ka + kd * band / (toon_levels - 1);
+    }
     for (int k = 0; k < 3; ++k) {
       double v = (double)alb[k] * diff + spec;
       rgb[3 * p + k] = v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v);
@@ -515,6 +547,54 @@ void orc_ssao_resolve(int64_t n_pix, int32_t n_samples, const double *depth, con
       }
     }
     ao[p] = 1.0 - occ / n_samples;
+  }
+}
+
+/* -------------------------------------------------------- post-process -- */
+
+/*
+ * Outline and fog, after shading and ambient occlusion (colour in rgb, in
+ * place).  nbr_depth[p*4 + u] is the depth at the 4-neighbour u (left, right,
+ * up, down; INFINITY for background; NAN when outside the image, which is
+ * ignored); nbr_amb marks id-ambiguous neighbours.  A step within edge_abs +
+ * edge_rel * depth of the threshold flags the pixel (EDGE).  A covered pixel with a
+ * neighbour that is background or deeper by more than outline_depth takes
+ * outline_color.  Fog: f = density * clamp((t - near)/(far - near), 0, 1),
+ * colour = (1 - f) colour + f background.
+ */
+void orc_post(int64_t n_pix, const double *depth, const uint32_t *id, const double *nbr_depth, const int32_t *nbr_amb,
+              double outline_depth, const float *outline_color, double fog_near, double fog_far, double fog_density,
+              const float *background, double edge_abs, double edge_rel, double *rgb, int32_t *flags) {
+  for (int64_t p = 0; p < n_pix; ++p) {
+    if (id[p] == ORC_NO_ID) continue;
+    if (outline_depth > 0.0) {
+      int edge = 0;
+      for (int u = 0; u < 4; ++u) {
+        double zq = nbr_depth[4 * p + u];
+        if (zq != zq) continue;
+        if (nbr_amb[4 * p + u]) flags[p] |= ORC_FLAG_FETCH;
+        if (!(zq < INFINITY)) {
+          edge = 1;
+          continue;
+        }
+        double step = zq - depth[p];
+        if (fabs(step - outline_depth) < edge_abs + edge_rel * depth[p]) flags[p] |= ORC_FLAG_EDGE;
+        if (step > outline_depth) edge = 1;
+      }
+      if (edge)
+        for (int k = 0; k < 3; ++k) rgb[3 * p + k] = outline_color[k];
+    }
+    if (fog_density > 0.0) {
+      double span = fog_far - fog_near, fz;
+      if (span > 0.0) {
+        fz = (depth[p] - fog_near) / span;
+        fz = fz < 0.0 ? 0.0 : (fz > 1.0 ? 1.0 : fz);
+      } else {
+        fz = depth[p] >= fog_far ? 1.0 : 0.0;
+      }
+      double fw = fog_density * fz;
+      for (int k = 0; k < 3; ++k) rgb[3 * p + k] = rgb[3 * p + k] + fw * ((double)background[k] - rgb[3 * p + k]);
+    }
   }
 }
 

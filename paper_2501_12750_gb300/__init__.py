@@ -23,6 +23,9 @@ from ._native import VtxCamera, VtxOutputs, VtxSettings, load
 
 MODE_VDW = 0
 MODE_BALL_AND_STICK = 1
+MODE_STICKS = 2
+MODE_SAS = 3
+SHADE_GLOSSY, SHADE_FLAT, SHADE_MATTE, SHADE_TOON = 0, 1, 2, 3
 FLAG_SYNC = 1
 FLAG_PROFILE = 2
 FLAG_NO_SSAO = 4
@@ -63,9 +66,9 @@ def default_settings(ssao_kernel: Optional[np.ndarray] = None, **kw) -> VtxSetti
             for c in range(3):
                 s.ssao_kernel[j][c] = float(k[j, c])
     for key, val in kw.items():
-        if key in ("light_dir", "background"):
+        if key in ("light_dir", "background", "outline_color", "clip_plane"):
             arr = getattr(s, key)
-            for c in range(3):
+            for c in range(len(arr)):
                 arr[c] = float(val[c])
         else:
             setattr(s, key, val)

@@ -85,7 +85,10 @@ class VtxSettings(ctypes.Structure):
                 ("light_dir", c_float * 3), ("background", c_float * 3),
                 ("ssao_samples", c_int32), ("ssao_radius", c_float), ("ssao_bias", c_float),
                 ("ssao_kernel", (c_float * 3) * 64),
-                ("tile_w", c_int32), ("tile_h", c_int32), ("splat_max_px", c_int32), ("flags", c_uint32)]
+                ("tile_w", c_int32), ("tile_h", c_int32), ("splat_max_px", c_int32), ("flags", c_uint32),
+                ("shading", c_int32), ("toon_levels", c_int32), ("probe_radius", c_float),
+                ("clip_plane", c_float * 4), ("fog_near", c_float), ("fog_far", c_float), ("fog_density", c_float),
+                ("outline_depth", c_float), ("outline_color", c_float * 3)]
 
 
 class VtxOutputs(ctypes.Structure):

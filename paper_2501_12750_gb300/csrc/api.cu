@@ -146,7 +146,13 @@ static bool cam_ok(const vtx_camera *c) {
 
 static vtx_status settings_ok(vtx_ctx *c, const vtx_settings *s) {
   if (!s) return fail(c, VTX_ERR_INVALID_ARG, "settings is NULL");
-  if (s->mode != VTX_MODE_VDW && s->mode != VTX_MODE_BALL_AND_STICK) return fail(c, VTX_ERR_INVALID_ARG, "bad mode");
+  if (s->mode < VTX_MODE_VDW || s->mode > VTX_MODE_SAS) return fail(c, VTX_ERR_INVALID_ARG, "bad mode");
+  if (s->shading < VTX_SHADE_GLOSSY || s->shading > VTX_SHADE_TOON) return fail(c, VTX_ERR_INVALID_ARG, "bad shading");
+  if (s->shading == VTX_SHADE_TOON && (s->toon_levels < 2 || s->toon_levels > 16))
+    return fail(c, VTX_ERR_INVALID_ARG, "toon_levels must be 2..16");
+  if (!(s->fog_density >= 0.0f && s->fog_density <= 1.0f)) return fail(c, VTX_ERR_INVALID_ARG, "fog_density");
+  if (!(s->outline_depth >= 0.0f)) return fail(c, VTX_ERR_INVALID_ARG, "outline_depth");
+  if (s->mode == VTX_MODE_SAS && !(s->probe_radius >= 0.0f)) return fail(c, VTX_ERR_INVALID_ARG, "probe_radius");
   if (s->ssao_samples < 0 || s->ssao_samples > VTX_MAX_SSAO_SAMPLES)
     return fail(c, VTX_ERR_INVALID_ARG, "ssao_samples out of range");
   if (s->tile_w != 0) {
@@ -155,7 +161,8 @@ static vtx_status settings_ok(vtx_ctx *c, const vtx_settings *s) {
       return fail(c, VTX_ERR_INVALID_ARG, "unsupported tile size");
   }
   if (s->splat_max_px < 0) return fail(c, VTX_ERR_INVALID_ARG, "splat_max_px < 0");
-  if (s->mode == VTX_MODE_BALL_AND_STICK && (!(s->ball_radius >= 0.0f) || !(s->bond_radius > 0.0f)))
+  if ((s->mode == VTX_MODE_BALL_AND_STICK || s->mode == VTX_MODE_STICKS) &&
+      (!(s->ball_radius >= 0.0f) || !(s->bond_radius > 0.0f)))
     return fail(c, VTX_ERR_INVALID_ARG, "ball-and-stick radii");
   return VTX_OK;
 }
@@ -163,6 +170,13 @@ static vtx_status settings_ok(vtx_ctx *c, const vtx_settings *s) {
 static ShadeParams make_shade(const vtx_ctx *c, const vtx_settings *s) {
   ShadeParams sh;
   memset(&sh, 0, sizeof(sh));
+  sh.model = s->shading;
+  sh.toon_levels = s->toon_levels;
+  sh.fog_near = s->fog_near;
+  sh.fog_far = s->fog_far;
+  sh.fog_density = s->fog_density;
+  sh.outline_depth = s->outline_depth;
+  for (int k = 0; k < 3; ++k) sh.outline_color[k] = s->outline_color[k];
   sh.ka = s->ka;
   sh.kd = s->kd;
   sh.ks = s->ks;
@@ -329,6 +343,13 @@ vtx_status vtx_default_settings(vtx_settings *s) {
   s->tile_w = 16;
   s->tile_h = 16;
   s->splat_max_px = 16;
+  s->shading = VTX_SHADE_GLOSSY;
+  s->toon_levels = 4;
+  s->probe_radius = 1.4f;
+  s->fog_near = 0.0f;
+  s->fog_far = 0.0f;
+  s->fog_density = 0.0f;
+  s->outline_depth = 0.0f;
   return VTX_OK;
 }
 
@@ -423,20 +444,27 @@ vtx_status vtx_set_camera(vtx_ctx *c, const vtx_camera *cam) {
   return VTX_OK;
 }
 
+static void set_representation(Geometry &g, const vtx_settings *s) {
+  g.mode = s->mode;
+  g.ball_radius = s->ball_radius;
+  g.bond_radius = s->bond_radius;
+  g.probe = s->probe_radius;
+  for (int k = 0; k < 4; ++k) g.clip[k] = s->clip_plane[k];
+  g.clip_on = (s->clip_plane[0] != 0.0f || s->clip_plane[1] != 0.0f || s->clip_plane[2] != 0.0f) ? 1 : 0;
+}
+
 static vtx_status render_once(vtx_ctx *c, const vtx_settings *s, const vtx_outputs *out, StageEvents *ev) {
   Geometry g;
   int tw = s->tile_w ? s->tile_w : 16, th = s->tile_h ? s->tile_h : 16;
   base_geometry(g, &c->cam, 1, tw, th);
   g.n_frames = 1;
   g.n_img = 1;
-  g.mode = s->mode;
-  g.ball_radius = s->ball_radius;
-  g.bond_radius = s->bond_radius;
+  set_representation(g, s);
   g.splat_max = s->splat_max_px ? s->splat_max_px : 16;
   g.soft = 0;
   g.stride = c->n_atoms;
   g.n_atoms = c->n_atoms;
-  g.n_bonds = s->mode == VTX_MODE_BALL_AND_STICK ? c->n_bonds : 0;
+  g.n_bonds = (s->mode == VTX_MODE_BALL_AND_STICK || s->mode == VTX_MODE_STICKS) ? c->n_bonds : 0;
   g.surv_cap = c->n_atoms + g.n_bonds + cull_survivor_slack(c->n_atoms);
   vtx_status st = prepare(c, g, false, 0);
   if (st) return st;
@@ -611,7 +639,7 @@ static vtx_status batch_once(vtx_ctx *c, const float *frames, int64_t stride, co
   base_geometry(g, cams, n_views, tw, th);
   g.n_frames = nf;
   g.n_img = nf * n_views;
-  g.mode = VTX_MODE_VDW;
+  set_representation(g, s);
   g.splat_max = s->splat_max_px ? s->splat_max_px : 16;
   g.stride = stride;
   g.n_atoms = stride;
@@ -657,7 +685,8 @@ vtx_status vtx_render_batch(vtx_ctx *c, const float *frames_xyzr, int64_t frame_
   cudaSetDevice(c->device);
   vtx_status st = settings_ok(c, s);
   if (st) return st;
-  if (s->mode != VTX_MODE_VDW) return fail(c, VTX_ERR_INVALID_ARG, "batch: van der Waals mode only");
+  if (s->mode != VTX_MODE_VDW && s->mode != VTX_MODE_SAS)
+    return fail(c, VTX_ERR_INVALID_ARG, "batch: van der Waals or SAS mode only (no bonds)");
   if (!frames_xyzr || ((uintptr_t)frames_xyzr & 15u)) return fail(c, VTX_ERR_INVALID_ARG, "frames: NULL or unaligned");
   if (n_frames < 1 || n_views < 1 || n_views > VTX_MAX_VIEWS || !cams || !atom_counts)
     return fail(c, VTX_ERR_INVALID_ARG, "batch: bad frame/view counts");

@@ -171,11 +171,11 @@ __global__ __launch_bounds__(kCullThreads, 5) void k_cull_atoms(Geometry g, cons
       for (int j = 0; j < kPerThread; ++j) {
         bool keep = false;
         if (a[j].w >= 0.0f) {
-          const float r = g.mode == 1 ? g.ball_radius : a[j].w;
+          const float r = atom_radius(g, a[j].w);
           float vx, vy, vz, err;
           view_f32(vp, a[j].x, a[j].y, a[j].z, vx, vy, vz, err);
           const float R = cull_radius(g, vp, r, vz);
-          keep = cull_lean(vp, vx, vy, vz, R + err);
+          keep = cull_lean(vp, vx, vy, vz, R + err) && clip_keep(g, a[j].x, a[j].y, a[j].z);
           if (g.soft && !(vz > vp.znear)) keep = false;
           if (keep) {
             zlo = fminf(zlo, vz - R - err);
@@ -337,11 +337,11 @@ __global__ __launch_bounds__(kCullThreads, 6) void k_cull_one(Geometry g, const 
     for (int j = 0; j < kPerThread; ++j) {
       bool keep = false;
       if (a[j].w >= 0.0f) {
-        const float r = g.mode == 1 ? g.ball_radius : a[j].w;
+        const float r = atom_radius(g, a[j].w);
         float vx, vy, vz, err;
         view_f32(vp, a[j].x, a[j].y, a[j].z, vx, vy, vz, err);
         const float Rm = r + err;
-        keep = cull_lean(vp, vx, vy, vz, Rm);
+        keep = cull_lean(vp, vx, vy, vz, Rm) && clip_keep(g, a[j].x, a[j].y, a[j].z);
         if (keep) {
           zlo = fminf(zlo, vz - Rm);
           zhi = fmaxf(zhi, vz + Rm);
@@ -430,7 +430,7 @@ __global__ __launch_bounds__(kCullThreads) void k_cull_bonds(Geometry g, const f
       float vx, vy, vz, err;
       view_f32(vp, mx, my, mz, vx, vy, vz, err);
       err += 1.2e-7f * (fabsf(mx) + fabsf(my) + fabsf(mz)) + 1e-6f;
-      keep = cull_lean(vp, vx, vy, vz, Rb + err);
+      keep = cull_lean(vp, vx, vy, vz, Rb + err) && clip_keep(g, A.x, A.y, A.z) && clip_keep(g, B.x, B.y, B.z);
       if (keep) {
         zlo = fminf(zlo, vz - Rb - err);
         zhi = fmaxf(zhi, vz + Rb + err);
@@ -500,7 +500,7 @@ __device__ __forceinline__ PrimGeom prim_geom(const Geometry &g, const ViewParam
   PrimGeom p;
   if ((long long)id < g.n_atoms || bonds == nullptr) {
     float4 a = pre ? *pre : X[id];
-    float r = g.mode == 1 ? g.ball_radius : a.w;
+    float r = atom_radius(g, a.w);
     p.rad = r;
     p.hl = 0.0f;
     p.A = make_float3(0.0f, 0.0f, 0.0f);
@@ -1091,14 +1091,36 @@ __device__ __forceinline__ void resolve_pixel(const Geometry &g, const ShadePara
       }
       aof = 1.0f - occ / (float)sh.ssao_n;
     }
+    float3 col = make_float3(c.x * aof, c.y * aof, c.z * aof);
+    if (sh.outline_depth > 0.0f) {
+      // front side of a depth discontinuity: a 4-neighbour is background or deeper by more than outline_depth
+      const unsigned long long *Kimg = keys + (long long)img * ppi;
+      const long long kP = (long long)(key >> 32);
+      const int nx[4] = {px - 1, px + 1, px, px};
+      const int ny[4] = {py, py, py - 1, py + 1};
+      bool edge = false;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (nx[u] < 0 || ny[u] < 0 || nx[u] >= g.W || ny[u] >= g.H) continue;
+        const unsigned long long kq = Kimg[(long long)ny[u] * g.W + nx[u]];
+        if ((uint32_t)kq == kNoId || (float)((long long)(kq >> 32) - kP) * s.invS > sh.outline_depth) edge = true;
+      }
+      if (edge) col = make_float3(sh.outline_color[0], sh.outline_color[1], sh.outline_color[2]);
+    }
+    if (sh.fog_density > 0.0f) {
+      const float span = sh.fog_far - sh.fog_near;
+      const float fz = span > 0.0f ? fminf(fmaxf((t - sh.fog_near) / span, 0.0f), 1.0f) : (t >= sh.fog_far ? 1.0f : 0.0f);
+      const float fw = sh.fog_density * fz;
+      col = make_float3(col.x + fw * (sh.bg[0] - col.x), col.y + fw * (sh.bg[1] - col.y), col.z + fw * (sh.bg[2] - col.z));
+    }
     out.depth[q] = t;
     out.id[q] = id;
     nrm[0] = n.x;
     nrm[ppi] = n.y;
     nrm[2 * ppi] = n.z;
-    rgb[0] = c.x * aof;
-    rgb[ppi] = c.y * aof;
-    rgb[2 * ppi] = c.z * aof;
+    rgb[0] = col.x;
+    rgb[ppi] = col.y;
+    rgb[2 * ppi] = col.z;
     if (out.ao) out.ao[q] = aof;
   }
 }

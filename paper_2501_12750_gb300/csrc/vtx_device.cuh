@@ -57,8 +57,11 @@ struct Geometry {
   int n_views, n_frames, n_img;
   int W, H;
   int tile_w, tile_h, tiles_x, tiles_y, tiles_per_img;
-  int mode;              // 0 = vdW spheres, 1 = ball-and-stick
+  int mode;              // 0 vdW, 1 ball-and-stick, 2 sticks, 3 SAS
   float ball_radius, bond_radius;
+  float probe;           // SAS probe radius
+  float clip[4];         // clip plane (n, d); clip_on = n != 0
+  int clip_on;
   int splat_max;         // max candidate pixels for the direct splat path
   int soft;              // 1 = soft-edge binning (dilated bounds, no splat, every survivor binned)
   float sigma;           // soft: sigmoid width in pixels
@@ -70,6 +73,11 @@ struct Geometry {
 };
 
 struct ShadeParams {
+  int model;             // 0 glossy, 1 flat, 2 matte, 3 toon
+  int toon_levels;
+  float fog_near, fog_far, fog_density;
+  float outline_depth;
+  float outline_color[3];
   float ka, kd, ks, shin;
   float L[3];            // normalised light direction (right-handed view frame)
   float bg[3];
@@ -110,6 +118,21 @@ struct __align__(16) PrimRec {
   float hl;                  // cylinder half length; 0 for spheres
   float ax, ay, az, pad;     // cylinder axis (internal frame)
 };
+
+// Sphere radius of an atom record in the current representation.
+__device__ __forceinline__ float atom_radius(const Geometry &g, float w) {
+  switch (g.mode) {
+    case 1: return g.ball_radius;
+    case 2: return g.bond_radius;
+    case 3: return w + g.probe;
+    default: return w;
+  }
+}
+
+// Clipping (per atom centre): false when the atom is removed.
+__device__ __forceinline__ bool clip_keep(const Geometry &g, float x, float y, float z) {
+  return !g.clip_on || fmaf(g.clip[0], x, fmaf(g.clip[1], y, fmaf(g.clip[2], z, g.clip[3]))) >= 0.0f;
+}
 
 __device__ __forceinline__ long long rec_key(const PrimRec &p) {
   return (long long)(((unsigned long long)(unsigned)p.key_hi << 32) | (unsigned long long)p.key_lo);
@@ -537,6 +560,17 @@ __device__ __forceinline__ void view_f32(const ViewParams &v, float x, float y, 
 // ------------------------------------------------------------- shading --
 
 __device__ __forceinline__ float3 blinn_phong(const ShadeParams &sh, float3 n, const PixRay &r, float3 alb) {
+  if (sh.model == 1) return alb;
+  if (sh.model == 2 || sh.model == 3) {
+    const float nl = fmaxf(n.x * sh.L[0] + n.y * sh.L[1] + n.z * sh.L[2], 0.0f);
+    float b = nl;
+    if (sh.model == 3) {
+      const float lv = (float)sh.toon_levels;
+      b = fminf(floorf(nl * lv), lv - 1.0f) / (lv - 1.0f);
+    }
+    const float d = sh.ka + sh.kd * b;
+    return make_float3(fminf(alb.x * d, 1.0f), fminf(alb.y * d, 1.0f), fminf(alb.z * d, 1.0f));
+  }
   float inv = 1.0f / sqrtf(r.uu);
   float3 V = make_float3(-r.a * inv, -r.b * inv, inv);
   float3 Hv = make_float3(sh.L[0] + V.x, sh.L[1] + V.y, sh.L[2] + V.z);

@@ -26,8 +26,9 @@ AO_ATOL = 2.0 / 255.0
 SSAO_FLAGS = oracle.FLAG_GRID | oracle.FLAG_MARGIN | oracle.FLAG_FETCH | oracle.FLAG_SILH
 
 
-def gpu_render(scene, cam_index=0, ssao=None, mode=None, tile=(16, 16), splat_max=16, bonds=True, renderer=None):
-    """Render a scene view through the C ABI; returns numpy planes."""
+def gpu_render(scene, cam_index=0, ssao=None, mode=None, tile=(16, 16), splat_max=16, bonds=True, renderer=None,
+               **settings):
+    """Render a scene view through the C ABI; returns numpy planes.  Extra keywords go to the settings."""
     import torch
 
     import paper_2501_12750_gb300 as vtx
@@ -37,12 +38,12 @@ def gpu_render(scene, cam_index=0, ssao=None, mode=None, tile=(16, 16), splat_ma
     elem = torch.from_numpy(np.ascontiguousarray(scene.elem)).to(dev)
     r.upload_atoms(xyzr, elem, scene.palette)
     m = scene.mode if mode is None else mode
-    if m == 1 and bonds and scene.bonds is not None and len(scene.bonds):
+    if m in (1, 2) and bonds and scene.bonds is not None and len(scene.bonds):
         r.upload_bonds(torch.from_numpy(scene.bonds.astype(np.int32)).to(dev))
     cam = scene.cameras[cam_index]
     r.set_camera(cam)
     s = vtx.default_settings(ssao_kernel=ssao, mode=m, tile_w=tile[0], tile_h=tile[1], splat_max_px=splat_max,
-                             flags=vtx.FLAG_SYNC)
+                             flags=vtx.FLAG_SYNC, **settings)
     out = r.render_frame(s, width=cam.width, height=cam.height)
     torch.cuda.synchronize()
     res = {k: v.cpu().numpy() for k, v in out.items()}
@@ -79,7 +80,7 @@ def compare(res, h, ssao: bool, allow_excluded=0.005, label="", colour=True):
         rel, nerr = np.zeros(1), 0.0
     bg = (~amb) & (~covered)
     assert np.isinf(g["depth"][bg]).all() and (g["normal"][bg] == 0).all()
-    rgb_ok = (~amb) & ((h.flags & oracle.FLAG_SPLIT) == 0)
+    rgb_ok = (~amb) & ((h.flags & (oracle.FLAG_SPLIT | oracle.FLAG_BAND | oracle.FLAG_EDGE)) == 0)
     if not colour:
         return dict(pixels=n, covered=int(covered.sum()), excluded=int(amb.sum()), depth_rel=float(rel.max()),
                     normal=float(nerr))
@@ -91,8 +92,10 @@ def compare(res, h, ssao: bool, allow_excluded=0.005, label="", colour=True):
         tol = AO_ATOL
     else:
         aoerr = 0.0
-        ref = h.rgb
+        ref = h.rgb_final if h.rgb_final is not None else h.rgb
         tol = RGB_ATOL
+        if h.rgb_final is not None and (h.flags & oracle.FLAG_FETCH).any():
+            rgb_ok &= (h.flags & oracle.FLAG_FETCH) == 0  # outline next to an id-ambiguous neighbour
     cerr = np.abs(g["rgb"][rgb_ok] - ref[rgb_ok]).max() if rgb_ok.any() else 0.0
     assert cerr <= tol, "%s: rgb err %.3g" % (label, cerr)
     excl = amb | (~rgb_ok)
@@ -100,7 +103,8 @@ def compare(res, h, ssao: bool, allow_excluded=0.005, label="", colour=True):
     by_flag = {name: int(((h.flags & bit) != 0)[covered].sum()) for name, bit in
                [("tie", oracle.FLAG_TIE), ("graze", oracle.FLAG_GRAZE), ("near", oracle.FLAG_NEAR),
                 ("split", oracle.FLAG_SPLIT), ("grid", oracle.FLAG_GRID), ("margin", oracle.FLAG_MARGIN),
-                ("fetch", oracle.FLAG_FETCH), ("silh", oracle.FLAG_SILH)]}
+                ("fetch", oracle.FLAG_FETCH), ("silh", oracle.FLAG_SILH), ("band", oracle.FLAG_BAND),
+                ("edge", oracle.FLAG_EDGE)]}
     assert frac <= allow_excluded, "%s: %.3f%% of covered pixels excluded %s" % (label, 100 * frac, by_flag)
     return dict(pixels=n, covered=int(covered.sum()), excluded=int(excl.sum()), depth_rel=float(rel.max()),
                 normal=float(nerr), rgb=float(cerr), ao=float(aoerr))

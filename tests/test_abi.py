@@ -33,8 +33,8 @@ def test_library_exports_every_declared_symbol():
 
 def test_struct_layouts_match_header():
     assert ctypes.sizeof(_native.VtxCamera) == 64
-    # mode..flags: 3 + 4 + 3 + 3 + 3 + 64*3 + 4 scalars of 4 bytes
-    assert ctypes.sizeof(_native.VtxSettings) == 4 * (3 + 4 + 3 + 3 + 3 + 64 * 3 + 4)
+    # mode..flags: 3 + 4 + 3 + 3 + 3 + 64*3 + 4 scalars of 4 bytes; shading..outline_color: 2 + 1 + 4 + 3 + 1 + 3
+    assert ctypes.sizeof(_native.VtxSettings) == 4 * (3 + 4 + 3 + 3 + 3 + 64 * 3 + 4 + 2 + 1 + 4 + 3 + 1 + 3)
     assert ctypes.sizeof(_native.VtxOutputs) == 5 * ctypes.sizeof(ctypes.c_void_p)
 
 

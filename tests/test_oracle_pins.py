@@ -397,3 +397,158 @@ def test_golden_config1_fixture():
     assert h.id.tolist() == g["id"]
     np.testing.assert_allclose(np.where(np.isfinite(h.depth), h.depth, -1.0), g["depth"], rtol=1e-12)
     np.testing.assert_allclose(h.rgb, np.array(g["rgb"]), rtol=1e-12)
+
+
+# ------------------------------------------------ representations, clipping --
+
+def test_sas_centre_depth_is_distance_minus_radius_plus_probe():
+    """Solvent accessible surface: a sphere of r + probe (float32 sum), so the centre depth is D - (r + p)."""
+    D, r, p = 50.0, 1.7, 1.4
+    cam = axis_camera(D, 65, 65, fovy_deg=20.0)
+    xyzr = np.array([[0, 0, 0, r]], np.float32)
+    h = oracle.hits(xyzr, cam, np.array([[32, 32]], np.int32), mode=3, probe=p)
+    R = float(np.float32(np.float32(r) + np.float32(p)))
+    assert h.id[0] == 0 and abs(h.depth[0] - (D - R)) < 1e-10
+    # coverage radius on screen grows accordingly: a ray at lateral offset between r and r + p hits
+    u = rays(cam, oracle.all_pixels(65, 65))
+    lateral = (D - 0.0) * np.hypot(u[:, 0], u[:, 1]) / np.sqrt(1 + u[:, 0] ** 2 + u[:, 1] ** 2)
+    hall = oracle.hits(xyzr, cam, oracle.all_pixels(65, 65), mode=3, probe=p)
+    ok = (hall.flags & oracle.ID_FLAGS) == 0
+    assert np.array_equal((hall.id == 0)[ok], (lateral <= R)[ok])
+
+
+def test_sticks_spheres_take_the_bond_radius():
+    """Sticks: atoms are drawn with the bond radius, so the centre pixel sees depth D - rho_b; bonds stay."""
+    D = 40.0
+    cam = axis_camera(D, 101, 31, fovy_deg=3.0)
+    xyzr = np.array([[-0.75, 0, 0, 1.7], [0.75, 0, 0, 1.5]], np.float32)
+    bonds = np.array([[0, 1]], np.uint32)
+    pix = oracle.all_pixels(101, 31)
+    h = oracle.hits(xyzr, cam, pix, bonds=bonds, mode=2, bond_radius=0.15)
+    rb = float(np.float32(0.15))
+    # the pixel through atom 0's centre: ray (a, b) with a = -0.75 / D at column (a / (th * W/H) + 1) * W / 2 - 0.5
+    th = np.float64(np.float32(cam.tan_half_fovy))
+    col = ((-0.75 / D) / (th * 101 / 31) + 1.0) * 101 / 2 - 0.5
+    k = 15 * 101 + int(round(col))
+    assert h.id[k] in (0, 2)  # the sphere and the bond's cap region meet at the centre line
+    assert abs(h.depth[k] - (D - rb)) < 2e-3  # off-centre by under half a pixel (< 1e-3 A laterally)
+    assert set(np.unique(h.id[h.id != oracle.NO_ID]).tolist()) == {0, 1, 2}
+    # no hit lies further than rho_b from the segment joining the centres
+    t = h.depth[h.id != oracle.NO_ID]
+    u = rays(cam, pix)[h.id != oracle.NO_ID]
+    P = u * t[:, None]
+    P[:, 2] += D
+    x = np.clip(P[:, 0], -0.75, 0.75)
+    dist = np.sqrt((P[:, 0] - x) ** 2 + P[:, 1] ** 2 + P[:, 2] ** 2)
+    assert dist.max() < rb + 1e-9
+
+
+def test_clip_plane_equals_removing_the_clipped_atoms():
+    """Clipping n.X + d >= 0 renders exactly like the scene without the other atoms (ids mapped back)."""
+    s = scenes.random_tiny(31, n=60, width=48, height=40)
+    cam = s.cameras[0]
+    plane = np.array([0.6, -0.8, 0.0, -1.3], np.float32)
+    pix = oracle.all_pixels(48, 40)
+    h = oracle.hits(s.xyzr, cam, pix, clip=plane)
+    keep = s.xyzr[:, :3].astype(np.float64) @ plane[:3].astype(np.float64) + plane[3] >= 0
+    assert 10 < keep.sum() < 50
+    idx = np.nonzero(keep)[0]
+    h2 = oracle.hits(s.xyzr[keep], cam, pix)
+    m = h2.id != oracle.NO_ID
+    mapped = h2.id.copy()
+    mapped[m] = idx[h2.id[m]]
+    assert np.array_equal(mapped, h.id)
+    np.testing.assert_array_equal(h.depth, h2.depth)
+    # a zero normal keeps everything
+    h3 = oracle.hits(s.xyzr, cam, pix, clip=np.zeros(4, np.float32))
+    h4 = oracle.hits(s.xyzr, cam, pix)
+    assert np.array_equal(h3.id, h4.id)
+
+
+def test_clip_plane_drops_a_bond_with_one_atom_clipped():
+    cam = axis_camera(40.0, 101, 31, fovy_deg=3.0)
+    xyzr = np.array([[-0.75, 0, 0, 1.7], [0.75, 0, 0, 1.5]], np.float32)
+    bonds = np.array([[0, 1]], np.uint32)
+    pix = oracle.all_pixels(101, 31)
+    h = oracle.hits(xyzr, cam, pix, bonds=bonds, mode=1, ball_radius=0.4, clip=np.array([-1, 0, 0, 0], np.float32))
+    assert set(np.unique(h.id).tolist()) == {0, oracle.NO_ID}
+
+
+# ------------------------------------------------------ shading variants --
+
+def test_flat_shading_is_the_albedo_and_matte_is_blinn_phong_without_specular():
+    s = scenes.random_tiny(5, n=40, width=40, height=32)
+    cam = s.cameras[0]
+    h = oracle.hits(s.xyzr, cam, oracle.all_pixels(40, 32))
+    cov = h.id != oracle.NO_ID
+    flat = oracle.shade(h, s.elem, s.palette, 40, cam, model=1)
+    np.testing.assert_array_equal(flat[cov], s.palette[s.elem[h.id[cov]]].astype(np.float64))
+    matte = oracle.shade(h, s.elem, s.palette, 40, cam, model=2)
+    glossy0 = oracle.shade(h, s.elem, s.palette, 40, cam, model=0, ks=0.0)
+    np.testing.assert_allclose(matte[cov], glossy0[cov], rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("levels", [2, 4, 7, 16])
+def test_toon_bands_are_monotone_steps_within_one_band_of_matte(levels):
+    """Toon takes at most `levels` values per albedo, is non-decreasing in n.L, and differs from matte by <= kd/(L-1)."""
+    cam = axis_camera(30.0, 81, 81, fovy_deg=12.0)
+    xyzr = np.array([[0, 0, 0, 2.5]], np.float32)
+    elem = np.array([2], np.uint8)
+    h = oracle.hits(xyzr, cam, oracle.all_pixels(81, 81))
+    cov = h.id == 0
+    toon = oracle.shade(h, elem, scenes.PALETTE, 1, cam, model=3, toon_levels=levels)[cov]
+    matte = oracle.shade(h, elem, scenes.PALETTE, 1, cam, model=2)[cov]
+    alb = scenes.PALETTE[2].astype(np.float64)
+    assert len(np.unique(np.round(toon[:, 0], 12))) <= levels
+    assert len(np.unique(np.round(toon[:, 0], 12))) >= min(levels, 2)
+    assert np.all(np.abs(toon - matte) <= 0.7 * alb / (levels - 1) + 1e-12)
+    order = np.argsort(matte[:, 0], kind="stable")
+    assert np.all(np.diff(toon[order, 0]) >= -1e-15)
+    # the brightest band is ka + kd (n.L = 1 reachable: the light direction lies inside the visible cap)
+    assert abs(toon[:, 0].max() - min(alb[0] * 0.9, 1.0)) < 1e-12
+
+
+def test_fog_limits_and_linear_ramp():
+    """Fog: no change before fog_near, the background from fog_far on (density 1), linear in between."""
+    cam = axis_camera(0.0, 3, 1, fovy_deg=1.0)
+    pix = np.array([[1, 0]], np.int32)
+    bg = (1.0, 1.0, 1.0)
+    base = None
+    for z, expect_w in [(10.0, 0.0), (25.0, 0.25), (40.0, 0.625), (60.0, 1.0)]:
+        xyzr = np.array([[0, 0, -z - 1.0, 1.0]], np.float32)
+        s = scenes.Scene("fog", xyzr, np.array([3], np.uint8), [cam], ssao=False)
+        plain = oracle.render_pixels(s, 0, pix)
+        fogged = oracle.render_pixels(s, 0, pix, fog_near=15.0, fog_far=55.0, fog_density=1.0)
+        assert abs(plain.depth[0] - z) < 1e-9
+        expect = plain.rgb_final + expect_w * (np.array(bg) - plain.rgb_final)
+        np.testing.assert_allclose(fogged.rgb_final, expect, atol=1e-12)
+        base = plain
+    assert base is not None
+
+
+def test_outline_marks_exactly_the_covered_pixels_next_to_background_or_a_deep_step():
+    """Brute force over the full depth image: outline where a 4-neighbour is background or deeper than the threshold."""
+    s = scenes.random_tiny(12, n=30, width=40, height=34)
+    cam = s.cameras[0]
+    pix = oracle.all_pixels(40, 34)
+    full = oracle.hits(s.xyzr, cam, pix)
+    Z = full.depth.reshape(34, 40)
+    step = 1.5
+    col = (1.0, 0.0, 0.5)
+    pad = np.pad(Z, 1, constant_values=np.nan)
+    edge = np.zeros_like(Z, bool)
+    for dy, dx in [(0, -1), (0, 1), (-1, 0), (1, 0)]:
+        nb = pad[1 + dy:35 + dy, 1 + dx:41 + dx]
+        with np.errstate(invalid="ignore"):
+            edge |= np.isinf(nb) | (np.nan_to_num(nb - Z, nan=-1.0, posinf=np.inf) > step)
+    edge &= np.isfinite(Z)
+    assert edge.sum() > 30 and (np.isfinite(Z) & ~edge).sum() > 30
+    # a sparse subset of pixels: their neighbours are ray-cast on demand
+    rng = np.random.default_rng(2)
+    sub = pix[rng.choice(len(pix), 400, replace=False)]
+    h = oracle.render_pixels(s, 0, sub, outline_depth=step, outline_color=col)
+    e = edge[sub[:, 1], sub[:, 0]]
+    ok = (h.flags & (oracle.FLAG_EDGE | oracle.FLAG_FETCH | oracle.ID_FLAGS)) == 0
+    got = np.all(np.abs(h.rgb_final - np.array(col)) < 1e-15, axis=1)
+    assert np.array_equal(got[ok & (h.id != oracle.NO_ID)], e[ok & (h.id != oracle.NO_ID)])
+    np.testing.assert_array_equal(h.rgb_final[h.id == oracle.NO_ID], 1.0)
