@@ -572,7 +572,7 @@ vtx_status vtx_render_frame(vtx_ctx *c, const vtx_settings *s, const vtx_outputs
     return fail(c, VTX_ERR_INVALID_ARG, "outputs: depth, id, normal and rgb are required");
   if (!c->has_cam) return fail(c, VTX_ERR_STATE, "no camera set");
   if (c->n_atoms > 0 && !c->xyzr) return fail(c, VTX_ERR_STATE, "no atoms uploaded");
-  if (s->mode == VTX_MODE_BALL_AND_STICK && c->n_bonds > 0 && c->n_atoms == 0)
+  if ((s->mode == VTX_MODE_BALL_AND_STICK || s->mode == VTX_MODE_STICKS) && c->n_bonds > 0 && c->n_atoms == 0)
     return fail(c, VTX_ERR_STATE, "bonds without atoms");
   vtx_settings tuned;
   if (s->tile_w == 0) {

@@ -1190,7 +1190,7 @@ cudaError_t run_binning(const Geometry &g, const Scene &sc, const Scratch &s, cu
     } else {
       k_cull_atoms<false><<<grid, kCullThreads, kCullSmem, st>>>(g, sc.frames, sc.counts, s.state, s.surv, s.status);
     }
-    if (g.mode == 1 && g.n_bonds > 0 && sc.bonds) {
+    if (g.n_bonds > 0 && sc.bonds) {  // n_bonds is zero unless the representation draws bonds
       long long bb = (g.n_bonds + kCullThreads - 1) / kCullThreads;
       int gb = (int)(bb < 8LL * sms ? bb : 8LL * sms);
       k_cull_bonds<<<gb, kCullThreads, 0, st>>>(g, sc.frames, sc.bonds, s.state, s.surv);

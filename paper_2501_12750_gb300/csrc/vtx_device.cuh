@@ -257,8 +257,8 @@ __device__ __forceinline__ PixRay pix_ray(const ViewParams &v, int px, int py) {
   PixRay r;
   r.pxc = (float)px + 0.5f;
   r.pyc = (float)py + 0.5f;
-  r.a = (r.pxc - v.cx) * v.inv_f;
-  r.b = (v.cy - r.pyc) * v.inv_f;
+  r.a = __fmul_rn(__fsub_rn(r.pxc, v.cx), v.inv_f);
+  r.b = __fmul_rn(__fsub_rn(v.cy, r.pyc), v.inv_f);
   r.uu = fmaf(r.a, r.a, fmaf(r.b, r.b, 1.0f));
   return r;
 }
@@ -321,36 +321,37 @@ __device__ __forceinline__ float3 local_o(float u0h, float u0l, float v0h, float
                                           const PixRay &r) {
   float ox = __fsub_rn(__fsub_rn(r.pxc, u0h), u0l);
   float oy = __fsub_rn(__fsub_rn(r.pyc, v0h), v0l);
-  return make_float3(k * ox, -k * oy, dz);
+  return make_float3(__fmul_rn(k, ox), __fmul_rn(-k, oy), dz);
 }
 
 // Entry parameter s (depth = zr + s) of the ray o + s u into a sphere of radius rad at the origin.
+// The hit tests spell every product-sum as an explicit fmaf or a plain
+// operation, leaving the compiler no contraction choice: the direct-splat and
+// binned paths, inlined into different kernels, then produce the same key bits.
 __device__ __forceinline__ bool sphere_local(float3 o, const PixRay &r, float rad, float &s) {
   float ou = fmaf(o.x, r.a, fmaf(o.y, r.b, o.z));
-  float oo = fmaf(o.x, o.x, fmaf(o.y, o.y, o.z * o.z));
-  float disc = fmaf(ou, ou, -r.uu * (oo - rad * rad));
+  float oo = fmaf(o.x, o.x, fmaf(o.y, o.y, __fmul_rn(o.z, o.z)));
+  float disc = fmaf(ou, ou, __fmul_rn(-r.uu, fmaf(-rad, rad, oo)));
   if (!(disc >= 0.0f)) return false;
-  s = (-ou - sqrtf(disc)) / r.uu;
+  s = __fdiv_rn(__fsub_rn(-ou, sqrtf(disc)), r.uu);
   return true;
 }
-
-// Entry into a capped cylinder (axis A through the origin, half length hl,
-// radius rb).  kind: 1 side, 2 cap at +hl, 3 cap at -hl.
 __device__ __forceinline__ bool cylinder_local(float3 o, const PixRay &r, float3 A, float hl, float rb, float &s,
                                                int &kind, float &axial) {
   float ua = fmaf(r.a, A.x, fmaf(r.b, A.y, A.z));
-  float oa = fmaf(o.x, A.x, fmaf(o.y, A.y, o.z * A.z));
-  float3 up = make_float3(r.a - ua * A.x, r.b - ua * A.y, 1.0f - ua * A.z);
-  float3 op = make_float3(o.x - oa * A.x, o.y - oa * A.y, o.z - oa * A.z);
-  float a2 = fmaf(up.x, up.x, fmaf(up.y, up.y, up.z * up.z));
-  float b2 = fmaf(op.x, up.x, fmaf(op.y, up.y, op.z * up.z));
-  float c2 = fmaf(op.x, op.x, fmaf(op.y, op.y, op.z * op.z)) - rb * rb;
+  float oa = fmaf(o.x, A.x, fmaf(o.y, A.y, __fmul_rn(o.z, A.z)));
+  float3 up = make_float3(fmaf(-ua, A.x, r.a), fmaf(-ua, A.y, r.b), fmaf(-ua, A.z, 1.0f));
+  float3 op = make_float3(fmaf(-oa, A.x, o.x), fmaf(-oa, A.y, o.y), fmaf(-oa, A.z, o.z));
+  float a2 = fmaf(up.x, up.x, fmaf(up.y, up.y, __fmul_rn(up.z, up.z)));
+  float b2 = fmaf(op.x, up.x, fmaf(op.y, up.y, __fmul_rn(op.z, up.z)));
+  float c2 = fmaf(-rb, rb, fmaf(op.x, op.x, fmaf(op.y, op.y, __fmul_rn(op.z, op.z))));
+  const float rb2 = __fmul_rn(rb, rb);
   float best = __int_as_float(0x7f800000);
   kind = 0;
   if (a2 > 1e-12f) {
-    float disc = fmaf(b2, b2, -a2 * c2);
+    float disc = fmaf(b2, b2, __fmul_rn(-a2, c2));
     if (disc >= 0.0f) {
-      float s1 = (-b2 - sqrtf(disc)) / a2;
+      float s1 = __fdiv_rn(__fsub_rn(-b2, sqrtf(disc)), a2);
       float ax = fmaf(s1, ua, oa);
       if (fabsf(ax) <= hl) {
         best = s1;
@@ -362,10 +363,10 @@ __device__ __forceinline__ bool cylinder_local(float3 o, const PixRay &r, float3
 #pragma unroll
     for (int sg = 0; sg < 2; ++sg) {
       float tgt = sg == 0 ? hl : -hl;
-      float sc = (tgt - oa) / ua;
+      float sc = __fdiv_rn(__fsub_rn(tgt, oa), ua);
       float qx = fmaf(sc, up.x, op.x), qy = fmaf(sc, up.y, op.y), qz = fmaf(sc, up.z, op.z);
-      float rad2 = fmaf(qx, qx, fmaf(qy, qy, qz * qz));
-      if (rad2 <= rb * rb && sc < best) {
+      float rad2 = fmaf(qx, qx, fmaf(qy, qy, __fmul_rn(qz, qz)));
+      if (rad2 <= rb2 && sc < best) {
         best = sc;
         kind = sg == 0 ? 2 : 3;
       }
