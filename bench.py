@@ -238,14 +238,14 @@ def main():
     alg_bytes = 16.0 * N
     achieved = alg_bytes / (cull_ms * 1e-3) / 1e9
     traffic = None
-    prof = os.path.join(ROOT, "profiles", "k_cull_one_traffic.txt")
+    prof = os.path.join(ROOT, "profiles", "k_cull_direct_traffic.txt")
     if os.path.exists(prof):
         kv = {}
         for ln in open(prof):
             if ":" in ln:
                 key, val = ln.split(":", 1)
                 kv[key.strip()] = val.strip()
-        if kv.get("kernel") == "k_cull_one" and kv.get("atoms") == str(N):
+        if kv.get("kernel") == "k_cull_direct" and kv.get("atoms") == str(N):
             traffic = float(kv["bytes_per_launch"])
 
     # end to end through the host-buffer entry point (copies inside the timed region)
@@ -284,7 +284,7 @@ def main():
                    "atoms": int(N), "width": W, "height": H, "l2": "inputs (1.6 GB) larger than L2; no flush",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "gatoms_per_s": fps * N / 1e9,
-        "roofline": {"bound": "hbm", "kernel": "k_cull_one", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "hbm", "kernel": "k_cull_direct", "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": cull_ms},
         "stages_ms": {kk: v for kk, v in stages.items() if kk != "runs"},

@@ -262,120 +262,94 @@ __global__ __launch_bounds__(kCullThreads, 5) void k_cull_atoms(Geometry g, cons
 
 constexpr int kSlab = 64;  // survivor slots a warp reserves at a time (single-view cull)
 
-// Single-view streaming cull.  As k_cull_atoms, but with no block-wide
-// barrier in the loop: every thread arrives on the stage's "empty" mbarrier
-// once its atoms are in registers and thread 0 refills the stage when all
-// have; survivors go straight to global memory through per-warp slabs of
-// kSlab slots (one global atomic per slab; a ballot that does not fit in the
-// current slab spills into the next one, so only each warp's last slab has
-// unused slots, which are filled with kNoId and skipped by the setup stage);
-// the depth range is kept in registers and reduced once at the end.
-__global__ __launch_bounds__(kCullThreads, 6) void k_cull_one(Geometry g, const float4 *__restrict__ X, ImageState *st,
-                                                              uint32_t *__restrict__ surv, Status *status) {
-  extern __shared__ __align__(128) unsigned char cull_smem[];
-  float4 *s_atoms = reinterpret_cast<float4 *>(cull_smem);
-  __shared__ __align__(8) uint64_t s_full[kStages];
-  __shared__ __align__(8) uint64_t s_empty[kStages];
+// Warp-aggregated survivor append through per-warp slabs: slots [used, kSlab)
+// of the current slab first, the rest in a fresh slab reserved with one
+// global atomic.  All 32 lanes call it together.
+__device__ __forceinline__ void slab_push(bool keep, uint32_t idx, int lane, unsigned lt, uint32_t &slab, int &used,
+                                          unsigned *n_surv, uint32_t *__restrict__ surv, long long cap) {
+  const unsigned m = __ballot_sync(0xffffffffu, keep);
+  if (!m) return;
+  const int c = __popc(m);
+  const int pos = used + __popc(m & lt);
+  uint32_t next = slab;
+  if (used + c > kSlab) {
+    unsigned nb = 0u;
+    if (lane == 0) nb = atomicAdd(n_surv, (unsigned)kSlab);
+    next = __shfl_sync(0xffffffffu, nb, 0);
+  }
+  if (keep) {
+    const long long dst = pos < kSlab ? (long long)slab + pos : (long long)next + (pos - kSlab);
+    if (dst < cap) surv[dst] = idx;
+  }
+  if (used + c > kSlab) {
+    slab = next;
+    used = used + c - kSlab;
+  } else {
+    used += c;
+  }
+}
+
+constexpr int kCullPT = 4;          // atoms per thread per pass of the single-view cull
+constexpr int kCullCtasPerSm = 5;   // resident CTAs per SM of the single-view cull (<= 48 registers)
+
+// Single-view streaming cull with direct streaming loads: each thread issues
+// its kCullPT 16-byte loads for a pass up front (evict-first), then tests
+// them two at a time on the paired FP32 pipes; resident warps hide each
+// other's load latency.  No block-wide barrier: survivors go straight to
+// global memory through per-warp slabs (slab_push; only each warp's last
+// slab has unused slots, which are filled with kNoId and skipped by the setup
+// stage), and the depth range is kept in registers and reduced once at the
+// end.  PLAIN: van der Waals radii and no clip plane.
+template <bool PLAIN>
+__global__ __launch_bounds__(kCullThreads, kCullCtasPerSm) void k_cull_direct(Geometry g, const float4 *__restrict__ X,
+                                                                            ImageState *st,
+                                                                            uint32_t *__restrict__ surv) {
+  static_assert(kCullPT % 2 == 0, "atoms are tested in pairs");
   const ViewParams &vp = g.views[0];
   const long long n = g.n_atoms;
-  const long long n_chunks = (n + kChunk - 1) / kChunk;
-  const long long mine = (long long)blockIdx.x < n_chunks ? (n_chunks - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  constexpr int CH = kCullPT * kCullThreads;
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
-  const long long cap = g.surv_cap;  // slots are reserved past it only if the host sized it wrongly
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
-      mbar_init(&s_full[s], 1u);
-      mbar_init(&s_empty[s], kCullThreads);
-    }
-    fence_mbar_init();
-  }
-  __syncthreads();
-  long long issued = 0;  // thread 0 only
-  if (threadIdx.x == 0) {
-    for (; issued < mine && issued < kStages; ++issued) {
-      const long long a0 = ((long long)blockIdx.x + issued * gridDim.x) * kChunk;
-      const uint32_t bytes = (uint32_t)min((long long)kChunk, n - a0) * 16u;
-      mbar_expect_tx(&s_full[issued], bytes);
-      bulk_g2s(s_atoms + issued * kChunk, X + a0, bytes, &s_full[issued]);
-    }
-  }
+  const long long cap = g.surv_cap;
   uint32_t slab = kNoId;
   int used = kSlab;
   float zlo = __int_as_float(0x7f800000), zhi = 0.0f;
-  int stg = 0;
-  uint32_t phase = 0u;
-  long long k = 0;
-  for (; k < mine; ++k) {
-    const bool ok = mbar_wait_bounded(&s_full[stg], phase, kWaitLimit);
-    if (__any_sync(0xffffffffu, !ok)) {
-      if (lane == 0) atomicOr(&status->overflow, 16u);
-      break;
-    }
-    const long long a0 = ((long long)blockIdx.x + k * gridDim.x) * kChunk;
-    const int cnt = (int)min((long long)kChunk, n - a0);
-    float4 a[kPerThread];
+  for (long long a0 = (long long)blockIdx.x * CH; a0 < n; a0 += (long long)gridDim.x * CH) {
+    float4 a[kCullPT];
 #pragma unroll
-    for (int j = 0; j < kPerThread; ++j) {
-      const int i = j * kCullThreads + threadIdx.x;
-      a[j] = i < cnt ? s_atoms[stg * kChunk + i] : make_float4(0.0f, 0.0f, 0.0f, -1.0f);
-    }
-    mbar_arrive(&s_empty[stg]);
-    if (threadIdx.x == 0 && issued < mine) {  // refill this stage once every thread has read it
-      if (!mbar_wait_bounded(&s_empty[stg], phase, kWaitLimit)) {
-        atomicOr(&status->overflow, 16u);
-      } else {
-        fence_proxy_async();
-        const long long b0 = ((long long)blockIdx.x + issued * gridDim.x) * kChunk;
-        const uint32_t bytes = (uint32_t)min((long long)kChunk, n - b0) * 16u;
-        mbar_expect_tx(&s_full[stg], bytes);
-        bulk_g2s(s_atoms + stg * kChunk, X + b0, bytes, &s_full[stg]);
-        ++issued;
-      }
+    for (int j = 0; j < kCullPT; ++j) {
+      const long long i = a0 + j * kCullThreads + threadIdx.x;
+      a[j] = i < n ? __ldcs(X + i) : make_float4(0.0f, 0.0f, 0.0f, -1.0f);
     }
 #pragma unroll
-    for (int j = 0; j < kPerThread; ++j) {
-      bool keep = false;
-      if (a[j].w >= 0.0f) {
-        const float r = atom_radius(g, a[j].w);
-        float vx, vy, vz, err;
-        view_f32(vp, a[j].x, a[j].y, a[j].z, vx, vy, vz, err);
-        const float Rm = r + err;
-        keep = cull_lean(vp, vx, vy, vz, Rm) && clip_keep(g, a[j].x, a[j].y, a[j].z);
-        if (keep) {
-          zlo = fminf(zlo, vz - Rm);
-          zhi = fmaxf(zhi, vz + Rm);
-        }
+    for (int j = 0; j < kCullPT; j += 2) {
+      const float4 p = a[j], q = a[j + 1];
+      float2 vx, vy, vz, err;
+      const float2 r = PLAIN ? make_float2(p.w, q.w) : make_float2(atom_radius(g, p.w), atom_radius(g, q.w));
+      view_f32x2(vp, make_float2(p.x, q.x), make_float2(p.y, q.y), make_float2(p.z, q.z), vx, vy, vz, err);
+      const float2 Rm = __fadd2_rn(r, err);
+      bool k0, k1;
+      cull_lean_x2(vp, vx, vy, vz, Rm, k0, k1);
+      k0 = k0 && p.w >= 0.0f;
+      k1 = k1 && q.w >= 0.0f;
+      if (!PLAIN) {
+        k0 = k0 && clip_keep(g, p.x, p.y, p.z);
+        k1 = k1 && clip_keep(g, q.x, q.y, q.z);
       }
-      const unsigned m = __ballot_sync(0xffffffffu, keep);
-      if (m) {
-        // slots [used, kSlab) of the current slab first, the rest in a fresh slab
-        const int c = __popc(m);
-        const int pos = used + __popc(m & lt);
-        uint32_t next = slab;
-        if (used + c > kSlab) {
-          unsigned nb = 0u;
-          if (lane == 0) nb = atomicAdd(&st[0].n_surv, (unsigned)kSlab);
-          next = __shfl_sync(0xffffffffu, nb, 0);
-        }
-        if (keep) {
-          const long long dst = pos < kSlab ? (long long)slab + pos : (long long)next + (pos - kSlab);
-          if (dst < cap) surv[dst] = (uint32_t)(a0 + j * kCullThreads + threadIdx.x);
-        }
-        if (used + c > kSlab) {
-          slab = next;
-          used = used + c - kSlab;
-        } else {
-          used += c;
-        }
+      if (k0) {
+        zlo = fminf(zlo, vz.x - Rm.x);
+        zhi = fmaxf(zhi, vz.x + Rm.x);
       }
-    }
-    if (++stg == kStages) {
-      stg = 0;
-      phase ^= 1u;
+      if (k1) {
+        zlo = fminf(zlo, vz.y - Rm.y);
+        zhi = fmaxf(zhi, vz.y + Rm.y);
+      }
+      slab_push(k0, (uint32_t)(a0 + j * kCullThreads + threadIdx.x), lane, lt, slab, used, &st[0].n_surv, surv, cap);
+      slab_push(k1, (uint32_t)(a0 + (j + 1) * kCullThreads + threadIdx.x), lane, lt, slab, used, &st[0].n_surv, surv,
+                cap);
     }
   }
-  if (slab != kNoId)  // the final slab's unused slots become holes
+  if (slab != kNoId)
     for (int i = used + lane; i < kSlab; i += 32)
       if ((long long)slab + i < cap) surv[slab + i] = kNoId;
   warp_minmax(zlo, zhi);
@@ -383,25 +357,17 @@ __global__ __launch_bounds__(kCullThreads, 6) void k_cull_one(Geometry g, const 
     atomicMin(&st[0].zlo_bits, __float_as_uint(fmaxf(zlo, 0.0f)));
     atomicMax(&st[0].zhi_bits, __float_as_uint(zhi));
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {  // copies still in flight (only after a failed wait)
-    uint32_t ph = phase;
-    int sg = stg;
-    for (long long q = k; q < issued; ++q) {
-      mbar_wait_bounded(&s_full[sg], ph, kWaitLimit);
-      if (++sg == kStages) {
-        sg = 0;
-        ph ^= 1u;
-      }
-    }
-  }
 }
 
-long long cull_survivor_slack(long long n_atoms) {
-  const long long chunks = (n_atoms + kChunk - 1) / kChunk;
-  const long long ctas = chunks < 6LL * sm_count() ? (chunks > 0 ? chunks : 1) : 6LL * sm_count();
-  return ctas * (kCullThreads / 32) * kSlab;
+// CTAs of the single-view cull: one per pass of atoms, at most kCullCtasPerSm per SM.
+static long long cull_one_ctas(long long n_atoms) {
+  const long long chunk = (long long)kCullPT * kCullThreads;
+  const long long chunks = (n_atoms + chunk - 1) / chunk;
+  const long long most = (long long)kCullCtasPerSm * sm_count();
+  return chunks < most ? (chunks > 0 ? chunks : 1) : most;
 }
+
+long long cull_survivor_slack(long long n_atoms) { return cull_one_ctas(n_atoms) * (kCullThreads / 32) * kSlab; }
 
 // Bond cylinders (ball-and-stick, single frame, single view): the bounding
 // sphere of each capped cylinder is culled like an atom.
@@ -1172,7 +1138,6 @@ cudaError_t run_binning(const Geometry &g, const Scene &sc, const Scratch &s, cu
     if (!attr) {
       cudaFuncSetAttribute(k_cull_atoms<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCullSmem);
       cudaFuncSetAttribute(k_cull_atoms<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCullSmem);
-      cudaFuncSetAttribute(k_cull_one, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCullSmem);
       attr = true;
     }
     // five resident CTAs per SM in total, spread over the frames of a batch
@@ -1183,8 +1148,11 @@ cudaError_t run_binning(const Geometry &g, const Scene &sc, const Scratch &s, cu
     int bx = (int)(chunks < want ? (chunks > 0 ? chunks : 1) : want);
     dim3 grid(bx, g.n_frames);
     if (g.n_views == 1 && g.n_frames == 1 && sc.counts == nullptr && !g.soft) {
-      const int b1 = (int)(chunks < 6LL * sms ? (chunks > 0 ? chunks : 1) : 6LL * sms);
-      k_cull_one<<<b1, kCullThreads, kCullSmem, st>>>(g, sc.frames, s.state, s.surv, s.status);
+      const int b1 = (int)cull_one_ctas(g.n_atoms);
+      if (g.mode == 0 && !g.clip_on)
+        k_cull_direct<true><<<b1, kCullThreads, 0, st>>>(g, sc.frames, s.state, s.surv);
+      else
+        k_cull_direct<false><<<b1, kCullThreads, 0, st>>>(g, sc.frames, s.state, s.surv);
     } else if (g.n_views == 1) {
       k_cull_atoms<true><<<grid, kCullThreads, kCullSmem, st>>>(g, sc.frames, sc.counts, s.state, s.surv, s.status);
     } else {

@@ -482,6 +482,41 @@ __device__ __forceinline__ bool cull_lean(const ViewParams &v, float vx, float v
   return fabsf(ux - nx) <= hx && fabsf(uy - ny) <= hy;
 }
 
+// cull_lean and view_f32 for two atoms at once on the paired FP32 pipes
+// (sm_100+ FFMA2/FMUL2/FADD2).  Each lane performs exactly the scalar
+// operations of view_f32 / cull_lean in the same order, so the decisions are
+// bit-identical to the scalar forms.
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+
+__device__ __forceinline__ void view_f32x2(const ViewParams &v, float2 x, float2 y, float2 z, float2 &vx, float2 &vy,
+                                           float2 &vz, float2 &err) {
+  const float2 dx = __fadd2_rn(x, bc2(-v.eye[0])), dy = __fadd2_rn(y, bc2(-v.eye[1])),
+               dz = __fadd2_rn(z, bc2(-v.eye[2]));
+  vx = __ffma2_rn(bc2(v.R[0]), dx, __ffma2_rn(bc2(v.R[1]), dy, __fmul2_rn(bc2(v.R[2]), dz)));
+  vy = __ffma2_rn(bc2(v.U[0]), dx, __ffma2_rn(bc2(v.U[1]), dy, __fmul2_rn(bc2(v.U[2]), dz)));
+  vz = __ffma2_rn(bc2(v.F[0]), dx, __ffma2_rn(bc2(v.F[1]), dy, __fmul2_rn(bc2(v.F[2]), dz)));
+  err = make_float2(4e-7f * (fabsf(dx.x) + fabsf(dy.x) + fabsf(dz.x)), 4e-7f * (fabsf(dx.y) + fabsf(dy.y) + fabsf(dz.y)));
+}
+
+__device__ __forceinline__ void cull_lean_x2(const ViewParams &v, float2 vx, float2 vy, float2 vz, float2 Rm, bool &k0,
+                                             bool &k1) {
+  const float2 front = __fadd2_rn(vz, Rm);
+  const float2 r8 = __fmul2_rn(bc2(8.0f), Rm);
+  const float2 rz = make_float2(rcp_approx(vz.x), rcp_approx(vz.y));
+  const float2 rho = __fmul2_rn(Rm, rz);
+  const float2 mx = __fmul2_rn(vx, rz), my = __fmul2_rn(vy, rz);
+  const float2 t = __fmul2_rn(__fmul2_rn(bc2(v.hc), rho), __ffma2_rn(__fmul2_rn(bc2(2.0f), rho), rho, bc2(1.0f)));
+  const float2 amx = make_float2(fabsf(mx.x), fabsf(mx.y)), amy = make_float2(fabsf(my.x), fabsf(my.y));
+  const float2 hx = __ffma2_rn(t, __ffma2_rn(amx, rho, __ffma2_rn(__fmul2_rn(bc2(0.5f), mx), mx, bc2(1.0f))), bc2(v.e0));
+  const float2 hy = __ffma2_rn(t, __ffma2_rn(amy, rho, __ffma2_rn(__fmul2_rn(bc2(0.5f), my), my, bc2(1.0f))), bc2(v.e0));
+  const float2 ux = __ffma2_rn(bc2(v.f), mx, bc2(v.cxm)), uy = __ffma2_rn(bc2(-v.f), my, bc2(v.cym));
+  const float2 nx = make_float2(fminf(fmaxf(rintf(ux.x), 0.0f), v.wm1), fminf(fmaxf(rintf(ux.y), 0.0f), v.wm1));
+  const float2 ny = make_float2(fminf(fmaxf(rintf(uy.x), 0.0f), v.hm1), fminf(fmaxf(rintf(uy.y), 0.0f), v.hm1));
+  const float2 ex = __fadd2_rn(ux, make_float2(-nx.x, -nx.y)), ey = __fadd2_rn(uy, make_float2(-ny.x, -ny.y));
+  k0 = front.x >= v.znear && (!(vz.x > r8.x) || (fabsf(ex.x) <= hx.x && fabsf(ey.x) <= hy.x));
+  k1 = front.y >= v.znear && (!(vz.y > r8.y) || (fabsf(ex.y) <= hx.y && fabsf(ey.y) <= hy.y));
+}
+
 // Candidate pixel box of a sphere from the cull_lean bound (the exact
 // tangent-slope box for spheres that come within 8 radii of the eye plane).
 __device__ __forceinline__ bool lean_box(const ViewParams &v, int W, int H, float vx, float vy, float vz, float Rm,
