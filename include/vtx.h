@@ -173,16 +173,28 @@ vtx_status vtx_set_stream(vtx_ctx *ctx, void *cuda_stream);
 
 /*
  * Record the atom set (the molecule of the paper's Methods: positions, radii).
- * xyzr: device float4 [n_atoms]; elem: device uint8 [n_atoms] element index
- * (< n_elem), may be NULL (element 0); palette_rgb: HOST float [n_elem][3]
- * element colours (copied).  n_atoms in 0..2^31-1, n_elem in 1..32.
+ * xyzr: float4 [n_atoms]; elem: uint8 [n_atoms] element index (< n_elem),
+ * may be NULL (element 0); palette_rgb: HOST float [n_elem][3] element
+ * colours (copied).  n_atoms in 0..2^31-1, n_elem in 1..32.  Not copied: the
+ * arrays must stay valid and unchanged while frames render.
+ *
+ * xyzr and elem may be device memory or PAGE-LOCKED host memory
+ * (cudaHostAlloc / cudaHostRegister).  Host-resident atoms are read by the
+ * kernels over the host link every frame (the streaming cull reads each
+ * record once; setup and resolve read only survivors and visible atoms), so
+ * the atom count is bounded by host memory, not device memory: the
+ * out-of-core form of the paper's Performance evaluation (several hundred
+ * million atoms, streamed).  Pageable host memory returns
+ * VTX_ERR_INVALID_ARG.  The same rule holds for vtx_upload_bonds pairs and
+ * vtx_render_batch frames.
  */
 vtx_status vtx_upload_atoms(vtx_ctx *ctx, const float *xyzr, const uint8_t *elem, const float *palette_rgb,
                             int32_t n_elem, int64_t n_atoms);
 
 /*
  * Record the connectivity (the paper's "connectivity"; drawn as capped
- * cylinders in ball-and-stick).  pairs: device uint32 [n_bonds][2], i < j <
+ * cylinders in ball-and-stick and sticks).  pairs: uint32 [n_bonds][2]
+ * (device or page-locked host memory), i < j <
  * n_atoms, endpoints at least 1e-3 A apart.  n_bonds = 0 clears them.
  */
 vtx_status vtx_upload_bonds(vtx_ctx *ctx, const uint32_t *pairs, int64_t n_bonds);
@@ -211,15 +223,17 @@ vtx_status vtx_render_frame_host(vtx_ctx *ctx, const float *xyzr_host, const uin
 
 /*
  * Batched trajectory rendering (the paper: trajectories re-rendered every
- * frame, ambient occlusion included).  frames_xyzr: device float4
- * [n_frames][frame_stride] (frame f uses its first atom_counts[f] records);
+ * frame, ambient occlusion included).  frames_xyzr: float4
+ * [n_frames][frame_stride] in device or page-locked host memory (a
+ * trajectory larger than device memory streams from the host); frame f uses
+ * its first atom_counts[f] records;
  * atom_counts: HOST int64 [n_frames], uneven allowed, each <= frame_stride;
  * the element array of vtx_upload_atoms is indexed by atom (must cover
  * frame_stride atoms, or be NULL).  cams: HOST [n_views] cameras, all with
  * the same width and height, n_views <= VTX_MAX_VIEWS.  out: ONE vtx_outputs
  * whose planes hold n_frames*n_views images back to back, image index
  * f*n_views + v (plane stride H*W, normal/rgb 3*H*W per image).
- * VTX_MODE_VDW only.  use_graph != 0 captures the whole batch into a CUDA
+ * VTX_MODE_VDW or VTX_MODE_SAS (no bonds).  use_graph != 0 captures the whole batch into a CUDA
  * graph on first use and replays it on later calls with identical
  * arguments (one cudaGraphLaunch per call).
  */

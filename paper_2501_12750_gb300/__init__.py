@@ -113,23 +113,29 @@ class Renderer:
             raise VtxError(code, msg)
 
     # -- scene --------------------------------------------------------------
+    @staticmethod
+    def _visible(t) -> bool:
+        """Device tensor, or a page-locked host tensor the kernels can read over the host link."""
+        return t.is_cuda or t.is_pinned()
+
     def upload_atoms(self, xyzr, elem=None, palette=None):
-        """xyzr: device float32 (N, 4); elem: device uint8 (N,) or None; palette: (E, 3) host floats."""
+        """xyzr: float32 (N, 4), on the device or in page-locked host memory (then streamed from the host by
+        every frame, so N is bounded by host memory); elem: uint8 (N,) likewise, or None; palette: (E, 3)."""
         torch = self._torch
-        assert xyzr.is_cuda and xyzr.dtype == torch.float32 and xyzr.is_contiguous()
+        assert self._visible(xyzr) and xyzr.dtype == torch.float32 and xyzr.is_contiguous()
         pal = np.ascontiguousarray(scenes.PALETTE if palette is None else palette, np.float32).reshape(-1, 3)
         if elem is not None:
-            assert elem.is_cuda and elem.dtype == torch.uint8 and elem.is_contiguous()
+            assert self._visible(elem) and elem.dtype == torch.uint8 and elem.is_contiguous()
         self._keep = [xyzr, elem, pal]
         self._check(self.lib.vtx_upload_atoms(self.ctx, _ptr(xyzr), _ptr(elem), pal.ctypes.data, pal.shape[0],
                                               xyzr.shape[0]))
 
     def upload_bonds(self, pairs):
-        """pairs: device int32/uint32 (B, 2) with i < j."""
+        """pairs: int32/uint32 (B, 2) with i < j, on the device or in page-locked host memory."""
         if pairs is None:
             self._check(self.lib.vtx_upload_bonds(self.ctx, None, 0))
             return
-        assert pairs.is_cuda and pairs.is_contiguous() and pairs.element_size() == 4
+        assert self._visible(pairs) and pairs.is_contiguous() and pairs.element_size() == 4
         self._keep.append(pairs)
         self._check(self.lib.vtx_upload_bonds(self.ctx, _ptr(pairs), pairs.shape[0]))
 
@@ -176,7 +182,8 @@ class Renderer:
 
     def render_batch(self, frames, counts: Sequence[int], cams: List, settings: VtxSettings, out=None,
                      use_graph: bool = False):
-        """frames: device float32 (F, stride, 4); counts: atoms per frame; cams: V cameras of one size."""
+        """frames: float32 (F, stride, 4) on the device or page-locked host; counts: atoms per frame; cams: V
+        cameras of one size."""
         F, stride = frames.shape[0], frames.shape[1]
         V = len(cams)
         carr = (VtxCamera * V)(*[camera_struct(c) for c in cams])

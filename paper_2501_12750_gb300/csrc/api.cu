@@ -405,16 +405,45 @@ vtx_status vtx_set_stream(vtx_ctx *c, void *cuda_stream) {
   return VTX_OK;
 }
 
+// Device-visible address of a caller array: device or managed memory as is,
+// page-locked host memory through its mapped alias (the kernels then read it
+// over the host link, so it never has to fit in device memory).  Pageable
+// host memory is refused rather than relying on the platform's support for
+// device access to it.
+static bool device_visible(vtx_ctx *c, const void *p, const void **dev, const char *what) {
+  *dev = p;
+  if (!p) return true;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    fail(c, VTX_ERR_INVALID_ARG, what);
+    return false;
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return true;
+  if (a.type == cudaMemoryTypeHost && a.devicePointer) {
+    *dev = a.devicePointer;
+    return true;
+  }
+  fail(c, VTX_ERR_INVALID_ARG, what);
+  return false;
+}
+
 vtx_status vtx_upload_atoms(vtx_ctx *c, const float *xyzr, const uint8_t *elem, const float *palette_rgb,
                             int32_t n_elem, int64_t n_atoms) {
   if (!c) return VTX_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
   if (n_atoms < 0 || n_atoms > 2147483647LL) return fail(c, VTX_ERR_INVALID_ARG, "n_atoms out of range");
   if (n_atoms > 0 && !xyzr) return fail(c, VTX_ERR_INVALID_ARG, "xyzr is NULL");
   if (((uintptr_t)xyzr & 15u) != 0) return fail(c, VTX_ERR_INVALID_ARG, "xyzr must be 16-byte aligned");
   if (n_elem < 1 || n_elem > VTX_MAX_ELEMENTS || !palette_rgb)
     return fail(c, VTX_ERR_INVALID_ARG, "palette: need 1..32 elements");
-  c->xyzr = (const float4 *)xyzr;
-  c->elem = elem;
+  const void *dx = nullptr, *de = nullptr;
+  if (!device_visible(c, xyzr, &dx, "xyzr: not device memory or page-locked host memory")) return VTX_ERR_INVALID_ARG;
+  if (!device_visible(c, elem, &de, "elem: not device memory or page-locked host memory")) return VTX_ERR_INVALID_ARG;
+  if (((uintptr_t)dx & 15u) != 0) return fail(c, VTX_ERR_INVALID_ARG, "xyzr alias must be 16-byte aligned");
+  c->xyzr = (const float4 *)dx;
+  c->elem = (const uint8_t *)de;
   c->n_atoms = n_atoms;
   c->n_elem = n_elem;
   for (int e = 0; e < n_elem; ++e)
@@ -430,7 +459,12 @@ vtx_status vtx_upload_bonds(vtx_ctx *c, const uint32_t *pairs, int64_t n_bonds) 
   if (n_bonds < 0 || c->n_atoms + n_bonds > 4294967040LL) return fail(c, VTX_ERR_INVALID_ARG, "n_bonds out of range");
   if (n_bonds > 0 && !pairs) return fail(c, VTX_ERR_INVALID_ARG, "pairs is NULL");
   if (((uintptr_t)pairs & 7u) != 0) return fail(c, VTX_ERR_INVALID_ARG, "pairs must be 8-byte aligned");
-  c->bonds = n_bonds > 0 ? (const uint2 *)pairs : nullptr;
+  cudaSetDevice(c->device);
+  const void *dp = nullptr;
+  if (n_bonds > 0 && !device_visible(c, pairs, &dp, "pairs: not device memory or page-locked host memory"))
+    return VTX_ERR_INVALID_ARG;
+  if (((uintptr_t)dp & 7u) != 0) return fail(c, VTX_ERR_INVALID_ARG, "pairs alias must be 8-byte aligned");
+  c->bonds = n_bonds > 0 ? (const uint2 *)dp : nullptr;
   c->n_bonds = n_bonds;
   drop_graphs(c);
   return VTX_OK;
@@ -688,6 +722,13 @@ vtx_status vtx_render_batch(vtx_ctx *c, const float *frames_xyzr, int64_t frame_
   if (s->mode != VTX_MODE_VDW && s->mode != VTX_MODE_SAS)
     return fail(c, VTX_ERR_INVALID_ARG, "batch: van der Waals or SAS mode only (no bonds)");
   if (!frames_xyzr || ((uintptr_t)frames_xyzr & 15u)) return fail(c, VTX_ERR_INVALID_ARG, "frames: NULL or unaligned");
+  {
+    const void *df_ = nullptr;
+    if (!device_visible(c, frames_xyzr, &df_, "frames: not device memory or page-locked host memory"))
+      return VTX_ERR_INVALID_ARG;
+    if (((uintptr_t)df_ & 15u) != 0) return fail(c, VTX_ERR_INVALID_ARG, "frames alias must be 16-byte aligned");
+    frames_xyzr = (const float *)df_;
+  }
   if (n_frames < 1 || n_views < 1 || n_views > VTX_MAX_VIEWS || !cams || !atom_counts)
     return fail(c, VTX_ERR_INVALID_ARG, "batch: bad frame/view counts");
   if (frame_stride < 1 || frame_stride > 2147483647LL) return fail(c, VTX_ERR_INVALID_ARG, "frame_stride");

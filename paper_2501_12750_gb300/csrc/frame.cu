@@ -551,9 +551,20 @@ __global__ __launch_bounds__(256, 3) void k_setup(Geometry g, const float4 *__re
     a_cur = a_nxt;
     id_nxt = id_nn;
     if (k < n && id != kNoId) {
-      PrimGeom p = prim_geom(g, v, X, bonds, id, s.zlo, s.S, true, &a_here);
-      float Rbox = p.hl == 0.0f ? cull_radius(g, v, p.rad, p.vz) : p.Rb;
-      bool any = lean_box(v, g.W, g.H, p.vx, p.vy, p.vz, Rbox + p.err, box);
+      const bool is_atom = (long long)id < g.n_atoms || bonds == nullptr;
+      bool any = true;
+      if (is_atom) {
+        // candidate box from the FP32 view centre (no precise setup needed for it)
+        const float r = atom_radius(g, a_here.w);
+        float vx, vy, vz, err;
+        view_f32(v, a_here.x, a_here.y, a_here.z, vx, vy, vz, err);
+        any = lean_box(v, g.W, g.H, vx, vy, vz, cull_radius(g, v, r, vz) + err, box);
+      }
+      PrimGeom p;
+      if (any) {
+        p = prim_geom(g, v, X, bonds, id, s.zlo, s.S, !is_atom, &a_here);
+        if (!is_atom) any = lean_box(v, g.W, g.H, p.vx, p.vy, p.vz, p.Rb + p.err, box);
+      }
       if (any) {
         const long long npx = (long long)(box.x1 - box.x0 + 1) * (long long)(box.y1 - box.y0 + 1);
         if (!SOFT && npx <= g.splat_max) {
