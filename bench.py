@@ -286,7 +286,7 @@ def main():
 
     extra = {}
     if not args.no_extra:
-        extra = run_extras(vtx, torch, dev, r)
+        extra = run_extras(vtx, torch, dev, r, s, cam, k)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -324,9 +324,62 @@ def main():
     return 0
 
 
-def run_extras(vtx, torch, dev, r):
+def _frame_ms(vtx, torch, r, settings, out, reps=10):
+    """Mean device time of `reps` frames (CUDA events on the renderer's stream) after 3 warm-ups."""
+    for _ in range(3):
+        r.render_frame(settings, out=out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(r.stream)
+    for _ in range(reps):
+        r.render_frame(settings, out=out)
+    e1.record(r.stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_extras(vtx, torch, dev, r, s3, cam, k):
+    import dataclasses
+
     from paper_2501_12750_gb300 import scenes
     res = {}
+    # 8K headless export of the benchmark frame (1e8 atoms, V1, SSAO), transparent background
+    cam8 = dataclasses.replace(cam, width=7680, height=4320)
+    r.set_camera(cam8)
+    out8 = r.alloc_outputs(7680, 4320)
+    st8 = vtx.default_settings(ssao_kernel=k)
+    r.render_frame(vtx.default_settings(ssao_kernel=k, flags=vtx.FLAG_SYNC), out=out8)
+    f8 = _frame_ms(vtx, torch, r, st8, out8)
+    rgba = r.export_rgba8(out8)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(r.stream)
+    for _ in range(10):
+        r.export_rgba8(out8, rgba=rgba)
+    e1.record(r.stream)
+    torch.cuda.synchronize()
+    x8 = e0.elapsed_time(e1) / 10
+    res["export_8k"] = {"workload": "1e8 atoms, V1, 7680x4320, SSAO16, RGBA8 with background alpha",
+                        "frame_ms": f8, "frames_per_s": 1e3 / f8, "export_ms": x8,
+                        "export_gb_per_s": 7680 * 4320 * 20 / x8 / 1e6}
+    del out8, rgba
+    r.set_camera(cam)
+    torch.cuda.empty_cache()
+    # size sweep on the whole-cell generator (the paper's 1.07e6 and 1.10e7 systems), 3840x2160, V1, SSAO
+    sweep = []
+    for nc in (214, 2200):
+        ss = scenes.config3(n_clusters=nc)
+        rs = vtx.Renderer()
+        rs.upload_atoms(torch.from_numpy(ss.xyzr).to(dev), torch.from_numpy(ss.elem).to(dev), ss.palette)
+        rs.set_camera(ss.cameras[0])
+        so = rs.alloc_outputs(3840, 2160)
+        rs.render_frame(vtx.default_settings(ssao_kernel=k, flags=vtx.FLAG_SYNC), out=so)
+        ms = _frame_ms(vtx, torch, rs, vtx.default_settings(ssao_kernel=k), so, reps=20)
+        sweep.append({"atoms": int(ss.xyzr.shape[0]), "frame_ms": ms, "frames_per_s": 1e3 / ms,
+                      "gatoms_per_s": ss.xyzr.shape[0] / ms / 1e6})
+        del rs, so, ss
+        torch.cuda.empty_cache()
+    res["size_sweep_3840x2160"] = sweep
     # batched trajectory: 256 frames x 4 views, one graph launch, against the per-frame loop
     s4 = scenes.config4()
     frames = torch.from_numpy(s4.frames).to(dev)

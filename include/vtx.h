@@ -264,6 +264,24 @@ vtx_status vtx_render_soft_bwd(vtx_ctx *ctx, const float *xyzr, int64_t n, const
                                int32_t n_views, float sigma_px, const float *g_cov, const float *g_depth,
                                const float *g_normal, float *grad_xyzr);
 
+/*
+ * Headless image export (Methods, High Quality Rendering: images up to 8K
+ * with a custom background of user-defined transparency): packs rendered
+ * planes into interleaved 8-bit RGBA.  R, G, B = round-to-nearest-even(255 *
+ * clamp(c, 0, 1)) of the rgb planes (shading, AO, outline and fog included);
+ * A = 255 where a primitive was hit (id != 0xFFFFFFFF), else
+ * round-to-nearest-even(255 * clamp(background_alpha, 0, 1)) (straight
+ * alpha: background pixels keep the background colour in R, G, B).  rgb:
+ * float [n_images][3][H][W] and id: uint32 [n_images][H][W] as written by
+ * vtx_render_frame / vtx_render_batch; rgba: uint8 [n_images][H][W][4],
+ * 4-byte aligned.  All three may be device or page-locked host memory (a
+ * host rgba buffer is written over the host link, 4 bytes per pixel instead
+ * of the planes' 36).  Enqueued on the context's stream; W, H in 1..16384
+ * (8K = 7680 x 4320).
+ */
+vtx_status vtx_export_rgba8(vtx_ctx *ctx, const float *rgb, const uint32_t *id, int32_t width, int32_t height,
+                            int32_t n_images, float background_alpha, uint8_t *rgba);
+
 /* Synchronise the context's stream and report (once) any device-side error. */
 vtx_status vtx_sync_status(vtx_ctx *ctx);
 

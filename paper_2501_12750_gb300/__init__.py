@@ -167,6 +167,19 @@ class Renderer:
         self._check(self.lib.vtx_render_frame(self.ctx, ctypes.byref(settings), ctypes.byref(o)))
         return out
 
+    def export_rgba8(self, out, background_alpha: float = 0.0, rgba=None):
+        """Pack the rgb and id planes of `out` (one image or a batch) into uint8 RGBA (..., H, W, 4)."""
+        torch = self._torch
+        rgb, ids = out["rgb"], out["id"]
+        H, W = ids.shape[-2], ids.shape[-1]
+        n = ids.numel() // (H * W)
+        if rgba is None:
+            rgba = torch.empty(tuple(ids.shape) + (4,), dtype=torch.uint8, device=ids.device)
+        assert self._visible(rgba) and rgba.dtype == torch.uint8 and rgba.is_contiguous() and rgba.numel() == 4 * n * H * W
+        self._check(self.lib.vtx_export_rgba8(self.ctx, _ptr(rgb), _ptr(ids), W, H, n, float(background_alpha),
+                                              _ptr(rgba)))
+        return rgba
+
     def render_frame_host(self, xyzr_host: np.ndarray, elem_host: Optional[np.ndarray], cam, settings: VtxSettings,
                           out_host: Dict[str, np.ndarray], palette=None):
         """Host buffers in and out (copies inside the call); synchronises."""

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(HERE, "_vtx.so")
-SOURCES = ["frame.cu", "soft.cu", "api.cu", "static_vis.cu"]
+SOURCES = ["frame.cu", "soft.cu", "api.cu", "static_vis.cu", "export.cu"]
 HEADERS = ["vtx_device.cuh", "vtx_internal.h"]
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
@@ -117,6 +117,7 @@ SIGNATURES = {
     "vtx_sync_status": ([c_void_p], c_int32),
     "vtx_stage_times": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
     "vtx_last_error": ([c_void_p], ctypes.c_char_p),
+    "vtx_export_rgba8": ([c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_float, c_void_p], c_int32),
     "vtx_render_visibility_static": ([c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
     "vtx_tuned_settings": ([c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
 }

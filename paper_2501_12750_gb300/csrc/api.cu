@@ -968,6 +968,28 @@ vtx_status vtx_tuned_settings(const vtx_ctx *c, int32_t *tile_w, int32_t *tile_h
   return VTX_OK;
 }
 
+vtx_status vtx_export_rgba8(vtx_ctx *c, const float *rgb, const uint32_t *id, int32_t width, int32_t height,
+                            int32_t n_images, float background_alpha, uint8_t *rgba) {
+  if (!c) return VTX_ERR_INVALID_ARG;
+  if (width < 1 || height < 1 || width > 16384 || height > 16384 || n_images < 1)
+    return fail(c, VTX_ERR_INVALID_ARG, "export: bad image size or count");
+  if (!rgb || !id || !rgba) return fail(c, VTX_ERR_INVALID_ARG, "export: NULL plane");
+  if (((uintptr_t)rgba & 3u) != 0) return fail(c, VTX_ERR_INVALID_ARG, "export: rgba must be 4-byte aligned");
+  if (!(background_alpha == background_alpha)) return fail(c, VTX_ERR_INVALID_ARG, "export: background_alpha is NaN");
+  cudaSetDevice(c->device);
+  const void *dr = nullptr, *di = nullptr, *dout = nullptr;
+  if (!device_visible(c, rgb, &dr, "export: rgb not device or page-locked host memory") ||
+      !device_visible(c, id, &di, "export: id not device or page-locked host memory") ||
+      !device_visible(c, rgba, &dout, "export: rgba not device or page-locked host memory"))
+    return VTX_ERR_INVALID_ARG;
+  if (((uintptr_t)dout & 3u) != 0) return fail(c, VTX_ERR_INVALID_ARG, "export: rgba alias must be 4-byte aligned");
+  const unsigned char bg_a = (unsigned char)std::lrint(255.0f * std::fmin(std::fmax(background_alpha, 0.0f), 1.0f));
+  cudaError_t e = run_export_rgba8((const float *)dr, (const uint32_t *)di, (long long)width * height, n_images,
+                                   bg_a, (uint8_t *)dout, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "export launch");
+  return VTX_OK;
+}
+
 const char *vtx_last_error(const vtx_ctx *c) { return c ? c->err.c_str() : "null context"; }
 
 }  // extern "C"

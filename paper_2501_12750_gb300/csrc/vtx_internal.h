@@ -57,6 +57,10 @@ cudaError_t run_soft_pipeline(const Geometry &g, const Scene &sc, const Scratch 
                               float *normal, const float *g_cov, const float *g_depth, const float *g_normal,
                               float *grad, cudaStream_t st, StageEvents *evs);
 
+// Interleaved RGBA8 of n_img images of ppi pixels from the rgb and id planes (background alpha bg_a).
+cudaError_t run_export_rgba8(const float *rgb, const uint32_t *id, long long ppi, long long n_img, unsigned char bg_a,
+                             uint8_t *rgba, cudaStream_t st);
+
 int sm_count();
 
 // Extra survivor slots the single-view cull may leave as holes (per-warp slabs).
