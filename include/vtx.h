@@ -28,14 +28,16 @@
  *     beyond znear (an entry point in front of znear skips the primitive).
  *   - Normals are reported in the right-handed view frame (x right, y up,
  *     z toward the viewer).
- *   - Output planes are caller-owned DEVICE buffers laid out [H][W]
- *     (normal and rgb: [3][H][W], one plane per component).
+ *   - Output planes are caller-owned buffers laid out [H][W] (normal and
+ *     rgb: [3][H][W], one plane per component), in device memory or, for
+ *     vtx_render_frame, page-locked host memory (written over the host
+ *     link by the resolve kernel).
  *   - Background pixels: depth +inf, id 0xFFFFFFFF, normal 0, rgb =
  *     settings.background, ao 1.
  *   - Primitive ids: atoms 0..n_atoms-1; bond b (ball-and-stick) is
  *     n_atoms + b.  Equal depths resolve to the smaller id.
  *
- * Ownership and asynchrony: device pointers given to vtx_upload_* are
+ * Ownership and asynchrony: pointers given to vtx_upload_* are
  * recorded, not copied; the caller keeps them alive and unchanged until the
  * next upload or vtx_destroy.  Every render call only enqueues work on the
  * context's stream and returns; results are ready after the caller
@@ -147,7 +149,7 @@ typedef struct {
   float outline_color[3];
 } vtx_settings;
 
-/* Output planes (device pointers, caller-owned).  ao may be NULL. */
+/* Output planes (caller-owned; device or, for vtx_render_frame, page-locked host memory).  ao may be NULL. */
 typedef struct {
   float *depth;     /* [H][W] depth of the visible hit, +inf for background */
   uint32_t *id;     /* [H][W] primitive id, 0xFFFFFFFF for background */

@@ -64,6 +64,8 @@ struct vtx_ctx {
   };
   std::vector<Tune> tunes;
   int last_tw = 0, last_th = 0, last_splat = 0;
+  // output planes last checked by visible_outputs (caller pointers -> device-visible aliases)
+  vtx_outputs out_in{}, out_dev{};
   std::string err;
 };
 
@@ -429,6 +431,29 @@ static bool device_visible(vtx_ctx *c, const void *p, const void **dev, const ch
   return false;
 }
 
+// Output planes as the kernels address them: device memory as is, page-locked
+// host planes through their mapped aliases (the resolve then writes them over
+// the host link).  The last translation is cached per context.
+static vtx_status visible_outputs(vtx_ctx *c, const vtx_outputs *in, vtx_outputs *dev) {
+  if (memcmp(in, &c->out_in, sizeof(vtx_outputs)) == 0 && c->out_dev.depth) {
+    *dev = c->out_dev;
+    return VTX_OK;
+  }
+  const void *d[5];
+  const void *src[5] = {in->depth, in->id, in->normal, in->rgb, in->ao};
+  for (int k = 0; k < 5; ++k)
+    if (!device_visible(c, src[k], &d[k], "outputs: not device memory or page-locked host memory"))
+      return VTX_ERR_INVALID_ARG;
+  dev->depth = (float *)d[0];
+  dev->id = (uint32_t *)d[1];
+  dev->normal = (float *)d[2];
+  dev->rgb = (float *)d[3];
+  dev->ao = (float *)d[4];
+  c->out_in = *in;
+  c->out_dev = *dev;
+  return VTX_OK;
+}
+
 vtx_status vtx_upload_atoms(vtx_ctx *c, const float *xyzr, const uint8_t *elem, const float *palette_rgb,
                             int32_t n_elem, int64_t n_atoms) {
   if (!c) return VTX_ERR_INVALID_ARG;
@@ -608,6 +633,9 @@ vtx_status vtx_render_frame(vtx_ctx *c, const vtx_settings *s, const vtx_outputs
   if (c->n_atoms > 0 && !c->xyzr) return fail(c, VTX_ERR_STATE, "no atoms uploaded");
   if ((s->mode == VTX_MODE_BALL_AND_STICK || s->mode == VTX_MODE_STICKS) && c->n_bonds > 0 && c->n_atoms == 0)
     return fail(c, VTX_ERR_STATE, "bonds without atoms");
+  vtx_outputs od;
+  if ((st = visible_outputs(c, out, &od))) return st;
+  out = &od;
   vtx_settings tuned;
   if (s->tile_w == 0) {
     const long long key[6] = {0, c->cam.width, c->cam.height, 1, ilog2ll(c->n_atoms + c->n_bonds + 1), s->mode};

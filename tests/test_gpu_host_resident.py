@@ -128,3 +128,26 @@ def test_three_hundred_million_atoms_streamed_from_host():
     pix = sample_pixels(cam.width, cam.height, 32, 5, covered_mask=cov)
     h = oracle.render_pixels(s, 0, pix)
     compare(res, h, ssao=False, allow_excluded=0.05, label="3e8 host")
+
+
+def test_output_planes_in_page_locked_host_memory():
+    """vtx_render_frame writes straight into page-locked host planes: identical to device planes."""
+    import torch
+
+    import paper_2501_12750_gb300 as vtx
+    s = scenes.config2(n=30000, width=640, height=360)
+    st = vtx.default_settings(ssao_kernel=scenes.ssao_kernel(), outline_depth=1.0, flags=vtx.FLAG_SYNC)
+    r = vtx.Renderer()
+    r.upload_atoms(torch.from_numpy(s.xyzr).pin_memory(), torch.from_numpy(s.elem).pin_memory(), s.palette)
+    r.set_camera(s.cameras[0])
+    dev = r.render_frame(st, width=640, height=360)
+    host = {k: torch.empty_like(v, device="cpu").pin_memory() for k, v in dev.items()}
+    r.render_frame(st, out=host)
+    torch.cuda.synchronize()
+    a, b = _planes(dev), _planes(host)
+    assert (a["id"] != oracle.NO_ID).sum() > 5000
+    _same(a, b, "host outputs")
+    # pageable output planes are refused before any launch
+    bad = {k: np.zeros(tuple(v.shape), np.float32) for k, v in dev.items()}
+    o = vtx.VtxOutputs(*(bad[k].ctypes.data for k in ("depth", "id", "normal", "rgb", "ao")))
+    assert r.lib.vtx_render_frame(r.ctx, ctypes.byref(st), ctypes.byref(o)) == 1
