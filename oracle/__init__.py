@@ -27,6 +27,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "vtx_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "ses_oracle.c")]
 _SO = os.path.join(_HERE, "_vtx_oracle.so")
 
 CFLAGS = ["-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
@@ -56,9 +57,9 @@ SHADE_DEFAULTS = dict(ka=0.2, kd=0.7, ks=0.3, shininess=32.0,
 
 def build(force: bool = False) -> str:
     """Compile the oracle library next to its source (gcc, no GPU needed)."""
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_SO) or any(os.path.getmtime(_SO) < os.path.getmtime(f) for f in _SRCS):
         tmp = _SO + ".%d.tmp" % os.getpid()
-        subprocess.check_call(["gcc", *CFLAGS, _SRC, "-o", tmp, "-lm"])
+        subprocess.check_call(["gcc", *CFLAGS, *_SRCS, "-o", tmp, "-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -78,6 +79,13 @@ def lib():
         L.orc_hits.restype = i32
         L.orc_shade.argtypes = [P, P, i64, P, P, P, i64, P, P, P, P, f64, f64, f64, f64, P, i32, i32, f64, P, P]
         L.orc_post.argtypes = [i64, P, P, P, P, f64, P, f64, f64, f64, P, f64, f64, P, P]
+        L.orc_ses_sas.argtypes = [P, i64, f32, P, f32, P, P, P]
+        L.orc_ses_k.argtypes = [f32, f32]
+        L.orc_ses_k.restype = i32
+        L.orc_ses_edt.argtypes = [P, P, i32, P]
+        L.orc_ses_mc.argtypes = [P, P, P, f32, f32, P, i64, P, P]
+        L.orc_ses_mc.restype = i64
+        L.orc_ses_case_counts.argtypes = [P]
         L.orc_ssao_project.argtypes = [P, P, i64, P, P, P, P, i32, f64, f64, f64, P, P, P]
         L.orc_ssao_resolve.argtypes = [i64, i32, P, P, P, P, P, f64, f64, f64, P, P]
         L.orc_soft_forward.argtypes = [P, i64, P, f64, P, i64, f64, P, P, P, P, P, P, i32]
@@ -292,3 +300,58 @@ def soft_vjp(xyzr64, cam, pix, gA, gD, gN, sigma=0.5, threads=0) -> np.ndarray:
                        _p(np.ascontiguousarray(gA, np.float64)), _p(np.ascontiguousarray(gD, np.float64)),
                        _p(np.ascontiguousarray(gN, np.float64).reshape(-1, 3)), _p(grad), threads)
     return grad
+
+
+# ------------------------------------------------------------------- SES --
+
+@dataclass
+class Ses:
+    origin: np.ndarray   # float32 (3,)
+    h: float
+    dims: np.ndarray     # int32 (nx, ny, nz)
+    K: int
+    sas: np.ndarray      # uint8 [nz][ny][nx]
+    edt2: np.ndarray     # uint16 [nz][ny][nx], K*K + 1 = "farther than K"
+    tris: np.ndarray     # float64 [T][3][3]
+    edges: np.ndarray    # int64 [T][3] vertex labels: cell * 16 + edge (0..11) or cell * 16 + 12 + loop
+
+
+def ses_grid(xyzr, probe=1.4, h=0.5, margin=2):
+    """A grid covering every SAS sphere with `margin` spare points on each side (origin float32, dims int32)."""
+    x = np.asarray(xyzr, np.float64)
+    R = x[:, 3] + probe
+    lo = (x[:, :3] - R[:, None]).min(0) - margin * h
+    hi = (x[:, :3] + R[:, None]).max(0) + margin * h
+    dims = (np.floor((hi - lo) / h).astype(np.int64) + 2).astype(np.int32)
+    return lo.astype(np.float32), np.float32(h), dims
+
+
+def ses(xyzr, origin, h, dims, probe=1.4, offset=None) -> Ses:
+    """SAS interior, windowed squared distance transform and marching-cubes triangles (see ses_oracle.c).
+
+    offset: grid index of this grid's first point within a larger grid of the same origin and spacing (the
+    coordinates are then those of the larger grid; cell labels stay local to this one).
+    """
+    x = np.ascontiguousarray(xyzr, np.float32).reshape(-1, 4)
+    o = np.ascontiguousarray(origin, np.float32).reshape(3)
+    d = np.ascontiguousarray(dims, np.int32).reshape(3)
+    off = None if offset is None else np.ascontiguousarray(offset, np.int32).reshape(3)
+    n = int(d[0]) * int(d[1]) * int(d[2])
+    sas = np.empty(n, np.uint8)
+    lib().orc_ses_sas(_p(x), x.shape[0], probe, _p(o), float(h), _p(d), _p(off), _p(sas))
+    K = int(lib().orc_ses_k(probe, float(h)))
+    edt2 = np.empty(n, np.uint16)
+    lib().orc_ses_edt(_p(sas), _p(d), K, _p(edt2))
+    T = int(lib().orc_ses_mc(_p(edt2), _p(d), _p(o), float(h), probe, _p(off), 0, None, None))
+    tris = np.empty((max(T, 1), 3, 3))
+    edges = np.empty((max(T, 1), 3), np.int64)
+    lib().orc_ses_mc(_p(edt2), _p(d), _p(o), float(h), probe, _p(off), T, _p(tris), _p(edges))
+    shp = (int(d[2]), int(d[1]), int(d[0]))
+    return Ses(o, float(h), d, K, sas.reshape(shp), edt2.reshape(shp), tris[:T], edges[:T])
+
+
+def ses_case_counts() -> np.ndarray:
+    c = np.empty(256, np.int32)
+    lib().orc_ses_case_counts(_p(c))
+    return c
+
