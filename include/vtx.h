@@ -284,6 +284,56 @@ vtx_status vtx_render_soft_bwd(vtx_ctx *ctx, const float *xyzr, int64_t n, const
 vtx_status vtx_export_rgba8(vtx_ctx *ctx, const float *rgb, const uint32_t *id, int32_t width, int32_t height,
                             int32_t n_images, float background_alpha, uint8_t *rgba);
 
+/*
+ * Solvent excluded surface (Methods, "Cartoon and SES representations": the
+ * SES is computed by a discrete approach and extracted with marching cubes).
+ * Grid point (i, j, k) is origin + spacing * (i, j, k).
+ */
+typedef struct {
+  float origin[3];  /* world position of grid point (0, 0, 0), A */
+  float spacing;    /* h > 0, A */
+  int32_t dims[3];  /* grid points along x, y, z, each >= 2; product <= 2^32 */
+  float probe;      /* probe radius p >= 0, A; p / h <= 150 */
+} vtx_ses_grid;
+
+/*
+ * A grid covering every atom's solvent accessible sphere (radius r + probe)
+ * with two spare points on each side: origin = min(c - r - p) - 2 h, dims =
+ * floor((max(c + r + p) - min(c - r - p)) / h) + 6.  xyzr: float4 [n_atoms],
+ * device or page-locked host memory.  Synchronises.
+ */
+vtx_status vtx_ses_fit_grid(vtx_ctx *ctx, const float *xyzr, int64_t n_atoms, float probe, float spacing,
+                            vtx_ses_grid *grid);
+
+/*
+ * The SES of the atoms on `grid` as a triangle soup.  Definitions:
+ *   SAS interior: point X is inside when some atom (c, r) has
+ *     ((X-c)_x^2 + (X-c)_y^2) + (X-c)_z^2 < (r + p)^2, evaluated in FP64 with
+ *     every operation correctly rounded in this order (X = (double)origin +
+ *     (double)h * i per axis);
+ *   edt2: squared distance in grid units to the nearest grid point outside
+ *     the SAS interior, exact when <= K^2 (K = ceil(p / h) + 1), else K^2 + 1;
+ *   SES interior: edt2 * h^2 >= p^2 (FP64);
+ *   marching cubes over the cells, cell order i fastest then j then k; per
+ *     cell, loops of crossing edges (a face with four crossings cuts its
+ *     inside corners apart), each running counter-clockwise about the
+ *     outward normal (inside to outside), starting at its smallest edge
+ *     (corner and edge numbering as in Lorensen and Cline's paper); a
+ *     three-edge loop is one triangle, a longer loop of L edges L triangles
+ *     around the mean of its vertices; a vertex on edge (a, b) is X_a + t (X_b
+ *     - X_a), t = f_a / (f_a - f_b) clamped to [0, 1], f = sqrt(edt2) h - p.
+ * Outputs (device or page-locked host memory): tris float [max_tris][3][3]
+ * (A); labels (nullable) int64 [max_tris][3]: cell * 16 + edge (0..11) for
+ * edge vertices, cell * 16 + 12 + loop for loop means, cell = (k (ny-1) +
+ * j) (nx-1) + i; sas (nullable) uint8 and edt2 (nullable) uint16, both
+ * [nz][ny][nx].  *n_tris (host) receives the total number of triangles;
+ * when it exceeds max_tris only the first max_tris are written and the call
+ * returns VTX_ERR_CAPACITY.  Scratch (7 bytes per grid point) is owned by
+ * the context.  Synchronises.
+ */
+vtx_status vtx_ses_mesh(vtx_ctx *ctx, const float *xyzr, int64_t n_atoms, const vtx_ses_grid *grid, float *tris,
+                        int64_t max_tris, int64_t *labels, uint8_t *sas, uint16_t *edt2, int64_t *n_tris);
+
 /* Synchronise the context's stream and report (once) any device-side error. */
 vtx_status vtx_sync_status(vtx_ctx *ctx);
 

@@ -19,7 +19,7 @@ from typing import Dict, List, Optional, Sequence
 import numpy as np
 
 from . import scenes
-from ._native import VtxCamera, VtxOutputs, VtxSettings, load
+from ._native import VtxCamera, VtxOutputs, VtxSesGrid, VtxSettings, load
 
 MODE_VDW = 0
 MODE_BALL_AND_STICK = 1
@@ -179,6 +179,55 @@ class Renderer:
         self._check(self.lib.vtx_export_rgba8(self.ctx, _ptr(rgb), _ptr(ids), W, H, n, float(background_alpha),
                                               _ptr(rgba)))
         return rgba
+
+    def ses_fit_grid(self, xyzr, probe: float = 1.4, spacing: float = 0.5) -> VtxSesGrid:
+        """Grid covering every solvent accessible sphere of `xyzr` (device or page-locked host float32 (N, 4))."""
+        g = VtxSesGrid()
+        self._check(self.lib.vtx_ses_fit_grid(self.ctx, _ptr(xyzr), xyzr.shape[0], float(probe), float(spacing),
+                                              ctypes.byref(g)))
+        return g
+
+    @staticmethod
+    def ses_grid(origin, spacing, dims, probe=1.4) -> VtxSesGrid:
+        g = VtxSesGrid()
+        for d in range(3):
+            g.origin[d] = float(origin[d])
+            g.dims[d] = int(dims[d])
+        g.spacing = float(spacing)
+        g.probe = float(probe)
+        return g
+
+    def ses_mesh(self, xyzr, grid: VtxSesGrid, max_tris: Optional[int] = None, labels: bool = False,
+                 planes: bool = False):
+        """Solvent excluded surface on `grid` as a triangle soup (device float32 (T, 3, 3)).
+
+        Returns a dict with "tris" and, on request, "labels" (int64 (T, 3)) and the "sas" / "edt2" planes
+        (uint8 / uint16 (nz, ny, nx)).  With max_tris None the call runs twice: once to count.
+        """
+        torch = self._torch
+        assert self._visible(xyzr) and xyzr.dtype == torch.float32 and xyzr.is_contiguous()
+        dev = torch.device("cuda", self.device)
+        nz, ny, nx = grid.dims[2], grid.dims[1], grid.dims[0]
+        sas = torch.empty((nz, ny, nx), dtype=torch.uint8, device=dev) if planes else None
+        edt = torch.empty((nz, ny, nx), dtype=torch.int16, device=dev) if planes else None
+        n = ctypes.c_int64(0)
+        if max_tris is None:
+            code = self.lib.vtx_ses_mesh(self.ctx, _ptr(xyzr), xyzr.shape[0], ctypes.byref(grid), None, 0, None,
+                                         None, None, ctypes.byref(n))
+            if code not in (0, 4):
+                self._check(code)
+            max_tris = n.value
+        tris = torch.empty((max(max_tris, 1), 3, 3), dtype=torch.float32, device=dev)
+        lab = torch.empty((max(max_tris, 1), 3), dtype=torch.int64, device=dev) if labels else None
+        self._check(self.lib.vtx_ses_mesh(self.ctx, _ptr(xyzr), xyzr.shape[0], ctypes.byref(grid), _ptr(tris),
+                                          max_tris, _ptr(lab), _ptr(sas), _ptr(edt), ctypes.byref(n)))
+        out = {"tris": tris[:n.value], "n": n.value}
+        if labels:
+            out["labels"] = lab[:n.value]
+        if planes:
+            out["sas"] = sas
+            out["edt2"] = edt  # uint16 values in int16 storage
+        return out
 
     def render_frame_host(self, xyzr_host: np.ndarray, elem_host: Optional[np.ndarray], cam, settings: VtxSettings,
                           out_host: Dict[str, np.ndarray], palette=None):

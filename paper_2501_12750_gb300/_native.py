@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(HERE, "_vtx.so")
-SOURCES = ["frame.cu", "soft.cu", "api.cu", "static_vis.cu", "export.cu"]
+SOURCES = ["frame.cu", "soft.cu", "api.cu", "static_vis.cu", "export.cu", "ses.cu"]
 HEADERS = ["vtx_device.cuh", "vtx_internal.h"]
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
@@ -91,6 +91,10 @@ class VtxSettings(ctypes.Structure):
                 ("outline_depth", c_float), ("outline_color", c_float * 3)]
 
 
+class VtxSesGrid(ctypes.Structure):
+    _fields_ = [("origin", c_float * 3), ("spacing", c_float), ("dims", c_int32 * 3), ("probe", c_float)]
+
+
 class VtxOutputs(ctypes.Structure):
     _fields_ = [("depth", c_void_p), ("id", c_void_p), ("normal", c_void_p), ("rgb", c_void_p), ("ao", c_void_p)]
 
@@ -117,6 +121,9 @@ SIGNATURES = {
     "vtx_sync_status": ([c_void_p], c_int32),
     "vtx_stage_times": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
     "vtx_last_error": ([c_void_p], ctypes.c_char_p),
+    "vtx_ses_fit_grid": ([c_void_p, c_void_p, c_int64, c_float, c_float, c_void_p], c_int32),
+    "vtx_ses_mesh": ([c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p,
+                      c_void_p], c_int32),
     "vtx_export_rgba8": ([c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_float, c_void_p], c_int32),
     "vtx_render_visibility_static": ([c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
     "vtx_tuned_settings": ([c_void_p, c_void_p, c_void_p, c_void_p], c_int32),

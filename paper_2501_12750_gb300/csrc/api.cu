@@ -46,6 +46,7 @@ struct vtx_ctx {
   // scratch
   Buf keys, surv, state, tcount, tstart, tcursor, tlist, bsums, recs, recimg, recbox, recof, entries, status, counts, hostin_x,
       hostin_e, hostout;
+  Buf ses_sas, ses_a, ses_b, ses_edt, ses_blk, ses_base, ses_total, ses_bbox;
   uint32_t cap_rec = 0;
   unsigned long long cap_entries = 0;
   Status *h_status = nullptr;
@@ -386,7 +387,8 @@ vtx_status vtx_destroy(vtx_ctx *c) {
   drop_graphs(c);
   Buf *bufs[] = {&c->keys,   &c->surv,   &c->state,  &c->tcount,   &c->tstart,   &c->tcursor,  &c->tlist,
                  &c->bsums,  &c->recs,   &c->recimg, &c->recbox,   &c->recof,    &c->entries,  &c->status,
-                 &c->counts, &c->hostin_x, &c->hostin_e, &c->hostout};
+                 &c->counts, &c->hostin_x, &c->hostin_e, &c->hostout, &c->ses_sas, &c->ses_a, &c->ses_b,
+                 &c->ses_edt, &c->ses_blk, &c->ses_base, &c->ses_total, &c->ses_bbox};
   for (Buf *b : bufs)
     if (b->p) cudaFree(b->p);
   if (c->h_status) cudaFreeHost(c->h_status);
@@ -1015,6 +1017,105 @@ vtx_status vtx_export_rgba8(vtx_ctx *c, const float *rgb, const uint32_t *id, in
   cudaError_t e = run_export_rgba8((const float *)dr, (const uint32_t *)di, (long long)width * height, n_images,
                                    bg_a, (uint8_t *)dout, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "export launch");
+  return VTX_OK;
+}
+
+vtx_status vtx_ses_fit_grid(vtx_ctx *c, const float *xyzr, int64_t n_atoms, float probe, float spacing,
+                            vtx_ses_grid *g) {
+  if (!c) return VTX_ERR_INVALID_ARG;
+  if (!g || n_atoms < 1 || !xyzr) return fail(c, VTX_ERR_INVALID_ARG, "ses grid: need atoms and an output");
+  if (!(spacing > 0.0f) || !(probe >= 0.0f) || !std::isfinite(spacing) || !std::isfinite(probe))
+    return fail(c, VTX_ERR_INVALID_ARG, "ses grid: spacing > 0 and probe >= 0 required");
+  cudaSetDevice(c->device);
+  const void *dx = nullptr;
+  if (!device_visible(c, xyzr, &dx, "ses: xyzr not device or page-locked host memory")) return VTX_ERR_INVALID_ARG;
+  if (((uintptr_t)dx & 15u) != 0) return fail(c, VTX_ERR_INVALID_ARG, "ses: xyzr must be 16-byte aligned");
+  const int nb = 4 * sm_count();
+  vtx_status st = ensure(c, c->ses_bbox, sizeof(float) * 6 * (size_t)nb, "ses bbox");
+  if (st) return st;
+  cudaError_t e = run_ses_bbox((const float4 *)dx, n_atoms, probe, (float *)c->ses_bbox.p, nb, c->stream);
+  std::vector<float> part((size_t)nb * 6);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(part.data(), c->ses_bbox.p, sizeof(float) * part.size(), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "ses bbox");
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int b = 0; b < nb; ++b)
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = std::fmin(lo[d], part[(size_t)b * 6 + d]);
+      hi[d] = std::fmax(hi[d], part[(size_t)b * 6 + 3 + d]);
+    }
+  for (int d = 0; d < 3; ++d) {
+    if (!std::isfinite(lo[d]) || !std::isfinite(hi[d])) return fail(c, VTX_ERR_INVALID_ARG, "ses: non-finite atoms");
+    g->origin[d] = (float)((double)lo[d] - 2.0 * (double)spacing);
+    const double n = std::floor(((double)hi[d] - (double)lo[d]) / (double)spacing) + 6.0;
+    if (n > 2147483647.0) return fail(c, VTX_ERR_INVALID_ARG, "ses: grid too large");
+    g->dims[d] = (int32_t)n;
+  }
+  g->spacing = spacing;
+  g->probe = probe;
+  return VTX_OK;
+}
+
+vtx_status vtx_ses_mesh(vtx_ctx *c, const float *xyzr, int64_t n_atoms, const vtx_ses_grid *g, float *tris,
+                        int64_t max_tris, int64_t *labels, uint8_t *sas, uint16_t *edt2, int64_t *n_tris) {
+  if (!c) return VTX_ERR_INVALID_ARG;
+  if (!g || !n_tris || max_tris < 0 || (max_tris > 0 && !tris) || n_atoms < 0 || (n_atoms > 0 && !xyzr))
+    return fail(c, VTX_ERR_INVALID_ARG, "ses: bad arguments");
+  if (!(g->spacing > 0.0f) || !(g->probe >= 0.0f) || !std::isfinite(g->spacing) || !std::isfinite(g->probe) ||
+      (double)g->probe / (double)g->spacing > 150.0)
+    return fail(c, VTX_ERR_INVALID_ARG, "ses: spacing > 0, probe >= 0 and probe / spacing <= 150 required");
+  for (int d = 0; d < 3; ++d)
+    if (g->dims[d] < 2 || !std::isfinite(g->origin[d])) return fail(c, VTX_ERR_INVALID_ARG, "ses: dims >= 2");
+  const long long n_pts = (long long)g->dims[0] * g->dims[1] * g->dims[2];
+  if (n_pts > 4294967296LL) return fail(c, VTX_ERR_INVALID_ARG, "ses: more than 2^32 grid points");
+  cudaSetDevice(c->device);
+  const void *dx = nullptr, *dt = nullptr, *dl = nullptr, *ds = nullptr, *de = nullptr;
+  if (!device_visible(c, xyzr, &dx, "ses: xyzr not device or page-locked host memory") ||
+      !device_visible(c, tris, &dt, "ses: tris not device or page-locked host memory") ||
+      !device_visible(c, labels, &dl, "ses: labels not device or page-locked host memory") ||
+      !device_visible(c, sas, &ds, "ses: sas not device or page-locked host memory") ||
+      !device_visible(c, edt2, &de, "ses: edt2 not device or page-locked host memory"))
+    return VTX_ERR_INVALID_ARG;
+  if (((uintptr_t)dx & 15u) != 0) return fail(c, VTX_ERR_INVALID_ARG, "ses: xyzr must be 16-byte aligned");
+  if (((uintptr_t)dt & 3u) != 0 || ((uintptr_t)dl & 7u) != 0 || ((uintptr_t)de & 1u) != 0)
+    return fail(c, VTX_ERR_INVALID_ARG, "ses: misaligned output");
+  const long long nb = ses_blocks(g->dims);
+  vtx_status st;
+  if (!ds && (st = ensure(c, c->ses_sas, (size_t)n_pts, "ses sas"))) return st;
+  if ((st = ensure(c, c->ses_a, 2 * (size_t)n_pts, "ses pass a"))) return st;
+  if ((st = ensure(c, c->ses_b, 2 * (size_t)n_pts, "ses pass b"))) return st;
+  if (!de && (st = ensure(c, c->ses_edt, 2 * (size_t)n_pts, "ses edt"))) return st;
+  if ((st = ensure(c, c->ses_blk, sizeof(unsigned) * (size_t)(nb + 1), "ses blocks"))) return st;
+  if ((st = ensure(c, c->ses_base, sizeof(unsigned long long) * (size_t)(nb + 1), "ses bases"))) return st;
+  if ((st = ensure(c, c->ses_total, sizeof(unsigned long long), "ses total"))) return st;
+  SesLaunch L;
+  L.X = (const float4 *)dx;
+  L.n_atoms = n_atoms;
+  for (int d = 0; d < 3; ++d) {
+    L.origin[d] = g->origin[d];
+    L.dims[d] = g->dims[d];
+  }
+  L.h = g->spacing;
+  L.probe = g->probe;
+  L.sas = ds ? (uint8_t *)ds : (uint8_t *)c->ses_sas.p;
+  L.g_a = (uint16_t *)c->ses_a.p;
+  L.g_b = (uint16_t *)c->ses_b.p;
+  L.edt2 = de ? (uint16_t *)de : (uint16_t *)c->ses_edt.p;
+  L.block_tris = (unsigned *)c->ses_blk.p;
+  L.block_base = (unsigned long long *)c->ses_base.p;
+  L.total = (unsigned long long *)c->ses_total.p;
+  L.tris = (float *)dt;
+  L.labels = (long long *)dl;
+  L.max_tris = max_tris;
+  cudaError_t e = run_ses_grid(L, c->stream);
+  unsigned long long total = 0;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&total, L.total, sizeof(total), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "ses mesh");
+  *n_tris = (int64_t)total;
+  if ((long long)total > max_tris) return fail(c, VTX_ERR_CAPACITY, "ses: more triangles than max_tris");
   return VTX_OK;
 }
 

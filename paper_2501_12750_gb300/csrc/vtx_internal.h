@@ -61,6 +61,28 @@ cudaError_t run_soft_pipeline(const Geometry &g, const Scene &sc, const Scratch 
 cudaError_t run_export_rgba8(const float *rgb, const uint32_t *id, long long ppi, long long n_img, unsigned char bg_a,
                              uint8_t *rgba, cudaStream_t st);
 
+// Solvent excluded surface on a grid (ses.cu).
+struct SesLaunch {
+  const float4 *X;
+  long long n_atoms;
+  float origin[3];
+  float h, probe;
+  int32_t dims[3];
+  uint8_t *sas;                   // [nz][ny][nx] SAS interior (0/1)
+  uint16_t *g_a, *g_b;            // distance-pass scratch, one value per grid point each
+  uint16_t *edt2;                 // [nz][ny][nx] windowed squared distance (grid units)
+  unsigned *block_tris;           // [ses_blocks(dims)]
+  unsigned long long *block_base; // [ses_blocks(dims)]
+  unsigned long long *total;      // [1]
+  float *tris;                    // [max_tris][3][3]
+  long long *labels;              // [max_tris][3] or null
+  long long max_tris;
+};
+cudaError_t run_ses_grid(const SesLaunch &L, cudaStream_t st);
+cudaError_t run_ses_bbox(const float4 *X, long long n, float probe, float *partial, int n_blocks, cudaStream_t st);
+long long ses_blocks(const int32_t dims[3]);
+int ses_window(float probe, float h);
+
 int sm_count();
 
 // Extra survivor slots the single-view cull may leave as holes (per-warp slabs).
