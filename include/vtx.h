@@ -313,12 +313,16 @@ vtx_status vtx_ses_fit_grid(vtx_ctx *ctx, const float *xyzr, int64_t n_atoms, fl
  *     (double)h * i per axis);
  *   edt2: squared distance in grid units to the nearest grid point outside
  *     the SAS interior, exact when <= K^2 (K = ceil(p / h) + 1), else K^2 + 1;
- *   SES interior: edt2 * h^2 >= p^2 (FP64);
+ *   SES interior: edt2 >= 1 and edt2 * h^2 >= p^2 (FP64; with p = 0 the
+ *     SES is the union of the spheres);
  *   marching cubes over the cells, cell order i fastest then j then k; per
  *     cell, loops of crossing edges (a face with four crossings cuts its
  *     inside corners apart), each running counter-clockwise about the
  *     outward normal (inside to outside), starting at its smallest edge
- *     (corner and edge numbering as in Lorensen and Cline's paper); a
+ *     (corners 0 (0,0,0), 1 (1,0,0), 2 (1,1,0), 3 (0,1,0), 4 (0,0,1),
+ *     5 (1,0,1), 6 (1,1,1), 7 (0,1,1); edges 0-3 the z = 0 square 0-1, 1-2,
+ *     2-3, 3-0, edges 4-7 the z = 1 square 4-5, 5-6, 6-7, 7-4, edges 8-11
+ *     the verticals 0-4, 1-5, 2-6, 3-7); a
  *     three-edge loop is one triangle, a longer loop of L edges L triangles
  *     around the mean of its vertices; a vertex on edge (a, b) is X_a + t (X_b
  *     - X_a), t = f_a / (f_a - f_b) clamped to [0, 1], f = sqrt(edt2) h - p.
@@ -328,7 +332,7 @@ vtx_status vtx_ses_fit_grid(vtx_ctx *ctx, const float *xyzr, int64_t n_atoms, fl
  * j) (nx-1) + i; sas (nullable) uint8 and edt2 (nullable) uint16, both
  * [nz][ny][nx].  *n_tris (host) receives the total number of triangles;
  * when it exceeds max_tris only the first max_tris are written and the call
- * returns VTX_ERR_CAPACITY.  Scratch (7 bytes per grid point) is owned by
+ * returns VTX_ERR_CAPACITY.  Scratch (8 bytes per grid point) is owned by
  * the context.  Synchronises.
  */
 vtx_status vtx_ses_mesh(vtx_ctx *ctx, const float *xyzr, int64_t n_atoms, const vtx_ses_grid *grid, float *tris,

@@ -22,8 +22,10 @@
  *   if that is <= K^2 with K = ceil(p / h) + 1; otherwise the sentinel
  *   K^2 + 1 ("farther").  0 for points outside the SAS interior.
  *
- *   SES interior: edt2 * h^2 >= p^2 (FP64: (double)edt2 * ((double)h *
- *   (double)h) >= (double)p * (double)p): no probe centre lies within p.
+ *   SES interior: edt2 > 0 and edt2 * h^2 >= p^2 (FP64: (double)edt2 *
+ *   ((double)h * (double)h) >= (double)p * (double)p): inside the SAS and no
+ *   probe centre within p (with p = 0 the SES is the SAS, the union of the
+ *   spheres).
  *   Field for interpolation: f = sqrt(edt2) h - p (>= 0 inside).
  *
  *   Marching cubes: cell (i, j, k) spans grid points (i..i+1, j..j+1, k..k+1),
@@ -118,7 +120,7 @@ void orc_ses_edt(const uint8_t *inside, const int32_t *dims, int32_t K, uint16_t
 }
 
 static int ses_in(uint16_t e, float h, float p) {
-  return (double)e * ((double)h * (double)h) >= (double)p * (double)p;
+  return e > 0 && (double)e * ((double)h * (double)h) >= (double)p * (double)p;
 }
 
 /* Outward normals of the faces above (corner coordinates are 0/1). */

@@ -46,7 +46,7 @@ struct vtx_ctx {
   // scratch
   Buf keys, surv, state, tcount, tstart, tcursor, tlist, bsums, recs, recimg, recbox, recof, entries, status, counts, hostin_x,
       hostin_e, hostout;
-  Buf ses_sas, ses_a, ses_b, ses_edt, ses_blk, ses_base, ses_total, ses_bbox;
+  Buf ses_sas, ses_a, ses_b, ses_edt, ses_blk, ses_base, ses_total, ses_bbox, ses_case;
   uint32_t cap_rec = 0;
   unsigned long long cap_entries = 0;
   Status *h_status = nullptr;
@@ -388,7 +388,7 @@ vtx_status vtx_destroy(vtx_ctx *c) {
   Buf *bufs[] = {&c->keys,   &c->surv,   &c->state,  &c->tcount,   &c->tstart,   &c->tcursor,  &c->tlist,
                  &c->bsums,  &c->recs,   &c->recimg, &c->recbox,   &c->recof,    &c->entries,  &c->status,
                  &c->counts, &c->hostin_x, &c->hostin_e, &c->hostout, &c->ses_sas, &c->ses_a, &c->ses_b,
-                 &c->ses_edt, &c->ses_blk, &c->ses_base, &c->ses_total, &c->ses_bbox};
+                 &c->ses_edt, &c->ses_blk, &c->ses_base, &c->ses_total, &c->ses_bbox, &c->ses_case};
   for (Buf *b : bufs)
     if (b->p) cudaFree(b->p);
   if (c->h_status) cudaFreeHost(c->h_status);
@@ -1087,6 +1087,7 @@ vtx_status vtx_ses_mesh(vtx_ctx *c, const float *xyzr, int64_t n_atoms, const vt
   if ((st = ensure(c, c->ses_b, 2 * (size_t)n_pts, "ses pass b"))) return st;
   if (!de && (st = ensure(c, c->ses_edt, 2 * (size_t)n_pts, "ses edt"))) return st;
   if ((st = ensure(c, c->ses_blk, sizeof(unsigned) * (size_t)(nb + 1), "ses blocks"))) return st;
+  if ((st = ensure(c, c->ses_case, (size_t)n_pts, "ses cases"))) return st;  // >= one byte per cell
   if ((st = ensure(c, c->ses_base, sizeof(unsigned long long) * (size_t)(nb + 1), "ses bases"))) return st;
   if ((st = ensure(c, c->ses_total, sizeof(unsigned long long), "ses total"))) return st;
   SesLaunch L;
@@ -1102,6 +1103,7 @@ vtx_status vtx_ses_mesh(vtx_ctx *c, const float *xyzr, int64_t n_atoms, const vt
   L.g_a = (uint16_t *)c->ses_a.p;
   L.g_b = (uint16_t *)c->ses_b.p;
   L.edt2 = de ? (uint16_t *)de : (uint16_t *)c->ses_edt.p;
+  L.cases = (uint8_t *)c->ses_case.p;
   L.block_tris = (unsigned *)c->ses_blk.p;
   L.block_base = (unsigned long long *)c->ses_base.p;
   L.total = (unsigned long long *)c->ses_total.p;

@@ -11,10 +11,11 @@
 //      interior, exact inside a (2K+1)^3 window (K = ceil(p/h) + 1) and
 //      K^2 + 1 beyond: three separable min-plus passes (x, y, z), integers
 //      only.  Marching cubes only ever needs values <= K^2.
-//   3. SES interior: edt2 h^2 >= p^2 (FP64).  Marching cubes in two passes:
-//      each CTA counts the triangles of a run of cells, one CTA scans the
-//      counts, then each CTA re-derives its cells and writes their triangles
-//      in cell order, so the output order is deterministic.  The per-case
+//   3. SES interior: edt2 >= 1 and edt2 h^2 >= p^2 (FP64; an integer threshold
+//      here, as the product is monotone in edt2).  Marching cubes in two passes:
+//      each CTA classifies a run of cells (one case byte per cell) and counts
+//      their triangles, one CTA scans the counts, then each CTA writes its
+//      cells' triangles in cell order, so the output order is deterministic.  The per-case
 //      loops come from a table built once on the host: faces with four
 //      crossings cut their inside corners apart, segments are directed by the
 //      face's outward normal so loops turn counter-clockwise about the
@@ -149,13 +150,38 @@ struct SesGrid {
   float ox, oy, oz, h, p;
   int nx, ny, nz;
   int K;
+  int t_in;      // smallest edt2 with edt2 * h^2 >= p^2 in FP64 (the SES test, monotone in edt2)
+  float xmax;    // largest |coordinate| of any grid point (bounds the FP32 rounding of the SAS filter)
 };
 
 __device__ __forceinline__ double grid_coord(float o, float h, long long i) {
   return __dadd_rn((double)o, __dmul_rn((double)h, (double)i));
 }
 
+// Set n bytes to 1: bytes up to a 4-byte boundary, then words, then bytes.
+__device__ __forceinline__ void fill_ones(uint8_t *p, long long n) {
+  while (n > 0 && ((uintptr_t)p & 3u)) {
+    *p++ = 1;
+    --n;
+  }
+  uint32_t *w = reinterpret_cast<uint32_t *>(p);
+  for (; n >= 4; n -= 4) *w++ = 0x01010101u;
+  p = reinterpret_cast<uint8_t *>(w);
+  while (n-- > 0) *p++ = 1;
+}
+
+__device__ __forceinline__ bool sas_exact(const SesGrid &G, long long i, double dy2, double dz2, double cx, double R2) {
+  const double dx = __dsub_rn(grid_coord(G.ox, G.h, i), cx);
+  return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), dy2), dz2) < R2;
+}
+
 // SAS interior: one warp per atom, lanes over the (j, k) rows of its box.
+// Each point is first classified in FP32 with a bound M on the FP32 error of
+// d^2 (coordinates, differences and squares, all at most a few ulps of
+// numbers <= xmax + R + 2h, and of R^2 itself); only points within M of the
+// sphere are decided by the exact FP64 test, so every decision equals the
+// FP64 one.  Per row, only the points of the chord |dx|^2 <= R^2 - dy^2 -
+// dz^2 + M are visited.
 __global__ __launch_bounds__(256) void k_ses_sas(SesGrid G, const float4 *__restrict__ X, long long n,
                                                  uint8_t *__restrict__ sas) {
   const int lane = threadIdx.x & 31;
@@ -163,17 +189,22 @@ __global__ __launch_bounds__(256) void k_ses_sas(SesGrid G, const float4 *__rest
   const long long n_warps = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long a = warp; a < n; a += n_warps) {
     const float4 c = X[a];
-    const double R = __dadd_rn((double)c.w, (double)G.p);
-    const double R2 = __dmul_rn(R, R);
-    // candidate index ranges, one point wider than the sphere's extent on each side
-    const double hh = (double)G.h;
+    // FP32 throughout except on the rare points the filter cannot decide (the
+    // FP64 pipes are a small fraction of the FP32 ones on this part)
+    const float Rf = c.w + G.p, R2f = Rf * Rf;
+    const float span = G.xmax + Rf + 2.0f * G.h;
+    const float delta = 4e-7f * span;                      // |FP32 difference - exact| per axis
+    const float ext = Rf + 2.0f * G.h;
+    const float M = 8.0f * ext * delta + 4.0f * delta * delta + 1e-6f * ext * ext + 1e-6f;
+    // candidate index ranges, two points wider than the sphere's extent on each side
+    const float inv_h = 1.0f / G.h;
     long long lo[3], hi[3];
-    const double cc[3] = {(double)c.x, (double)c.y, (double)c.z};
-    const double oo[3] = {(double)G.ox, (double)G.oy, (double)G.oz};
+    const float cf[3] = {c.x, c.y, c.z};
+    const float of[3] = {G.ox, G.oy, G.oz};
     const long long nn[3] = {G.nx, G.ny, G.nz};
     for (int d = 0; d < 3; ++d) {
-      lo[d] = (long long)floor((cc[d] - R - oo[d]) / hh) - 1;
-      hi[d] = (long long)ceil((cc[d] + R - oo[d]) / hh) + 1;
+      lo[d] = (long long)floorf((cf[d] - Rf - of[d]) * inv_h) - 2;
+      hi[d] = (long long)ceilf((cf[d] + Rf - of[d]) * inv_h) + 2;
       lo[d] = lo[d] < 0 ? 0 : lo[d];
       hi[d] = hi[d] > nn[d] - 1 ? nn[d] - 1 : hi[d];
     }
@@ -182,14 +213,58 @@ __global__ __launch_bounds__(256) void k_ses_sas(SesGrid G, const float4 *__rest
     const long long rows = ny_box * (hi[2] - lo[2] + 1);
     for (long long r = lane; r < rows; r += 32) {
       const long long j = lo[1] + r % ny_box, k = lo[2] + r / ny_box;
-      const double dy = __dsub_rn(grid_coord(G.oy, G.h, j), cc[1]);
-      const double dz = __dsub_rn(grid_coord(G.oz, G.h, k), cc[2]);
-      const double dy2 = __dmul_rn(dy, dy), dz2 = __dmul_rn(dz, dz);
+      const float dyf = __fsub_rn(__fmaf_rn(G.h, (float)j, G.oy), c.y);
+      const float dzf = __fsub_rn(__fmaf_rn(G.h, (float)k, G.oz), c.z);
+      const float yz = __fmaf_rn(dyf, dyf, __fmul_rn(dzf, dzf));
+      const float t = R2f - yz;
+      if (t < -M) continue;  // the whole row is outside
+      const float w = sqrtf(fmaxf(t + M, 0.0f)) + 2.0f * delta;
+      long long i0 = (long long)floorf((c.x - w - G.ox) * inv_h) - 2, i1 = (long long)ceilf((c.x + w - G.ox) * inv_h) + 2;
+      i0 = i0 < lo[0] ? lo[0] : i0;
+      i1 = i1 > hi[0] ? hi[0] : i1;
+      bool have64 = false;
+      double dy2 = 0.0, dz2 = 0.0, R2 = 0.0;
       uint8_t *row = sas + (k * G.ny + j) * (long long)G.nx;
-      for (long long i = lo[0]; i <= hi[0]; ++i) {
-        const double dx = __dsub_rn(grid_coord(G.ox, G.h, i), cc[0]);
-        const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), dy2), dz2);
-        if (d2 < R2) row[i] = 1;
+      // 1 = certainly inside, 0 = certainly outside, else the exact FP64 decision
+      auto classify = [&](long long i, bool &certain) -> bool {
+        const float dxf = __fsub_rn(__fmaf_rn(G.h, (float)i, G.ox), c.x);
+        const float d2f = __fmaf_rn(dxf, dxf, yz);
+        certain = d2f < R2f - M;
+        if (certain) return true;
+        if (d2f > R2f + M) return false;
+        if (!have64) {
+          const double dy = __dsub_rn(grid_coord(G.oy, G.h, j), (double)c.y);
+          const double dz = __dsub_rn(grid_coord(G.oz, G.h, k), (double)c.z);
+          dy2 = __dmul_rn(dy, dy);
+          dz2 = __dmul_rn(dz, dz);
+          const double R = __dadd_rn((double)c.w, (double)G.p);
+          R2 = __dmul_rn(R, R);
+          have64 = true;
+        }
+        return sas_exact(G, i, dy2, dz2, (double)c.x, R2);
+      };
+      // from each end of the chord, decide points one by one up to the first one
+      // certainly inside; d^2 is convex along the row, so every point between the
+      // two certain ones is inside with the same margin and is filled directly
+      long long a_in = -1, b_in = -1;
+      for (long long i = i0; i <= i1; ++i) {
+        bool certain;
+        if (classify(i, certain)) row[i] = 1;
+        if (certain) {
+          a_in = i;
+          break;
+        }
+      }
+      if (a_in >= 0) {
+        for (long long i = i1; i > a_in; --i) {
+          bool certain;
+          if (classify(i, certain)) row[i] = 1;
+          if (certain) {
+            b_in = i;
+            break;
+          }
+        }
+        if (b_in > a_in + 1) fill_ones(row + a_in + 1, b_in - a_in - 1);
       }
     }
   }
@@ -246,9 +321,7 @@ __global__ __launch_bounds__(256) void k_ses_edt_yz(SesGrid G, const uint16_t *_
   }
 }
 
-__device__ __forceinline__ bool ses_inside(uint16_t e, float h, float p) {
-  return __dmul_rn((double)e, __dmul_rn((double)h, (double)h)) >= __dmul_rn((double)p, (double)p);
-}
+
 
 __device__ __forceinline__ int cell_case(const SesGrid &G, const uint16_t *__restrict__ edt, long long i, long long j,
                                          long long k) {
@@ -256,21 +329,24 @@ __device__ __forceinline__ int cell_case(const SesGrid &G, const uint16_t *__res
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     const long long q = ((k + c_corner[c][2]) * G.ny + (j + c_corner[c][1])) * (long long)G.nx + (i + c_corner[c][0]);
-    if (ses_inside(edt[q], G.h, G.p)) cs |= 1 << c;
+    if ((int)edt[q] >= G.t_in) cs |= 1 << c;
   }
   return cs;
 }
 
-// Triangles of the cells [c0, c0 + kSesCellsPerThread) of thread t: their count.
+// Triangles of the cells [c0, c0 + kSesCellsPerThread) of a thread; their cases
+// are stored (one byte per cell) for the emit pass.
 __device__ __forceinline__ int thread_cells_count(const SesGrid &G, const uint16_t *__restrict__ edt, long long c0,
-                                                  long long n_cells) {
+                                                  long long n_cells, uint8_t *__restrict__ cases) {
   int n = 0;
   const long long cx = G.nx - 1, cy = G.ny - 1;
   for (int u = 0; u < kSesCellsPerThread; ++u) {
     const long long c = c0 + u;
     if (c >= n_cells) break;
     const long long i = c % cx, j = (c / cx) % cy, k = c / (cx * cy);
-    n += c_ses_case[cell_case(G, edt, i, j, k)].n_tris;
+    const int cs = cell_case(G, edt, i, j, k);
+    cases[c] = (uint8_t)cs;
+    n += c_ses_case[cs].n_tris;
   }
   return n;
 }
@@ -303,10 +379,11 @@ __device__ __forceinline__ unsigned block_exclusive_sum(unsigned v, unsigned *to
 }
 
 __global__ __launch_bounds__(kSesThreads) void k_ses_count(SesGrid G, const uint16_t *__restrict__ edt,
-                                                           long long n_cells, unsigned *__restrict__ block_tris) {
+                                                           long long n_cells, uint8_t *__restrict__ cases,
+                                                           unsigned *__restrict__ block_tris) {
   const long long c0 = (long long)blockIdx.x * kSesCellsPerBlock + (long long)threadIdx.x * kSesCellsPerThread;
   unsigned total;
-  block_exclusive_sum((unsigned)thread_cells_count(G, edt, c0, n_cells), &total);
+  block_exclusive_sum((unsigned)thread_cells_count(G, edt, c0, n_cells, cases), &total);
   if (threadIdx.x == 0) block_tris[blockIdx.x] = total;
 }
 
@@ -345,59 +422,90 @@ __device__ __forceinline__ void store_tri(float *__restrict__ tris, long long *_
   }
 }
 
+// Vertex on edge e of cell (i, j, k): X_a + t (X_b - X_a), t = f_a / (f_a - f_b) clamped.
+__device__ __forceinline__ float3 edge_vertex(const SesGrid &G, const uint16_t *__restrict__ edt, long long i,
+                                              long long j, long long k, int e) {
+  const int a = c_edge[e][0], b = c_edge[e][1];
+  const long long ai = i + c_corner[a][0], aj = j + c_corner[a][1], ak = k + c_corner[a][2];
+  const long long bi = i + c_corner[b][0], bj = j + c_corner[b][1], bk = k + c_corner[b][2];
+  const float fa = sqrtf((float)edt[(ak * G.ny + aj) * (long long)G.nx + ai]) * G.h - G.p;
+  const float fb = sqrtf((float)edt[(bk * G.ny + bj) * (long long)G.nx + bi]) * G.h - G.p;
+  float s = fa == fb ? 0.5f : fa / (fa - fb);
+  s = fminf(fmaxf(s, 0.0f), 1.0f);
+  const float3 A = make_float3(G.ox + G.h * (float)ai, G.oy + G.h * (float)aj, G.oz + G.h * (float)ak);
+  const float3 B = make_float3(G.ox + G.h * (float)bi, G.oy + G.h * (float)bj, G.oz + G.h * (float)bk);
+  return make_float3(A.x + s * (B.x - A.x), A.y + s * (B.y - A.y), A.z + s * (B.z - A.z));
+}
+
+// One thread per output triangle of the CTA's run of cells: the cells'
+// triangle offsets are scanned into shared memory, each thread finds its cell
+// by binary search, its loop and fan position from the case table, and writes
+// its triangle next to its neighbours' (coalesced).
 __global__ __launch_bounds__(kSesThreads) void k_ses_emit(SesGrid G, const uint16_t *__restrict__ edt,
-                                                          long long n_cells,
+                                                          const uint8_t *__restrict__ cases, long long n_cells,
                                                           const unsigned long long *__restrict__ block_base,
                                                           float *__restrict__ tris, long long *__restrict__ labels,
                                                           unsigned long long max_tris) {
-  const long long c0 = (long long)blockIdx.x * kSesCellsPerBlock + (long long)threadIdx.x * kSesCellsPerThread;
-  const unsigned before = block_exclusive_sum((unsigned)thread_cells_count(G, edt, c0, n_cells), nullptr);
-  unsigned long long t = block_base[blockIdx.x] + before;
-  const long long cx = G.nx - 1, cy = G.ny - 1;
+  __shared__ unsigned s_off[kSesCellsPerBlock + 1];
+  __shared__ unsigned char s_case[kSesCellsPerBlock];
+  const long long cb = (long long)blockIdx.x * kSesCellsPerBlock;
+  unsigned n4[kSesCellsPerThread];
+  unsigned mine = 0;
   for (int u = 0; u < kSesCellsPerThread; ++u) {
-    const long long c = c0 + u;
-    if (c >= n_cells) break;
-    const long long i = c % cx, j = (c / cx) % cy, k = c / (cx * cy);
-    const int cs = cell_case(G, edt, i, j, k);
-    const SesCase &tc = c_ses_case[cs];
-    if (tc.n_tris == 0) continue;
-    float f[8];
-    float3 P[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const long long a = i + c_corner[q][0], b = j + c_corner[q][1], d = k + c_corner[q][2];
-      const uint16_t e = edt[(d * G.ny + b) * (long long)G.nx + a];
-      f[q] = sqrtf((float)e) * G.h - G.p;
-      P[q] = make_float3(G.ox + G.h * (float)a, G.oy + G.h * (float)b, G.oz + G.h * (float)d);
+    const int lc = threadIdx.x * kSesCellsPerThread + u;
+    const unsigned char cs = cb + lc < n_cells ? cases[cb + lc] : 0;
+    s_case[lc] = cs;
+    n4[u] = c_ses_case[cs].n_tris;
+    mine += n4[u];
+  }
+  unsigned total;
+  unsigned run = block_exclusive_sum(mine, &total);
+  for (int u = 0; u < kSesCellsPerThread; ++u) {
+    s_off[threadIdx.x * kSesCellsPerThread + u] = run;
+    run += n4[u];
+  }
+  if (threadIdx.x == 0) s_off[kSesCellsPerBlock] = total;
+  __syncthreads();
+  const unsigned long long base_t = block_base[blockIdx.x];
+  const long long cx = G.nx - 1, cy = G.ny - 1;
+  for (unsigned q = threadIdx.x; q < total; q += kSesThreads) {
+    int lo = 0, hi = kSesCellsPerBlock - 1;  // last cell with s_off <= q
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (s_off[mid] <= q) lo = mid; else hi = mid - 1;
     }
-    int at = 0;
-    for (int l = 0; l < tc.n_loops; ++l) {
-      const int L = tc.len[l];
-      float3 V[12];
+    const long long c = cb + lo;
+    const SesCase &tc = c_ses_case[s_case[lo]];
+    unsigned r = q - s_off[lo];
+    int at = 0, l = 0;
+    while (l < tc.n_loops) {
+      const unsigned nt = tc.len[l] == 3 ? 1u : tc.len[l];
+      if (r < nt) break;
+      r -= nt;
+      at += tc.len[l];
+      ++l;
+    }
+    const long long i = c % cx, j = (c / cx) % cy, k = c / (cx * cy);
+    const long long base = c * 16;
+    const int L = tc.len[l];
+    if (L == 3) {
+      const int e0 = tc.edge[at], e1 = tc.edge[at + 1], e2 = tc.edge[at + 2];
+      store_tri(tris, labels, base_t + q, max_tris, edge_vertex(G, edt, i, j, k, e0), edge_vertex(G, edt, i, j, k, e1),
+                edge_vertex(G, edt, i, j, k, e2), base + e0, base + e1, base + e2);
+    } else {
       float3 M = make_float3(0.0f, 0.0f, 0.0f);
-      for (int q = 0; q < L; ++q) {
-        const int e = tc.edge[at + q], a = c_edge[e][0], b = c_edge[e][1];
-        float s = f[a] == f[b] ? 0.5f : f[a] / (f[a] - f[b]);
-        s = fminf(fmaxf(s, 0.0f), 1.0f);
-        V[q] = make_float3(P[a].x + s * (P[b].x - P[a].x), P[a].y + s * (P[b].y - P[a].y), P[a].z + s * (P[b].z - P[a].z));
-        M.x += V[q].x;
-        M.y += V[q].y;
-        M.z += V[q].z;
+      for (int v = 0; v < L; ++v) {
+        const float3 p = edge_vertex(G, edt, i, j, k, tc.edge[at + v]);
+        M.x += p.x;
+        M.y += p.y;
+        M.z += p.z;
       }
-      const long long base = c * 16;
-      if (L == 3) {
-        store_tri(tris, labels, t++, max_tris, V[0], V[1], V[2], base + tc.edge[at], base + tc.edge[at + 1],
-                  base + tc.edge[at + 2]);
-      } else {
-        const float inv = 1.0f / (float)L;
-        M = make_float3(M.x * inv, M.y * inv, M.z * inv);
-        for (int q = 0; q < L; ++q) {
-          const int q1 = q + 1 == L ? 0 : q + 1;
-          store_tri(tris, labels, t++, max_tris, M, V[q], V[q1], base + 12 + l, base + tc.edge[at + q],
-                    base + tc.edge[at + q1]);
-        }
-      }
-      at += L;
+      const float inv = 1.0f / (float)L;
+      M = make_float3(M.x * inv, M.y * inv, M.z * inv);
+      const int q0 = (int)r, q1 = q0 + 1 == L ? 0 : q0 + 1;
+      const int ea = tc.edge[at + q0], eb = tc.edge[at + q1];
+      store_tri(tris, labels, base_t + q, max_tris, M, edge_vertex(G, edt, i, j, k, ea),
+                edge_vertex(G, edt, i, j, k, eb), base + 12 + l, base + ea, base + eb);
     }
   }
 }
@@ -450,7 +558,23 @@ cudaError_t run_ses_grid(const SesLaunch &L, cudaStream_t st) {
   cudaGetDevice(&dev);
   if (!ses_table_ready(dev)) return cudaErrorInvalidValue;
   SesGrid G{L.origin[0], L.origin[1], L.origin[2], L.h, L.probe, L.dims[0], L.dims[1], L.dims[2],
-            ses_window(L.probe, L.h)};
+            ses_window(L.probe, L.h), 1, 0.0f};
+  {
+    // SES interior <=> edt2 >= 1 (inside the SAS) and edt2 * h^2 >= p^2 in FP64: the product is monotone in
+    // edt2, so the test is edt2 >= t_in for the smallest such integer
+    const double hh = (double)L.h * (double)L.h, pp = (double)L.probe * (double)L.probe;
+    long long t = (long long)std::floor(pp / hh);
+    while (t > 0 && (double)(t - 1) * hh >= pp) --t;
+    while ((double)t * hh < pp) ++t;
+    G.t_in = (int)(t < 1 ? 1 : t);
+    double xm = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      const double a0 = std::fabs((double)L.origin[d]);
+      const double a1 = std::fabs((double)L.origin[d] + (double)L.h * (double)(L.dims[d] - 1));
+      xm = std::fmax(xm, std::fmax(a0, a1));
+    }
+    G.xmax = (float)(xm * 1.001 + 1.0);
+  }
   const long long n_pts = (long long)G.nx * G.ny * G.nz;
   const int sms = sm_count();
   cudaError_t e = cudaMemsetAsync(L.sas, 0, (size_t)n_pts, st);
@@ -467,10 +591,10 @@ cudaError_t run_ses_grid(const SesLaunch &L, cudaStream_t st) {
   const long long n_cells = (long long)(G.nx - 1) * (G.ny - 1) * (G.nz - 1);
   const long long n_blocks = (n_cells + kSesCellsPerBlock - 1) / kSesCellsPerBlock;
   if (n_blocks > 0) {
-    k_ses_count<<<(unsigned)n_blocks, kSesThreads, 0, st>>>(G, L.edt2, n_cells, L.block_tris);
+    k_ses_count<<<(unsigned)n_blocks, kSesThreads, 0, st>>>(G, L.edt2, n_cells, L.cases, L.block_tris);
     k_ses_scan<<<1, kSesThreads, 0, st>>>(L.block_tris, n_blocks, L.block_base, L.total);
-    k_ses_emit<<<(unsigned)n_blocks, kSesThreads, 0, st>>>(G, L.edt2, n_cells, L.block_base, L.tris, L.labels,
-                                                           (unsigned long long)L.max_tris);
+    k_ses_emit<<<(unsigned)n_blocks, kSesThreads, 0, st>>>(G, L.edt2, L.cases, n_cells, L.block_base, L.tris,
+                                                           L.labels, (unsigned long long)L.max_tris);
   } else {
     cudaMemsetAsync(L.total, 0, sizeof(unsigned long long), st);
   }

@@ -71,6 +71,7 @@ struct SesLaunch {
   uint8_t *sas;                   // [nz][ny][nx] SAS interior (0/1)
   uint16_t *g_a, *g_b;            // distance-pass scratch, one value per grid point each
   uint16_t *edt2;                 // [nz][ny][nx] windowed squared distance (grid units)
+  uint8_t *cases;                 // [(nz-1)(ny-1)(nx-1)] marching-cubes case of every cell
   unsigned *block_tris;           // [ses_blocks(dims)]
   unsigned long long *block_base; // [ses_blocks(dims)]
   unsigned long long *total;      // [1]

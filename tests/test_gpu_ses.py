@@ -64,6 +64,7 @@ def test_ses_probe_sizes_and_offsets():
         o, hh, d = oracle.ses_grid(x, probe=p, h=h)
         o = o + np.float32(0.0123)
         ref = oracle.ses(x, o, hh, d, probe=p)
+        assert len(ref.tris) > 1000
         check_same(gpu_ses(x, o, hh, d, p), ref, "p=%g h=%g" % (p, h))
 
 

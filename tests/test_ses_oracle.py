@@ -197,3 +197,15 @@ def test_probe_passes_between_distant_atoms():
     assert topo["manifold"] and topo["oriented"] and topo["chi"] == 4
     V = s.tris.reshape(-1, 3)
     assert (np.abs(V[:, 2]) > 1.5).all()
+
+
+def test_zero_probe_gives_the_union_of_spheres():
+    """p = 0: the SES is the van der Waals surface; one atom gives its sphere (radius within one cell diagonal)."""
+    r = 1.6
+    x = np.array([[0.1, 0.2, -0.3, r]], np.float32)
+    o, h, d = oracle.ses_grid(x, probe=0.0, h=0.2)
+    s = oracle.ses(x, o, h, d, probe=0.0)
+    rr = np.linalg.norm(s.tris.reshape(-1, 3) - x[0, :3].astype(np.float64), axis=1)
+    assert len(s.tris) > 100 and rr.min() > r - math.sqrt(3) * h and rr.max() < r + math.sqrt(3) * h
+    topo = topology(s.edges, d)
+    assert topo["manifold"] and topo["oriented"] and topo["chi"] == 2
