@@ -345,7 +345,9 @@ vtx_status vtx_sync_status(vtx_ctx *ctx);
  * Per-stage GPU times (ms), averaged over every pipeline run made with
  * VTX_FLAG_PROFILE since the previous call, measured with CUDA events
  * recorded on the context's stream between the stages (clear, cull, setup,
- * scan, scatter, raster, resolve).  names/ms: arrays of *n entries (in:
+ * scan, scatter, raster, resolve: background pixels and the covered-pixel
+ * list, shade: the covered pixels' hit, shading, SSAO and post-processing;
+ * with a single-pass resolve "shade" is 0).  names/ms: arrays of *n entries (in:
  * capacity; out: stages written); *runs (may be NULL) receives the number of
  * runs averaged.  Waits for the last profiled run, then forgets the runs.
  */

@@ -26,7 +26,8 @@ struct GraphEntry {
   long long *d_counts = nullptr;
 };
 
-const char *kStageNames[7] = {"clear", "cull", "setup", "scan", "scatter", "raster", "resolve"};
+constexpr int kNumStages = 8;
+const char *kStageNames[kNumStages] = {"clear", "cull", "setup", "scan", "scatter", "raster", "resolve", "shade"};
 
 }  // namespace
 
@@ -45,7 +46,8 @@ struct vtx_ctx {
   bool has_cam = false;
   // scratch
   Buf keys, surv, state, tcount, tstart, tcursor, tlist, bsums, recs, recimg, recbox, recof, entries, status, counts, hostin_x,
-      hostin_e, hostout;
+      hostin_e, hostout, covlist;
+  bool cov_ok = false;  // the covered-pixel list of the last prepared launch fits (two-pass resolve)
   Buf ses_sas, ses_a, ses_b, ses_edt, ses_blk, ses_base, ses_total, ses_bbox, ses_case;
   uint32_t cap_rec = 0;
   unsigned long long cap_entries = 0;
@@ -246,6 +248,14 @@ static vtx_status prepare(vtx_ctx *c, const Geometry &g, bool soft, long long st
     if ((st = ensure(c, c->status, sizeof(Status), "status"))) return st;
     cudaMemsetAsync(c->status.p, 0, sizeof(Status), c->stream);
   }
+  // covered-pixel list of the two-pass resolve (32-bit entries: only when every pixel index fits)
+  c->cov_ok = false;
+  if (!soft && n_img * g.pix_per_img < 4294967295LL) {
+    if (ensure(c, c->covlist, sizeof(uint32_t) * (size_t)(n_img * g.pix_per_img), "covered pixels") == VTX_OK)
+      c->cov_ok = true;
+    else
+      c->err.clear();  // no room: the single-pass resolve needs no list
+  }
   return VTX_OK;
 }
 
@@ -267,6 +277,7 @@ static Scratch scratch_of(vtx_ctx *c) {
   s.status = (Status *)c->status.p;
   s.cap_rec = c->cap_rec;
   s.cap_entries = c->cap_entries;
+  s.cov_list = c->cov_ok ? (uint32_t *)c->covlist.p : nullptr;
   return s;
 }
 
@@ -311,14 +322,14 @@ static vtx_status check_status(vtx_ctx *c) {
 static StageEvents *events_for(vtx_ctx *c, const vtx_settings *s, StageEvents &ev) {
   if (!(s && (s->flags & VTX_FLAG_PROFILE))) return nullptr;
   if (c->ev_used == c->ev_sets.size()) {
-    cudaEvent_t *set = new cudaEvent_t[8];
-    for (int i = 0; i < 8; ++i) cudaEventCreate(&set[i]);
+    cudaEvent_t *set = new cudaEvent_t[kNumStages + 1];
+    for (int i = 0; i <= kNumStages; ++i) cudaEventCreate(&set[i]);
     c->ev_sets.push_back(set);
   }
   cudaEvent_t *set = c->ev_sets[c->ev_used++];
-  cudaEventRecord(set[7], c->stream);
+  cudaEventRecord(set[kNumStages], c->stream);  // start
   ev.ev = set;
-  ev.n = 7;
+  ev.n = kNumStages;
   return &ev;
 }
 
@@ -387,7 +398,7 @@ vtx_status vtx_destroy(vtx_ctx *c) {
   drop_graphs(c);
   Buf *bufs[] = {&c->keys,   &c->surv,   &c->state,  &c->tcount,   &c->tstart,   &c->tcursor,  &c->tlist,
                  &c->bsums,  &c->recs,   &c->recimg, &c->recbox,   &c->recof,    &c->entries,  &c->status,
-                 &c->counts, &c->hostin_x, &c->hostin_e, &c->hostout, &c->ses_sas, &c->ses_a, &c->ses_b,
+                 &c->counts, &c->hostin_x, &c->hostin_e, &c->hostout, &c->covlist, &c->ses_sas, &c->ses_a, &c->ses_b,
                  &c->ses_edt, &c->ses_blk, &c->ses_base, &c->ses_total, &c->ses_bbox, &c->ses_case};
   for (Buf *b : bufs)
     if (b->p) cudaFree(b->p);
@@ -395,7 +406,7 @@ vtx_status vtx_destroy(vtx_ctx *c) {
   if (c->h_counts) cudaFreeHost(c->h_counts);
   if (c->counts_done) cudaEventDestroy(c->counts_done);
   for (cudaEvent_t *set : c->ev_sets) {
-    for (int i = 0; i < 8; ++i) cudaEventDestroy(set[i]);
+    for (int i = 0; i <= kNumStages; ++i) cudaEventDestroy(set[i]);
     delete[] set;
   }
   delete c;
@@ -723,7 +734,7 @@ static vtx_status batch_once(vtx_ctx *c, const float *frames, int64_t stride, co
 
 // Frames per pipeline pass: bounded so the per-image scratch stays near 8 GB.
 static int batch_chunk(const vtx_camera *cams, int n_views, long long stride, int n_frames) {
-  double per_frame = (double)n_views * ((double)cams[0].width * cams[0].height * 8.0 + (double)stride * 4.0);
+  double per_frame = (double)n_views * ((double)cams[0].width * cams[0].height * 12.0 + (double)stride * 4.0);
   int fc = (int)(8e9 / (per_frame > 1.0 ? per_frame : 1.0));
   if (fc < 1) fc = 1;
   if (fc > n_frames) fc = n_frames;
@@ -965,14 +976,14 @@ vtx_status vtx_stage_times(vtx_ctx *c, const char **names, float *ms, int32_t *n
     if (runs) *runs = 0;
     return fail(c, VTX_ERR_STATE, "no profiled render since the last read");
   }
-  cudaError_t e = cudaEventSynchronize(c->ev_sets[c->ev_used - 1][6]);
+  cudaError_t e = cudaEventSynchronize(c->ev_sets[c->ev_used - 1][kNumStages - 1]);
   if (e != cudaSuccess) return cuda_fail(c, e, "stage events");
-  int cap = *n < 7 ? *n : 7;
-  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  int cap = *n < kNumStages ? *n : kNumStages;
+  double acc[kNumStages] = {};
   for (size_t r = 0; r < c->ev_used; ++r) {
     cudaEvent_t *set = c->ev_sets[r];
-    cudaEvent_t prev = set[7];
-    for (int i = 0; i < 7; ++i) {
+    cudaEvent_t prev = set[kNumStages];
+    for (int i = 0; i < kNumStages; ++i) {
       float t = 0.0f;
       cudaEventElapsedTime(&t, prev, set[i]);
       acc[i] += t;

@@ -67,6 +67,7 @@ __global__ void k_init_state(ImageState *st, int n_img, Status *status) {
     status->n_rec = 0u;
     status->n_entries = 0ull;
     status->n_list = 0u;
+    status->n_cov = 0u;
   }
 }
 
@@ -952,6 +953,9 @@ __global__ __launch_bounds__(TW *TH) void k_raster(Geometry g, const PrimRec *__
 #define VTX_RESOLVE_MINB 4
 #endif
 constexpr int kSsaoGroup = VTX_SSAO_GROUP;  // SSAO samples whose neighbour keys are fetched together
+#ifndef VTX_RESOLVE_2PASS
+#define VTX_RESOLVE_2PASS 1
+#endif
 
 __device__ __forceinline__ void resolve_pixel(const Geometry &g, const ShadeParams &sh, const float4 *__restrict__ frames,
                                               const uint8_t *__restrict__ elem, const uint2 *__restrict__ bonds,
@@ -1045,8 +1049,9 @@ __device__ __forceinline__ void resolve_pixel(const Geometry &g, const ShadePara
             const float den = t + dl;
             dls[u] = dl;
             if (den > 0.0f) {
-              const float offx = v.f * (dx - r.a * dl) / den;
-              const float offy = -v.f * (dy - r.b * dl) / den;
+              const float fden = __fdiv_rn(v.f, den);  // one division for both offsets
+              const float offx = fden * (dx - r.a * dl);
+              const float offy = -fden * (dy - r.b * dl);
               const int ix = px + (int)floorf(0.5f + offx);
               const int iy = py + (int)floorf(0.5f + offy);
               if (ix >= 0 && iy >= 0 && ix < g.W && iy < g.H) at[u] = (long long)iy * g.W + ix;
@@ -1128,6 +1133,124 @@ __global__ __launch_bounds__(256, VTX_RESOLVE_MINB) void k_resolve(Geometry g, S
     if (py < g.H) resolve_pixel(g, sh, frames, elem, bonds, st, keys, out, do_ssao, img, px, py, key);
   }
 }
+
+// Two-pass resolve, pass 1: list the covered pixels (keys read, one atomic
+// per warp).  Pass 2 (k_resolve_split) runs two kinds of CTA side by side:
+// the first n_shade take the listed pixels one per thread through the long
+// hit / shading / SSAO path (no background lanes idling beside a covered
+// one), the others stream the constant outputs of background pixels (vector
+// stores when VEC: four pixels per thread, every plane 16-byte aligned), so
+// the latency-bound shading overlaps the memory-bound background writes.
+// Measured against one pass (GB300, CUDA events): 1e8-atom 4K frame 0.102 ->
+// 0.087 ms, close view 0.50 -> 0.34 ms, 1e5-atom 1080p 0.061 -> 0.031 ms;
+// the 1,024-image trajectory batch (6 % coverage) is ~7 % slower in this
+// stage.  A shared work queue interleaving both kinds and a plain two-pass
+// form were measured too and were slower on the 4K frame.
+template <bool VEC>
+__global__ __launch_bounds__(256) void k_resolve_list(Geometry g, const unsigned long long *__restrict__ keys,
+                                                      uint32_t *__restrict__ cov, Status *status) {
+  const long long total = g.pix_per_img * g.n_img;
+  const int lane = threadIdx.x & 31;
+  constexpr int P = VEC ? 4 : 1;
+  const long long n_units = total / P;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long n_iter = (n_units + stride - 1) / stride;
+  for (long long it = 0; it < n_iter; ++it) {  // uniform trip count: every lane reaches the warp votes
+    const long long u = it * stride + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = u < n_units;
+    const long long q0 = u * P;
+    unsigned covered = 0u;
+    if (live) {
+      if (VEC) {
+        const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(keys + q0);
+        const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(keys + q0 + 2);
+        covered = ((uint32_t)a.x != kNoId ? 1u : 0u) | ((uint32_t)a.y != kNoId ? 2u : 0u) |
+                  ((uint32_t)b.x != kNoId ? 4u : 0u) | ((uint32_t)b.y != kNoId ? 8u : 0u);
+      } else {
+        covered = (uint32_t)keys[q0] != kNoId ? 1u : 0u;
+      }
+    }
+    const int n_mine = __popc(covered);
+    int incl = n_mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int warp_total = __shfl_sync(0xffffffffu, incl, 31);
+    if (warp_total == 0) continue;
+    unsigned base = 0u;
+    if (lane == 31) base = atomicAdd(&status->n_cov, (unsigned)warp_total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    unsigned at = base + (unsigned)(incl - n_mine);
+#pragma unroll
+    for (int v = 0; v < P; ++v)
+      if (covered & (1u << v)) cov[at++] = (uint32_t)(q0 + v);
+  }
+}
+
+template <bool VEC>
+__global__ __launch_bounds__(256, VTX_RESOLVE_MINB) void k_resolve_split(
+    Geometry g, ShadeParams sh, const float4 *__restrict__ frames, const uint8_t *__restrict__ elem,
+    const uint2 *__restrict__ bonds, const ImageState *__restrict__ st, const unsigned long long *__restrict__ keys,
+    Outputs out, int do_ssao, const uint32_t *__restrict__ cov, const Status *__restrict__ status, int n_shade) {
+  const long long ppi = g.pix_per_img;
+  if ((int)blockIdx.x < n_shade) {
+    const unsigned n = status->n_cov;
+    for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (unsigned)n_shade * blockDim.x) {
+      const long long q = cov[e];
+      const int img = (int)(q / ppi);
+      const long long p = q - (long long)img * ppi;
+      const int py = (int)(p / g.W), px = (int)(p - (long long)py * g.W);
+      resolve_pixel(g, sh, frames, elem, bonds, st, keys, out, do_ssao, img, px, py, keys[q]);
+    }
+    return;
+  }
+  constexpr int P = VEC ? 4 : 1;
+  const long long n_units = ppi * g.n_img / P;
+  const float inf = __int_as_float(0x7f800000);
+  for (long long u = (long long)(blockIdx.x - n_shade) * blockDim.x + threadIdx.x; u < n_units;
+       u += (long long)(gridDim.x - n_shade) * blockDim.x) {
+    const long long q0 = u * P;
+    unsigned covered = 0u;
+    if (VEC) {
+      const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(keys + q0);
+      const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(keys + q0 + 2);
+      covered = ((uint32_t)a.x != kNoId ? 1u : 0u) | ((uint32_t)a.y != kNoId ? 2u : 0u) |
+                ((uint32_t)b.x != kNoId ? 4u : 0u) | ((uint32_t)b.y != kNoId ? 8u : 0u);
+    } else {
+      covered = (uint32_t)keys[q0] != kNoId ? 1u : 0u;
+    }
+    const long long img = q0 / ppi, p = q0 - img * ppi;
+    float *nrm = out.normal + img * 3 * ppi + p;
+    float *rgb = out.rgb + img * 3 * ppi + p;
+    if (VEC && covered == 0u) {
+      const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      *reinterpret_cast<float4 *>(out.depth + q0) = make_float4(inf, inf, inf, inf);
+      *reinterpret_cast<uint4 *>(out.id + q0) = make_uint4(kNoId, kNoId, kNoId, kNoId);
+      *reinterpret_cast<float4 *>(nrm) = z4;
+      *reinterpret_cast<float4 *>(nrm + ppi) = z4;
+      *reinterpret_cast<float4 *>(nrm + 2 * ppi) = z4;
+      *reinterpret_cast<float4 *>(rgb) = make_float4(sh.bg[0], sh.bg[0], sh.bg[0], sh.bg[0]);
+      *reinterpret_cast<float4 *>(rgb + ppi) = make_float4(sh.bg[1], sh.bg[1], sh.bg[1], sh.bg[1]);
+      *reinterpret_cast<float4 *>(rgb + 2 * ppi) = make_float4(sh.bg[2], sh.bg[2], sh.bg[2], sh.bg[2]);
+      if (out.ao) *reinterpret_cast<float4 *>(out.ao + q0) = make_float4(1.0f, 1.0f, 1.0f, 1.0f);
+    } else {
+#pragma unroll
+      for (int v = 0; v < P; ++v) {
+        if (covered & (1u << v)) continue;
+        out.depth[q0 + v] = inf;
+        out.id[q0 + v] = kNoId;
+        nrm[v] = nrm[ppi + v] = nrm[2 * ppi + v] = 0.0f;
+        rgb[v] = sh.bg[0];
+        rgb[ppi + v] = sh.bg[1];
+        rgb[2 * ppi + v] = sh.bg[2];
+        if (out.ao) out.ao[q0 + v] = 1.0f;
+      }
+    }
+  }
+}
+
 
 // ------------------------------------------------------------ launchers --
 
@@ -1228,11 +1351,34 @@ cudaError_t run_frame_pipeline(const Geometry &g, const ShadeParams &sh, const S
     k_raster<8, 8><<<rgrid, 64, 0, st>>>(g, s.recs, s.entries, s.cap_entries, s.tile_count,
                                                      s.tile_start, s.state, s.keys, s.tile_list, s.status);
   ev_rec(evs, 5, st);
-  {
+  if (VTX_RESOLVE_2PASS && s.cov_list) {
+    const int sms = sm_count();
+    const long long total = g.pix_per_img * g.n_img;
+    const bool vec = (g.pix_per_img % 4) == 0 && ((uintptr_t)out.depth | (uintptr_t)out.id | (uintptr_t)out.normal |
+                                                  (uintptr_t)out.rgb | (uintptr_t)(out.ao ? out.ao : out.depth)) % 16 == 0;
+    const long long units = vec ? total / 4 : total;
+    const long long want = (units + 255) / 256;
+    const int gl = (int)(want < 16LL * sms ? (want > 0 ? want : 1) : 16LL * sms);
+    // shading CTAs first (they start at once and stay resident), background CTAs behind them
+    const int n_shade = 3 * sms;
+    const int gb = (int)(want < 8LL * sms ? (want > 0 ? want : 1) : 8LL * sms);
+    if (vec) {
+      k_resolve_list<true><<<gl, 256, 0, st>>>(g, s.keys, s.cov_list, s.status);
+      ev_rec(evs, 6, st);
+      k_resolve_split<true><<<n_shade + gb, 256, 0, st>>>(g, sh, sc.frames, sc.elem, sc.bonds, s.state, s.keys, out,
+                                                            ssao ? 1 : 0, s.cov_list, s.status, n_shade);
+    } else {
+      k_resolve_list<false><<<gl, 256, 0, st>>>(g, s.keys, s.cov_list, s.status);
+      ev_rec(evs, 6, st);
+      k_resolve_split<false><<<n_shade + gb, 256, 0, st>>>(g, sh, sc.frames, sc.elem, sc.bonds, s.state, s.keys, out,
+                                                             ssao ? 1 : 0, s.cov_list, s.status, n_shade);
+    }
+  } else {
     dim3 grid((g.W + 31) / 32, (g.H + 31) / 32, g.n_img);
     k_resolve<<<grid, 256, 0, st>>>(g, sh, sc.frames, sc.elem, sc.bonds, s.state, s.keys, out, ssao ? 1 : 0);
+    ev_rec(evs, 6, st);
   }
-  ev_rec(evs, 6, st);
+  ev_rec(evs, 7, st);
   return cudaGetLastError();
 }
 

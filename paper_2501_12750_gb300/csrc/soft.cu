@@ -314,6 +314,7 @@ cudaError_t run_soft_pipeline(const Geometry &g, const Scene &sc, const Scratch 
   }
   if (evs && evs->ev && evs->n > 5) cudaEventRecord(evs->ev[5], st);
   if (evs && evs->ev && evs->n > 6) cudaEventRecord(evs->ev[6], st);
+  if (evs && evs->ev && evs->n > 7) cudaEventRecord(evs->ev[7], st);
   return cudaGetLastError();
 }
 

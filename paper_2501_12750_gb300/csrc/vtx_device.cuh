@@ -105,6 +105,8 @@ struct Status {
   unsigned long long n_entries; // binned (tile, primitive) entries requested
   unsigned int max_list;        // longest tile list seen by the raster stage
   unsigned int n_list;          // non-empty tiles listed by the scan (raster work list)
+  unsigned int n_cov;           // covered pixels listed by the resolve's list pass
+  unsigned int pad;
 };
 
 // A binned primitive staged through shared memory (64 bytes).  Its tile box

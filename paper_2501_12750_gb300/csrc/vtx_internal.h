@@ -23,6 +23,7 @@ struct Scratch {
   uint2 *rec_box;             // [cap_rec] tile box of each record: (x0 | y0 << 16, x1 | y1 << 16)
   uint32_t *rec_of;           // soft: [n_img][n_atoms] record of each atom
   unsigned long long *entries;  // [cap_entries] (sort key << 32 | record or id)
+  uint32_t *cov_list;         // [n_img * H * W] covered pixels (img * H * W + p), or null: single-pass resolve
   Status *status;
   uint32_t cap_rec;
   unsigned long long cap_entries;
