@@ -34,7 +34,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-KERNELS_PER_FRAME = 8  # init, cull, finalize, setup, scan, scatter, raster, resolve
+KERNELS_PER_FRAME = 9  # init, cull, finalize, setup, scan, scatter, raster, resolve list, resolve/shade
 
 
 def parse():
@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline (profiling runs)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--clusters", type=int, default=20000, help="blobs of 5,000 atoms (20,000 = 1e8 atoms)")
+    ap.add_argument("--ses-only", action="store_true",
+                    help="only the SES of the 1e5-atom system (one JSON line; for profiling its kernels)")
     return ap.parse_args()
 
 
@@ -187,6 +189,12 @@ def main():
     torch.cuda.set_device(dev)
 
     import paper_2501_12750_gb300 as vtx
+
+    if args.ses_only:
+        if rank == 0:
+            print(json.dumps({"metric": "ses_ms", "unit": "ms", "higher_is_better": False, "data": "synthetic",
+                              **ses_extra(vtx, torch, dev)}))
+        return 0
 
     t_gen = time.time()
     s = scenes.config3(n_clusters=args.clusters)
@@ -362,6 +370,36 @@ def _frame_ms(vtx, torch, r, settings, out, reps=10):
     return e0.elapsed_time(e1) / reps
 
 
+def ses_extra(vtx, torch, dev, reps=5):
+    """SES of the 1e5-atom protein-like system on a 0.5 A grid (probe 1.4 A): wall time of the synchronous call."""
+    import ctypes
+
+    from paper_2501_12750_gb300 import scenes
+    s2 = scenes.config2()
+    rs = vtx.Renderer()
+    x2 = torch.from_numpy(s2.xyzr).to(dev)
+    g2 = rs.ses_fit_grid(x2, probe=1.4, spacing=0.5)
+    first = rs.ses_mesh(x2, g2)
+    n_tri = first["n"]
+    tri_buf = first["tris"]
+    cnt = ctypes.c_int64(0)
+
+    def call():
+        code = rs.lib.vtx_ses_mesh(rs.ctx, x2.data_ptr(), x2.shape[0], ctypes.byref(g2), tri_buf.data_ptr(), n_tri,
+                                   None, None, None, ctypes.byref(cnt))
+        assert code == 0 and cnt.value == n_tri
+    for _ in range(2):
+        call()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        call()
+    ses_ms = (time.perf_counter() - t0) / reps * 1e3
+    pts = int(g2.dims[0]) * int(g2.dims[1]) * int(g2.dims[2])
+    return {"workload": "1e5 atoms, SES (probe 1.4 A) on a 0.5 A grid, marching cubes", "grid_points": pts,
+            "triangles": int(n_tri), "ms": ses_ms, "gpoints_per_s": pts / ses_ms / 1e6,
+            "note": "wall time of the synchronous call (SAS, 3 distance passes, count, scan, emit)"}
+
+
 def run_extras(vtx, torch, dev, r, s3, cam, k):
     import dataclasses
 
@@ -404,31 +442,7 @@ def run_extras(vtx, torch, dev, r, s3, cam, k):
         del rs, so, ss
         torch.cuda.empty_cache()
     res["size_sweep_3840x2160"] = sweep
-    # solvent excluded surface of the 1e5-atom protein-like system on a 0.5 A grid (probe 1.4 A)
-    s2 = scenes.config2()
-    rs = vtx.Renderer()
-    x2 = torch.from_numpy(s2.xyzr).to(dev)
-    g2 = rs.ses_fit_grid(x2, probe=1.4, spacing=0.5)
-    first = rs.ses_mesh(x2, g2)
-    n_tri = first["n"]
-    tri_buf = first["tris"]
-    import ctypes
-    cnt = ctypes.c_int64(0)
-    for _ in range(2):
-        rs.lib.vtx_ses_mesh(rs.ctx, x2.data_ptr(), x2.shape[0], ctypes.byref(g2), tri_buf.data_ptr(), n_tri, None,
-                            None, None, ctypes.byref(cnt))
-    t0 = time.perf_counter()
-    reps = 5
-    for _ in range(reps):
-        rs.lib.vtx_ses_mesh(rs.ctx, x2.data_ptr(), x2.shape[0], ctypes.byref(g2), tri_buf.data_ptr(), n_tri, None,
-                            None, None, ctypes.byref(cnt))
-    ses_ms = (time.perf_counter() - t0) / reps * 1e3
-    pts = int(g2.dims[0]) * int(g2.dims[1]) * int(g2.dims[2])
-    res["ses_config2"] = {"workload": "1e5 atoms, SES (probe 1.4 A) on a 0.5 A grid, marching cubes",
-                          "grid_points": pts, "triangles": int(n_tri), "ms": ses_ms,
-                          "gpoints_per_s": pts / ses_ms / 1e6,
-                          "note": "wall time of the synchronous call (SAS, 3 distance passes, count, scan, emit)"}
-    del rs, x2, first, tri_buf
+    res["ses_config2"] = ses_extra(vtx, torch, dev)
     torch.cuda.empty_cache()
     # batched trajectory: 256 frames x 4 views, one graph launch, against the per-frame loop
     s4 = scenes.config4()
