@@ -36,6 +36,7 @@ struct vtx_ctx {
   cudaStream_t stream = nullptr;
   // scene
   const float4 *xyzr = nullptr;
+  bool atoms_on_host = false;  // xyzr is page-locked host memory (read over the host link)
   const uint8_t *elem = nullptr;
   long long n_atoms = 0;
   float palette[kMaxElem][3];
@@ -46,7 +47,7 @@ struct vtx_ctx {
   bool has_cam = false;
   // scratch
   Buf keys, surv, state, tcount, tstart, tcursor, tlist, bsums, recs, recimg, recbox, recof, entries, status, counts, hostin_x,
-      hostin_e, hostout, covlist;
+      hostin_e, hostout, covlist, stage;
   bool cov_ok = false;  // the covered-pixel list of the last prepared launch fits (two-pass resolve)
   Buf ses_sas, ses_a, ses_b, ses_edt, ses_blk, ses_base, ses_total, ses_bbox, ses_case;
   uint32_t cap_rec = 0;
@@ -398,7 +399,7 @@ vtx_status vtx_destroy(vtx_ctx *c) {
   drop_graphs(c);
   Buf *bufs[] = {&c->keys,   &c->surv,   &c->state,  &c->tcount,   &c->tstart,   &c->tcursor,  &c->tlist,
                  &c->bsums,  &c->recs,   &c->recimg, &c->recbox,   &c->recof,    &c->entries,  &c->status,
-                 &c->counts, &c->hostin_x, &c->hostin_e, &c->hostout, &c->covlist, &c->ses_sas, &c->ses_a, &c->ses_b,
+                 &c->counts, &c->hostin_x, &c->hostin_e, &c->hostout, &c->covlist, &c->stage, &c->ses_sas, &c->ses_a, &c->ses_b,
                  &c->ses_edt, &c->ses_blk, &c->ses_base, &c->ses_total, &c->ses_bbox, &c->ses_case};
   for (Buf *b : bufs)
     if (b->p) cudaFree(b->p);
@@ -425,8 +426,9 @@ vtx_status vtx_set_stream(vtx_ctx *c, void *cuda_stream) {
 // over the host link, so it never has to fit in device memory).  Pageable
 // host memory is refused rather than relying on the platform's support for
 // device access to it.
-static bool device_visible(vtx_ctx *c, const void *p, const void **dev, const char *what) {
+static bool device_visible(vtx_ctx *c, const void *p, const void **dev, const char *what, bool *on_host = nullptr) {
   *dev = p;
+  if (on_host) *on_host = false;
   if (!p) return true;
   cudaPointerAttributes a;
   cudaError_t e = cudaPointerGetAttributes(&a, p);
@@ -438,6 +440,7 @@ static bool device_visible(vtx_ctx *c, const void *p, const void **dev, const ch
   if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return true;
   if (a.type == cudaMemoryTypeHost && a.devicePointer) {
     *dev = a.devicePointer;
+    if (on_host) *on_host = true;
     return true;
   }
   fail(c, VTX_ERR_INVALID_ARG, what);
@@ -477,10 +480,13 @@ vtx_status vtx_upload_atoms(vtx_ctx *c, const float *xyzr, const uint8_t *elem, 
   if (n_elem < 1 || n_elem > VTX_MAX_ELEMENTS || !palette_rgb)
     return fail(c, VTX_ERR_INVALID_ARG, "palette: need 1..32 elements");
   const void *dx = nullptr, *de = nullptr;
-  if (!device_visible(c, xyzr, &dx, "xyzr: not device memory or page-locked host memory")) return VTX_ERR_INVALID_ARG;
+  bool host_atoms = false;
+  if (!device_visible(c, xyzr, &dx, "xyzr: not device memory or page-locked host memory", &host_atoms))
+    return VTX_ERR_INVALID_ARG;
   if (!device_visible(c, elem, &de, "elem: not device memory or page-locked host memory")) return VTX_ERR_INVALID_ARG;
   if (((uintptr_t)dx & 15u) != 0) return fail(c, VTX_ERR_INVALID_ARG, "xyzr alias must be 16-byte aligned");
   c->xyzr = (const float4 *)dx;
+  c->atoms_on_host = host_atoms;
   c->elem = (const uint8_t *)de;
   c->n_atoms = n_atoms;
   c->n_elem = n_elem;
@@ -540,7 +546,15 @@ static vtx_status render_once(vtx_ctx *c, const vtx_settings *s, const vtx_outpu
   g.surv_cap = c->n_atoms + g.n_bonds + cull_survivor_slack(c->n_atoms);
   vtx_status st = prepare(c, g, false, 0);
   if (st) return st;
-  Scene sc{c->xyzr, nullptr, c->elem, g.n_bonds ? c->bonds : nullptr};
+  Scene sc{c->xyzr, nullptr, c->elem, g.n_bonds ? c->bonds : nullptr, nullptr};
+  // host-resident atoms: the cull copies its survivors into device memory (when there is room), so setup and
+  // resolve gather them from HBM instead of over the host link (bonds need their end atoms: not staged)
+  if (c->atoms_on_host && g.n_bonds == 0 && c->n_atoms > 0) {
+    if (ensure(c, c->stage, sizeof(float4) * (size_t)c->n_atoms, "staged survivors") == VTX_OK)
+      sc.stage = (float4 *)c->stage.p;
+    else
+      c->err.clear();
+  }
   Outputs o{out->depth, out->id, out->normal, out->rgb, out->ao};
   ShadeParams sh = make_shade(c, s);
   cudaError_t e = run_frame_pipeline(g, sh, sc, scratch_of(c), o, sh.ssao_n > 0, c->stream, ev);

@@ -301,10 +301,11 @@ constexpr int kCullCtasPerSm = 5;   // resident CTAs per SM of the single-view c
 // slab has unused slots, which are filled with kNoId and skipped by the setup
 // stage), and the depth range is kept in registers and reduced once at the
 // end.  PLAIN: van der Waals radii and no clip plane.
-template <bool PLAIN>
+template <bool PLAIN, bool STAGE>
 __global__ __launch_bounds__(kCullThreads, kCullCtasPerSm) void k_cull_direct(Geometry g, const float4 *__restrict__ X,
                                                                             ImageState *st,
-                                                                            uint32_t *__restrict__ surv) {
+                                                                            uint32_t *__restrict__ surv,
+                                                                            float4 *__restrict__ stage) {
   static_assert(kCullPT % 2 == 0, "atoms are tested in pairs");
   const ViewParams &vp = g.views[0];
   const long long n = g.n_atoms;
@@ -344,6 +345,10 @@ __global__ __launch_bounds__(kCullThreads, kCullCtasPerSm) void k_cull_direct(Ge
       if (k1) {
         zlo = fminf(zlo, vz.y - Rm.y);
         zhi = fmaxf(zhi, vz.y + Rm.y);
+      }
+      if (STAGE) {  // survivors' records into device memory for setup and resolve (X is in host memory)
+        if (k0) stage[a0 + j * kCullThreads + threadIdx.x] = p;
+        if (k1) stage[a0 + (j + 1) * kCullThreads + threadIdx.x] = q;
       }
       slab_push(k0, (uint32_t)(a0 + j * kCullThreads + threadIdx.x), lane, lt, slab, used, &st[0].n_surv, surv, cap);
       slab_push(k1, (uint32_t)(a0 + (j + 1) * kCullThreads + threadIdx.x), lane, lt, slab, used, &st[0].n_surv, surv,
@@ -1283,10 +1288,15 @@ cudaError_t run_binning(const Geometry &g, const Scene &sc, const Scratch &s, cu
     dim3 grid(bx, g.n_frames);
     if (g.n_views == 1 && g.n_frames == 1 && sc.counts == nullptr && !g.soft) {
       const int b1 = (int)cull_one_ctas(g.n_atoms);
-      if (g.mode == 0 && !g.clip_on)
-        k_cull_direct<true><<<b1, kCullThreads, 0, st>>>(g, sc.frames, s.state, s.surv);
+      const bool plain = g.mode == 0 && !g.clip_on;
+      if (sc.stage && plain)
+        k_cull_direct<true, true><<<b1, kCullThreads, 0, st>>>(g, sc.frames, s.state, s.surv, sc.stage);
+      else if (sc.stage)
+        k_cull_direct<false, true><<<b1, kCullThreads, 0, st>>>(g, sc.frames, s.state, s.surv, sc.stage);
+      else if (plain)
+        k_cull_direct<true, false><<<b1, kCullThreads, 0, st>>>(g, sc.frames, s.state, s.surv, nullptr);
       else
-        k_cull_direct<false><<<b1, kCullThreads, 0, st>>>(g, sc.frames, s.state, s.surv);
+        k_cull_direct<false, false><<<b1, kCullThreads, 0, st>>>(g, sc.frames, s.state, s.surv, nullptr);
     } else if (g.n_views == 1) {
       k_cull_atoms<true><<<grid, kCullThreads, kCullSmem, st>>>(g, sc.frames, sc.counts, s.state, s.surv, s.status);
     } else {
@@ -1307,8 +1317,9 @@ cudaError_t run_binning(const Geometry &g, const Scene &sc, const Scratch &s, cu
       k_setup<true><<<grid, 256, 0, st>>>(g, sc.frames, sc.bonds, s.state, s.surv, s.keys, s.recs, s.rec_img,
                                           s.rec_box, s.rec_of, s.tile_count, s.status, s.cap_rec);
     else
-      k_setup<false><<<grid, 256, 0, st>>>(g, sc.frames, sc.bonds, s.state, s.surv, s.keys, s.recs, s.rec_img,
-                                           s.rec_box, s.rec_of, s.tile_count, s.status, s.cap_rec);
+      k_setup<false><<<grid, 256, 0, st>>>(g, sc.stage ? sc.stage : sc.frames, sc.bonds, s.state, s.surv, s.keys,
+                                           s.recs, s.rec_img, s.rec_box, s.rec_of, s.tile_count, s.status,
+                                           s.cap_rec);
   }
   ev_rec(evs, 2, st);
   {
@@ -1339,6 +1350,7 @@ cudaError_t run_frame_pipeline(const Geometry &g, const ShadeParams &sh, const S
                                const Outputs &out, bool ssao, cudaStream_t st, StageEvents *evs) {
   cudaError_t e = run_binning(g, sc, s, st, evs, false);
   if (e != cudaSuccess) return e;
+  const float4 *Xr = sc.stage ? sc.stage : sc.frames;  // winners are survivors: staged when staging is on
   const long long n_tiles = (long long)g.n_img * g.tiles_per_img;
   const unsigned rgrid = (unsigned)(n_tiles < 8LL * sm_count() ? n_tiles : 8LL * sm_count());
   if (g.tile_w == 16 && g.tile_h == 16)
@@ -1365,17 +1377,17 @@ cudaError_t run_frame_pipeline(const Geometry &g, const ShadeParams &sh, const S
     if (vec) {
       k_resolve_list<true><<<gl, 256, 0, st>>>(g, s.keys, s.cov_list, s.status);
       ev_rec(evs, 6, st);
-      k_resolve_split<true><<<n_shade + gb, 256, 0, st>>>(g, sh, sc.frames, sc.elem, sc.bonds, s.state, s.keys, out,
+      k_resolve_split<true><<<n_shade + gb, 256, 0, st>>>(g, sh, Xr, sc.elem, sc.bonds, s.state, s.keys, out,
                                                             ssao ? 1 : 0, s.cov_list, s.status, n_shade);
     } else {
       k_resolve_list<false><<<gl, 256, 0, st>>>(g, s.keys, s.cov_list, s.status);
       ev_rec(evs, 6, st);
-      k_resolve_split<false><<<n_shade + gb, 256, 0, st>>>(g, sh, sc.frames, sc.elem, sc.bonds, s.state, s.keys, out,
+      k_resolve_split<false><<<n_shade + gb, 256, 0, st>>>(g, sh, Xr, sc.elem, sc.bonds, s.state, s.keys, out,
                                                              ssao ? 1 : 0, s.cov_list, s.status, n_shade);
     }
   } else {
     dim3 grid((g.W + 31) / 32, (g.H + 31) / 32, g.n_img);
-    k_resolve<<<grid, 256, 0, st>>>(g, sh, sc.frames, sc.elem, sc.bonds, s.state, s.keys, out, ssao ? 1 : 0);
+    k_resolve<<<grid, 256, 0, st>>>(g, sh, Xr, sc.elem, sc.bonds, s.state, s.keys, out, ssao ? 1 : 0);
     ev_rec(evs, 6, st);
   }
   ev_rec(evs, 7, st);

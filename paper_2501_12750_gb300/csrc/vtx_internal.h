@@ -34,6 +34,8 @@ struct Scene {
   const long long *counts;    // device [n_frames] atom counts, or null (all = n_atoms)
   const uint8_t *elem;        // [stride] or null
   const uint2 *bonds;         // [n_bonds] or null
+  float4 *stage;              // single view, no bonds: device copy of the surviving records, written by the cull
+                              // and read by setup and resolve instead of frames (frames in host memory), or null
 };
 
 struct Outputs {
