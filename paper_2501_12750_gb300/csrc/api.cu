@@ -47,7 +47,7 @@ struct vtx_ctx {
   bool has_cam = false;
   // scratch
   Buf keys, surv, state, tcount, tstart, tcursor, tlist, bsums, recs, recimg, recbox, recof, entries, status, counts, hostin_x,
-      hostin_e, hostout, covlist, stage;
+      hostin_e, hostout, covlist, covmask, stage;
   bool cov_ok = false;  // the covered-pixel list of the last prepared launch fits (two-pass resolve)
   Buf ses_sas, ses_a, ses_b, ses_edt, ses_blk, ses_base, ses_total, ses_bbox, ses_case;
   uint32_t cap_rec = 0;
@@ -252,7 +252,8 @@ static vtx_status prepare(vtx_ctx *c, const Geometry &g, bool soft, long long st
   // covered-pixel list of the two-pass resolve (32-bit entries: only when every pixel index fits)
   c->cov_ok = false;
   if (!soft && n_img * g.pix_per_img < 4294967295LL) {
-    if (ensure(c, c->covlist, sizeof(uint32_t) * (size_t)(n_img * g.pix_per_img), "covered pixels") == VTX_OK)
+    if (ensure(c, c->covlist, sizeof(uint32_t) * (size_t)(n_img * g.pix_per_img), "covered pixels") == VTX_OK &&
+        ensure(c, c->covmask, sizeof(uint32_t) * (size_t)(n_img * g.pix_per_img / 32 + 8), "coverage bits") == VTX_OK)
       c->cov_ok = true;
     else
       c->err.clear();  // no room: the single-pass resolve needs no list
@@ -279,6 +280,7 @@ static Scratch scratch_of(vtx_ctx *c) {
   s.cap_rec = c->cap_rec;
   s.cap_entries = c->cap_entries;
   s.cov_list = c->cov_ok ? (uint32_t *)c->covlist.p : nullptr;
+  s.cov_mask = c->cov_ok ? (uint32_t *)c->covmask.p : nullptr;
   return s;
 }
 
@@ -399,7 +401,7 @@ vtx_status vtx_destroy(vtx_ctx *c) {
   drop_graphs(c);
   Buf *bufs[] = {&c->keys,   &c->surv,   &c->state,  &c->tcount,   &c->tstart,   &c->tcursor,  &c->tlist,
                  &c->bsums,  &c->recs,   &c->recimg, &c->recbox,   &c->recof,    &c->entries,  &c->status,
-                 &c->counts, &c->hostin_x, &c->hostin_e, &c->hostout, &c->covlist, &c->stage, &c->ses_sas, &c->ses_a, &c->ses_b,
+                 &c->counts, &c->hostin_x, &c->hostin_e, &c->hostout, &c->covlist, &c->covmask, &c->stage, &c->ses_sas, &c->ses_a, &c->ses_b,
                  &c->ses_edt, &c->ses_blk, &c->ses_base, &c->ses_total, &c->ses_bbox, &c->ses_case};
   for (Buf *b : bufs)
     if (b->p) cudaFree(b->p);

@@ -1153,7 +1153,8 @@ __global__ __launch_bounds__(256, VTX_RESOLVE_MINB) void k_resolve(Geometry g, S
 // form were measured too and were slower on the 4K frame.
 template <bool VEC>
 __global__ __launch_bounds__(256) void k_resolve_list(Geometry g, const unsigned long long *__restrict__ keys,
-                                                      uint32_t *__restrict__ cov, Status *status) {
+                                                      uint32_t *__restrict__ cov, uint32_t *__restrict__ mask,
+                                                      Status *status) {
   const long long total = g.pix_per_img * g.n_img;
   const int lane = threadIdx.x & 31;
   constexpr int P = VEC ? 4 : 1;
@@ -1174,6 +1175,12 @@ __global__ __launch_bounds__(256) void k_resolve_list(Geometry g, const unsigned
       } else {
         covered = (uint32_t)keys[q0] != kNoId ? 1u : 0u;
       }
+    }
+    // coverage bits of the warp's 32 units (one word per pixel of a unit), for the background CTAs
+#pragma unroll
+    for (int v = 0; v < P; ++v) {
+      const unsigned m = __ballot_sync(0xffffffffu, (covered >> v) & 1u);
+      if (lane == 0 && live) mask[(u >> 5) * P + v] = m;
     }
     const int n_mine = __popc(covered);
     int incl = n_mine;
@@ -1198,7 +1205,8 @@ template <bool VEC>
 __global__ __launch_bounds__(256, VTX_RESOLVE_MINB) void k_resolve_split(
     Geometry g, ShadeParams sh, const float4 *__restrict__ frames, const uint8_t *__restrict__ elem,
     const uint2 *__restrict__ bonds, const ImageState *__restrict__ st, const unsigned long long *__restrict__ keys,
-    Outputs out, int do_ssao, const uint32_t *__restrict__ cov, const Status *__restrict__ status, int n_shade) {
+    Outputs out, int do_ssao, const uint32_t *__restrict__ cov, const uint32_t *__restrict__ mask,
+    const Status *__restrict__ status, int n_shade) {
   const long long ppi = g.pix_per_img;
   if ((int)blockIdx.x < n_shade) {
     const unsigned n = status->n_cov;
@@ -1217,15 +1225,9 @@ __global__ __launch_bounds__(256, VTX_RESOLVE_MINB) void k_resolve_split(
   for (long long u = (long long)(blockIdx.x - n_shade) * blockDim.x + threadIdx.x; u < n_units;
        u += (long long)(gridDim.x - n_shade) * blockDim.x) {
     const long long q0 = u * P;
-    unsigned covered = 0u;
-    if (VEC) {
-      const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(keys + q0);
-      const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(keys + q0 + 2);
-      covered = ((uint32_t)a.x != kNoId ? 1u : 0u) | ((uint32_t)a.y != kNoId ? 2u : 0u) |
-                ((uint32_t)b.x != kNoId ? 4u : 0u) | ((uint32_t)b.y != kNoId ? 8u : 0u);
-    } else {
-      covered = (uint32_t)keys[q0] != kNoId ? 1u : 0u;
-    }
+    unsigned covered = 0u;  // from the list pass's bits (1 bit per pixel) instead of the 8-byte keys
+#pragma unroll
+    for (int v = 0; v < P; ++v) covered |= ((mask[(u >> 5) * P + v] >> (u & 31)) & 1u) << v;
     const long long img = q0 / ppi, p = q0 - img * ppi;
     float *nrm = out.normal + img * 3 * ppi + p;
     float *rgb = out.rgb + img * 3 * ppi + p;
@@ -1375,15 +1377,15 @@ cudaError_t run_frame_pipeline(const Geometry &g, const ShadeParams &sh, const S
     const int n_shade = 3 * sms;
     const int gb = (int)(want < 8LL * sms ? (want > 0 ? want : 1) : 8LL * sms);
     if (vec) {
-      k_resolve_list<true><<<gl, 256, 0, st>>>(g, s.keys, s.cov_list, s.status);
+      k_resolve_list<true><<<gl, 256, 0, st>>>(g, s.keys, s.cov_list, s.cov_mask, s.status);
       ev_rec(evs, 6, st);
       k_resolve_split<true><<<n_shade + gb, 256, 0, st>>>(g, sh, Xr, sc.elem, sc.bonds, s.state, s.keys, out,
-                                                            ssao ? 1 : 0, s.cov_list, s.status, n_shade);
+                                                            ssao ? 1 : 0, s.cov_list, s.cov_mask, s.status, n_shade);
     } else {
-      k_resolve_list<false><<<gl, 256, 0, st>>>(g, s.keys, s.cov_list, s.status);
+      k_resolve_list<false><<<gl, 256, 0, st>>>(g, s.keys, s.cov_list, s.cov_mask, s.status);
       ev_rec(evs, 6, st);
       k_resolve_split<false><<<n_shade + gb, 256, 0, st>>>(g, sh, Xr, sc.elem, sc.bonds, s.state, s.keys, out,
-                                                             ssao ? 1 : 0, s.cov_list, s.status, n_shade);
+                                                             ssao ? 1 : 0, s.cov_list, s.cov_mask, s.status, n_shade);
     }
   } else {
     dim3 grid((g.W + 31) / 32, (g.H + 31) / 32, g.n_img);

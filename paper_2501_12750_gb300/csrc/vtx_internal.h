@@ -24,6 +24,7 @@ struct Scratch {
   uint32_t *rec_of;           // soft: [n_img][n_atoms] record of each atom
   unsigned long long *entries;  // [cap_entries] (sort key << 32 | record or id)
   uint32_t *cov_list;         // [n_img * H * W] covered pixels (img * H * W + p), or null: single-pass resolve
+  uint32_t *cov_mask;         // [n_img * H * W / 32 + 8] coverage bits written by the list pass
   Status *status;
   uint32_t cap_rec;
   unsigned long long cap_entries;
