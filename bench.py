@@ -34,7 +34,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-KERNELS_PER_FRAME = 9  # init, cull, finalize, setup, scan, scatter, raster, resolve list, resolve/shade
+KERNELS_PER_FRAME = 8  # clear, cull, setup, scan, scatter, raster, resolve list, resolve/shade
 
 
 def parse():

@@ -6,11 +6,12 @@
 // occlusion ("High Quality Rendering").  Here the same per-pixel result --
 // the nearest ray/primitive hit -- is computed without a graphics API:
 //
-//   k_cull_atoms / k_cull_bonds  stream every record once (16-byte vector
-//        loads), reject what cannot cover a pixel centre, append survivors
-//        (block-aggregated, one global atomic per 2,048 atoms per view);
-//   k_finalize   fixes each image's depth-key range from the survivors;
-//   k_setup      precise double-float setup per survivor; footprints of at
+//   k_clear      resets image states and counters, tile counts and keys;
+//   k_cull_direct / k_cull_atoms / k_cull_bonds  stream every record once,
+//        reject what cannot cover a pixel centre, append survivors through
+//        per-warp slabs or per-block runs;
+//   k_setup      fixes each image's depth-key range from the survivors, then
+//        precise double-float setup per survivor; footprints of at
 //        most splat_max candidate pixels are ray-cast right there and
 //        merged with a 64-bit atomicMin of (depth key << 32 | id); larger
 //        ones become 64-byte records counted per screen tile;
@@ -20,8 +21,10 @@
 //        (bitonic), stages records chunk by chunk, ray-casts every pixel,
 //        and stops once every pixel's hit is nearer than the next entry's
 //        nearest possible depth (__syncthreads_and);
-//   k_resolve    decodes id, recomputes the hit -> depth, normal, Blinn-Phong
-//        colour, SSAO from neighbouring depth keys; writes every plane once.
+//   k_resolve_list / k_resolve_split  list the covered pixels, then shade
+//        them (id decoded, hit recomputed -> depth, normal, colour, SSAO
+//        from neighbouring depth keys, outline, fog) beside CTAs that write
+//        the background pixels; every output plane is written once.
 #include <cstdio>
 
 #include "vtx_internal.h"
@@ -49,9 +52,13 @@ int sm_count() {
 
 // ----------------------------------------------------------------- init --
 
-__global__ void k_init_state(ImageState *st, int n_img, Status *status) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n_img) {
+// Frame set-up in one launch: image states and launch counters reset, tile
+// counts zeroed and (hard edges) every depth key set to the background key.
+__global__ __launch_bounds__(256) void k_clear(ImageState *st, int n_img, Status *status, uint32_t *tile_count,
+                                               long long n_tiles, unsigned long long *keys, long long n_keys) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  if (tid < n_img) {
     ImageState s;
     s.zlo_bits = 0x7f800000u;
     s.zhi_bits = 0u;
@@ -61,14 +68,20 @@ __global__ void k_init_state(ImageState *st, int n_img, Status *status) {
     s.S = 0.0f;
     s.invS = 0.0f;
     s.pad = 0.0f;
-    st[i] = s;
+    st[tid] = s;
   }
-  if (i == 0) {
+  if (tid == 0) {
     status->n_rec = 0u;
     status->n_entries = 0ull;
     status->n_list = 0u;
     status->n_cov = 0u;
   }
+  for (long long i = tid; i < n_tiles; i += stride) tile_count[i] = 0u;
+  // keys: 16-byte stores over the (256-byte aligned) buffer, then the odd tail
+  const ulonglong2 bg2 = make_ulonglong2(kBgKey, kBgKey);
+  ulonglong2 *k2 = reinterpret_cast<ulonglong2 *>(keys);
+  for (long long i = tid; i < n_keys / 2; i += stride) k2[i] = bg2;
+  if ((n_keys & 1) && tid == 0) keys[n_keys - 1] = kBgKey;
 }
 
 // ----------------------------------------------------------------- cull --
@@ -434,23 +447,24 @@ __global__ __launch_bounds__(kCullThreads) void k_cull_bonds(Geometry g, const f
 
 // Depth-key range per image: [zlo, zhi] of the survivors, widened past the
 // FP32 error of the cull and clamped to half the near plane.
-__global__ void k_finalize(Geometry g, ImageState *st) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= g.n_img) return;
-  ImageState s = st[i];
+// Depth-key range of image img from its survivors' range (the cull's
+// atomics), widened by the FP32 rounding of those bounds.  Computed by every
+// setup CTA of the image alike; CTA 0 stores it for the later stages.
+__device__ __forceinline__ ImageState finalize_state(const Geometry &g, int img, ImageState s) {
   if (s.n_surv == 0u || s.zhi_bits == 0u) {
-    st[i].valid = 0u;
-    return;
+    s.valid = 0u;
+    return s;
   }
-  const ViewParams &v = g.views[i % g.n_views];
+  const ViewParams &v = g.views[img % g.n_views];
   float lo = __uint_as_float(s.zlo_bits), hi = __uint_as_float(s.zhi_bits);
   lo = fmaxf(lo - 4e-6f * fabsf(lo) - 1e-4f, 0.5f * v.znear);
   hi = hi + 4e-6f * fabsf(hi) + 1e-4f;
   if (!(hi > lo)) hi = lo + 1.0f;
-  st[i].zlo = lo;
-  st[i].S = kKeySpanF / (hi - lo);
-  st[i].invS = (hi - lo) / kKeySpanF;
-  st[i].valid = 1u;
+  s.zlo = lo;
+  s.S = kKeySpanF / (hi - lo);
+  s.invS = (hi - lo) / kKeySpanF;
+  s.valid = 1u;
+  return s;
 }
 
 // ---------------------------------------------------------------- setup --
@@ -522,12 +536,18 @@ __device__ __forceinline__ bool prim_hit(const PrimGeom &p, float3 o, const PixR
 
 template <bool SOFT>
 __global__ __launch_bounds__(256, 3) void k_setup(Geometry g, const float4 *__restrict__ frames,
-                                               const uint2 *__restrict__ bonds, const ImageState *__restrict__ st,
+                                               const uint2 *__restrict__ bonds, ImageState *st,
                                                const uint32_t *__restrict__ surv, unsigned long long *keys,
                                                PrimRec *recs, uint32_t *rec_img, uint2 *rec_box, uint32_t *rec_of,
                                                uint32_t *tile_count, Status *status, uint32_t cap_rec) {
   const int img = blockIdx.y;
-  const ImageState s = st[img];
+  const ImageState s = finalize_state(g, img, st[img]);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st[img].zlo = s.zlo;
+    st[img].S = s.S;
+    st[img].invS = s.invS;
+    st[img].valid = s.valid;
+  }
   if (!s.valid) return;
   const ViewParams &v = g.views[img % g.n_views];
   const int frame = img / g.n_views;
@@ -1270,9 +1290,14 @@ cudaError_t run_binning(const Geometry &g, const Scene &sc, const Scratch &s, cu
                         bool soft) {
   const int sms = sm_count();
   const long long n_tiles = (long long)g.n_img * g.tiles_per_img;
-  k_init_state<<<(g.n_img + 255) / 256, 256, 0, st>>>(s.state, g.n_img, s.status);
-  cudaMemsetAsync(s.tile_count, 0, sizeof(uint32_t) * (size_t)n_tiles, st);
-  if (!soft) cudaMemsetAsync(s.keys, 0xff, sizeof(unsigned long long) * (size_t)g.pix_per_img * g.n_img, st);
+  {
+    const long long n_keys = soft ? 0 : g.pix_per_img * g.n_img;
+    long long want = n_keys / 2 > n_tiles ? n_keys / 2 : n_tiles;
+    want = want > g.n_img ? want : g.n_img;
+    const long long blocks = (want + 255) / 256;
+    const int gc = (int)(blocks < 16LL * sms ? (blocks > 0 ? blocks : 1) : 16LL * sms);
+    k_clear<<<gc, 256, 0, st>>>(s.state, g.n_img, s.status, s.tile_count, n_tiles, s.keys, n_keys);
+  }
   ev_rec(evs, 0, st);
   {
     static bool attr = false;
@@ -1311,7 +1336,6 @@ cudaError_t run_binning(const Geometry &g, const Scene &sc, const Scratch &s, cu
     }
   }
   ev_rec(evs, 1, st);
-  k_finalize<<<(g.n_img + 127) / 128, 128, 0, st>>>(g, s.state);
   {
     int bx = g.n_img >= 64 ? 8 : (4 * sms + g.n_img - 1) / g.n_img;
     dim3 grid(bx, g.n_img);
