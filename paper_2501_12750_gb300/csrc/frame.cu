@@ -274,7 +274,14 @@ __global__ __launch_bounds__(kCullThreads, 5) void k_cull_atoms(Geometry g, cons
   }
 }
 
-constexpr int kSlab = 64;  // survivor slots a warp reserves at a time (single-view cull)
+// Survivor slab size: one global atomic per slab.  On the close view (tens of
+// millions of survivors) the shared counter was the cull's bottleneck at 64
+// slots (0.84 ms; 128: 0.61 ms; 256: 0.30 ms); at 1024 the holes (a warp's
+// last slab) start to cost setup time on the overview.
+#ifndef VTX_SLAB
+#define VTX_SLAB 256
+#endif
+constexpr int kSlab = VTX_SLAB;  // survivor slots a warp reserves at a time (single-view cull)
 
 // Warp-aggregated survivor append through per-warp slabs: slots [used, kSlab)
 // of the current slab first, the rest in a fresh slab reserved with one
