@@ -994,6 +994,16 @@ __global__ __launch_bounds__(TW *TH) void k_raster(Geometry g, const PrimRec *__
 #define VTX_RESOLVE_MINB 4
 #endif
 constexpr int kSsaoGroup = VTX_SSAO_GROUP;  // SSAO samples whose neighbour keys are fetched together
+// Measured: 3 shading CTAs per SM beat 2 and 4 (2 starves the close view and
+// the batch, 4 leaves too few CTAs for the background writes of the batch);
+// 16 raster CTAs per SM beat 4 and 8 on the close view (0.23 -> 0.20 ms) and
+// tie elsewhere.
+#ifndef VTX_SHADE_PER_SM
+#define VTX_SHADE_PER_SM 3
+#endif
+#ifndef VTX_RASTER_GRID
+#define VTX_RASTER_GRID 16
+#endif
 #ifndef VTX_RESOLVE_2PASS
 #define VTX_RESOLVE_2PASS 1
 #endif
@@ -1394,7 +1404,8 @@ cudaError_t run_frame_pipeline(const Geometry &g, const ShadeParams &sh, const S
   if (e != cudaSuccess) return e;
   const float4 *Xr = sc.stage ? sc.stage : sc.frames;  // winners are survivors: staged when staging is on
   const long long n_tiles = (long long)g.n_img * g.tiles_per_img;
-  const unsigned rgrid = (unsigned)(n_tiles < 8LL * sm_count() ? n_tiles : 8LL * sm_count());
+  const unsigned rgrid = (unsigned)(n_tiles < (long long)VTX_RASTER_GRID * sm_count() ? n_tiles
+                                                                          : (long long)VTX_RASTER_GRID * sm_count());
   if (g.tile_w == 16 && g.tile_h == 16)
     k_raster<16, 16><<<rgrid, 256, 0, st>>>(g, s.recs, s.entries, s.cap_entries, s.tile_count,
                                                         s.tile_start, s.state, s.keys, s.tile_list, s.status);
@@ -1414,7 +1425,7 @@ cudaError_t run_frame_pipeline(const Geometry &g, const ShadeParams &sh, const S
     const long long want = (units + 255) / 256;
     const int gl = (int)(want < 16LL * sms ? (want > 0 ? want : 1) : 16LL * sms);
     // shading CTAs first (they start at once and stay resident), background CTAs behind them
-    const int n_shade = 3 * sms;
+    const int n_shade = VTX_SHADE_PER_SM * sms;
     const int gb = (int)(want < 8LL * sms ? (want > 0 ? want : 1) : 8LL * sms);
     if (vec) {
       k_resolve_list<true><<<gl, 256, 0, st>>>(g, s.keys, s.cov_list, s.cov_mask, s.status);
