@@ -750,7 +750,11 @@ constexpr long long kScanSingleMax = 32LL * 32 * kScanRounds;   // 32 warps x 32
 __global__ __launch_bounds__(1024) void k_scan_single(const uint32_t *__restrict__ cnt, long long n,
                                                       uint32_t *__restrict__ start, uint32_t *__restrict__ cursor,
                                                       uint32_t *__restrict__ list, Status *status,
-                                                      unsigned long long cap_entries) {
+                                                      unsigned long long cap_entries, int skip_if_empty) {
+  // hard edges: with no binned record every tile is empty; the raster reads
+  // only the tile list (left empty by the set-up kernel) and the scatter has
+  // nothing to place, so the scan has nothing to do
+  if (skip_if_empty && status->n_rec == 0u) return;
   __shared__ unsigned long long s_wsum[32];
   __shared__ unsigned int s_n;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -1390,7 +1394,7 @@ cudaError_t run_binning(const Geometry &g, const Scene &sc, const Scratch &s, cu
   {
     if (n_tiles <= kScanSingleMax) {
       k_scan_single<<<1, 1024, 0, st>>>(s.tile_count, n_tiles, s.tile_start, s.tile_cursor, s.tile_list, s.status,
-                                        s.cap_entries);
+                                        s.cap_entries, soft ? 0 : 1);
     } else {
       int nb = (int)((n_tiles + kScanItems - 1) / kScanItems);
       unsigned long long *bs = reinterpret_cast<unsigned long long *>(s.block_sums);
