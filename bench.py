@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--clusters", type=int, default=20000, help="blobs of 5,000 atoms (20,000 = 1e8 atoms)")
     ap.add_argument("--ses-only", action="store_true",
                     help="only the SES of the 1e5-atom system (one JSON line; for profiling its kernels)")
+    ap.add_argument("--soft-only", action="store_true",
+                    help="only the soft-edge forward and backward (one JSON line; for profiling their kernels)")
     return ap.parse_args()
 
 
@@ -194,6 +196,11 @@ def main():
         if rank == 0:
             print(json.dumps({"metric": "ses_ms", "unit": "ms", "higher_is_better": False, "data": "synthetic",
                               **ses_extra(vtx, torch, dev)}))
+        return 0
+    if args.soft_only:
+        if rank == 0:
+            print(json.dumps({"metric": "soft_fwd_bwd_ms", "unit": "ms", "higher_is_better": False,
+                              "data": "synthetic", **soft_extra(vtx, torch, dev, vtx.Renderer(dev.index))}))
         return 0
 
     t_gen = time.time()
@@ -400,6 +407,56 @@ def ses_extra(vtx, torch, dev, reps=5):
             "note": "wall time of the synchronous call (SAS, 3 distance passes, count, scan, emit)"}
 
 
+def soft_extra(vtx, torch, dev, r, reps=5):
+    """Soft-edge forward and backward on 20,000 atoms x 16 views at 512x512, and the hard renderer on the same
+    views."""
+    from paper_2501_12750_gb300 import scenes
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    res = {}
+    s5 = scenes.config5()
+    x = torch.from_numpy(s5.xyzr).to(dev)
+    tgt = torch.from_numpy(s5.extra["target"]).to(dev)
+    with torch.no_grad():
+        A_t, D_t, N_t = r.render_soft_fwd(tgt, s5.cameras)
+    for _ in range(2):
+        A, D, Nn = r.render_soft_fwd(x, s5.cameras)
+        gA, gD, gN = 2 * (A - A_t), 0.2 * (D - D_t), 2 * (Nn - N_t)
+        r.render_soft_bwd(x, s5.cameras, gA, gD, gN)
+    torch.cuda.synchronize()
+    e0.record(r.stream)
+    for _ in range(reps):
+        A, D, Nn = r.render_soft_fwd(x, s5.cameras)
+    e1.record(r.stream)
+    torch.cuda.synchronize()
+    fwd_ms = e0.elapsed_time(e1) / reps
+    e0.record(r.stream)
+    for _ in range(reps):
+        r.render_soft_bwd(x, s5.cameras, gA, gD, gN)
+    e1.record(r.stream)
+    torch.cuda.synchronize()
+    bwd_ms = e0.elapsed_time(e1) / reps
+    # hard renderer on the same 16 views
+    r.upload_atoms(x, torch.from_numpy(s5.elem).to(dev), s5.palette)
+    hs = vtx.default_settings()
+    ho = r.alloc_outputs(512, 512)
+    for c in s5.cameras[:2]:
+        r.set_camera(c)
+        r.render_frame(vtx.default_settings(flags=vtx.FLAG_SYNC), out=ho)
+    torch.cuda.synchronize()
+    e0.record(r.stream)
+    for c in s5.cameras:
+        r.set_camera(c)
+        r.render_frame(hs, out=ho)
+    e1.record(r.stream)
+    torch.cuda.synchronize()
+    hard_ms = e0.elapsed_time(e1)
+    res["soft"] = {"workload": "20,000 atoms, 16 views at 512x512, sigma 0.5 px", "fwd_ms": fwd_ms,
+                   "bwd_ms": bwd_ms, "fwd_bwd_ms": fwd_ms + bwd_ms, "hard_16_views_ms": hard_ms,
+                   "note": "fwd and bwd each rebuild their tile lists (cull, setup, scan, scatter)"}
+    return res
+
+
 def run_extras(vtx, torch, dev, r, s3, cam, k):
     import dataclasses
 
@@ -489,48 +546,7 @@ def run_extras(vtx, torch, dev, r, s3, cam, k):
                            "per_frame_loop_images_per_s": 1e3 / loop_ms, "graph": True}
     del out, frames
     torch.cuda.empty_cache()
-    # soft forward + backward
-    s5 = scenes.config5()
-    x = torch.from_numpy(s5.xyzr).to(dev)
-    tgt = torch.from_numpy(s5.extra["target"]).to(dev)
-    with torch.no_grad():
-        A_t, D_t, N_t = r.render_soft_fwd(tgt, s5.cameras)
-    for _ in range(2):
-        A, D, Nn = r.render_soft_fwd(x, s5.cameras)
-        gA, gD, gN = 2 * (A - A_t), 0.2 * (D - D_t), 2 * (Nn - N_t)
-        r.render_soft_bwd(x, s5.cameras, gA, gD, gN)
-    torch.cuda.synchronize()
-    reps = 5
-    e0.record(r.stream)
-    for _ in range(reps):
-        A, D, Nn = r.render_soft_fwd(x, s5.cameras)
-    e1.record(r.stream)
-    torch.cuda.synchronize()
-    fwd_ms = e0.elapsed_time(e1) / reps
-    e0.record(r.stream)
-    for _ in range(reps):
-        r.render_soft_bwd(x, s5.cameras, gA, gD, gN)
-    e1.record(r.stream)
-    torch.cuda.synchronize()
-    bwd_ms = e0.elapsed_time(e1) / reps
-    # hard renderer on the same 16 views
-    r.upload_atoms(x, torch.from_numpy(s5.elem).to(dev), s5.palette)
-    hs = vtx.default_settings()
-    ho = r.alloc_outputs(512, 512)
-    for c in s5.cameras[:2]:
-        r.set_camera(c)
-        r.render_frame(vtx.default_settings(flags=vtx.FLAG_SYNC), out=ho)
-    torch.cuda.synchronize()
-    e0.record(r.stream)
-    for c in s5.cameras:
-        r.set_camera(c)
-        r.render_frame(hs, out=ho)
-    e1.record(r.stream)
-    torch.cuda.synchronize()
-    hard_ms = e0.elapsed_time(e1)
-    res["soft"] = {"workload": "20,000 atoms, 16 views at 512x512, sigma 0.5 px", "fwd_ms": fwd_ms,
-                   "bwd_ms": bwd_ms, "fwd_bwd_ms": fwd_ms + bwd_ms, "hard_16_views_ms": hard_ms,
-                   "note": "fwd and bwd each rebuild their tile lists (cull, setup, scan, scatter)"}
+    res["soft"] = soft_extra(vtx, torch, dev, r)["soft"]
     return res
 
 

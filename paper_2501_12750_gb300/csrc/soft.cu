@@ -12,12 +12,16 @@
 //   coverage = sum w_i, depth = sum w_i t_i, normal = sum w_i n_i.
 // Binning (cull with 4 px dilation, precise setup, per-tile counting sort)
 // is shared with the hard-edge path; each tile CTA sorts its list by
-// (centre depth key, id) in shared memory.  The backward kernel rebuilds the
-// lists, re-walks each pixel front to back to find its last contributor and
-// final transmittance, then walks back to front with the carry
+// (centre depth key, id) in shared memory, then each warp walks the sorted
+// list on its own, staging 32 entries at a time with their per-sphere
+// constants (f / z_c, 1 / r and a bound on rho^2 that rejects most entries
+// before any square root or division).  The backward kernel rebuilds the
+// lists, re-walks each pixel front to back for its last contributor and final
+// transmittance, then walks back to front with the carry
 // R_i = alpha_{i+1} c_{i+1} + (1 - alpha_{i+1}) R_{i+1}, recovering T_i from
 // T_{i+1} / (1 - alpha_i) (alpha <= 0.99 keeps this safe), and accumulates
-// d/d(x, y, z, r) per sphere with warp reductions and FP32 atomics.
+// d/d(x, y, z, r) per sphere as a warp sum (a six-shuffle reduce-scatter)
+// and one 16-byte FP32 atomic per sphere and warp.
 #include "vtx_internal.h"
 
 namespace vtx {
@@ -29,41 +33,87 @@ constexpr int kSoftCap = 4096;
 constexpr int kSoftNT = 256;
 constexpr float kTStop = 1e-4f;
 constexpr float kAMax = 0.99f;
-constexpr size_t kSoftSmem = kSoftCap * sizeof(unsigned long long) + kSoftNT * sizeof(PrimRec);
 
-struct SoftTerm {
-  float alpha, sg, t, delta;
-  float3 n;      // internal frame
-  float3 q;      // centre minus closest ray point (internal frame)
-  float sq, sm, m, zc, rho2;
+// A tile entry as the per-pixel loop reads it from shared memory: the record's
+// projection terms plus the per-sphere constants of the soft terms, computed
+// once per entry when a warp stages it instead of once per pixel.
+struct __align__(16) SoftPrim {
+  float u0h, u0l, v0h, v0l;   // projected reference point (pixels), double-float
+  float k, dz, zr, rad;       // A per pixel at zr, zr - centre depth, reference depth, radius
+  float fz, inv_rad, eta, rej2;  // f / centre depth, 1 / rad, 0.05 rad, bound on rho^2 of a used sphere
+};
+static_assert(sizeof(SoftPrim) == 48, "SoftPrim is three 16-byte words");
+
+constexpr size_t kSoftSmem = kSoftCap * sizeof(unsigned long long) + kSoftNT * sizeof(SoftPrim);
+
+__device__ __forceinline__ SoftPrim soft_prim(const PrimRec &p, float f) {
+  SoftPrim s;
+  s.u0h = p.u0h;
+  s.u0l = p.u0l;
+  s.v0h = p.v0h;
+  s.v0l = p.v0l;
+  s.k = p.k;
+  s.dz = p.dz;
+  s.zr = p.zr;
+  s.rad = p.rad;
+  s.fz = f / (p.zr - p.dz);
+  s.inv_rad = 1.0f / p.rad;
+  s.eta = 0.05f * p.rad;
+  // delta >= -4 px needs sqrt(rho^2) <= rad + 4 / fz; the bound is widened by
+  // 0.05 % so that rounding never drops a sphere the exact test keeps.
+  const float reach = p.rad + 4.0f / s.fz;
+  s.rej2 = reach * reach * 1.001f + 1e-6f;
+  return s;
+}
+
+// Per-pixel ray constants.
+struct SoftPix {
+  PixRay r;
+  float inv_uu, inv_un;  // 1 / |u|^2, 1 / |u|
 };
 
-__device__ __forceinline__ bool soft_term(const PrimRec &p, const PixRay &r, float f, float sigma, SoftTerm &o) {
-  float3 ov = local_o(p.u0h, p.u0l, p.v0h, p.v0l, p.k, p.dz, r);
-  float ou = fmaf(ov.x, r.a, fmaf(ov.y, r.b, ov.z));
-  float oo = fmaf(ov.x, ov.x, fmaf(ov.y, ov.y, ov.z * ov.z));
-  float sst = -ou / r.uu;
-  o.rho2 = fmaxf(oo - ou * ou / r.uu, 0.0f);
-  o.zc = p.zr - p.dz;
-  o.sq = sqrtf(o.rho2 + 1e-12f);
-  o.delta = (p.rad - o.sq) * f / o.zc;
+__device__ __forceinline__ SoftPix soft_pix(const ViewParams &v, int px, int py) {
+  SoftPix x;
+  x.r = pix_ray(v, px, py);
+  x.inv_uu = 1.0f / x.r.uu;
+  x.inv_un = 1.0f / sqrtf(x.r.uu);
+  return x;
+}
+
+struct SoftTerm {
+  float3 ov;        // ray origin minus centre (internal frame)
+  float sst;        // ray parameter of the closest approach, relative to zr
+  float rho2, rho2s, delta, sg, alpha, m, ism, si, t;
+  float3 n;         // internal frame
+};
+
+// The soft term of one sphere for one pixel; false when delta < -4 px.
+__device__ __forceinline__ bool soft_term(const SoftPrim &p, const SoftPix &x, float inv_sigma, SoftTerm &o) {
+  const PixRay &r = x.r;
+  o.ov = local_o(p.u0h, p.u0l, p.v0h, p.v0l, p.k, p.dz, r);
+  const float ou = fmaf(o.ov.x, r.a, fmaf(o.ov.y, r.b, o.ov.z));
+  const float oo = fmaf(o.ov.x, o.ov.x, fmaf(o.ov.y, o.ov.y, o.ov.z * o.ov.z));
+  o.sst = -ou * x.inv_uu;
+  o.rho2 = fmaxf(fmaf(ou, o.sst, oo), 0.0f);  // |o|^2 - (o.u)^2 / |u|^2
+  if (o.rho2 > p.rej2) return false;
+  o.rho2s = o.rho2 + 1e-12f;
+  o.delta = (p.rad - sqrtf(o.rho2s)) * p.fz;
   if (!(o.delta >= -4.0f)) return false;
-  o.sg = 1.0f / (1.0f + expf(-o.delta / sigma));
+  o.sg = __frcp_rn(1.0f + expf(-o.delta * inv_sigma));
   o.alpha = fminf(kAMax, o.sg);
-  float eta = 0.05f * p.rad;
-  o.m = fmaxf(p.rad * p.rad - o.rho2, 0.0f);
-  o.sm = sqrtf(o.m + eta * eta);
-  float gv = o.sm - eta;
-  float si = sst - gv / sqrtf(r.uu);
-  o.t = p.zr + si;
-  float inv = 1.0f / p.rad;
-  o.n = make_float3((ov.x + si * r.a) * inv, (ov.y + si * r.b) * inv, (ov.z + si) * inv);
-  o.q = make_float3(-(ov.x + sst * r.a), -(ov.y + sst * r.b), -(ov.z + sst));
+  o.m = fmaxf(fmaf(p.rad, p.rad, -o.rho2), 0.0f);
+  const float m2 = fmaf(p.eta, p.eta, o.m);
+  o.ism = rsqrtf(m2);
+  o.si = fmaf(-(m2 * o.ism - p.eta), x.inv_un, o.sst);  // smoothed entry, relative to zr
+  o.t = p.zr + o.si;
+  o.n = make_float3(fmaf(o.si, r.a, o.ov.x) * p.inv_rad, fmaf(o.si, r.b, o.ov.y) * p.inv_rad,
+                    (o.ov.z + o.si) * p.inv_rad);
   return true;
 }
 
 struct SoftTile {
   int img, px, py, m;
+  int px0, py0;  // the tile's first column and row
   bool inside;
   uint32_t start;
 };
@@ -77,8 +127,10 @@ __device__ __forceinline__ bool soft_load(const Geometry &g, const unsigned long
   T.img = (int)(gt / g.tiles_per_img);
   const int t = (int)(gt % g.tiles_per_img);
   const int tx = t % g.tiles_x, ty = t / g.tiles_x;
-  T.px = tx * 16 + (threadIdx.x & 15);
-  T.py = ty * 16 + (threadIdx.x >> 4);
+  T.px0 = tx * 16;
+  T.py0 = ty * 16;
+  T.px = T.px0 + (threadIdx.x & 15);
+  T.py = T.py0 + (threadIdx.x >> 4);
   T.inside = T.px < g.W && T.py < g.H;
   uint32_t cnt = tile_count[gt];
   T.start = tile_start[gt];
@@ -114,6 +166,43 @@ __device__ __forceinline__ bool soft_load(const Geometry &g, const unsigned long
   return true;
 }
 
+// Each warp walks the sorted list on its own (no block barrier after the
+// sort, so a warp of saturated pixels never waits for a warp of silhouette
+// pixels): it stages 32 entries at a time, lane i converting entry c0 + i, in
+// its private 32-slot window of shared memory.
+//
+// Staging also culls the window for the warp.  The warp covers two 16-pixel
+// rows; `am` marks the lanes still compositing.  For a sphere whose reference
+// point is its centre (dz = 0) the offset at the reference depth is
+// o = k (du, -dv, 0) with (du, dv) the pixel offset from the projected centre,
+// and rho^2 = |o|^2 - (o.u)^2 / |u|^2 >= |o|^2 / |u|^2 (Cauchy-Schwarz on the
+// x, y part), so rho^2 > rej2 whenever k^2 d^2 > rej2 |u|^2_max.  Entries whose
+// disc of that radius misses the bounding rectangle of the active lanes'
+// pixel centres are dropped from the returned mask; the radius is widened
+// (0.01 % plus 1e-3 px plus 2e-7 of the coordinates) to cover FP32 rounding.
+__device__ __forceinline__ unsigned soft_stage(const Geometry &g, const PrimRec *__restrict__ recs,
+                                               const uint32_t *__restrict__ rec_of, const unsigned long long *s_e,
+                                               const SoftTile &T, int c0, float f, SoftPrim *s_w, unsigned am,
+                                               float col0, float row0, float uu_max) {
+  const int lane = threadIdx.x & 31;
+  const int j = c0 + lane;
+  bool keep = false;
+  if (j < T.m) {
+    const SoftPrim sp = soft_prim(recs[rec_of[(long long)T.img * g.n_atoms + (uint32_t)s_e[j]]], f);
+    s_w[lane] = sp;
+    const unsigned cols = (am | (am >> 16)) & 0xffffu;
+    const float rx0 = col0 + (float)(__ffs(cols) - 1), rx1 = col0 + (float)(31 - __clz(cols));
+    const float ry0 = row0 + ((am & 0xffffu) ? 0.0f : 1.0f), ry1 = row0 + ((am >> 16) ? 1.0f : 0.0f);
+    const float cu = sp.u0h + sp.u0l, cv = sp.v0h + sp.v0l;
+    const float dx = fmaxf(fmaxf(rx0 - cu, cu - rx1), 0.0f);
+    const float dy = fmaxf(fmaxf(ry0 - cv, cv - ry1), 0.0f);
+    const float r2 = sp.rej2 * uu_max;  // approximate root and quotient: the 0.01 % widening covers their error
+    const float rt = __fdividef(r2 * rsqrtf(r2), sp.k) * 1.0001f + 1e-3f + 2e-7f * (fabsf(cu) + fabsf(cv));
+    keep = sp.dz != 0.0f || !(dx * dx + dy * dy > rt * rt);
+  }
+  return __ballot_sync(0xffffffffu, keep);
+}
+
 __global__ __launch_bounds__(kSoftNT) void k_soft_fwd(Geometry g, const PrimRec *__restrict__ recs,
                                                       const uint32_t *__restrict__ rec_of,
                                                       const unsigned long long *__restrict__ entries,
@@ -123,33 +212,36 @@ __global__ __launch_bounds__(kSoftNT) void k_soft_fwd(Geometry g, const PrimRec 
                                                       float *cov, float *dep, float *nrm) {
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned long long *s_e = reinterpret_cast<unsigned long long *>(smem);
-  PrimRec *s_r = reinterpret_cast<PrimRec *>(smem + kSoftCap * sizeof(unsigned long long));
+  SoftPrim *s_w = reinterpret_cast<SoftPrim *>(smem + kSoftCap * sizeof(unsigned long long)) + (threadIdx.x & ~31);
   SoftTile T;
   const bool any = soft_load(g, entries, cap_entries, tile_count, tile_start, status, s_e, T);
   const ViewParams &v = g.views[T.img % g.n_views];
-  const PixRay r = pix_ray(v, T.px, T.py);
+  const SoftPix x = soft_pix(v, T.px, T.py);
+  const float inv_sigma = 1.0f / g.sigma;
+  const float uu_max = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(x.r.uu)));
+  const float col0 = (float)T.px0 + 0.5f, row0 = (float)(T.py0 + 2 * (int)(threadIdx.x >> 5)) + 0.5f;
   float A = 0.0f, D = 0.0f, N0 = 0.0f, N1 = 0.0f, N2 = 0.0f, Tr = 1.0f;
   bool done = !T.inside;
   if (any) {
-    for (int c0 = 0; c0 < T.m; c0 += kSoftNT) {
-      if (__syncthreads_and(done)) break;
-      const int j = c0 + threadIdx.x;
-      if (j < T.m) s_r[threadIdx.x] = recs[rec_of[(long long)T.img * g.n_atoms + (uint32_t)s_e[j]]];
-      __syncthreads();
-      const int nj = min(kSoftNT, T.m - c0);
-      for (int q = 0; q < nj && !done; ++q) {
+    for (int c0 = 0; c0 < T.m; c0 += 32) {
+      const unsigned am = __ballot_sync(0xffffffffu, !done);
+      if (am == 0u) break;
+      const unsigned keep = soft_stage(g, recs, rec_of, s_e, T, c0, v.f, s_w, am, col0, row0, uu_max);
+      __syncwarp();
+      for (unsigned b = keep; b != 0u; b &= b - 1u) {
+        if (done) continue;
         SoftTerm o;
-        if (!soft_term(s_r[q], r, v.f, g.sigma, o)) continue;
-        float w = o.alpha * Tr;
+        if (!soft_term(s_w[__ffs(b) - 1], x, inv_sigma, o)) continue;
+        const float w = o.alpha * Tr;
         A += w;
-        D += w * o.t;
-        N0 += w * o.n.x;
-        N1 += w * o.n.y;
-        N2 -= w * o.n.z;
+        D = fmaf(w, o.t, D);
+        N0 = fmaf(w, o.n.x, N0);
+        N1 = fmaf(w, o.n.y, N1);
+        N2 = fmaf(-w, o.n.z, N2);
         Tr *= 1.0f - o.alpha;
         if (Tr < kTStop) done = true;
       }
-      __syncthreads();
+      __syncwarp();
     }
   }
   if (T.inside) {
@@ -164,6 +256,23 @@ __global__ __launch_bounds__(kSoftNT) void k_soft_fwd(Geometry g, const PrimRec 
   }
 }
 
+// Sum of four per-lane values over the warp, scattered: lanes 0, 8, 16 and 24
+// receive the sums of a0, a1, a2 and a3 (six shuffles instead of twenty).
+__device__ __forceinline__ float warp_sum4_scatter(float a0, float a1, float a2, float a3, int lane) {
+  const bool hi16 = (lane & 16) != 0;
+  float k0 = hi16 ? a2 : a0, k1 = hi16 ? a3 : a1;
+  const float s0 = hi16 ? a0 : a2, s1 = hi16 ? a1 : a3;
+  k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
+  k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+  const bool hi8 = (lane & 8) != 0;
+  float k = hi8 ? k1 : k0;
+  k += __shfl_xor_sync(0xffffffffu, hi8 ? k0 : k1, 8);
+  k += __shfl_xor_sync(0xffffffffu, k, 4);
+  k += __shfl_xor_sync(0xffffffffu, k, 2);
+  k += __shfl_xor_sync(0xffffffffu, k, 1);
+  return k;
+}
+
 __global__ __launch_bounds__(kSoftNT) void k_soft_bwd(Geometry g, const PrimRec *__restrict__ recs,
                                                       const uint32_t *__restrict__ rec_of,
                                                       const unsigned long long *__restrict__ entries,
@@ -174,12 +283,13 @@ __global__ __launch_bounds__(kSoftNT) void k_soft_bwd(Geometry g, const PrimRec 
                                                       float *grad) {
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned long long *s_e = reinterpret_cast<unsigned long long *>(smem);
-  PrimRec *s_r = reinterpret_cast<PrimRec *>(smem + kSoftCap * sizeof(unsigned long long));
-  __shared__ int s_maxlast;
+  SoftPrim *s_w = reinterpret_cast<SoftPrim *>(smem + kSoftCap * sizeof(unsigned long long)) + (threadIdx.x & ~31);
   SoftTile T;
   if (!soft_load(g, entries, cap_entries, tile_count, tile_start, status, s_e, T)) return;
   const ViewParams &v = g.views[T.img % g.n_views];
-  const PixRay r = pix_ray(v, T.px, T.py);
+  const SoftPix x = soft_pix(v, T.px, T.py);
+  const PixRay &r = x.r;
+  const float inv_sigma = 1.0f / g.sigma;
   const long long ppi = g.pix_per_img;
   const long long p = (long long)T.py * g.W + T.px;
   float gA = 0.0f, gD = 0.0f;
@@ -195,75 +305,77 @@ __global__ __launch_bounds__(kSoftNT) void k_soft_bwd(Geometry g, const PrimRec 
   }
   const bool need = T.inside && (gA != 0.0f || gD != 0.0f || gN.x != 0.0f || gN.y != 0.0f || gN.z != 0.0f);
   // pass 1: front to back, last contributor and final transmittance
+  const float uu_max = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(r.uu)));
+  const float col0 = (float)T.px0 + 0.5f, row0 = (float)(T.py0 + 2 * (int)(threadIdx.x >> 5)) + 0.5f;
   float Tr = 1.0f;
   int last = -1;
   bool done = !need;
-  if (threadIdx.x == 0) s_maxlast = -1;
-  for (int c0 = 0; c0 < T.m; c0 += kSoftNT) {
-    if (__syncthreads_and(done)) break;
-    const int j = c0 + threadIdx.x;
-    if (j < T.m) s_r[threadIdx.x] = recs[rec_of[(long long)T.img * g.n_atoms + (uint32_t)s_e[j]]];
-    __syncthreads();
-    const int nj = min(kSoftNT, T.m - c0);
-    for (int q = 0; q < nj && !done; ++q) {
+  for (int c0 = 0; c0 < T.m; c0 += 32) {
+    const unsigned am = __ballot_sync(0xffffffffu, !done);
+    if (am == 0u) break;
+    const unsigned keep = soft_stage(g, recs, rec_of, s_e, T, c0, v.f, s_w, am, col0, row0, uu_max);
+    __syncwarp();
+    for (unsigned b = keep; b != 0u; b &= b - 1u) {
+      if (done) continue;
+      const int q = __ffs(b) - 1;
       SoftTerm o;
-      if (!soft_term(s_r[q], r, v.f, g.sigma, o)) continue;
+      if (!soft_term(s_w[q], x, inv_sigma, o)) continue;
       Tr *= 1.0f - o.alpha;
       last = c0 + q;
       if (Tr < kTStop) done = true;
     }
-    __syncthreads();
+    __syncwarp();
   }
-  if (last >= 0) atomicMax(&s_maxlast, last);
-  __syncthreads();
-  const int maxlast = s_maxlast;
-  if (maxlast < 0) return;
-  // pass 2: back to front
+  const int wlast = __reduce_max_sync(0xffffffffu, last);
+  if (wlast < 0) return;
+  // pass 2: back to front; per-sphere sums leave the warp as one 16-byte atomic
   const int lane = threadIdx.x & 31;
-  const float f = v.f;
-  const float un = sqrtf(r.uu);
+  const float ugn0 = fmaf(r.a, gN.x, fmaf(r.b, gN.y, gN.z));
   float R = 0.0f, Tc = Tr;
-  for (int c0 = (maxlast / kSoftNT) * kSoftNT; c0 >= 0; c0 -= kSoftNT) {
-    __syncthreads();
-    const int j = c0 + threadIdx.x;
-    if (j < T.m) s_r[threadIdx.x] = recs[rec_of[(long long)T.img * g.n_atoms + (uint32_t)s_e[j]]];
-    __syncthreads();
-    const int nj = min(kSoftNT, T.m - c0);
-    for (int q = nj - 1; q >= 0; --q) {
-      const PrimRec &pr = s_r[q];
+  for (int c0 = (wlast / 32) * 32; c0 >= 0; c0 -= 32) {
+    const unsigned am = __ballot_sync(0xffffffffu, last >= c0);
+    if (am == 0u) continue;
+    __syncwarp();
+    unsigned keep = soft_stage(g, recs, rec_of, s_e, T, c0, v.f, s_w, am, col0, row0, uu_max);
+    if (wlast - c0 < 31) keep &= (2u << (wlast - c0)) - 1u;
+    __syncwarp();
+    while (keep != 0u) {
+      const int q = 31 - __clz(keep);
+      keep &= ~(1u << q);
+      const SoftPrim &pr = s_w[q];
       float gx = 0.0f, gy = 0.0f, gz = 0.0f, grr = 0.0f;
       SoftTerm o;
-      if (need && c0 + q <= last && soft_term(pr, r, f, g.sigma, o)) {
+      if (c0 + q <= last && soft_term(pr, x, inv_sigma, o)) {
         const float Ti = Tc / (1.0f - o.alpha);
         const float w = o.alpha * Ti;
         const float ci = gA + gD * o.t + gN.x * o.n.x + gN.y * o.n.y + gN.z * o.n.z;
         const float dalpha = Ti * (ci - R);
         R = o.alpha * ci + (1.0f - o.alpha) * R;
         Tc = Ti;
-        const float rad = pr.rad;
-        const float dadd = o.sg < kAMax ? o.sg * (1.0f - o.sg) / g.sigma : 0.0f;
+        const float dadd = o.sg < kAMax ? o.sg * (1.0f - o.sg) * inv_sigma : 0.0f;
         const float dd = dalpha * dadd;
-        const float fz = f / o.zc;
+        // closest-approach offset q = C - (o + s u), |q|^2 = rho^2
+        const float3 qv = make_float3(-fmaf(o.sst, r.a, o.ov.x), -fmaf(o.sst, r.b, o.ov.y), -(o.ov.z + o.sst));
+        const float ddf = dd * pr.fz;
+        const float isq = rsqrtf(o.rho2s);
         // delta(C, r)
-        gx = -dd * fz * o.q.x / o.sq;
-        gy = -dd * fz * o.q.y / o.sq;
-        gz = -dd * fz * o.q.z / o.sq - dd * o.delta / o.zc;
-        grr = dd * fz;
+        gx = -ddf * qv.x * isq;
+        gy = -ddf * qv.y * isq;
+        gz = -ddf * qv.z * isq - ddf * o.delta * v.inv_f;  // d delta / d zc = -delta / zc = -delta fz / f
+        grr = ddf;
         // t_i(C, r) and n_i = (t_i u - C) / r
-        float dg_drho2 = 0.0f, dg_dr = 0.0f;
+        float c2 = 0.0f, dg_dr = 0.0f;
         if (o.m > 0.0f) {
-          const float eta = 0.05f * rad;
-          dg_drho2 = -0.5f / o.sm;
-          dg_dr = (rad + 0.05f * eta) / o.sm - 0.05f;
+          c2 = -o.ism * x.inv_un;                       // 2 (dg / drho^2) / |u|
+          dg_dr = fmaf(0.05f, pr.eta, pr.rad) * o.ism - 0.05f;
         }
-        const float c2 = 2.0f * dg_drho2 / un;
-        const float dtx = r.a / r.uu - c2 * o.q.x;
-        const float dty = r.b / r.uu - c2 * o.q.y;
-        const float dtz = 1.0f / r.uu - c2 * o.q.z;
-        const float dtr = -dg_dr / un;
+        const float dtx = fmaf(r.a, x.inv_uu, -c2 * qv.x);
+        const float dty = fmaf(r.b, x.inv_uu, -c2 * qv.y);
+        const float dtz = x.inv_uu - c2 * qv.z;
+        const float dtr = -dg_dr * x.inv_un;
         const float ut = w * gD;
-        const float ugn = w * (r.a * gN.x + r.b * gN.y + gN.z);
-        const float inv = 1.0f / rad;
+        const float ugn = w * ugn0;
+        const float inv = pr.inv_rad;
         gx += ut * dtx + (dtx * ugn - w * gN.x) * inv;
         gy += ut * dty + (dty * ugn - w * gN.y) * inv;
         gz += ut * dtz + (dtz * ugn - w * gN.z) * inv;
@@ -271,19 +383,16 @@ __global__ __launch_bounds__(kSoftNT) void k_soft_bwd(Geometry g, const PrimRec 
       }
       const bool nz = gx != 0.0f || gy != 0.0f || gz != 0.0f || grr != 0.0f;
       if (__any_sync(0xffffffffu, nz)) {
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-          gx += __shfl_xor_sync(0xffffffffu, gx, off);
-          gy += __shfl_xor_sync(0xffffffffu, gy, off);
-          gz += __shfl_xor_sync(0xffffffffu, gz, off);
-          grr += __shfl_xor_sync(0xffffffffu, grr, off);
-        }
+        const float sum = warp_sum4_scatter(gx, gy, gz, grr, lane);
+        const float sy = __shfl_sync(0xffffffffu, sum, 8);
+        const float sz = __shfl_sync(0xffffffffu, sum, 16);
+        const float sr = __shfl_sync(0xffffffffu, sum, 24);
         if (lane == 0) {
-          float *dst = grad + 4LL * pr.id;
-          atomicAdd(dst + 0, v.R[0] * gx + v.U[0] * gy + v.F[0] * gz);
-          atomicAdd(dst + 1, v.R[1] * gx + v.U[1] * gy + v.F[1] * gz);
-          atomicAdd(dst + 2, v.R[2] * gx + v.U[2] * gy + v.F[2] * gz);
-          atomicAdd(dst + 3, grr);
+          const uint32_t id = (uint32_t)s_e[c0 + q];
+          const float4 wv = make_float4(v.R[0] * sum + v.U[0] * sy + v.F[0] * sz,
+                                        v.R[1] * sum + v.U[1] * sy + v.F[1] * sz,
+                                        v.R[2] * sum + v.U[2] * sy + v.F[2] * sz, sr);
+          atomicAdd(reinterpret_cast<float4 *>(grad) + id, wv);
         }
       }
     }
