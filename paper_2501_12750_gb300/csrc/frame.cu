@@ -18,9 +18,11 @@
 //   k_scan_*     exclusive scan of the per-tile counts (counting sort by tile);
 //   k_scatter    writes (min depth key << 32 | record) entries per tile;
 //   k_raster     one CTA per tile: depth-sorts its entries in shared memory
-//        (bitonic), stages records chunk by chunk, ray-casts every pixel,
-//        and stops once every pixel's hit is nearer than the next entry's
-//        nearest possible depth (__syncthreads_and);
+//        (bitonic); then each warp walks the sorted list on its own, staging
+//        32 records at a time, dropping those whose bounding sphere misses
+//        every ray of its still-searching pixels, ray-casting the rest, and
+//        stopping once every pixel's hit is nearer than the next entry's
+//        nearest possible depth;
 //   k_resolve_list / k_resolve_split  list the covered pixels, then shade
 //        them (id decoded, hit recomputed -> depth, normal, colour, SSAO
 //        from neighbouring depth keys, outline, fog) beside CTAs that write
@@ -930,6 +932,26 @@ __device__ __forceinline__ void bitonic_sort_u64(unsigned long long *s, int n2) 
 
 constexpr int kListCap = 2048;
 
+// A warp's 32-entry window is culled against the bounding rectangle
+// [x0, x1] x [y0, y1] of its still-searching pixels (integer pixel indices).
+// With the reference point at the bounding sphere's centre (dz = 0), the
+// offset at the reference depth is o = k (du, -dv, 0), and the centre's
+// distance to a pixel ray is >= |o| / |u| (Cauchy-Schwarz on the x, y part),
+// so no ray of the rectangle meets the bounding sphere (radius Rb) when the
+// pixel distance d from the projected centre exceeds Rb |u|_max / k.  The
+// radius is widened (0.1 % plus 0.01 px plus 2e-7 of the coordinates) so that
+// FP32 rounding never drops an entry the hit test would accept.
+__device__ __forceinline__ bool raster_keep(const PrimRec &p, unsigned x0, unsigned x1, unsigned y0, unsigned y1,
+                                            float uu_max) {
+  if (p.dz != 0.0f) return true;
+  const float rb = p.hl == 0.0f ? p.rad : sqrtf(fmaf(p.hl, p.hl, p.rad * p.rad));
+  const float cu = p.u0h + p.u0l, cv = p.v0h + p.v0l;
+  const float dx = fmaxf(fmaxf((float)x0 + 0.5f - cu, cu - ((float)x1 + 0.5f)), 0.0f);
+  const float dy = fmaxf(fmaxf((float)y0 + 0.5f - cv, cv - ((float)y1 + 0.5f)), 0.0f);
+  const float rt = __fdividef(rb * uu_max * rsqrtf(uu_max), p.k) * 1.001f + 0.01f + 2e-7f * (fabsf(cu) + fabsf(cv));
+  return !(dx * dx + dy * dy > rt * rt);
+}
+
 template <int TW, int TH>
 __global__ __launch_bounds__(TW *TH) void k_raster(Geometry g, const PrimRec *__restrict__ recs,
                                                    const unsigned long long *__restrict__ entries,
@@ -939,8 +961,11 @@ __global__ __launch_bounds__(TW *TH) void k_raster(Geometry g, const PrimRec *__
                                                    const ImageState *__restrict__ st, unsigned long long *keys,
                                                    const uint32_t *__restrict__ tile_list, Status *status) {
   constexpr int NT = TW * TH;
+  static_assert(NT % 32 == 0, "whole warps per tile");
   __shared__ unsigned long long s_e[kListCap];
   __shared__ PrimRec s_r[NT];
+  PrimRec *s_w = s_r + (threadIdx.x & ~31u);  // this warp's 32-entry window
+  const int lane = threadIdx.x & 31;
   const uint32_t n_list = status->n_list;
   for (uint32_t li = blockIdx.x; li < n_list; li += gridDim.x) {  // only the non-empty tiles
   const long long gt = tile_list[li];
@@ -957,6 +982,7 @@ __global__ __launch_bounds__(TW *TH) void k_raster(Geometry g, const PrimRec *__
   const int px = tx * TW + (threadIdx.x % TW), py = ty * TH + (threadIdx.x / TW);
   const bool inside = px < g.W && py < g.H;
   const PixRay r = pix_ray(v, px, py);
+  const float uu_max = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(r.uu)));
   unsigned long long *K = keys + (long long)img * g.pix_per_img + (long long)py * g.W + px;
   unsigned long long best = inside ? *K : kBgKey;
   if (threadIdx.x == 0) atomicMax(&status->max_list, cnt);
@@ -967,34 +993,49 @@ __global__ __launch_bounds__(TW *TH) void k_raster(Geometry g, const PrimRec *__
     for (int i = threadIdx.x; i < n2; i += NT) s_e[i] = i < m ? entries[start + seg + i] : ~0ull;
     __syncthreads();
     bitonic_sort_u64<NT>(s_e, n2);
-    for (int c0 = 0; c0 < m; c0 += NT) {
-      const uint32_t kmin = (uint32_t)(s_e[c0] >> 32);
-      const bool done = !inside || (uint32_t)(best >> 32) < kmin;
-      if (__syncthreads_and(done)) break;
-      const int j = c0 + threadIdx.x;
-      if (j < m) s_r[threadIdx.x] = recs[(uint32_t)s_e[j]];
-      __syncthreads();
-      const int nj = min(NT, m - c0);
-      if (!done) {
-        for (int q = 0; q < nj; ++q) {
-          const PrimRec &p = s_r[q];
-          float3 o = local_o(p.u0h, p.u0l, p.v0h, p.v0l, p.k, p.dz, r);
-          float s;
-          bool hit;
-          if (p.hl == 0.0f) {
-            hit = sphere_local(o, r, p.rad, s);
-          } else {
-            int kind;
-            float axial;
-            hit = cylinder_local(o, r, make_float3(p.ax, p.ay, p.az), p.hl, p.rad, s, kind, axial);
-          }
-          if (hit && p.zr + s >= v.znear) {
-            unsigned long long key = pack_key(rec_key(p), s, S, p.id);
-            best = key < best ? key : best;
-          }
+    // each warp walks the sorted segment on its own, 32 entries at a time; a
+    // pixel is finished once its hit is nearer than the next entry's nearest
+    // possible depth
+    bool done = !inside;
+    for (int c0 = 0; c0 < m; c0 += 32) {
+      if (!done && (uint32_t)(best >> 32) < (uint32_t)(s_e[c0] >> 32)) done = true;
+      if (__all_sync(0xffffffffu, done)) break;
+      const unsigned x0 = __reduce_min_sync(0xffffffffu, done ? 0xffffffffu : (unsigned)px);
+      const unsigned x1 = __reduce_max_sync(0xffffffffu, done ? 0u : (unsigned)px);
+      const unsigned y0 = __reduce_min_sync(0xffffffffu, done ? 0xffffffffu : (unsigned)py);
+      const unsigned y1 = __reduce_max_sync(0xffffffffu, done ? 0u : (unsigned)py);
+      bool keep = false;
+      if (c0 + lane < m) {
+        const PrimRec p = recs[(uint32_t)s_e[c0 + lane]];
+        s_w[lane] = p;
+        keep = raster_keep(p, x0, x1, y0, y1, uu_max);
+      }
+      const unsigned kept = __ballot_sync(0xffffffffu, keep);
+      __syncwarp();
+      for (unsigned b = kept; b != 0u; b &= b - 1u) {
+        const int q = __ffs(b) - 1;
+        if (done) continue;
+        if ((uint32_t)(best >> 32) < (uint32_t)(s_e[c0 + q] >> 32)) {
+          done = true;
+          continue;
+        }
+        const PrimRec &p = s_w[q];
+        float3 o = local_o(p.u0h, p.u0l, p.v0h, p.v0l, p.k, p.dz, r);
+        float s;
+        bool hit;
+        if (p.hl == 0.0f) {
+          hit = sphere_local(o, r, p.rad, s);
+        } else {
+          int kind;
+          float axial;
+          hit = cylinder_local(o, r, make_float3(p.ax, p.ay, p.az), p.hl, p.rad, s, kind, axial);
+        }
+        if (hit && p.zr + s >= v.znear) {
+          unsigned long long key = pack_key(rec_key(p), s, S, p.id);
+          best = key < best ? key : best;
         }
       }
-      __syncthreads();
+      __syncwarp();
     }
     __syncthreads();
   }
