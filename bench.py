@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--clusters", type=int, default=20000, help="blobs of 5,000 atoms (20,000 = 1e8 atoms)")
     ap.add_argument("--ses-only", action="store_true",
                     help="only the SES of the 1e5-atom system (one JSON line; for profiling its kernels)")
+    ap.add_argument("--protein-only", action="store_true",
+                    help="only the 1e5-atom protein frame at 1920x1080 (one JSON line; for profiling its kernels)")
     ap.add_argument("--soft-only", action="store_true",
                     help="only the soft-edge forward and backward (one JSON line; for profiling their kernels)")
     return ap.parse_args()
@@ -196,6 +198,11 @@ def main():
         if rank == 0:
             print(json.dumps({"metric": "ses_ms", "unit": "ms", "higher_is_better": False, "data": "synthetic",
                               **ses_extra(vtx, torch, dev)}))
+        return 0
+    if args.protein_only:
+        if rank == 0:
+            print(json.dumps({"metric": "protein_frame_ms", "unit": "ms", "higher_is_better": False,
+                              "data": "synthetic", **protein_extra(vtx, torch, dev)}))
         return 0
     if args.soft_only:
         if rank == 0:
@@ -377,6 +384,33 @@ def _frame_ms(vtx, torch, r, settings, out, reps=10):
     return e0.elapsed_time(e1) / reps
 
 
+def protein_extra(vtx, torch, dev, reps=20):
+    """The 1e5-atom protein-like system at 1920x1080 with SSAO16: library-default tiles (with per-stage device
+    times) and autotuned tiles."""
+    from paper_2501_12750_gb300 import scenes
+    s2 = scenes.config2()
+    k = scenes.ssao_kernel()
+    r = vtx.Renderer(dev.index)
+    r.upload_atoms(torch.from_numpy(s2.xyzr).to(dev), torch.from_numpy(s2.elem).to(dev), s2.palette)
+    cam = s2.cameras[0]
+    r.set_camera(cam)
+    out = r.alloc_outputs(cam.width, cam.height)
+    r.render_frame(vtx.default_settings(ssao_kernel=k, flags=vtx.FLAG_SYNC), out=out)
+    default_ms = _frame_ms(vtx, torch, r, vtx.default_settings(ssao_kernel=k), out, reps)
+    for _ in range(reps):
+        r.render_frame(vtx.default_settings(ssao_kernel=k, flags=vtx.FLAG_PROFILE), out=out)
+    stages = r.stage_times()
+    r.render_frame(vtx.default_settings(ssao_kernel=k, tile_w=0, flags=vtx.FLAG_SYNC), out=out)
+    tuned = r.tuned_settings()
+    tuned_ms = _frame_ms(vtx, torch, r, vtx.default_settings(ssao_kernel=k, tile_w=0), out, reps)
+    r.close()
+    return {"protein_1080p": {"workload": "1e5 protein-like atoms, 1920x1080, vdW, SSAO16",
+                              "default_tiles_ms": default_ms, "frames_per_s": 1e3 / default_ms,
+                              "stages_ms": {kk: v for kk, v in stages.items() if kk != "runs"},
+                              "autotuned_ms": tuned_ms, "autotuned": {"tile_w": tuned[0], "tile_h": tuned[1],
+                                                                      "splat_max_px": tuned[2]}}}
+
+
 def ses_extra(vtx, torch, dev, reps=5):
     """SES of the 1e5-atom protein-like system on a 0.5 A grid (probe 1.4 A): wall time of the synchronous call."""
     import ctypes
@@ -547,6 +581,7 @@ def run_extras(vtx, torch, dev, r, s3, cam, k):
     del out, frames
     torch.cuda.empty_cache()
     res["soft"] = soft_extra(vtx, torch, dev, r)["soft"]
+    res["protein_1080p"] = protein_extra(vtx, torch, dev)["protein_1080p"]
     return res
 
 

@@ -744,11 +744,14 @@ __global__ __launch_bounds__(1024) void k_scan_blocks(const uint32_t *__restrict
 constexpr int kScanRounds = 32;                                 // values per lane in the one-CTA scan
 constexpr long long kScanSingleMax = 32LL * 32 * kScanRounds;   // 32 warps x 32 lanes x rounds
 
-// Exclusive scan of every tile count in one CTA (up to kScanSingleMax tiles),
-// listing the non-empty tiles for the raster stage on the way.  Warp w owns
-// the contiguous segment [w S, (w+1) S), S = 32 * kScanRounds; each lane loads
-// its kScanRounds values up front (coalesced rows of 32), warps scan their
-// rows with shuffles, and one pass over the 32 warp totals links the segments.
+// Exclusive scan of every tile count in one CTA (up to 1024 R tiles), listing
+// the non-empty tiles for the raster stage on the way.  Warp w owns the
+// contiguous segment [w S, (w+1) S), S = 32 R; each lane loads its R values
+// up front (coalesced rows of 32), warps scan their rows with shuffles, and
+// one pass over the 32 warp totals links the segments.  The launch picks the
+// smallest R in {8, 16, 32} that covers the tiles: a 1080p frame's 8,160
+// tiles take 8 rounds instead of the 32 a 4K frame needs.
+template <int R>
 __global__ __launch_bounds__(1024) void k_scan_single(const uint32_t *__restrict__ cnt, long long n,
                                                       uint32_t *__restrict__ start, uint32_t *__restrict__ cursor,
                                                       uint32_t *__restrict__ list, Status *status,
@@ -760,17 +763,17 @@ __global__ __launch_bounds__(1024) void k_scan_single(const uint32_t *__restrict
   __shared__ unsigned long long s_wsum[32];
   __shared__ unsigned int s_n;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const long long seg = (long long)wid * 32 * kScanRounds;
+  const long long seg = (long long)wid * 32 * R;
   if (threadIdx.x == 0) s_n = 0u;
-  uint32_t v[kScanRounds];
+  uint32_t v[R];
   unsigned long long wsum = 0;
 #pragma unroll
-  for (int r = 0; r < kScanRounds; ++r) {
+  for (int r = 0; r < R; ++r) {
     const long long i = seg + r * 32 + lane;
     v[r] = i < n ? cnt[i] : 0u;
   }
 #pragma unroll
-  for (int r = 0; r < kScanRounds; ++r) wsum += v[r];
+  for (int r = 0; r < R; ++r) wsum += v[r];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
   if (lane == 0) s_wsum[wid] = wsum;
@@ -792,7 +795,7 @@ __global__ __launch_bounds__(1024) void k_scan_single(const uint32_t *__restrict
   __syncthreads();
   unsigned long long carry = s_wsum[wid];
 #pragma unroll
-  for (int r = 0; r < kScanRounds; ++r) {
+  for (int r = 0; r < R; ++r) {
     unsigned long long x = v[r];
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -876,6 +879,12 @@ __global__ __launch_bounds__(1024) void k_scan_add(uint32_t *__restrict__ start,
 
 // -------------------------------------------------------------- scatter --
 
+// Each lane takes one record; a warp walks its records' tiles in lockstep,
+// four tile slots at a time.  Lanes that target the same tile in the same
+// slot (neighbouring records share tiles) are merged with __match_any_sync:
+// their leader reserves all their places with one atomicAdd, so the four
+// slots' atomics are in flight together and the per-tile cursors see one
+// atomic per warp instead of one per record.
 template <bool SOFT>
 __global__ __launch_bounds__(256) void k_scatter(Geometry g, const PrimRec *__restrict__ recs,
                                                  const uint32_t *__restrict__ rec_img,
@@ -884,27 +893,53 @@ __global__ __launch_bounds__(256) void k_scatter(Geometry g, const PrimRec *__re
                                                  uint32_t cap_rec, uint32_t *tile_cursor,
                                                  unsigned long long *entries, unsigned long long cap_entries) {
   const uint32_t n = min(status->n_rec, cap_rec);
-  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
-    const PrimRec &q = recs[r];
-    const int img = (int)rec_img[r];
-    const uint2 bx = rec_box[r];
-    unsigned long long key;
-    if (SOFT) {
-      key = ((unsigned long long)q.key_lo << 32) | (unsigned long long)q.id;
-    } else {
-      const float S = st[img].S;
-      float Rb = q.hl == 0.0f ? q.rad : sqrtf(q.hl * q.hl + q.rad * q.rad);
-      long long kmin = rec_key(q) - (long long)ceilf((Rb + fabsf(q.dz)) * S * 1.000001f) - 2;
-      kmin = kmin < 0 ? 0 : (kmin > kKeySpan ? kKeySpan : kmin);
-      key = ((unsigned long long)kmin << 32) | (unsigned long long)r;
-    }
-    int tx0 = bx.x & 0xffff, ty0 = bx.x >> 16, tx1 = bx.y & 0xffff, ty1 = bx.y >> 16;
-    uint32_t *cur = tile_cursor + (long long)img * g.tiles_per_img;
-    for (int ty = ty0; ty <= ty1; ++ty)
-      for (int tx = tx0; tx <= tx1; ++tx) {
-        unsigned pos = atomicAdd(cur + ty * g.tiles_x + tx, 1u);
-        if (pos < cap_entries) entries[pos] = key;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n; base += stride) {
+    const uint32_t r = base + (uint32_t)lane;
+    unsigned long long key = 0ull;
+    long long tile0 = 0;
+    int nx = 1, nt = 0;
+    if (r < n) {
+      const PrimRec &q = recs[r];
+      const int img = (int)rec_img[r];
+      const uint2 bx = rec_box[r];
+      if (SOFT) {
+        key = ((unsigned long long)q.key_lo << 32) | (unsigned long long)q.id;
+      } else {
+        const float S = st[img].S;
+        float Rb = q.hl == 0.0f ? q.rad : sqrtf(q.hl * q.hl + q.rad * q.rad);
+        long long kmin = rec_key(q) - (long long)ceilf((Rb + fabsf(q.dz)) * S * 1.000001f) - 2;
+        kmin = kmin < 0 ? 0 : (kmin > kKeySpan ? kKeySpan : kmin);
+        key = ((unsigned long long)kmin << 32) | (unsigned long long)r;
       }
+      const int tx0 = bx.x & 0xffff, ty0 = bx.x >> 16, tx1 = bx.y & 0xffff, ty1 = bx.y >> 16;
+      nx = tx1 - tx0 + 1;
+      nt = nx * (ty1 - ty0 + 1);
+      tile0 = (long long)img * g.tiles_per_img + (long long)ty0 * g.tiles_x + tx0;
+    }
+    const int maxnt = __reduce_max_sync(0xffffffffu, (unsigned)nt);
+    for (int k0 = 0; k0 < maxnt; k0 += 4) {
+      unsigned peers[4];
+      uint32_t got[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int k = k0 + u;
+        const long long tile = k < nt ? tile0 + (long long)(k / nx) * g.tiles_x + (k % nx) : -1LL;
+        peers[u] = __match_any_sync(0xffffffffu, (unsigned long long)tile);
+        got[u] = 0u;
+        if (k < nt && lane == __ffs(peers[u]) - 1) got[u] = atomicAdd(tile_cursor + tile, (unsigned)__popc(peers[u]));
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const uint32_t b0 = __shfl_sync(0xffffffffu, got[u], __ffs(peers[u]) - 1);
+        if (k0 + u < nt) {
+          const unsigned long long pos = (unsigned long long)b0 + (unsigned)__popc(peers[u] & lt);
+          if (pos < cap_entries) entries[pos] = key;
+        }
+      }
+    }
   }
 }
 
@@ -1434,8 +1469,16 @@ cudaError_t run_binning(const Geometry &g, const Scene &sc, const Scratch &s, cu
   ev_rec(evs, 2, st);
   {
     if (n_tiles <= kScanSingleMax) {
-      k_scan_single<<<1, 1024, 0, st>>>(s.tile_count, n_tiles, s.tile_start, s.tile_cursor, s.tile_list, s.status,
-                                        s.cap_entries, soft ? 0 : 1);
+      const int skip = soft ? 0 : 1;
+      if (n_tiles <= 1024LL * 8)
+        k_scan_single<8><<<1, 1024, 0, st>>>(s.tile_count, n_tiles, s.tile_start, s.tile_cursor, s.tile_list,
+                                             s.status, s.cap_entries, skip);
+      else if (n_tiles <= 1024LL * 16)
+        k_scan_single<16><<<1, 1024, 0, st>>>(s.tile_count, n_tiles, s.tile_start, s.tile_cursor, s.tile_list,
+                                              s.status, s.cap_entries, skip);
+      else
+        k_scan_single<kScanRounds><<<1, 1024, 0, st>>>(s.tile_count, n_tiles, s.tile_start, s.tile_cursor,
+                                                       s.tile_list, s.status, s.cap_entries, skip);
     } else {
       int nb = (int)((n_tiles + kScanItems - 1) / kScanItems);
       unsigned long long *bs = reinterpret_cast<unsigned long long *>(s.block_sums);
