@@ -17,12 +17,13 @@
 //        ones become 64-byte records counted per screen tile;
 //   k_scan_*     exclusive scan of the per-tile counts (counting sort by tile);
 //   k_scatter    writes (min depth key << 32 | record) entries per tile;
-//   k_raster     one CTA per tile: depth-sorts its entries in shared memory
-//        (bitonic); then each warp walks the sorted list on its own, staging
-//        32 records at a time, dropping those whose bounding sphere misses
-//        every ray of its still-searching pixels, ray-casting the rest, and
-//        stopping once every pixel's hit is nearer than the next entry's
-//        nearest possible depth;
+//   k_raster     one CTA per tile: orders its entries front to back by depth
+//        bucket in shared memory (one-pass counting sort); then each warp
+//        walks the ordered list on its own, staging 32 records at a time,
+//        dropping those whose bounding sphere misses every ray of its
+//        still-searching pixels, ray-casting the rest, and stopping once
+//        every pixel's hit is nearer than the next entry's nearest possible
+//        depth;
 //   k_resolve_list / k_resolve_split  list the covered pixels, then shade
 //        them (id decoded, hit recomputed -> depth, normal, colour, SSAO
 //        from neighbouring depth keys, outline, fog) beside CTAs that write
@@ -945,24 +946,91 @@ __global__ __launch_bounds__(256) void k_scatter(Geometry g, const PrimRec *__re
 
 // --------------------------------------------------------------- raster --
 
+// Front-to-back order of one list segment by depth bucket (a one-pass
+// counting sort in shared memory, replacing a full sort of the 64-bit
+// entries).  The segment's nearest-depth keys [lo, hi] are cut into
+// kRasterBuckets buckets by a monotone FP32 map, so every key of a bucket is
+// <= every key of a later bucket.  Each entry is written to s_e as
+// (smallest key of its bucket << 32 | record): that bound is non-decreasing
+// along s_e and no later entry can be nearer than it, which is all the walk's
+// early termination needs.  Order within a bucket follows shared-memory
+// atomics; the visibility result (a minimum over all hits) does not depend
+// on it.  src is the segment in global memory, read three times (L1 hits
+// after the first).
+constexpr int kRasterBuckets = 256;
+
 template <int NT>
-__device__ __forceinline__ void bitonic_sort_u64(unsigned long long *s, int n2) {
-  for (int k = 2; k <= n2; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = threadIdx.x; i < n2; i += NT) {
-        int ixj = i ^ j;
-        if (ixj > i) {
-          unsigned long long a = s[i], b = s[ixj];
-          bool up = (i & k) == 0;
-          if ((a > b) == up) {
-            s[i] = b;
-            s[ixj] = a;
-          }
-        }
-      }
-      __syncthreads();
-    }
+__device__ __forceinline__ void bucket_order(const unsigned long long *__restrict__ src, int m,
+                                             unsigned long long *s_e, uint16_t *s_off, uint32_t *s_cnt,
+                                             uint32_t *s_lo, uint32_t *s_red) {
+  constexpr int NB = kRasterBuckets;
+  static_assert(NB % NT == 0 && NT <= NB, "buckets per thread");
+  constexpr int PER = NB / NT;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t lo = 0xffffffffu, hi = 0u;
+  for (int i = threadIdx.x; i < m; i += NT) {
+    const uint32_t k = (uint32_t)(src[i] >> 32);
+    lo = min(lo, k);
+    hi = max(hi, k);
   }
+  lo = __reduce_min_sync(0xffffffffu, lo);
+  hi = __reduce_max_sync(0xffffffffu, hi);
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    s_cnt[threadIdx.x * PER + j] = 0u;
+    s_lo[threadIdx.x * PER + j] = 0xffffffffu;
+  }
+  if (threadIdx.x == 0) {
+    s_red[0] = 0xffffffffu;
+    s_red[1] = 0u;
+  }
+  __syncthreads();
+  if (lane == 0) {
+    atomicMin(s_red, lo);
+    atomicMax(s_red + 1, hi);
+  }
+  __syncthreads();
+  lo = s_red[0];
+  hi = s_red[1];
+  const float scale = (float)NB / ((float)(hi - lo) + 1.0f);
+  for (int i = threadIdx.x; i < m; i += NT) {
+    const uint32_t k = (uint32_t)(src[i] >> 32);
+    const int b = min(NB - 1, (int)((float)(k - lo) * scale));
+    s_off[i] = (uint16_t)atomicAdd(s_cnt + b, 1u);
+    atomicMin(s_lo + b, k);
+  }
+  __syncthreads();
+  // exclusive scan of the bucket counts: PER consecutive buckets per thread
+  __shared__ uint32_t s_wt[NT / 32];
+  uint32_t c[PER], sum = 0u;
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    c[j] = s_cnt[threadIdx.x * PER + j];
+    sum += c[j];
+  }
+  uint32_t inc = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) s_wt[wid] = inc;
+  __syncthreads();
+  uint32_t base = inc - sum;
+  for (int w = 0; w < wid; ++w) base += s_wt[w];
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    s_cnt[threadIdx.x * PER + j] = base;
+    base += c[j];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < m; i += NT) {
+    const unsigned long long e = src[i];
+    const uint32_t k = (uint32_t)(e >> 32);
+    const int b = min(NB - 1, (int)((float)(k - lo) * scale));
+    s_e[s_cnt[b] + s_off[i]] = ((unsigned long long)s_lo[b] << 32) | (e & 0xffffffffull);
+  }
+  __syncthreads();
 }
 
 constexpr int kListCap = 2048;
@@ -979,7 +1047,8 @@ constexpr int kListCap = 2048;
 __device__ __forceinline__ bool raster_keep(const PrimRec &p, unsigned x0, unsigned x1, unsigned y0, unsigned y1,
                                             float uu_max) {
   if (p.dz != 0.0f) return true;
-  const float rb = p.hl == 0.0f ? p.rad : sqrtf(fmaf(p.hl, p.hl, p.rad * p.rad));
+  const float rb2 = fmaf(p.hl, p.hl, p.rad * p.rad);
+  const float rb = p.hl == 0.0f ? p.rad : rb2 * rsqrtf(rb2);
   const float cu = p.u0h + p.u0l, cv = p.v0h + p.v0l;
   const float dx = fmaxf(fmaxf((float)x0 + 0.5f - cu, cu - ((float)x1 + 0.5f)), 0.0f);
   const float dy = fmaxf(fmaxf((float)y0 + 0.5f - cv, cv - ((float)y1 + 0.5f)), 0.0f);
@@ -998,7 +1067,11 @@ __global__ __launch_bounds__(TW *TH) void k_raster(Geometry g, const PrimRec *__
   constexpr int NT = TW * TH;
   static_assert(NT % 32 == 0, "whole warps per tile");
   __shared__ unsigned long long s_e[kListCap];
-  __shared__ PrimRec s_r[NT];
+  // the warps' record windows, which also hold the bucket offsets while a segment is ordered
+  constexpr int kRawBytes = NT * (int)sizeof(PrimRec) > kListCap * 2 ? NT * (int)sizeof(PrimRec) : kListCap * 2;
+  __shared__ __align__(16) unsigned char s_raw[kRawBytes];
+  __shared__ uint32_t s_cnt[kRasterBuckets], s_lo[kRasterBuckets], s_red[2];
+  PrimRec *s_r = reinterpret_cast<PrimRec *>(s_raw);
   PrimRec *s_w = s_r + (threadIdx.x & ~31u);  // this warp's 32-entry window
   const int lane = threadIdx.x & 31;
   const uint32_t n_list = status->n_list;
@@ -1023,11 +1096,7 @@ __global__ __launch_bounds__(TW *TH) void k_raster(Geometry g, const PrimRec *__
   if (threadIdx.x == 0) atomicMax(&status->max_list, cnt);
   for (uint32_t seg = 0; seg < cnt; seg += kListCap) {
     const int m = (int)min((uint32_t)kListCap, cnt - seg);
-    int n2 = 1;
-    while (n2 < m) n2 <<= 1;
-    for (int i = threadIdx.x; i < n2; i += NT) s_e[i] = i < m ? entries[start + seg + i] : ~0ull;
-    __syncthreads();
-    bitonic_sort_u64<NT>(s_e, n2);
+    bucket_order<NT>(entries + start + seg, m, s_e, reinterpret_cast<uint16_t *>(s_raw), s_cnt, s_lo, s_red);
     // each warp walks the sorted segment on its own, 32 entries at a time; a
     // pixel is finished once its hit is nearer than the next entry's nearest
     // possible depth
