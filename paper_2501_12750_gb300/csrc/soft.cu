@@ -12,7 +12,8 @@
 //   coverage = sum w_i, depth = sum w_i t_i, normal = sum w_i n_i.
 // Binning (cull with 4 px dilation, precise setup, per-tile counting sort)
 // is shared with the hard-edge path; each tile CTA sorts its list by
-// (centre depth key, id) in shared memory, then each warp walks the sorted
+// (centre depth key, id) in shared memory (bucket pass plus per-bucket
+// insertion sort), then each warp walks the sorted
 // list on its own, staging 32 entries at a time with their per-sphere
 // constants (f / z_c, 1 / r and a bound on rho^2 that rejects most entries
 // before any square root or division).  The backward kernel rebuilds the
@@ -43,6 +44,7 @@ struct __align__(16) SoftPrim {
   float fz, inv_rad, eta, rej2;  // f / centre depth, 1 / rad, 0.05 rad, bound on rho^2 of a used sphere
 };
 static_assert(sizeof(SoftPrim) == 48, "SoftPrim is three 16-byte words");
+static_assert(kSoftNT * sizeof(SoftPrim) >= kSoftCap * sizeof(uint16_t), "the record windows hold the sort's offsets");
 
 constexpr size_t kSoftSmem = kSoftCap * sizeof(unsigned long long) + kSoftNT * sizeof(SoftPrim);
 
@@ -118,11 +120,109 @@ struct SoftTile {
   uint32_t start;
 };
 
-// Load and sort a tile's entries (shared by forward and backward).
+// Exact ascending order of a tile's m entries (centre-depth key << 32 | id)
+// in s_e.  A one-pass counting sort first places the entries into 256 buckets
+// of the tile's key range by a monotone FP32 map (every key of a bucket is <=
+// every key of a later bucket, and equal keys share a bucket); each thread
+// then insertion-sorts its own bucket.  A tile whose fullest bucket holds more
+// than 32 entries is finished by a bitonic sort instead.  src is the list in
+// global memory (read three times, L1 hits after the first); s_off (2 bytes
+// per entry) is scratch.
+__device__ __forceinline__ void soft_order(const unsigned long long *__restrict__ src, int m,
+                                           unsigned long long *s_e, uint16_t *s_off) {
+  constexpr int NB = kSoftNT;  // one bucket per thread
+  __shared__ uint32_t s_cnt[NB], s_red[3], s_wt[kSoftNT / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t lo = 0xffffffffu, hi = 0u;
+  for (int i = threadIdx.x; i < m; i += kSoftNT) {
+    const uint32_t k = (uint32_t)(src[i] >> 32);
+    lo = min(lo, k);
+    hi = max(hi, k);
+  }
+  lo = __reduce_min_sync(0xffffffffu, lo);
+  hi = __reduce_max_sync(0xffffffffu, hi);
+  s_cnt[threadIdx.x] = 0u;
+  if (threadIdx.x == 0) {
+    s_red[0] = 0xffffffffu;
+    s_red[1] = 0u;
+    s_red[2] = 0u;
+  }
+  __syncthreads();
+  if (lane == 0) {
+    atomicMin(s_red, lo);
+    atomicMax(s_red + 1, hi);
+  }
+  __syncthreads();
+  lo = s_red[0];
+  hi = s_red[1];
+  const float scale = (float)NB / ((float)(hi - lo) + 1.0f);
+  for (int i = threadIdx.x; i < m; i += kSoftNT) {
+    const uint32_t k = (uint32_t)(src[i] >> 32);
+    s_off[i] = (uint16_t)atomicAdd(s_cnt + min(NB - 1, (int)((float)(k - lo) * scale)), 1u);
+  }
+  __syncthreads();
+  const uint32_t c = s_cnt[threadIdx.x];
+  uint32_t inc = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  const uint32_t cmax = __reduce_max_sync(0xffffffffu, c);
+  if (lane == 31) s_wt[wid] = inc;
+  if (lane == 0) atomicMax(s_red + 2, cmax);
+  __syncthreads();
+  uint32_t base = inc - c;
+  for (int w = 0; w < wid; ++w) base += s_wt[w];
+  s_cnt[threadIdx.x] = base;
+  __syncthreads();
+  for (int i = threadIdx.x; i < m; i += kSoftNT) {
+    const unsigned long long e = src[i];
+    const uint32_t k = (uint32_t)(e >> 32);
+    s_e[s_cnt[min(NB - 1, (int)((float)(k - lo) * scale))] + s_off[i]] = e;
+  }
+  const bool small = s_red[2] <= 32u;
+  __syncthreads();
+  if (small) {
+    for (int i = (int)base + 1; i < (int)(base + c); ++i) {
+      const unsigned long long x = s_e[i];
+      int j = i - 1;
+      while (j >= (int)base && s_e[j] > x) {
+        s_e[j + 1] = s_e[j];
+        --j;
+      }
+      s_e[j + 1] = x;
+    }
+    __syncthreads();
+    return;
+  }
+  int n2 = 1;
+  while (n2 < m) n2 <<= 1;
+  for (int i = m + threadIdx.x; i < n2; i += kSoftNT) s_e[i] = ~0ull;
+  __syncthreads();
+  for (int k = 2; k <= n2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < n2; i += kSoftNT) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const unsigned long long a = s_e[i], b2 = s_e[ixj];
+          const bool up = (i & k) == 0;
+          if ((a > b2) == up) {
+            s_e[i] = b2;
+            s_e[ixj] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Load and order a tile's entries (shared by forward and backward).
 __device__ __forceinline__ bool soft_load(const Geometry &g, const unsigned long long *entries,
                                           unsigned long long cap_entries, const uint32_t *tile_count,
                                           const uint32_t *tile_start, Status *status, unsigned long long *s_e,
-                                          SoftTile &T) {
+                                          uint16_t *s_off, SoftTile &T) {
   const long long gt = blockIdx.x;
   T.img = (int)(gt / g.tiles_per_img);
   const int t = (int)(gt % g.tiles_per_img);
@@ -143,26 +243,7 @@ __device__ __forceinline__ bool soft_load(const Geometry &g, const unsigned long
   if (threadIdx.x == 0) atomicMax(&status->max_list, cnt);
   T.m = (int)cnt;
   if (cnt == 0) return false;
-  int n2 = 1;
-  while (n2 < T.m) n2 <<= 1;
-  for (int i = threadIdx.x; i < n2; i += kSoftNT) s_e[i] = i < T.m ? entries[T.start + i] : ~0ull;
-  __syncthreads();
-  for (int k = 2; k <= n2; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = threadIdx.x; i < n2; i += kSoftNT) {
-        int ixj = i ^ j;
-        if (ixj > i) {
-          unsigned long long a = s_e[i], b = s_e[ixj];
-          bool up = (i & k) == 0;
-          if ((a > b) == up) {
-            s_e[i] = b;
-            s_e[ixj] = a;
-          }
-        }
-      }
-      __syncthreads();
-    }
-  }
+  soft_order(entries + T.start, T.m, s_e, s_off);
   return true;
 }
 
@@ -214,7 +295,8 @@ __global__ __launch_bounds__(kSoftNT) void k_soft_fwd(Geometry g, const PrimRec 
   unsigned long long *s_e = reinterpret_cast<unsigned long long *>(smem);
   SoftPrim *s_w = reinterpret_cast<SoftPrim *>(smem + kSoftCap * sizeof(unsigned long long)) + (threadIdx.x & ~31);
   SoftTile T;
-  const bool any = soft_load(g, entries, cap_entries, tile_count, tile_start, status, s_e, T);
+  const bool any = soft_load(g, entries, cap_entries, tile_count, tile_start, status, s_e,
+                             reinterpret_cast<uint16_t *>(s_w - (threadIdx.x & ~31)), T);
   const ViewParams &v = g.views[T.img % g.n_views];
   const SoftPix x = soft_pix(v, T.px, T.py);
   const float inv_sigma = 1.0f / g.sigma;
@@ -285,7 +367,9 @@ __global__ __launch_bounds__(kSoftNT) void k_soft_bwd(Geometry g, const PrimRec 
   unsigned long long *s_e = reinterpret_cast<unsigned long long *>(smem);
   SoftPrim *s_w = reinterpret_cast<SoftPrim *>(smem + kSoftCap * sizeof(unsigned long long)) + (threadIdx.x & ~31);
   SoftTile T;
-  if (!soft_load(g, entries, cap_entries, tile_count, tile_start, status, s_e, T)) return;
+  if (!soft_load(g, entries, cap_entries, tile_count, tile_start, status, s_e,
+                 reinterpret_cast<uint16_t *>(s_w - (threadIdx.x & ~31)), T))
+    return;
   const ViewParams &v = g.views[T.img % g.n_views];
   const SoftPix x = soft_pix(v, T.px, T.py);
   const PixRay &r = x.r;
