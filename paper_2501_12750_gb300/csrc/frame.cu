@@ -59,6 +59,7 @@ int sm_count() {
 // counts zeroed and (hard edges) every depth key set to the background key.
 __global__ __launch_bounds__(256) void k_clear(ImageState *st, int n_img, Status *status, uint32_t *tile_count,
                                                long long n_tiles, unsigned long long *keys, long long n_keys) {
+  pdl_enter();
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long stride = (long long)gridDim.x * blockDim.x;
   if (tid < n_img) {
@@ -116,6 +117,7 @@ template <bool ONE_VIEW>
 __global__ __launch_bounds__(kCullThreads, 5) void k_cull_atoms(Geometry g, const float4 *__restrict__ frames,
                                                                 const long long *__restrict__ counts, ImageState *st,
                                                                 uint32_t *__restrict__ surv, Status *status) {
+  pdl_enter();
   extern __shared__ __align__(128) unsigned char cull_smem[];
   float4 *s_atoms = reinterpret_cast<float4 *>(cull_smem);
   __shared__ ViewParams s_views[ONE_VIEW ? 1 : kMaxViews];
@@ -342,6 +344,7 @@ __global__ __launch_bounds__(kCullThreads, kCullCtasPerSm) void k_cull_direct(Ge
                                                                             ImageState *st,
                                                                             uint32_t *__restrict__ surv,
                                                                             float4 *__restrict__ stage) {
+  pdl_enter();
   static_assert(kCullPT % 2 == 0, "atoms are tested in pairs");
   const ViewParams &vp = g.views[0];
   const long long n = g.n_atoms;
@@ -416,6 +419,7 @@ long long cull_survivor_slack(long long n_atoms) { return cull_one_ctas(n_atoms)
 __global__ __launch_bounds__(kCullThreads) void k_cull_bonds(Geometry g, const float4 *__restrict__ X,
                                                              const uint2 *__restrict__ pairs, ImageState *st,
                                                              uint32_t *__restrict__ surv) {
+  pdl_enter();
   __shared__ uint32_t s_idx[kCullThreads];
   __shared__ int s_cnt;
   __shared__ unsigned int s_base;
@@ -572,6 +576,7 @@ __global__ __launch_bounds__(256, VTX_SETUP_MINB) void k_setup(Geometry g, const
                                                const uint32_t *__restrict__ surv, unsigned long long *keys,
                                                PrimRec *recs, uint32_t *rec_img, uint2 *rec_box, uint32_t *rec_of,
                                                uint32_t *tile_count, Status *status, uint32_t cap_rec) {
+  pdl_enter();
   const int img = blockIdx.y;
   const ImageState s = finalize_state(g, img, st[img]);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -723,6 +728,7 @@ __device__ __forceinline__ unsigned long long block_exclusive_scan_1024(unsigned
 // Per-block exclusive scan of 4,096 tile counts; block totals to block_sums.
 __global__ __launch_bounds__(1024) void k_scan_blocks(const uint32_t *__restrict__ cnt, long long n,
                                                       uint32_t *__restrict__ start, unsigned long long *block_sums) {
+  pdl_enter();
   __shared__ unsigned long long s_warp[32];
   const long long base = (long long)blockIdx.x * kScanItems + (long long)threadIdx.x * 4;
   uint32_t c[4];
@@ -757,6 +763,7 @@ __global__ __launch_bounds__(1024) void k_scan_single(const uint32_t *__restrict
                                                       uint32_t *__restrict__ start, uint32_t *__restrict__ cursor,
                                                       uint32_t *__restrict__ list, Status *status,
                                                       unsigned long long cap_entries, int skip_if_empty) {
+  pdl_enter();
   // hard edges: with no binned record every tile is empty; the raster reads
   // only the tile list (left empty by the set-up kernel) and the scatter has
   // nothing to place, so the scan has nothing to do
@@ -827,6 +834,7 @@ __global__ __launch_bounds__(1024) void k_scan_single(const uint32_t *__restrict
 // Scan of the block totals (one CTA, loops when there are more than 1,024 blocks).
 __global__ __launch_bounds__(1024) void k_scan_top(unsigned long long *block_sums, int nb, Status *status,
                                                    unsigned long long cap_entries) {
+  pdl_enter();
   __shared__ unsigned long long s_warp[32];
   unsigned long long carry = 0;
   for (int b0 = 0; b0 < nb; b0 += 1024) {
@@ -849,6 +857,7 @@ __global__ __launch_bounds__(1024) void k_scan_add(uint32_t *__restrict__ start,
                                                    long long n, const unsigned long long *__restrict__ block_sums,
                                                    unsigned long long cap_entries, const uint32_t *__restrict__ cnt,
                                                    uint32_t *__restrict__ list, Status *status) {
+  pdl_enter();
   const long long base = (long long)blockIdx.x * kScanItems + (long long)threadIdx.x * 4;
   const unsigned long long off = block_sums[blockIdx.x];
   const int lane = threadIdx.x & 31;
@@ -893,6 +902,7 @@ __global__ __launch_bounds__(256) void k_scatter(Geometry g, const PrimRec *__re
                                                  const ImageState *__restrict__ st, const Status *__restrict__ status,
                                                  uint32_t cap_rec, uint32_t *tile_cursor,
                                                  unsigned long long *entries, unsigned long long cap_entries) {
+  pdl_enter();
   const uint32_t n = min(status->n_rec, cap_rec);
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
@@ -1064,6 +1074,7 @@ __global__ __launch_bounds__(TW *TH) void k_raster(Geometry g, const PrimRec *__
                                                    const uint32_t *__restrict__ tile_start,
                                                    const ImageState *__restrict__ st, unsigned long long *keys,
                                                    const uint32_t *__restrict__ tile_list, Status *status) {
+  pdl_enter();
   constexpr int NT = TW * TH;
   static_assert(NT % 32 == 0, "whole warps per tile");
   __shared__ unsigned long long s_e[kListCap];
@@ -1327,6 +1338,7 @@ __global__ __launch_bounds__(256, VTX_RESOLVE_MINB) void k_resolve(Geometry g, S
                                                  const ImageState *__restrict__ st,
                                                  const unsigned long long *__restrict__ keys, Outputs out,
                                                  int do_ssao) {
+  pdl_enter();
   const int px = blockIdx.x * 32 + (threadIdx.x & 31);
   const int py0 = blockIdx.y * 32 + (threadIdx.x >> 5);
   const int img = blockIdx.z;
@@ -1363,6 +1375,7 @@ template <bool VEC>
 __global__ __launch_bounds__(256) void k_resolve_list(Geometry g, const unsigned long long *__restrict__ keys,
                                                       uint32_t *__restrict__ cov, uint32_t *__restrict__ mask,
                                                       Status *status) {
+  pdl_enter();
   const long long total = g.pix_per_img * g.n_img;
   const int lane = threadIdx.x & 31;
   constexpr int P = VEC ? 4 : 1;
@@ -1415,6 +1428,7 @@ __global__ __launch_bounds__(256, VTX_RESOLVE_MINB) void k_resolve_split(
     const uint2 *__restrict__ bonds, const ImageState *__restrict__ st, const unsigned long long *__restrict__ keys,
     Outputs out, int do_ssao, const uint32_t *__restrict__ cov, const uint32_t *__restrict__ mask,
     const Status *__restrict__ status, int n_shade) {
+  pdl_enter();
   const long long ppi = g.pix_per_img;
   if ((int)blockIdx.x < n_shade) {
     const unsigned n = status->n_cov;
@@ -1473,6 +1487,28 @@ static inline void ev_rec(StageEvents *e, int i, cudaStream_t st) {
   if (e && e->ev && i < e->n) cudaEventRecord(e->ev[i], st);
 }
 
+// Kernels of a frame are launched with programmatic stream serialisation:
+// a kernel may be scheduled while its predecessor drains, and every kernel
+// opens with pdl_enter(), which waits for the predecessor grid to complete
+// (and its writes to be visible) before any memory access, then lets its
+// successor start launching.  The stream order of all memory effects is
+// unchanged; the launch latency and prologue of each kernel overlap the
+// previous kernel's tail.
+template <typename... P, typename... A>
+static cudaError_t launch_pdl(void (*k)(P...), dim3 grid, int block, size_t smem, cudaStream_t st, A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, static_cast<P>(args)...);
+}
+
 // Shared binning front end: init, cull, finalize, setup (+splat), scan, scatter.
 cudaError_t run_binning(const Geometry &g, const Scene &sc, const Scratch &s, cudaStream_t st, StageEvents *evs,
                         bool soft) {
@@ -1484,7 +1520,7 @@ cudaError_t run_binning(const Geometry &g, const Scene &sc, const Scratch &s, cu
     want = want > g.n_img ? want : g.n_img;
     const long long blocks = (want + 255) / 256;
     const int gc = (int)(blocks < 16LL * sms ? (blocks > 0 ? blocks : 1) : 16LL * sms);
-    k_clear<<<gc, 256, 0, st>>>(s.state, g.n_img, s.status, s.tile_count, n_tiles, s.keys, n_keys);
+    launch_pdl(k_clear, gc, 256, 0, st, s.state, g.n_img, s.status, s.tile_count, n_tiles, s.keys, n_keys);
   }
   ev_rec(evs, 0, st);
   {
@@ -1505,22 +1541,22 @@ cudaError_t run_binning(const Geometry &g, const Scene &sc, const Scratch &s, cu
       const int b1 = (int)cull_one_ctas(g.n_atoms);
       const bool plain = g.mode == 0 && !g.clip_on;
       if (sc.stage && plain)
-        k_cull_direct<true, true><<<b1, kCullThreads, 0, st>>>(g, sc.frames, s.state, s.surv, sc.stage);
+        launch_pdl(k_cull_direct<true, true>, b1, kCullThreads, 0, st, g, sc.frames, s.state, s.surv, sc.stage);
       else if (sc.stage)
-        k_cull_direct<false, true><<<b1, kCullThreads, 0, st>>>(g, sc.frames, s.state, s.surv, sc.stage);
+        launch_pdl(k_cull_direct<false, true>, b1, kCullThreads, 0, st, g, sc.frames, s.state, s.surv, sc.stage);
       else if (plain)
-        k_cull_direct<true, false><<<b1, kCullThreads, 0, st>>>(g, sc.frames, s.state, s.surv, nullptr);
+        launch_pdl(k_cull_direct<true, false>, b1, kCullThreads, 0, st, g, sc.frames, s.state, s.surv, nullptr);
       else
-        k_cull_direct<false, false><<<b1, kCullThreads, 0, st>>>(g, sc.frames, s.state, s.surv, nullptr);
+        launch_pdl(k_cull_direct<false, false>, b1, kCullThreads, 0, st, g, sc.frames, s.state, s.surv, nullptr);
     } else if (g.n_views == 1) {
-      k_cull_atoms<true><<<grid, kCullThreads, kCullSmem, st>>>(g, sc.frames, sc.counts, s.state, s.surv, s.status);
+      launch_pdl(k_cull_atoms<true>, grid, kCullThreads, kCullSmem, st, g, sc.frames, sc.counts, s.state, s.surv, s.status);
     } else {
-      k_cull_atoms<false><<<grid, kCullThreads, kCullSmem, st>>>(g, sc.frames, sc.counts, s.state, s.surv, s.status);
+      launch_pdl(k_cull_atoms<false>, grid, kCullThreads, kCullSmem, st, g, sc.frames, sc.counts, s.state, s.surv, s.status);
     }
     if (g.n_bonds > 0 && sc.bonds) {  // n_bonds is zero unless the representation draws bonds
       long long bb = (g.n_bonds + kCullThreads - 1) / kCullThreads;
       int gb = (int)(bb < 8LL * sms ? bb : 8LL * sms);
-      k_cull_bonds<<<gb, kCullThreads, 0, st>>>(g, sc.frames, sc.bonds, s.state, s.surv);
+      launch_pdl(k_cull_bonds, gb, kCullThreads, 0, st, g, sc.frames, sc.bonds, s.state, s.surv);
     }
   }
   ev_rec(evs, 1, st);
@@ -1528,10 +1564,10 @@ cudaError_t run_binning(const Geometry &g, const Scene &sc, const Scratch &s, cu
     int bx = g.n_img >= 64 ? VTX_SETUP_BATCH_CTAS : (VTX_SETUP_GRID * sms + g.n_img - 1) / g.n_img;
     dim3 grid(bx, g.n_img);
     if (soft)
-      k_setup<true><<<grid, 256, 0, st>>>(g, sc.frames, sc.bonds, s.state, s.surv, s.keys, s.recs, s.rec_img,
+      launch_pdl(k_setup<true>, grid, 256, 0, st, g, sc.frames, sc.bonds, s.state, s.surv, s.keys, s.recs, s.rec_img,
                                           s.rec_box, s.rec_of, s.tile_count, s.status, s.cap_rec);
     else
-      k_setup<false><<<grid, 256, 0, st>>>(g, sc.stage ? sc.stage : sc.frames, sc.bonds, s.state, s.surv, s.keys,
+      launch_pdl(k_setup<false>, grid, 256, 0, st, g, sc.stage ? sc.stage : sc.frames, sc.bonds, s.state, s.surv, s.keys,
                                            s.recs, s.rec_img, s.rec_box, s.rec_of, s.tile_count, s.status,
                                            s.cap_rec);
   }
@@ -1540,29 +1576,29 @@ cudaError_t run_binning(const Geometry &g, const Scene &sc, const Scratch &s, cu
     if (n_tiles <= kScanSingleMax) {
       const int skip = soft ? 0 : 1;
       if (n_tiles <= 1024LL * 8)
-        k_scan_single<8><<<1, 1024, 0, st>>>(s.tile_count, n_tiles, s.tile_start, s.tile_cursor, s.tile_list,
+        launch_pdl(k_scan_single<8>, 1, 1024, 0, st, s.tile_count, n_tiles, s.tile_start, s.tile_cursor, s.tile_list,
                                              s.status, s.cap_entries, skip);
       else if (n_tiles <= 1024LL * 16)
-        k_scan_single<16><<<1, 1024, 0, st>>>(s.tile_count, n_tiles, s.tile_start, s.tile_cursor, s.tile_list,
+        launch_pdl(k_scan_single<16>, 1, 1024, 0, st, s.tile_count, n_tiles, s.tile_start, s.tile_cursor, s.tile_list,
                                               s.status, s.cap_entries, skip);
       else
-        k_scan_single<kScanRounds><<<1, 1024, 0, st>>>(s.tile_count, n_tiles, s.tile_start, s.tile_cursor,
+        launch_pdl(k_scan_single<kScanRounds>, 1, 1024, 0, st, s.tile_count, n_tiles, s.tile_start, s.tile_cursor,
                                                        s.tile_list, s.status, s.cap_entries, skip);
     } else {
       int nb = (int)((n_tiles + kScanItems - 1) / kScanItems);
       unsigned long long *bs = reinterpret_cast<unsigned long long *>(s.block_sums);
-      k_scan_blocks<<<nb, 1024, 0, st>>>(s.tile_count, n_tiles, s.tile_start, bs);
-      k_scan_top<<<1, 1024, 0, st>>>(bs, nb, s.status, s.cap_entries);
-      k_scan_add<<<nb, 1024, 0, st>>>(s.tile_start, s.tile_cursor, n_tiles, bs, s.cap_entries, s.tile_count,
+      launch_pdl(k_scan_blocks, nb, 1024, 0, st, s.tile_count, n_tiles, s.tile_start, bs);
+      launch_pdl(k_scan_top, 1, 1024, 0, st, bs, nb, s.status, s.cap_entries);
+      launch_pdl(k_scan_add, nb, 1024, 0, st, s.tile_start, s.tile_cursor, n_tiles, bs, s.cap_entries, s.tile_count,
                                       s.tile_list, s.status);
     }
   }
   ev_rec(evs, 3, st);
   if (soft)
-    k_scatter<true><<<4 * sms, 256, 0, st>>>(g, s.recs, s.rec_img, s.rec_box, s.state, s.status, s.cap_rec,
+    launch_pdl(k_scatter<true>, 4 * sms, 256, 0, st, g, s.recs, s.rec_img, s.rec_box, s.state, s.status, s.cap_rec,
                                              s.tile_cursor, s.entries, s.cap_entries);
   else
-    k_scatter<false><<<4 * sms, 256, 0, st>>>(g, s.recs, s.rec_img, s.rec_box, s.state, s.status, s.cap_rec,
+    launch_pdl(k_scatter<false>, 4 * sms, 256, 0, st, g, s.recs, s.rec_img, s.rec_box, s.state, s.status, s.cap_rec,
                                               s.tile_cursor, s.entries, s.cap_entries);
   ev_rec(evs, 4, st);
   return cudaGetLastError();
@@ -1577,13 +1613,13 @@ cudaError_t run_frame_pipeline(const Geometry &g, const ShadeParams &sh, const S
   const unsigned rgrid = (unsigned)(n_tiles < (long long)VTX_RASTER_GRID * sm_count() ? n_tiles
                                                                           : (long long)VTX_RASTER_GRID * sm_count());
   if (g.tile_w == 16 && g.tile_h == 16)
-    k_raster<16, 16><<<rgrid, 256, 0, st>>>(g, s.recs, s.entries, s.cap_entries, s.tile_count,
+    launch_pdl(k_raster<16, 16>, rgrid, 256, 0, st, g, s.recs, s.entries, s.cap_entries, s.tile_count,
                                                         s.tile_start, s.state, s.keys, s.tile_list, s.status);
   else if (g.tile_w == 32 && g.tile_h == 8)
-    k_raster<32, 8><<<rgrid, 256, 0, st>>>(g, s.recs, s.entries, s.cap_entries, s.tile_count,
+    launch_pdl(k_raster<32, 8>, rgrid, 256, 0, st, g, s.recs, s.entries, s.cap_entries, s.tile_count,
                                                        s.tile_start, s.state, s.keys, s.tile_list, s.status);
   else
-    k_raster<8, 8><<<rgrid, 64, 0, st>>>(g, s.recs, s.entries, s.cap_entries, s.tile_count,
+    launch_pdl(k_raster<8, 8>, rgrid, 64, 0, st, g, s.recs, s.entries, s.cap_entries, s.tile_count,
                                                      s.tile_start, s.state, s.keys, s.tile_list, s.status);
   ev_rec(evs, 5, st);
   if (VTX_RESOLVE_2PASS && s.cov_list) {
@@ -1598,19 +1634,19 @@ cudaError_t run_frame_pipeline(const Geometry &g, const ShadeParams &sh, const S
     const int n_shade = VTX_SHADE_PER_SM * sms;
     const int gb = (int)(want < 8LL * sms ? (want > 0 ? want : 1) : 8LL * sms);
     if (vec) {
-      k_resolve_list<true><<<gl, 256, 0, st>>>(g, s.keys, s.cov_list, s.cov_mask, s.status);
+      launch_pdl(k_resolve_list<true>, gl, 256, 0, st, g, s.keys, s.cov_list, s.cov_mask, s.status);
       ev_rec(evs, 6, st);
-      k_resolve_split<true><<<n_shade + gb, 256, 0, st>>>(g, sh, Xr, sc.elem, sc.bonds, s.state, s.keys, out,
+      launch_pdl(k_resolve_split<true>, n_shade + gb, 256, 0, st, g, sh, Xr, sc.elem, sc.bonds, s.state, s.keys, out,
                                                             ssao ? 1 : 0, s.cov_list, s.cov_mask, s.status, n_shade);
     } else {
-      k_resolve_list<false><<<gl, 256, 0, st>>>(g, s.keys, s.cov_list, s.cov_mask, s.status);
+      launch_pdl(k_resolve_list<false>, gl, 256, 0, st, g, s.keys, s.cov_list, s.cov_mask, s.status);
       ev_rec(evs, 6, st);
-      k_resolve_split<false><<<n_shade + gb, 256, 0, st>>>(g, sh, Xr, sc.elem, sc.bonds, s.state, s.keys, out,
+      launch_pdl(k_resolve_split<false>, n_shade + gb, 256, 0, st, g, sh, Xr, sc.elem, sc.bonds, s.state, s.keys, out,
                                                              ssao ? 1 : 0, s.cov_list, s.cov_mask, s.status, n_shade);
     }
   } else {
     dim3 grid((g.W + 31) / 32, (g.H + 31) / 32, g.n_img);
-    k_resolve<<<grid, 256, 0, st>>>(g, sh, Xr, sc.elem, sc.bonds, s.state, s.keys, out, ssao ? 1 : 0);
+    launch_pdl(k_resolve, grid, 256, 0, st, g, sh, Xr, sc.elem, sc.bonds, s.state, s.keys, out, ssao ? 1 : 0);
     ev_rec(evs, 6, st);
   }
   ev_rec(evs, 7, st);

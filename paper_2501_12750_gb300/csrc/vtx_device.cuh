@@ -540,6 +540,15 @@ __device__ __forceinline__ bool lean_box(const ViewParams &v, int W, int H, floa
 }
 
 // ------------------------------------------------- TMA bulk copy helpers --
+// Programmatic dependent launch (sm_90+ PTX): wait until the preceding grid
+// of the stream has completed and its memory writes are visible (a no-op for
+// a kernel launched without programmatic serialisation), then allow the next
+// grid to begin launching.  Called first thing in every frame kernel.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // 1-D bulk copies global -> shared completed on an mbarrier (sm_90+ PTX).
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
