@@ -255,6 +255,10 @@ def main():
     ms_total, fps = aggregate_replicas(elapsed_ms, args.steps, world, dev)
     ms_per_step = ms_total / args.steps
 
+    # the same frames without per-stage events: events recorded between the kernels serialise their
+    # programmatically dependent launches, so this is the frame rate a caller sees without FLAG_PROFILE
+    unprof_ms = _frame_ms(vtx, torch, r, vtx.default_settings(ssao_kernel=k), out, reps=args.steps)
+
     peak, peak_kind = measured_peaks()
     cull_ms = stages["cull"]
     alg_bytes = 16.0 * N
@@ -347,6 +351,10 @@ def main():
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": cull_ms},
         "stages_ms": {kk: v for kk, v in stages.items() if kk != "runs"},
+        "unprofiled": {"ms_per_step": unprof_ms, "frames_per_s": 1e3 / unprof_ms,
+                       "note": "same frames timed without the per-stage CUDA events (which serialise the "
+                               "kernels' programmatically dependent launches); value and roofline use the "
+                               "profiled frames"},
         "e2e": {"value": 1.0 / pipe_s, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "api": "vtx_upload_atoms(page-locked host atoms) + vtx_render_frame into page-locked host output "
                        "planes, two contexts on two streams taking alternate frames (%d frames)" % n_pipe},
