@@ -256,7 +256,8 @@ vtx_status vtx_render_soft_fwd(vtx_ctx *ctx, const float *xyzr, int64_t n, const
                                int32_t n_views, float sigma_px, float *cov, float *depth, float *normal);
 
 /*
- * Soft-edge renderer, backward: grad_xyzr (device float4 [n], OVERWRITTEN)
+ * Soft-edge renderer, backward: grad_xyzr (device float4 [n], 16-byte aligned, OVERWRITTEN;
+ * VTX_ERR_INVALID_ARG when NULL or unaligned, before any launch)
  * = d/d(x,y,z,r) of sum over views and pixels of
  *   g_cov*cov + g_depth*depth + g_normal . normal.
  * Tile lists are rebuilt (not stored by the forward call).  Gradient
