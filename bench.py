@@ -8,10 +8,18 @@ precise setup + direct splat, tile binning, tile ray-cast, resolve, shading,
 SSAO.  Inputs (1.6 GB of atom records) are larger than L2, so no flush is
 needed between steps.
 
+The timed frames record eight per-stage CUDA events (the cull's live
+duration feeds the roofline object); the same frames are timed once more
+without them ("unprofiled"), since those events serialise the kernels'
+programmatically dependent launches.
+
 Also measured in the same run (keys under "extra", skipped with --no-extra):
-the batched trajectory (500,000 atoms x 256 frames x 4 views at 1280x720,
-one graph launch) against the plain per-frame loop, and the soft-edge
-renderer's forward+backward time (20,000 atoms, 16 views at 512x512).
+the 8K frame and its RGBA8 export, the 1.07e6 / 1.10e7-atom size sweep, the
+SES of the 1e5-atom system, the batched trajectory (500,000 atoms x 256
+frames x 4 views at 1280x720, one graph launch) against the plain per-frame
+loop, the soft-edge renderer's forward+backward time (20,000 atoms, 16 views
+at 512x512), and the 1e5-atom protein frame at 1920x1080.  --ses-only,
+--soft-only and --protein-only print just one of these (for profiling).
 
 --impl reference times the CPU FP64 oracle (the only reference there is) on
 a bounded sample of the same frame on the host cores.
