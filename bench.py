@@ -8,10 +8,11 @@ precise setup + direct splat, tile binning, tile ray-cast, resolve, shading,
 SSAO.  Inputs (1.6 GB of atom records) are larger than L2, so no flush is
 needed between steps.
 
-The timed frames record eight per-stage CUDA events (the cull's live
-duration feeds the roofline object); the same frames are timed once more
-without them ("unprofiled"), since those events serialise the kernels'
-programmatically dependent launches.
+The timed frames record two CUDA events around the cull (its live duration
+feeds the roofline object); events between all stages would serialise the
+kernels' programmatically dependent launches, so the per-stage breakdown
+comes from the same frames re-run after the timed region, and the frames are
+timed once more with no event inside them ("unprofiled").
 
 Also measured in the same run (keys under "extra", skipped with --no-extra):
 the 8K frame and its RGBA8 export, the 1.07e6 / 1.10e7-atom size sweep, the
@@ -232,7 +233,7 @@ def main():
     r.set_camera(cam)
     out = r.alloc_outputs(W, H)
     warm = vtx.default_settings(ssao_kernel=k, flags=vtx.FLAG_SYNC)
-    timed = vtx.default_settings(ssao_kernel=k, flags=vtx.FLAG_PROFILE)
+    timed = vtx.default_settings(ssao_kernel=k, flags=vtx.FLAG_PROFILE_CULL)
     for _ in range(max(3, args.warmup)):
         r.render_frame(warm, out=out)
     r.sync_status()
@@ -258,17 +259,20 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     elapsed_ms = ev0.elapsed_time(ev1)
-    stages = r.stage_times()
+    cull_ms = r.stage_times()["cull"]  # live, from the two events around each timed frame's cull
     r.sync_status()  # raises on a capacity overflow inside the timed region
     ms_total, fps = aggregate_replicas(elapsed_ms, args.steps, world, dev)
     ms_per_step = ms_total / args.steps
 
-    # the same frames without per-stage events: events recorded between the kernels serialise their
-    # programmatically dependent launches, so this is the frame rate a caller sees without FLAG_PROFILE
+    # per-stage breakdown: the same frames again with all eight stage events (outside the timed region;
+    # events between every pair of kernels serialise their programmatically dependent launches)
+    for _ in range(args.steps):
+        r.render_frame(vtx.default_settings(ssao_kernel=k, flags=vtx.FLAG_PROFILE), out=out)
+    stages = r.stage_times()
+    # and with no event at all inside the frames
     unprof_ms = _frame_ms(vtx, torch, r, vtx.default_settings(ssao_kernel=k), out, reps=args.steps)
 
     peak, peak_kind = measured_peaks()
-    cull_ms = stages["cull"]
     alg_bytes = 16.0 * N
     achieved = alg_bytes / (cull_ms * 1e-3) / 1e9
     traffic = None
@@ -359,10 +363,11 @@ def main():
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": cull_ms},
         "stages_ms": {kk: v for kk, v in stages.items() if kk != "runs"},
+        "stages_note": "stages_ms: the same frames re-run after the timed region with an event after every "
+                       "stage; the timed frames record events around the cull only (its live duration feeds "
+                       "the roofline)",
         "unprofiled": {"ms_per_step": unprof_ms, "frames_per_s": 1e3 / unprof_ms,
-                       "note": "same frames timed without the per-stage CUDA events (which serialise the "
-                               "kernels' programmatically dependent launches); value and roofline use the "
-                               "profiled frames"},
+                       "note": "the same frames timed with no event inside them"},
         "e2e": {"value": 1.0 / pipe_s, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "api": "vtx_upload_atoms(page-locked host atoms) + vtx_render_frame into page-locked host output "
                        "planes, two contexts on two streams taking alternate frames (%d frames)" % n_pipe},

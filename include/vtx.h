@@ -94,7 +94,10 @@ enum {
 enum {
   VTX_FLAG_SYNC = 1u,     /* synchronise at the end of the call and report device-side errors */
   VTX_FLAG_PROFILE = 2u,  /* record per-stage CUDA events (read with vtx_stage_times) */
-  VTX_FLAG_NO_SSAO = 4u   /* skip ambient occlusion even if ssao_samples > 0 */
+  VTX_FLAG_NO_SSAO = 4u,  /* skip ambient occlusion even if ssao_samples > 0 */
+  VTX_FLAG_PROFILE_CULL = 8u /* record CUDA events around the cull stage only (vtx_stage_times reports its
+                                time, the other stages 0): two events per frame instead of nine, so the
+                                other kernels keep their overlapped launches */
 };
 
 /* Pinhole camera, 64 bytes.  forward/right/up: the view basis (float32 as passed). */
@@ -344,13 +347,16 @@ vtx_status vtx_sync_status(vtx_ctx *ctx);
 
 /*
  * Per-stage GPU times (ms), averaged over every pipeline run made with
- * VTX_FLAG_PROFILE since the previous call, measured with CUDA events
+ * VTX_FLAG_PROFILE or VTX_FLAG_PROFILE_CULL since the previous call, measured with CUDA events
  * recorded on the context's stream between the stages (clear, cull, setup,
  * scan, scatter, raster, resolve: background pixels and the covered-pixel
  * list, shade: the covered pixels' hit, shading, SSAO and post-processing;
- * with a single-pass resolve "shade" is 0).  names/ms: arrays of *n entries (in:
- * capacity; out: stages written); *runs (may be NULL) receives the number of
- * runs averaged.  Waits for the last profiled run, then forgets the runs.
+ * with a single-pass resolve "shade" is 0).  Runs made with
+ * VTX_FLAG_PROFILE_CULL (and not VTX_FLAG_PROFILE) contribute to the cull's
+ * average only; a stage no run measured reports 0.  names/ms: arrays of *n
+ * entries (in: capacity; out: stages written); *runs (may be NULL) receives
+ * the number of profiled runs.  Waits for the last profiled run, then
+ * forgets the runs.
  */
 vtx_status vtx_stage_times(vtx_ctx *ctx, const char **names, float *ms, int32_t *n, int32_t *runs);
 

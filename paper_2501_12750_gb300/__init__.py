@@ -29,6 +29,7 @@ SHADE_GLOSSY, SHADE_FLAT, SHADE_MATTE, SHADE_TOON = 0, 1, 2, 3
 FLAG_SYNC = 1
 FLAG_PROFILE = 2
 FLAG_NO_SSAO = 4
+FLAG_PROFILE_CULL = 8
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "CAPACITY", 5: "TIMEOUT", 6: "BOUNDS", 7: "STATE"}
 

@@ -58,6 +58,7 @@ struct vtx_ctx {
   cudaEvent_t counts_done = nullptr;
   // profiling: one set of 8 events per profiled pipeline run since the last read
   std::vector<cudaEvent_t *> ev_sets;
+  std::vector<unsigned> ev_masks;  // per used set: the stage events it recorded
   size_t ev_used = 0;
   // graphs
   std::vector<GraphEntry> graphs;
@@ -322,17 +323,25 @@ static vtx_status check_status(vtx_ctx *c) {
   return fail(c, VTX_ERR_CAPACITY, msg + " (arena grown; render again)");
 }
 
+// Events for one profiled render.  VTX_FLAG_PROFILE: a start event and one
+// after every stage.  VTX_FLAG_PROFILE_CULL: only the events after the clear
+// and after the cull (the cull's duration is their difference).
 static StageEvents *events_for(vtx_ctx *c, const vtx_settings *s, StageEvents &ev) {
-  if (!(s && (s->flags & VTX_FLAG_PROFILE))) return nullptr;
+  if (!(s && (s->flags & (VTX_FLAG_PROFILE | VTX_FLAG_PROFILE_CULL)))) return nullptr;
   if (c->ev_used == c->ev_sets.size()) {
     cudaEvent_t *set = new cudaEvent_t[kNumStages + 1];
     for (int i = 0; i <= kNumStages; ++i) cudaEventCreate(&set[i]);
     c->ev_sets.push_back(set);
+    c->ev_masks.push_back(0u);
   }
-  cudaEvent_t *set = c->ev_sets[c->ev_used++];
-  cudaEventRecord(set[kNumStages], c->stream);  // start
+  const size_t r = c->ev_used++;
+  cudaEvent_t *set = c->ev_sets[r];
+  const bool full = (s->flags & VTX_FLAG_PROFILE) != 0;
+  c->ev_masks[r] = full ? ~0u : 3u;
+  if (full) cudaEventRecord(set[kNumStages], c->stream);  // start
   ev.ev = set;
   ev.n = kNumStages;
+  ev.mask = c->ev_masks[r];
   return &ev;
 }
 
@@ -607,7 +616,7 @@ static vtx_status tune(vtx_ctx *c, const long long key[6], const vtx_settings *s
       cand.tile_w = kTuneShapes[i][0];
       cand.tile_h = kTuneShapes[i][1];
       cand.splat_max_px = kTuneSplat[j];
-      cand.flags &= ~(uint32_t)(VTX_FLAG_SYNC | VTX_FLAG_PROFILE);
+      cand.flags &= ~(uint32_t)(VTX_FLAG_SYNC | VTX_FLAG_PROFILE | VTX_FLAG_PROFILE_CULL);
       // warm-up (also grows the arena), then one timed run
       for (int attempt = 0; attempt < 4; ++attempt) {
         st = run(&cand);
@@ -992,23 +1001,33 @@ vtx_status vtx_stage_times(vtx_ctx *c, const char **names, float *ms, int32_t *n
     if (runs) *runs = 0;
     return fail(c, VTX_ERR_STATE, "no profiled render since the last read");
   }
-  cudaError_t e = cudaEventSynchronize(c->ev_sets[c->ev_used - 1][kNumStages - 1]);
+  const size_t last = c->ev_used - 1;
+  cudaError_t e = cudaEventSynchronize(c->ev_sets[last][c->ev_masks[last] == ~0u ? kNumStages - 1 : 1]);
   if (e != cudaSuccess) return cuda_fail(c, e, "stage events");
   int cap = *n < kNumStages ? *n : kNumStages;
   double acc[kNumStages] = {};
+  int cnt[kNumStages] = {};
   for (size_t r = 0; r < c->ev_used; ++r) {
     cudaEvent_t *set = c->ev_sets[r];
+    if (c->ev_masks[r] != ~0u) {  // cull only
+      float t = 0.0f;
+      cudaEventElapsedTime(&t, set[0], set[1]);
+      acc[1] += t;
+      ++cnt[1];
+      continue;
+    }
     cudaEvent_t prev = set[kNumStages];
     for (int i = 0; i < kNumStages; ++i) {
       float t = 0.0f;
       cudaEventElapsedTime(&t, prev, set[i]);
       acc[i] += t;
+      ++cnt[i];
       prev = set[i];
     }
   }
   for (int i = 0; i < cap; ++i) {
     if (names) names[i] = kStageNames[i];
-    if (ms) ms[i] = (float)(acc[i] / (double)c->ev_used);
+    if (ms) ms[i] = cnt[i] ? (float)(acc[i] / (double)cnt[i]) : 0.0f;
   }
   *n = cap;
   if (runs) *runs = (int32_t)c->ev_used;

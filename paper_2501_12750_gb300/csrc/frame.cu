@@ -1484,7 +1484,7 @@ __global__ __launch_bounds__(256, VTX_RESOLVE_MINB) void k_resolve_split(
 // ------------------------------------------------------------ launchers --
 
 static inline void ev_rec(StageEvents *e, int i, cudaStream_t st) {
-  if (e && e->ev && i < e->n) cudaEventRecord(e->ev[i], st);
+  if (e && e->ev && i < e->n && ((e->mask >> i) & 1u)) cudaEventRecord(e->ev[i], st);
 }
 
 // Kernels of a frame are launched with programmatic stream serialisation:

@@ -50,6 +50,7 @@ struct Outputs {
 struct StageEvents {
   cudaEvent_t *ev;  // array of events, one recorded after each stage (may be null)
   int n;
+  unsigned mask = ~0u;  // bit i set: record event i
 };
 
 // Hard-edge pipeline: cull .. resolve.  Returns the first launch error.
