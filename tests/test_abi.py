@@ -62,3 +62,31 @@ def test_camera_struct_roundtrip():
     assert c.width == 256 and c.height == 256
     np.testing.assert_array_equal(np.array(c.eye[:], np.float32), cam.eye)
     np.testing.assert_array_equal(np.array(c.forward[:], np.float32), cam.forward)
+
+
+def header_enums():
+    """NAME = value pairs of the header's enums (comments removed)."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    out = {}
+    for body in re.findall(r"enum\s*\{(.*?)\}", text, flags=re.S):
+        for name, val in re.findall(r"\b(VTX_[A-Z0-9_]+)\s*=\s*(\d+)u?", body):
+            out[name] = int(val)
+    return out
+
+
+def test_binding_constants_match_the_header():
+    import paper_2501_12750_gb300 as vtx
+    e = header_enums()
+    pairs = {"VTX_MODE_VDW": vtx.MODE_VDW, "VTX_MODE_BALL_AND_STICK": vtx.MODE_BALL_AND_STICK,
+             "VTX_MODE_STICKS": vtx.MODE_STICKS, "VTX_MODE_SAS": vtx.MODE_SAS,
+             "VTX_SHADE_GLOSSY": vtx.SHADE_GLOSSY, "VTX_SHADE_FLAT": vtx.SHADE_FLAT,
+             "VTX_SHADE_MATTE": vtx.SHADE_MATTE, "VTX_SHADE_TOON": vtx.SHADE_TOON,
+             "VTX_FLAG_SYNC": vtx.FLAG_SYNC, "VTX_FLAG_PROFILE": vtx.FLAG_PROFILE,
+             "VTX_FLAG_NO_SSAO": vtx.FLAG_NO_SSAO, "VTX_FLAG_PROFILE_CULL": vtx.FLAG_PROFILE_CULL}
+    for name, val in pairs.items():
+        assert e.get(name) == val, (name, e.get(name), val)
+    flags = [v for k, v in e.items() if k.startswith("VTX_FLAG_")]
+    assert len(flags) == len(set(flags)) and all(v & (v - 1) == 0 for v in flags)  # distinct single bits
+    status = {v: k[len("VTX_ERR_"):] if k.startswith("VTX_ERR_") else "OK" for k, v in e.items()
+              if k.startswith("VTX_ERR_") or k == "VTX_OK"}
+    assert status == vtx.STATUS, (status, vtx.STATUS)
