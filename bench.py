@@ -283,7 +283,7 @@ def main():
             if ":" in ln:
                 key, val = ln.split(":", 1)
                 kv[key.strip()] = val.strip()
-        if kv.get("kernel") == "k_cull_direct" and kv.get("atoms") == str(N):
+        if kv.get("kernel") == "k_cull_direct" and kv.get("atoms") == str(N) and kv.get("current") == "yes":
             traffic = float(kv["bytes_per_launch"])
 
     # end to end through the host-buffer entry point (copies inside the timed region)
