@@ -748,7 +748,7 @@ static vtx_status batch_once(vtx_ctx *c, const float *frames, int64_t stride, co
   if (st) return st;
   const long long ppi = g.pix_per_img;
   const long long img0 = (long long)f0 * n_views;
-  Scene sc{(const float4 *)frames + (long long)f0 * stride, d_counts + f0, c->elem, nullptr};
+  Scene sc{(const float4 *)frames + (long long)f0 * stride, d_counts + f0, c->elem, nullptr, nullptr};
   Outputs o{out->depth + img0 * ppi, out->id + img0 * ppi, out->normal + img0 * 3 * ppi, out->rgb + img0 * 3 * ppi,
             out->ao ? out->ao + img0 * ppi : nullptr};
   ShadeParams sh = make_shade(c, s);
@@ -959,7 +959,7 @@ static vtx_status soft_run(vtx_ctx *c, const float *xyzr, int64_t n, const vtx_c
     Geometry g;
     st = soft_common(c, xyzr, n, cams, n_views, sigma, g);
     if (st) return st;
-    Scene sc{(const float4 *)xyzr, nullptr, nullptr, nullptr};
+    Scene sc{(const float4 *)xyzr, nullptr, nullptr, nullptr, nullptr};
     cudaError_t e =
         run_soft_pipeline(g, sc, scratch_of(c), cov, depth, normal, gc, gd, gn, grad, c->stream, nullptr);
     if (e != cudaSuccess) return cuda_fail(c, e, "soft launch");
