@@ -552,3 +552,162 @@ def test_outline_marks_exactly_the_covered_pixels_next_to_background_or_a_deep_s
     got = np.all(np.abs(h.rgb_final - np.array(col)) < 1e-15, axis=1)
     assert np.array_equal(got[ok & (h.id != oracle.NO_ID)], e[ok & (h.id != oracle.NO_ID)])
     np.testing.assert_array_equal(h.rgb_final[h.id == oracle.NO_ID], 1.0)
+
+
+# ----------------------------------------------- oblique capped cylinders --
+
+def line_sphere_t(E, d, C, r):
+    """Entry parameter of E + t d into spheres (C, r) by the textbook quadratic."""
+    w = E[None, None, :] - C[None, :, :]
+    a = (d * d).sum(-1)[:, None]
+    b = (d[:, None, :] * w).sum(-1)
+    c = (w * w).sum(-1) - r[None, :] ** 2
+    disc = b * b - a * c
+    t = (-b - np.sqrt(np.maximum(disc, 0.0))) / a
+    return np.where(disc >= 0.0, t, np.inf)
+
+
+def line_capped_cylinder(E, d, Pi, Pj, rho):
+    """Nearest hit of E + t d on capped cylinders Pi -> Pj of radius rho (any orthonormal frame).
+
+    The lateral surface is the textbook quadratic |(X - Pi) - ((X - Pi).A) A|^2 = rho^2 restricted to axial
+    coordinates in [0, L]; each cap is the plane through its end point with normal A, restricted to radial
+    distance <= rho.  Returns (t, kind, axial): kind 1 side, 2 the cap at Pj, 3 the cap at Pi.
+    """
+    Av = Pj - Pi
+    L = np.linalg.norm(Av, axis=1)
+    A = Av / L[:, None]
+    w0 = E[None, :] - Pi                                    # (B, 3)
+    dA = d @ A.T                                            # (P, B)
+    w0A = (w0 * A).sum(-1)[None, :]
+    dd = (d * d).sum(-1)[:, None]
+    dw = d @ w0.T
+    ww = (w0 * w0).sum(-1)[None, :]
+    qa = dd - dA * dA
+    qb = dw - dA * w0A
+    qc = ww - w0A * w0A - rho * rho
+    disc = qb * qb - qa * qc
+    with np.errstate(invalid="ignore", divide="ignore"):
+        ts = (-qb - np.sqrt(np.maximum(disc, 0.0))) / qa
+    ax = w0A + ts * dA
+    side_ok = (disc >= 0.0) & (qa > 0.0) & (ax >= 0.0) & (ax <= L[None, :])
+    best = np.where(side_ok, ts, np.inf)
+    kind = np.where(side_ok, 1, 0)
+    for s_end, k_end in ((L[None, :], 2), (0.0, 3)):
+        with np.errstate(invalid="ignore", divide="ignore"):
+            tc = (s_end - w0A) / dA
+        # radial distance of the cap-plane point from the axis
+        X = w0[None, :, :] + tc[:, :, None] * d[:, None, :]   # X - Pi
+        rad2 = (X * X).sum(-1) - (w0A + tc * dA) ** 2
+        ok = (np.abs(dA) > 1e-12) & np.isfinite(tc) & (rad2 <= rho * rho) & (tc < best)
+        best = np.where(ok, tc, best)
+        kind = np.where(ok, k_end, kind)
+    axial = w0A + best * dA
+    return best, kind, axial
+
+
+def oblique_bond_scene(seed, n=24, box=5.0, W=96, H=80, distance=10.0, fovy=25.0):
+    rng = np.random.default_rng(seed)
+    pos = rng.uniform(0.0, box, (n, 3))
+    elem = scenes.draw_elements(rng, n)
+    xyzr = scenes.pack_xyzr(pos, elem)
+    bonds = scenes.bonds_within(xyzr[:, :3])
+    c = np.full(3, box / 2)
+    cam = scenes.orbit_camera(c, distance, rng.uniform(0, 360), rng.uniform(-70, 70), W, H)
+    cam = scenes.Camera(cam.eye, cam.forward, cam.right, cam.up,
+                        float(np.float32(math.tan(math.radians(fovy) / 2))), cam.znear, W, H)
+    return xyzr, bonds, cam
+
+
+@pytest.mark.parametrize("seed,mode,ball", [(0, 1, 0.0), (1, 1, 0.0), (2, 1, 0.4), (3, 2, 0.0), (4, 1, 0.0),
+                                            (5, 2, 0.0)])
+def test_oblique_capped_cylinders_match_world_space_brute_force(seed, mode, ball):
+    """Bonds at every angle to the view, where a cap and the side compete at the rim: the oracle's nearest
+    primitive, depth, normal and half-bond side equal an independent brute force: rays from the eye,
+    endpoint-relative textbook side quadratic and cap planes through the end points (the oracle works
+    relative to the bond midpoint with the ray split along and across the axis).  Both use view coordinates
+    with the float32 basis as passed, which is how the oracle defines them.
+
+    mode 1 is ball-and-stick (ball radius 0 leaves the caps of free-standing cylinders visible), mode 2 is
+    sticks (spheres of the bond radius at every atom)."""
+    xyzr, bonds, cam = oblique_bond_scene(seed)
+    assert len(bonds) >= 10
+    rho = float(np.float32(0.15))
+    pix = oracle.all_pixels(cam.width, cam.height)
+    E = np.zeros(3)
+    d = rays(cam, pix)
+    X = view_coords(cam, xyzr[:, :3])
+    r_sph = np.full(len(X), float(np.float32(ball if mode == 1 else 0.15)))
+    ts = line_sphere_t(E, d, X, r_sph)
+    tb, kind, axial = line_capped_cylinder(E, d, X[bonds[:, 0]], X[bonds[:, 1]], rho)
+    zn = float(np.float32(cam.znear))
+    t_all = np.concatenate([ts, tb], axis=1)
+    t_all = np.where(t_all >= zn, t_all, np.inf)
+    best = np.argmin(t_all, axis=1)                       # first minimum: the smaller id on exact ties
+    tmin = t_all[np.arange(len(pix)), best]
+    ref_id = np.where(np.isfinite(tmin), best, oracle.NO_ID).astype(np.uint32)
+    h = oracle.hits(xyzr, cam, pix, bonds=bonds, mode=mode, ball_radius=ball, bond_radius=0.15)
+    ok = (h.flags & oracle.ID_FLAGS) == 0
+    assert ok.mean() > 0.995
+    assert np.array_equal(h.id[ok], ref_id[ok])
+    n_at = len(xyzr)
+    on_bond = ok & (ref_id != oracle.NO_ID) & (ref_id >= n_at)
+    b = ref_id[on_bond].astype(np.int64) - n_at
+    rows = np.nonzero(on_bond)[0]
+    k = kind[rows, b]
+    assert (k == 1).sum() > 30
+    if mode == 1 and ball == 0.0:
+        assert (k >= 2).sum() > 10  # caps seen obliquely
+    np.testing.assert_allclose(h.depth[on_bond], tmin[on_bond], rtol=1e-10)
+    # normals: radial unit vector on the side, +/- axis on the caps
+    Pi, Pj = X[bonds[b, 0]], X[bonds[b, 1]]
+    A = (Pj - Pi) / np.linalg.norm(Pj - Pi, axis=1)[:, None]
+    q = tmin[on_bond][:, None] * d[on_bond] - Pi
+    radial = q - (q * A).sum(1)[:, None] * A
+    n_ref = np.where((k == 1)[:, None], radial / rho, np.where((k == 2)[:, None], A, -A))
+    np.testing.assert_allclose(h.normal[on_bond], n_ref, atol=1e-8)
+    # the half-bond colour: atom i's half when the axial coordinate is at most half the length
+    L = np.linalg.norm(Pj - Pi, axis=1)
+    split_ok = (h.flags[on_bond] & oracle.FLAG_SPLIT) == 0
+    side_ref = np.where(axial[rows, b] <= 0.5 * L, 0, 1)
+    assert np.array_equal(h.side[on_bond][split_ok], side_ref[split_ok])
+
+
+def test_ssao_tangent_frame_branch_for_normals_along_screen_up():
+    """|n_y| > 0.9 takes the tangent a = (1, 0, 0): T = n x a / |n x a| = (0, n_z, -n_y), so kernel sample
+    (0.5, 0, 0.25) moves the hit 2 A (0.5 T + 0.25 n) up the screen and deeper.  A blocker placed there
+    occludes it; under the other tangent rule the sample lands 1 A to the left, on the unoccluded floor.
+
+    The floor is a sphere of radius 1e4 A whose surface at the centre pixel (depth 50) has normal
+    (0, 0.95, 0.3122); the blocker is a 0.5 A sphere centred 0.787 A above the centre ray at depth 49.8."""
+    W = H = 101
+    cam = axis_camera(0.0, W, H, fovy_deg=8.0)
+    R = 1e4
+    ny = 0.95
+    nz = math.sqrt(1.0 - ny * ny)
+    C = np.array([0.0, -ny * R, -50.0 - nz * R])
+    xyzr = np.array([[C[0], C[1], C[2], R], [0.0, 0.78725, -49.8, 0.5]], np.float32)
+    s = scenes.Scene("branch", xyzr, np.zeros(2, np.uint8), [cam], ssao=True)
+    k = np.array([[0.5, 0.0, 0.25]], np.float32)
+    h = oracle.render_pixels(s, 0, np.array([[50, 50]], np.int32), kernel=k)
+    assert h.id[0] == 0
+    # independent closed form: hit point and normal from the textbook quadratic on the float32 floor
+    u = rays(cam, np.array([[50, 50]]))[0]
+    Cf = view_coords(cam, xyzr[:1, :3])[0]
+    t = textbook_sphere(u[None, :], Cf[None, :], float(np.float32(R)))[0]
+    P = t * u
+    n = (P - Cf) / float(np.float32(R))
+    assert abs(n[0]) < 1e-12 and n[1] > 0.9
+    T = np.array([0.0, n[2], -n[1]]) / math.hypot(n[1], n[2])
+    S = P + 2.0 * (0.5 * T + 0.25 * n)
+    f = H / (2 * float(np.float32(math.tan(math.radians(8.0) / 2))))
+    fx = math.floor(W / 2 + f * S[0] / -S[2])
+    fy = math.floor(H / 2 - f * S[1] / -S[2])
+    assert fy < 50  # up the screen
+    uf = rays(cam, np.array([[fx, fy]]))
+    Cb = view_coords(cam, xyzr[1:, :3])
+    zf = textbook_sphere(uf, Cb, float(np.float32(0.5)))[0]
+    assert np.isfinite(zf) and zf <= -S[2] - 0.025
+    w = min(1.0, 2.0 / abs(t - zf))
+    assert w > 0.5
+    assert abs(h.ao[0] - (1.0 - w)) < 1e-9
