@@ -43,10 +43,18 @@ NO_ID = 0xFFFFFFFF
 
 TIE_TOL = 1e-4      # A: pixels whose two nearest depths differ by less are id-ambiguous
 GRAZE_TOL = 1e-6    # A: distance to a silhouette/rim/near-plane decision
-GRID_ABS = 1e-5     # px: SSAO sample distance to a pixel-grid line ...
-GRID_LEN = 1e-5     # A: ... plus the projected size of this displacement of the sample
-MARGIN_TOL = 5e-5   # A: SSAO occlusion-test margin
-SIL_TOL = 1e-4      # relative: (R^2 - rho^2)/(2 R^2) below this makes an FP32 normal ill-conditioned
+# SSAO ambiguity bands: test tolerances sized from the FP32 error of a renderer that computes the hit point,
+# normal and sample offsets in FP32 relative to each primitive.  Near a silhouette the closest-approach
+# discriminant is small and its rounding error grows as 1/sqrt(sil) (sil = (R^2 - rho^2)/(2 R^2)); measured
+# on the GPU planes of the parity scenes, the sample offset stays within 9e-8 (f/d) r_ssao (1 + 1/sqrt(sil))
+# px and the normal within 1e-7 (1 + 1/sqrt(sil)); the constants below keep a factor of 4 over that.
+ERR_POS = 4e-7      # sample position error bound: ERR_POS * ssao radius * (1 + 1/sqrt(sil)) A
+ERR_T = 2e-7        # hit depth error bound: ERR_T * R_hit * (1 + 1/sqrt(sil)) + one depth-key step
+GRID_ABS = 1e-6     # px: absolute part of the grid-line band (rounding of the projected offset)
+GRID_REL = 1.2e-7   # relative part
+MARGIN_ABS = 2e-7   # A: absolute part of the occlusion-test margin
+KEY_SPAN = 4294966784.0  # depth-key steps over a frame's depth range (32-bit keys)
+SIL_TOL = 1e-7      # relative: (R^2 - rho^2)/(2 R^2) below this the FP32 normal itself is unreliable
 BAND_TOL = 1e-3     # toon: |n.L * levels - boundary| (an FP32 normal is good to 1e-4 per component)
 EDGE_ABS = 1e-4     # A: outline depth-step decision ...
 EDGE_REL = 2e-5     # ... plus this fraction of the pixel's depth (FP32 depth keys)
@@ -86,8 +94,8 @@ def lib():
         L.orc_ses_mc.argtypes = [P, P, P, f32, f32, P, i64, P, P]
         L.orc_ses_mc.restype = i64
         L.orc_ses_case_counts.argtypes = [P]
-        L.orc_ssao_project.argtypes = [P, P, i64, P, P, P, P, i32, f64, f64, f64, P, P, P]
-        L.orc_ssao_resolve.argtypes = [i64, i32, P, P, P, P, P, f64, f64, f64, P, P]
+        L.orc_ssao_project.argtypes = [P, P, i64, P, P, P, P, i32, f64, f64, f64, P, P, P, P, P]
+        L.orc_ssao_resolve.argtypes = [i64, i32, P, P, P, P, P, P, P, f64, f64, f64, P, P, P, P]
         L.orc_soft_forward.argtypes = [P, i64, P, f64, P, i64, f64, P, P, P, P, P, P, i32]
         L.orc_soft_vjp.argtypes = [P, i64, P, f64, P, i64, P, P, P, P, i32]
         _lib = L
@@ -118,6 +126,7 @@ class Hits:
     flags: np.ndarray
     side: np.ndarray
     sil: np.ndarray
+    rad: Optional[np.ndarray] = None  # radius of the surface hit (0 for background)
     rgb: Optional[np.ndarray] = None
     ao: Optional[np.ndarray] = None
     rgb_final: Optional[np.ndarray] = None
@@ -143,6 +152,8 @@ def hits(xyzr, cam, pix, bonds=None, mode=0, ball_radius=0.4, bond_radius=0.15, 
                    _p(pix), P,
                    tie_tol, graze_tol, _p(out.depth), _p(out.id), _p(out.normal), _p(out.gap), _p(out.flags),
                    _p(out.side), _p(out.sil), threads)
+    out.rad = hit_radius(out, xyzr, xyzr.shape[0], mode=mode, ball_radius=ball_radius, bond_radius=bond_radius,
+                         probe=probe)
     return out
 
 
@@ -163,45 +174,110 @@ def shade(h: Hits, elem, palette, n_atoms, cam, bonds=None, model=0, toon_levels
     return rgb
 
 
+def hit_radius(h: Hits, xyzr, n_atoms, mode=0, ball_radius=0.4, bond_radius=0.15, probe=1.4) -> np.ndarray:
+    """Radius of the surface hit at each pixel (0 for background)."""
+    rad = np.zeros(h.id.shape[0])
+    cov = h.id != NO_ID
+    atom = cov & (h.id.astype(np.int64) < n_atoms)
+    ids = h.id[atom].astype(np.int64)
+    if mode == 1:
+        rad[atom] = float(np.float32(ball_radius))
+    elif mode == 2:
+        rad[atom] = float(np.float32(bond_radius))
+    elif mode == 3:
+        rad[atom] = (np.asarray(xyzr, np.float32)[ids, 3] + np.float32(probe)).astype(np.float64)
+    else:
+        rad[atom] = np.asarray(xyzr, np.float32)[ids, 3].astype(np.float64)
+    rad[cov & ~atom] = float(np.float32(bond_radius))
+    return rad
+
+
+def key_step(xyzr, cam, chunk=1 << 22) -> float:
+    """Depth-key step of a renderer that spreads 2^32 keys over the depth range of the primitives in front of
+    the eye: (max(z + r) - max(min(z - r), near / 2)) / KEY_SPAN over every atom (a superset of any visible
+    set, so the step is an upper bound)."""
+    x = np.asarray(xyzr, np.float32)
+    E = cam.eye.astype(np.float64)
+    F = cam.forward.astype(np.float64)
+    lo, hi = np.inf, 0.0
+    for i0 in range(0, x.shape[0], chunk):
+        c = x[i0:i0 + chunk].astype(np.float64)
+        z = (c[:, :3] - E) @ F
+        r = c[:, 3] + 1.5  # covers every representation's radius (probe, ball, bond)
+        front = z + r > float(cam.znear)
+        if front.any():
+            lo = min(lo, float((z - r)[front].min()))
+            hi = max(hi, float((z + r)[front].max()))
+    if hi <= 0.0:
+        return 0.0
+    lo = max(lo, 0.5 * float(cam.znear))
+    return max(hi - lo, 1.0) / KEY_SPAN
+
+
+def hit_errors(h: Hits, rad: np.ndarray, step: float, radius: float = 2.0):
+    """Per-pixel bounds on the SSAO sample position error (A) and the hit depth error of an FP32 renderer."""
+    sil = np.maximum(h.sil, 1e-30)
+    amp = 1.0 + 1.0 / np.sqrt(sil)
+    err_pos = ERR_POS * radius * amp
+    err_t = ERR_T * rad * amp + step
+    cov = h.id != NO_ID
+    return np.where(cov, err_pos, 0.0), np.where(cov, err_t, 0.0)
+
+
 def ssao(h: Hits, xyzr, cam, kernel, radius=2.0, bias=0.025, bonds=None, mode=0, ball_radius=0.4,
-         bond_radius=0.15, probe=1.4, clip=None, grid_abs=GRID_ABS, grid_len=GRID_LEN, margin_tol=MARGIN_TOL, sil_tol=SIL_TOL,
-         threads=0):
-    """AO per listed pixel; flags gain GRID / MARGIN / FETCH / SILH bits.  Fetched pixels are ray-cast on demand."""
+         bond_radius=0.15, probe=1.4, clip=None, grid_abs=GRID_ABS, grid_rel=GRID_REL, margin_abs=MARGIN_ABS,
+         sil_tol=SIL_TOL, depth_step=None, threads=0):
+    """AO per listed pixel; flags gain GRID / MARGIN / FETCH / SILH bits.  Fetched pixels are ray-cast on demand.
+
+    The bands flag samples whose projection or occlusion test a renderer computing the hit point in FP32
+    could decide differently (see orc_ssao_project / orc_ssao_resolve); depth_step is that renderer's
+    depth-key step (default: key_step() of the scene).
+    """
     kernel = np.ascontiguousarray(kernel, np.float32).reshape(-1, 3)
     ns = kernel.shape[0]
     P = h.pix.shape[0]
+    n_atoms = np.asarray(xyzr).shape[0]
     fetch = np.empty((P, ns, 2), np.int32)
     sdepth = np.empty((P, ns))
     c = _cam(cam)
+    step = key_step(xyzr, cam) if depth_step is None else float(depth_step)
+    rkw = dict(mode=mode, ball_radius=ball_radius, bond_radius=bond_radius, probe=probe)
+    err_pos, err_t = hit_errors(h, hit_radius(h, xyzr, n_atoms, **rkw), step, radius)
     h.flags[(h.id != NO_ID) & (h.sil < sil_tol)] |= FLAG_SILH
     lib().orc_ssao_project(_p(c), _p(h.pix), P, _p(h.depth), _p(h.id), _p(h.normal), _p(kernel), ns, radius,
-                           grid_abs, grid_len, _p(fetch), _p(sdepth), _p(h.flags))
+                           grid_abs, grid_rel, _p(err_pos), _p(err_t), _p(fetch), _p(sdepth), _p(h.flags))
     W = int(c["width"][0])
     lin = np.where(fetch[..., 0] >= 0, fetch[..., 1].astype(np.int64) * W + fetch[..., 0], -1)
     own = h.pix[:, 1].astype(np.int64) * W + h.pix[:, 0]
     need = np.unique(lin[lin >= 0])
     known = dict(zip(own.tolist(), range(P)))
     missing = np.array([q for q in need.tolist() if q not in known], dtype=np.int64)
-    zf = np.full((P, ns), np.inf)
-    famb = np.zeros((P, ns), np.int32)
-    depth_of, amb_of = {}, {}
+    info = {}  # pixel -> (depth, id flags, gap, depth error bound)
     for q, k in known.items():
-        depth_of[q] = h.depth[k]
-        amb_of[q] = int(h.flags[k] & ID_FLAGS)
+        info[q] = (h.depth[k], int(h.flags[k] & ID_FLAGS), h.gap[k], err_t[k])
     if missing.size:
         mp = np.stack([missing % W, missing // W], axis=1).astype(np.int32)
-        hm = hits(xyzr, cam, mp, bonds=bonds, mode=mode, ball_radius=ball_radius, bond_radius=bond_radius,
-                  probe=probe, clip=clip, threads=threads)
+        hm = hits(xyzr, cam, mp, bonds=bonds, clip=clip, threads=threads, **rkw)
+        _, et_m = hit_errors(hm, hit_radius(hm, xyzr, n_atoms, **rkw), step, radius)
         for k, q in enumerate(missing.tolist()):
-            depth_of[q] = hm.depth[k]
-            amb_of[q] = int(hm.flags[k] & ID_FLAGS)
+            info[q] = (hm.depth[k], int(hm.flags[k] & ID_FLAGS), hm.gap[k], et_m[k])
     valid = lin >= 0
     flat = lin[valid].tolist()
-    zf[valid] = np.array([depth_of[q] for q in flat]) if flat else []
-    famb[valid] = np.array([amb_of[q] for q in flat], dtype=np.int32) if flat else []
+    zf = np.full((P, ns), np.inf)
+    famb = np.zeros((P, ns), np.int32)
+    fgap = np.zeros((P, ns))
+    ferr = np.zeros((P, ns))
+    if flat:
+        rows = np.array([info[q] for q in flat])
+        zf[valid] = rows[:, 0]
+        famb[valid] = rows[:, 1].astype(np.int32)
+        fgap[valid] = rows[:, 2]
+        ferr[valid] = rows[:, 3]
     ao = np.empty(P)
     lib().orc_ssao_resolve(P, ns, _p(h.depth), _p(h.id), _p(sdepth), _p(np.ascontiguousarray(zf)),
-                           _p(np.ascontiguousarray(famb)), radius, bias, margin_tol, _p(ao), _p(h.flags))
+                           _p(np.ascontiguousarray(famb)), _p(np.ascontiguousarray(fgap)),
+                           _p(np.ascontiguousarray(ferr)), radius, bias, margin_abs, _p(err_pos), _p(err_t),
+                           _p(ao), _p(h.flags))
     return ao
 
 

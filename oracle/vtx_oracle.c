@@ -58,8 +58,8 @@ enum {
   ORC_FLAG_NEAR = 4,   /* an entry point within graze_tol of the near plane */
   ORC_FLAG_SPLIT = 16, /* bond hit within graze_tol of the half-bond colour split */
   ORC_FLAG_GRID = 32,  /* an SSAO sample within grid_tol px of a pixel-grid line */
-  ORC_FLAG_MARGIN = 64,/* an SSAO occlusion test within margin_tol of its threshold */
-  ORC_FLAG_FETCH = 128,/* an SSAO sample fetched an id-ambiguous pixel */
+  ORC_FLAG_MARGIN = 64,/* an SSAO occlusion test within its error margin of the threshold */
+  ORC_FLAG_FETCH = 128,/* an SSAO sample fetched a pixel whose visible surface is in doubt */
   ORC_FLAG_CUTOFF = 256, /* soft: a primitive within tol of the -4 px cutoff */
   ORC_FLAG_ORDER = 512,  /* soft: two contributors' centre depths within tol */
   ORC_FLAG_STOP = 1024,  /* soft: transmittance within tol of the stop threshold */
@@ -468,14 +468,20 @@ void orc_shade(const uint8_t *elem, const float *palette, int64_t n_atoms, const
  * B = n x T.  Sample j is S_j = P + radius (k_x T + k_y B + k_z n), projected
  * to pixel coordinates and floored.  Output per (pixel, sample): the fetched
  * pixel (fx, fy) or (-1, -1) when off screen, and the sample's own depth.
- * A sample within grid_abs + grid_len f/depth(S) px of a grid line (the
- * projected size of a grid_len Angstrom displacement) flags the pixel
- * ORC_FLAG_GRID.
+ *
+ * Ambiguity band (a test tolerance, not part of the method): a renderer that
+ * computes the hit point in FP32 places the sample slightly off S_j, so a
+ * sample that projects within `band` px of a pixel-grid line may be floored
+ * to the neighbouring pixel; such a pixel is flagged ORC_FLAG_GRID.  Per axis
+ *   band = grid_abs + grid_rel |off| + (f / ds) err_pos[p] + |off| err_t[p] / ds,
+ * where off is the sample's offset from the pixel centre (px), ds its depth,
+ * and err_pos / err_t (per pixel, inputs) bound the error of the sample's
+ * position (A) and of the hit depth.
  */
 void orc_ssao_project(const orc_camera *camera, const int32_t *pix, int64_t n_pix, const double *depth,
                       const uint32_t *id, const double *normal, const float *kernel, int32_t n_samples,
-                      double radius, double grid_abs, double grid_len, int32_t *fetch, double *sample_depth,
-                      int32_t *flags) {
+                      double radius, double grid_abs, double grid_rel, const double *err_pos, const double *err_t,
+                      int32_t *fetch, double *sample_depth, int32_t *flags) {
   ocam c;
   cam_load(camera, &c);
   for (int64_t p = 0; p < n_pix; ++p) {
@@ -508,8 +514,11 @@ void orc_ssao_project(const orc_camera *camera, const int32_t *pix, int64_t n_pi
       if (ds <= 0.0) continue;
       double x = 0.5 * c.W * (1.0 + (S[0] / ds) / (c.th * c.aspect));
       double y = 0.5 * c.H * (1.0 - (S[1] / ds) / c.th);
-      double grid_tol = grid_abs + grid_len * c.f / ds;
-      if (fabs(x - floor(x + 0.5)) < grid_tol || fabs(y - floor(y + 0.5)) < grid_tol) flags[p] |= ORC_FLAG_GRID;
+      const double fd = c.f / ds;
+      const double offx = x - (pix[2 * p] + 0.5), offy = y - (pix[2 * p + 1] + 0.5);
+      const double bx = grid_abs + grid_rel * fabs(offx) + fd * err_pos[p] + fabs(offx) * err_t[p] / ds;
+      const double by = grid_abs + grid_rel * fabs(offy) + fd * err_pos[p] + fabs(offy) * err_t[p] / ds;
+      if (fabs(x - floor(x + 0.5)) < bx || fabs(y - floor(y + 0.5)) < by) flags[p] |= ORC_FLAG_GRID;
       double fx = floor(x), fy = floor(y);
       if (fx < 0.0 || fy < 0.0 || fx >= c.W || fy >= c.H) continue;
       fetch[2 * (p * n_samples + j)] = (int32_t)fx;
@@ -523,11 +532,21 @@ void orc_ssao_project(const orc_camera *camera, const int32_t *pix, int64_t n_pi
  * fetched pixel (INFINITY for background or off screen).  A sample is
  * occluded when z_f <= depth(S_j) - bias; its weight is min(1, radius/|t - z_f|).
  * AO = 1 - (1/ns) sum occ_j w_j; background pixels get AO = 1.
- * fetched_amb[p*ns+j] != 0 marks a fetched pixel whose id is ambiguous.
+ *
+ * Ambiguity bands (test tolerances): fetched_amb[p*ns+j] holds the fetched
+ * pixel's id flags, fetched_gap its second-minus-first depth and fetched_err
+ * the bound on its depth error.  A fetched pixel whose visible surface is in
+ * doubt (GRAZE or NEAR) flags ORC_FLAG_FETCH; a tie (TIE) can only move its
+ * depth by its gap, which widens the occlusion margin.  An occlusion test
+ * within
+ *   margin = margin_abs + err_t[p] + fetched_err + err_pos[p] + 2e-7 |t - z_f|
+ *            (+ fetched_gap for a tie)
+ * of its threshold flags ORC_FLAG_MARGIN.
  */
 void orc_ssao_resolve(int64_t n_pix, int32_t n_samples, const double *depth, const uint32_t *id,
                       const double *sample_depth, const double *fetched_depth, const int32_t *fetched_amb,
-                      double radius, double bias, double margin_tol, double *ao, int32_t *flags) {
+                      const double *fetched_gap, const double *fetched_err, double radius, double bias,
+                      double margin_abs, const double *err_pos, const double *err_t, double *ao, int32_t *flags) {
   for (int64_t p = 0; p < n_pix; ++p) {
     if (id[p] == ORC_NO_ID) {
       ao[p] = 1.0;
@@ -535,11 +554,14 @@ void orc_ssao_resolve(int64_t n_pix, int32_t n_samples, const double *depth, con
     }
     double occ = 0.0;
     for (int j = 0; j < n_samples; ++j) {
-      double zf = fetched_depth[p * n_samples + j];
-      if (fetched_amb[p * n_samples + j]) flags[p] |= ORC_FLAG_FETCH;
+      const int64_t q = p * n_samples + j;
+      double zf = fetched_depth[q];
+      if (fetched_amb[q] & (ORC_FLAG_GRAZE | ORC_FLAG_NEAR)) flags[p] |= ORC_FLAG_FETCH;
       if (!(zf < INFINITY)) continue;
-      double thr = sample_depth[p * n_samples + j] - bias;
-      if (fabs(zf - thr) < margin_tol) flags[p] |= ORC_FLAG_MARGIN;
+      double thr = sample_depth[q] - bias;
+      double margin = margin_abs + err_t[p] + fetched_err[q] + err_pos[p] + 2e-7 * fabs(depth[p] - zf);
+      if (fetched_amb[q] & ORC_FLAG_TIE) margin += fetched_gap[q];
+      if (fabs(zf - thr) < margin) flags[p] |= ORC_FLAG_MARGIN;
       if (zf <= thr) {
         double dz = fabs(depth[p] - zf);
         double w = dz <= radius ? 1.0 : radius / dz;

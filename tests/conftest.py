@@ -25,3 +25,15 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+def pytest_terminal_summary(terminalreporter):
+    """Excluded-pixel fractions of every parity comparison run in this session."""
+    helpers = sys.modules.get("helpers")
+    log = getattr(helpers, "EXCLUSION_LOG", None)
+    if not log:
+        return
+    cov = sum(c for _, c, _, _ in log)
+    exc = sum(e for _, _, e, _ in log)
+    terminalreporter.write_line("excluded pixels: %d of %d covered (%.4f%%) over %d comparisons"
+                                % (exc, cov, 100.0 * exc / max(cov, 1), len(log)))
