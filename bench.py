@@ -62,7 +62,46 @@ def parse():
                     help="only the 1e5-atom protein frame at 1920x1080 (one JSON line; for profiling its kernels)")
     ap.add_argument("--soft-only", action="store_true",
                     help="only the soft-edge forward and backward (one JSON line; for profiling their kernels)")
+    ap.add_argument("--fp32-only", action="store_true",
+                    help="only the FP32 multiply-add rate microbenchmark (one JSON line)")
     return ap.parse_args()
+
+
+def frame_config(n_atoms, width, height, world=1):
+    """The benchmark workload's config, shared by the GPU arm and the reference arm."""
+    return {"workload": "cell4k: 1e8-atom whole-cell stand-in (20,000 protein-like blobs in a 12,000 A cube), "
+                        "3840x2160, vdW spheres + Blinn-Phong + SSAO16, view V1 at 36,000 A",
+            "atoms": int(n_atoms), "width": int(width), "height": int(height),
+            "l2": "inputs (1.6 GB) larger than L2; no flush",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
+def fp32_rates(vtx, torch, dev, iters=4000):
+    """Measured FP32 multiply-add rate of this GPU (scalar FFMA and paired FFMA2) with the SM clock sampled
+    during the runs.  The scalar rate / 64 flops is the warp-instruction issue rate."""
+    import ctypes
+    lib = vtx.load()
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    time.sleep(0.3)
+    res = {}
+    for name, paired in (("scalar_ffma", 0), ("paired_ffma2", 1)):
+        best = None
+        for _ in range(3):
+            ms, fl = ctypes.c_float(), ctypes.c_double()
+            code = lib.vtx_measure_fp32_rate(paired, iters, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream),
+                                             ctypes.byref(ms), ctypes.byref(fl))
+            if code != 0:
+                raise RuntimeError("vtx_measure_fp32_rate failed: %d" % code)
+            t = fl.value / (ms.value * 1e-3) / 1e12
+            best = t if best is None or t > best else best
+        res[name] = {"tflops": best, "ms": ms.value}
+    clk = clocks.stop()
+    scalar = res["scalar_ffma"]["tflops"]
+    return {"fp32_tflops": max(scalar, res["paired_ffma2"]["tflops"]), "scalar_ffma_tflops": scalar,
+            "paired_ffma2_tflops": res["paired_ffma2"]["tflops"],
+            "warp_instr_per_s": scalar * 1e12 / 64.0, "clocks": clk,
+            "note": "8 blocks of 256 threads per SM, 8 independent FMA chains per thread, CUDA events, best of 3"}
 
 
 class ClockSampler:
@@ -175,19 +214,25 @@ def main():
         s = scenes.config3(n_clusters=args.clusters)
         k = scenes.ssao_kernel()
         # each step is one bounded sample of the same frame
-        vals = []
+        vals, sample_s = [], []
         cb = None
         for i in range(max(1, args.warmup // 5) + args.steps):
             cb = oracle_baseline(s, k, 0, max(1.0, args.cpu_seconds / max(1, args.steps)), max_pixels=512)
             if i >= max(1, args.warmup // 5):
                 vals.append(cb["value"])
+                sample_s.append(cb["seconds"])
         v = float(np.median(vals))
         cb["value"] = v
+        # a step is one bounded pixel sample of the frame: ms_per_step is its measured wall time, and value
+        # extrapolates the sample's per-pixel time to the whole frame
+        step_ms = 1e3 * float(np.median(sample_s))
         line = {"impl": "reference", "metric": "frames/s", "value": v, "unit": "frames/s", "n_gpus": 1,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": "cell4k: 1e8-atom whole-cell stand-in, 3840x2160, vdW + SSAO16, view V1",
-                           "atoms": int(s.xyzr.shape[0]), "width": 3840, "height": 2160},
+                "config": frame_config(s.xyzr.shape[0], s.cameras[0].width, s.cameras[0].height),
+                "extrapolated_ms_per_frame": 1e3 / v,
+                "step_note": "each step renders a bounded random pixel sample of the frame with the FP64 oracle; "
+                             "value = frames/s extrapolated from the sample's time per pixel",
                 "cpu_baseline": cb, "e2e": {"value": v, "unit": "frames/s", "h2d_bytes_per_step": 0,
                                             "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
@@ -213,10 +258,17 @@ def main():
             print(json.dumps({"metric": "protein_frame_ms", "unit": "ms", "higher_is_better": False,
                               "data": "synthetic", **protein_extra(vtx, torch, dev)}))
         return 0
+    if args.fp32_only:
+        if rank == 0:
+            print(json.dumps({"metric": "fp32_tflops", "unit": "TFLOP/s", "higher_is_better": True,
+                              **fp32_rates(vtx, torch, dev)}))
+        return 0
     if args.soft_only:
         if rank == 0:
+            peak = fp32_rates(vtx, torch, dev)["fp32_tflops"]
             print(json.dumps({"metric": "soft_fwd_bwd_ms", "unit": "ms", "higher_is_better": False,
-                              "data": "synthetic", **soft_extra(vtx, torch, dev, vtx.Renderer(dev.index))}))
+                              "data": "synthetic",
+                              **soft_extra(vtx, torch, dev, vtx.Renderer(dev.index), fp32_peak=peak)}))
         return 0
 
     t_gen = time.time()
@@ -354,10 +406,7 @@ def main():
         "metric": "frames/s", "value": fps, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "cell4k: 1e8-atom whole-cell stand-in (20,000 protein-like blobs in a 12,000 A cube), "
-                               "3840x2160, vdW spheres + Blinn-Phong + SSAO16, view V1 at 36,000 A",
-                   "atoms": int(N), "width": W, "height": H, "l2": "inputs (1.6 GB) larger than L2; no flush",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "config": frame_config(N, W, H, world),
         "gatoms_per_s": fps * N / 1e9,
         "roofline": {"bound": "hbm", "kernel": "k_cull_direct", "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
@@ -405,6 +454,17 @@ def _frame_ms(vtx, torch, r, settings, out, reps=10):
     return e0.elapsed_time(e1) / reps
 
 
+OUT_BYTES_PER_PX = 36  # depth 4, id 4, normal 12, rgb 12, ao 4: the output planes every frame writes
+
+
+def hbm_roofline(alg_bytes, ms, what):
+    """Roofline object of an HBM-bound workload: algorithmic bytes over its measured time."""
+    peak, kind = measured_peaks()
+    achieved = alg_bytes / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "unit": "GB/s", "achieved": achieved, "peak": peak, "peak_kind": kind,
+            "frac": achieved / peak, "traffic": None, "algorithmic_bytes": alg_bytes, "bytes": what}
+
+
 def protein_extra(vtx, torch, dev, reps=20):
     """The 1e5-atom protein-like system at 1920x1080 with SSAO16: library-default tiles (with per-stage device
     times) and autotuned tiles."""
@@ -425,7 +485,10 @@ def protein_extra(vtx, torch, dev, reps=20):
     tuned = r.tuned_settings()
     tuned_ms = _frame_ms(vtx, torch, r, vtx.default_settings(ssao_kernel=k, tile_w=0), out, reps)
     r.close()
+    alg = 16.0 * s2.xyzr.shape[0] + OUT_BYTES_PER_PX * cam.width * cam.height
     return {"protein_1080p": {"workload": "1e5 protein-like atoms, 1920x1080, vdW, SSAO16",
+                              "roofline": hbm_roofline(alg, default_ms, "16 B per atom read + 36 B per pixel "
+                                                       "written (the frame at library-default tiles)"),
                               "default_tiles_ms": default_ms, "frames_per_s": 1e3 / default_ms,
                               "stages_ms": {kk: v for kk, v in stages.items() if kk != "runs"},
                               "autotuned_ms": tuned_ms, "autotuned": {"tile_w": tuned[0], "tile_h": tuned[1],
@@ -462,9 +525,21 @@ def ses_extra(vtx, torch, dev, reps=5):
             "note": "wall time of the synchronous call (SAS, 3 distance passes, count, scan, emit)"}
 
 
-def soft_extra(vtx, torch, dev, r, reps=5):
-    """Soft-edge forward and backward on 20,000 atoms x 16 views at 512x512, and the hard renderer on the same
-    views."""
+# FP32 operations of one composited soft term (the definition's arithmetic, counted from the formula with an
+# FMA as 2 and exp, sqrt, rsqrt and a reciprocal as 1 each): the ray offset at the reference depth (6), o.u and
+# |o|^2 (9), the closest approach and rho^2 (4), delta (4), the sigmoid and clamp (5), the smoothed entry depth
+# (9), the normal (9) and the front-to-back accumulation of coverage, depth, normal and transmittance (14).
+SOFT_FWD_FLOPS_PER_TERM = 60
+# The backward recomputes the term (46, without the accumulation) and forms its vector-Jacobian product:
+# the carry and the opacity derivative (12), the gradients through delta (16), through the entry depth and the
+# normal (44) and the view-to-world rotation of the per-sphere sum (amortised over the warp, not counted).
+SOFT_BWD_FLOPS_PER_TERM = 118
+
+
+def soft_extra(vtx, torch, dev, r, reps=5, fp32_peak=None):
+    """Soft-edge forward and backward on 20,000 atoms x 16 views at 512x512: the asynchronous calls with the
+    forward's per-pixel state (the autograd wrapper's path), the synchronous calls, and the hard renderer on the
+    same views."""
     from paper_2501_12750_gb300 import scenes
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -474,23 +549,32 @@ def soft_extra(vtx, torch, dev, r, reps=5):
     tgt = torch.from_numpy(s5.extra["target"]).to(dev)
     with torch.no_grad():
         A_t, D_t, N_t = r.render_soft_fwd(tgt, s5.cameras)
+    state = r.soft_state(s5.cameras)
     for _ in range(2):
-        A, D, Nn = r.render_soft_fwd(x, s5.cameras)
+        A, D, Nn = r.render_soft_fwd(x, s5.cameras, state=state)
         gA, gD, gN = 2 * (A - A_t), 0.2 * (D - D_t), 2 * (Nn - N_t)
+        r.render_soft_bwd(x, s5.cameras, gA, gD, gN, state=state)
         r.render_soft_bwd(x, s5.cameras, gA, gD, gN)
-    torch.cuda.synchronize()
-    e0.record(r.stream)
-    for _ in range(reps):
-        A, D, Nn = r.render_soft_fwd(x, s5.cameras)
-    e1.record(r.stream)
-    torch.cuda.synchronize()
-    fwd_ms = e0.elapsed_time(e1) / reps
-    e0.record(r.stream)
-    for _ in range(reps):
-        r.render_soft_bwd(x, s5.cameras, gA, gD, gN)
-    e1.record(r.stream)
-    torch.cuda.synchronize()
-    bwd_ms = e0.elapsed_time(e1) / reps
+    r.render_soft_fwd(x, s5.cameras, state=state)
+    n_terms = r.soft_terms()  # of the forward call just made
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0.record(r.stream)
+        for _ in range(reps):
+            fn()
+        e1.record(r.stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    # asynchronous calls with the forward's state (no host synchronisation inside)
+    fwd_ms = timed(lambda: r.render_soft_fwd(x, s5.cameras, state=state, sync=False))
+    bwd_ms = timed(lambda: r.render_soft_bwd(x, s5.cameras, gA, gD, gN, state=state, sync=False))
+    r.sync_status()
+    # per-kernel device times of the same calls (events around each call's soft kernel are not available
+    # through the API, so the kernel share is read from the launch list in profiles/)
+    fwd_sync_ms = timed(lambda: r.render_soft_fwd(x, s5.cameras))
+    bwd_sync_ms = timed(lambda: r.render_soft_bwd(x, s5.cameras, gA, gD, gN))
     # hard renderer on the same 16 views
     r.upload_atoms(x, torch.from_numpy(s5.elem).to(dev), s5.palette)
     hs = vtx.default_settings()
@@ -506,9 +590,22 @@ def soft_extra(vtx, torch, dev, r, reps=5):
     e1.record(r.stream)
     torch.cuda.synchronize()
     hard_ms = e0.elapsed_time(e1)
-    res["soft"] = {"workload": "20,000 atoms, 16 views at 512x512, sigma 0.5 px", "fwd_ms": fwd_ms,
-                   "bwd_ms": bwd_ms, "fwd_bwd_ms": fwd_ms + bwd_ms, "hard_16_views_ms": hard_ms,
-                   "note": "fwd and bwd each rebuild their tile lists (cull, setup, scan, scatter)"}
+    flops = n_terms * (SOFT_FWD_FLOPS_PER_TERM + SOFT_BWD_FLOPS_PER_TERM)
+    achieved = flops / ((fwd_ms + bwd_ms) * 1e-3) / 1e12
+    soft = {"workload": "20,000 atoms, 16 views at 512x512, sigma 0.5 px", "fwd_ms": fwd_ms, "bwd_ms": bwd_ms,
+            "fwd_bwd_ms": fwd_ms + bwd_ms, "api": "vtx_render_soft_fwd_ex / _bwd_ex, asynchronous, with the "
+            "forward's per-pixel state (the autograd wrapper's path); each call rebuilds its tile lists",
+            "sync_fwd_ms": fwd_sync_ms, "sync_bwd_ms": bwd_sync_ms, "hard_16_views_ms": hard_ms,
+            "terms": n_terms}
+    if fp32_peak:
+        soft["roofline"] = {"bound": "fp32", "unit": "TFLOP/s", "achieved": achieved, "peak": fp32_peak,
+                            "peak_kind": "measured (FFMA microbenchmark, same run)", "frac": achieved / fp32_peak,
+                            "traffic": None,
+                            "algorithmic_flops": flops,
+                            "units": "%d composited terms x (%d forward + %d backward) FP32 operations"
+                                     % (n_terms, SOFT_FWD_FLOPS_PER_TERM, SOFT_BWD_FLOPS_PER_TERM),
+                            "time": "fwd + bwd calls (binning included)"}
+    res["soft"] = soft
     return res
 
 
@@ -596,12 +693,17 @@ def run_extras(vtx, torch, dev, r, s3, cam, k):
     e1.record(r.stream)
     torch.cuda.synchronize()
     loop_ms = e0.elapsed_time(e1) / (loop_frames * len(cams))
+    alg = 16.0 * F * N4 + OUT_BYTES_PER_PX * F * len(cams) * cams[0].width * cams[0].height
     res["batched_traj"] = {"workload": "500,000 atoms x 256 frames x 4 views, 1280x720, SSAO16",
+                           "roofline": hbm_roofline(alg, batch_ms, "16 B per atom and frame read once + 36 B "
+                                                    "per pixel of the 1,024 images written"),
                            "images_per_s": F * len(cams) / (batch_ms / 1e3), "batch_ms": batch_ms,
                            "per_frame_loop_images_per_s": 1e3 / loop_ms, "graph": True}
     del out, frames
     torch.cuda.empty_cache()
-    res["soft"] = soft_extra(vtx, torch, dev, r)["soft"]
+    peaks = fp32_rates(vtx, torch, dev)
+    res["fp32_peak"] = peaks
+    res["soft"] = soft_extra(vtx, torch, dev, r, fp32_peak=peaks["fp32_tflops"])["soft"]
     res["protein_1080p"] = protein_extra(vtx, torch, dev)["protein_1080p"]
     return res
 

@@ -71,7 +71,7 @@ typedef enum {
   VTX_ERR_OOM = 3,         /* device allocation of scratch memory failed */
   VTX_ERR_CAPACITY = 4,    /* a previous frame overflowed the scratch arena (now grown: render again) */
   VTX_ERR_TIMEOUT = 5,     /* a bounded device-side wait for a bulk copy gave up; the frame is invalid */
-  VTX_ERR_BOUNDS = 6,      /* a device-side bounds check failed (debug builds) */
+  VTX_ERR_BOUNDS = 6,      /* a device-side bounds check failed: a decoded primitive id out of range */
   VTX_ERR_STATE = 7        /* call order: no atoms uploaded, no camera set */
 } vtx_status;
 
@@ -271,6 +271,39 @@ vtx_status vtx_render_soft_bwd(vtx_ctx *ctx, const float *xyzr, int64_t n, const
                                const float *g_normal, float *grad_xyzr);
 
 /*
+ * The two soft-edge calls above with a flags word and an optional per-pixel
+ * state.  flags: VTX_FLAG_SYNC makes the call synchronise and, after a
+ * capacity overflow, grow the arena and render again (what
+ * vtx_render_soft_fwd / _bwd always do).  Without it the first call of a
+ * problem size (atoms, views, W, H) on a context still does that, and later
+ * calls only enqueue: a device-side error is then reported by the next
+ * vtx_sync_status() (or synchronising call), and the outputs of the call
+ * that raised it are invalid.
+ * state: NULL, or uint32 [n_views][H][W][2], 8-byte aligned, caller-owned.
+ * The forward call writes per pixel the final transmittance (float bits)
+ * and 1 + the position of its last contributor in the tile's sorted list;
+ * a backward call given the state of the forward call made with the SAME
+ * xyzr, cams and sigma_px skips its front-to-back walk (the tile lists are
+ * still rebuilt).  Any other state gives wrong gradients.
+ */
+vtx_status vtx_render_soft_fwd_ex(vtx_ctx *ctx, const float *xyzr, int64_t n, const vtx_camera *cams,
+                                  int32_t n_views, float sigma_px, uint32_t flags, float *cov, float *depth,
+                                  float *normal, uint32_t *state);
+vtx_status vtx_render_soft_bwd_ex(vtx_ctx *ctx, const float *xyzr, int64_t n, const vtx_camera *cams,
+                                  int32_t n_views, float sigma_px, uint32_t flags, const float *g_cov,
+                                  const float *g_depth, const float *g_normal, const uint32_t *state,
+                                  float *grad_xyzr);
+
+/*
+ * Number of sigmoid terms the most recent soft forward call composited,
+ * summed over its pixels (the oracle's contributor count: spheres within
+ * -4 px of their silhouette, front to back until the transmittance stop).
+ * This is the forward pass's algorithmic work, used for its FP32 roofline.
+ * Synchronises.
+ */
+vtx_status vtx_soft_terms(vtx_ctx *ctx, uint64_t *n_terms);
+
+/*
  * Headless image export (Methods, High Quality Rendering: images up to 8K
  * with a custom background of user-defined transparency): packs rendered
  * planes into interleaved 8-bit RGBA.  R, G, B = round-to-nearest-even(255 *
@@ -371,8 +404,44 @@ vtx_status vtx_stage_times(vtx_ctx *ctx, const char **names, float *ms, int32_t 
  */
 vtx_status vtx_tuned_settings(const vtx_ctx *ctx, int32_t *tile_w, int32_t *tile_h, int32_t *splat_max_px);
 
+/*
+ * Failure-injection hooks for tests of the error paths (the paper has no
+ * counterpart).  Every hook acts on the host side or bounds a device wait,
+ * so none of them can fault or hang the GPU:
+ *   first_wait_polls >= 0: the multi-view / batch cull gives its FIRST
+ *     bulk-copy wait only that many polls (0: it gives up at once), sets the
+ *     timeout bit and stops; its drain of copies in flight keeps the normal
+ *     limit.  The next synchronising call reports VTX_ERR_TIMEOUT.  -1
+ *     restores the normal limit.
+ *   cap_records, cap_entries > 0: set the scratch arena's record and
+ *     tile-entry capacities (smaller capacities overflow; the next
+ *     synchronising call reports VTX_ERR_CAPACITY once and grows them).
+ *   corrupt_key != 0: after the tile ray-cast, pixel (0, 0)'s depth key is
+ *     overwritten by a host memset with an out-of-range primitive id; the
+ *     resolve's bounds check draws it as background and the next
+ *     synchronising call reports VTX_ERR_BOUNDS.  0 turns it off.
+ * Hooks persist on the context until changed.  Cached batch graphs are
+ * dropped.
+ */
+vtx_status vtx_debug_hooks(vtx_ctx *ctx, int32_t first_wait_polls, uint32_t cap_records, uint64_t cap_entries,
+                           int32_t corrupt_key);
+
 /* Text of the most recent error on this context ("" if none). */
 const char *vtx_last_error(const vtx_ctx *ctx);
+
+/*
+ * Measurement helper, with no counterpart in the paper: the FP32
+ * multiply-add rate of the current device, the denominator of the rooflines
+ * of the compute-bound kernels (tile ray-cast, soft forward and backward).
+ * Runs 8 blocks of 256 threads per SM, each thread with 8 independent FMA
+ * chains of `iters` x 16 steps, once untimed and once timed with CUDA events
+ * on cuda_stream (NULL = default); paired != 0 issues them as paired FFMA2
+ * instructions, 0 as scalar FFMA (whose rate / 64 is also the warp
+ * instruction issue rate).  *ms receives the timed launch's duration and
+ * *flops its floating-point operations (2 per FMA).  Allocates and frees 4
+ * bytes of device memory; synchronises.  Clocks are left as they are.
+ */
+vtx_status vtx_measure_fp32_rate(int32_t paired, int32_t iters, void *cuda_stream, float *ms, double *flops);
 
 /*
  * Allocation-free visibility buffer.  The paper has no counterpart: this

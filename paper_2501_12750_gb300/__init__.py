@@ -258,7 +258,16 @@ class Renderer:
                                               ctypes.byref(settings), ctypes.byref(o), 1 if use_graph else 0))
         return out
 
-    def render_soft_fwd(self, xyzr, cams: List, sigma_px: float = 0.5):
+    def soft_state(self, cams: List):
+        """A per-pixel state buffer for render_soft_fwd / render_soft_bwd (uint32 (V, H, W, 2))."""
+        torch = self._torch
+        return torch.empty((len(cams), cams[0].height, cams[0].width, 2), dtype=torch.int32,
+                           device=torch.device("cuda", self.device))
+
+    def render_soft_fwd(self, xyzr, cams: List, sigma_px: float = 0.5, state=None, sync: bool = True):
+        """Soft-edge coverage, depth and normal planes.  state (from soft_state) receives each pixel's final
+        transmittance and last contributor for a later render_soft_bwd; sync=False only enqueues (after the
+        first call of a problem size)."""
         torch = self._torch
         V = len(cams)
         W, H = cams[0].width, cams[0].height
@@ -267,11 +276,15 @@ class Renderer:
         dep = torch.empty((V, H, W), dtype=torch.float32, device=dev)
         nrm = torch.empty((V, 3, H, W), dtype=torch.float32, device=dev)
         carr = (VtxCamera * V)(*[camera_struct(c) for c in cams])
-        self._check(self.lib.vtx_render_soft_fwd(self.ctx, _ptr(xyzr), xyzr.shape[0], carr, V, sigma_px,
-                                                 _ptr(cov), _ptr(dep), _ptr(nrm)))
+        self._check(self.lib.vtx_render_soft_fwd_ex(self.ctx, _ptr(xyzr), xyzr.shape[0], carr, V, sigma_px,
+                                                    FLAG_SYNC if sync else 0, _ptr(cov), _ptr(dep), _ptr(nrm),
+                                                    _ptr(state)))
         return cov, dep, nrm
 
-    def render_soft_bwd(self, xyzr, cams: List, g_cov, g_depth, g_normal, sigma_px: float = 0.5):
+    def render_soft_bwd(self, xyzr, cams: List, g_cov, g_depth, g_normal, sigma_px: float = 0.5, state=None,
+                        sync: bool = True):
+        """d/d(x, y, z, r) of sum(g_cov cov + g_depth depth + g_normal . normal); state from the matching
+        forward call (same xyzr, cams, sigma) skips the backward's front-to-back walk."""
         torch = self._torch
         V = len(cams)
         grad = torch.empty_like(xyzr)
@@ -279,9 +292,16 @@ class Renderer:
         gc = None if g_cov is None else g_cov.contiguous()
         gd = None if g_depth is None else g_depth.contiguous()
         gn = None if g_normal is None else g_normal.contiguous()
-        self._check(self.lib.vtx_render_soft_bwd(self.ctx, _ptr(xyzr), xyzr.shape[0], carr, V, sigma_px,
-                                                 _ptr(gc), _ptr(gd), _ptr(gn), _ptr(grad)))
+        self._check(self.lib.vtx_render_soft_bwd_ex(self.ctx, _ptr(xyzr), xyzr.shape[0], carr, V, sigma_px,
+                                                    FLAG_SYNC if sync else 0, _ptr(gc), _ptr(gd), _ptr(gn),
+                                                    _ptr(state), _ptr(grad)))
         return grad
+
+    def soft_terms(self) -> int:
+        """Sigmoid terms composited by the most recent soft forward call (synchronises)."""
+        n = ctypes.c_uint64(0)
+        self._check(self.lib.vtx_soft_terms(self.ctx, ctypes.byref(n)))
+        return int(n.value)
 
     def tuned_settings(self):
         """(tile_w, tile_h, splat_max_px) picked by the autotuner for the last call with tile_w = 0."""
@@ -291,6 +311,13 @@ class Renderer:
 
     def sync_status(self):
         self._check(self.lib.vtx_sync_status(self.ctx))
+
+    def debug_hooks(self, first_wait_polls: int = -1, cap_records: int = 0, cap_entries: int = 0,
+                    corrupt_key: bool = False):
+        """Failure injection for tests (vtx_debug_hooks): a short first bulk-copy wait, small arena
+        capacities, a corrupted depth key.  The defaults switch the wait and key hooks off."""
+        self._check(self.lib.vtx_debug_hooks(self.ctx, int(first_wait_polls), int(cap_records), int(cap_entries),
+                                             1 if corrupt_key else 0))
 
     def stage_times(self) -> Dict[str, float]:
         """Average per-stage ms over the profiled runs since the last call (key "runs": their number)."""
@@ -312,16 +339,19 @@ def _soft_function():
 
         @staticmethod
         def forward(ctx, xyzr, renderer, cams, sigma_px=0.5):
-            cov, dep, nrm = renderer.render_soft_fwd(xyzr.detach().contiguous(), cams, sigma_px)
-            ctx.save_for_backward(xyzr)
+            x = xyzr.detach().contiguous()
+            state = renderer.soft_state(cams)
+            cov, dep, nrm = renderer.render_soft_fwd(x, cams, sigma_px, state=state, sync=False)
+            ctx.save_for_backward(x, state)
             ctx.renderer, ctx.cams, ctx.sigma = renderer, cams, sigma_px
             return cov, dep, nrm
 
         @staticmethod
         def backward(ctx, g_cov, g_dep, g_nrm):
-            (xyzr,) = ctx.saved_tensors
-            grad = ctx.renderer.render_soft_bwd(xyzr.detach().contiguous(), ctx.cams, g_cov, g_dep, g_nrm,
-                                                ctx.sigma)
+            x, state = ctx.saved_tensors
+            grad = ctx.renderer.render_soft_bwd(x, ctx.cams, g_cov, g_dep, g_nrm, ctx.sigma, state=state,
+                                                sync=False)
+            ctx.renderer.sync_status()  # a capacity overflow in either call surfaces here
             return grad, None, None, None
 
     return SoftRender

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(HERE, "_vtx.so")
-SOURCES = ["frame.cu", "soft.cu", "api.cu", "static_vis.cu", "export.cu", "ses.cu"]
+SOURCES = ["frame.cu", "soft.cu", "api.cu", "static_vis.cu", "export.cu", "ses.cu", "peak.cu"]
 HEADERS = ["vtx_device.cuh", "vtx_internal.h"]
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
@@ -118,7 +118,13 @@ SIGNATURES = {
                              c_void_p], c_int32),
     "vtx_render_soft_bwd": ([c_void_p, c_void_p, c_int64, c_void_p, c_int32, c_float, c_void_p, c_void_p,
                              c_void_p, c_void_p], c_int32),
+    "vtx_render_soft_fwd_ex": ([c_void_p, c_void_p, c_int64, c_void_p, c_int32, c_float, c_uint32, c_void_p,
+                                c_void_p, c_void_p, c_void_p], c_int32),
+    "vtx_render_soft_bwd_ex": ([c_void_p, c_void_p, c_int64, c_void_p, c_int32, c_float, c_uint32, c_void_p,
+                                c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
+    "vtx_soft_terms": ([c_void_p, c_void_p], c_int32),
     "vtx_sync_status": ([c_void_p], c_int32),
+    "vtx_debug_hooks": ([c_void_p, c_int32, c_uint32, ctypes.c_uint64, c_int32], c_int32),
     "vtx_stage_times": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
     "vtx_last_error": ([c_void_p], ctypes.c_char_p),
     "vtx_ses_fit_grid": ([c_void_p, c_void_p, c_int64, c_float, c_float, c_void_p], c_int32),
@@ -127,6 +133,7 @@ SIGNATURES = {
     "vtx_export_rgba8": ([c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_float, c_void_p], c_int32),
     "vtx_render_visibility_static": ([c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
     "vtx_tuned_settings": ([c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
+    "vtx_measure_fp32_rate": ([c_int32, c_int32, c_void_p, c_void_p, c_void_p], c_int32),
 }
 
 _lib = None

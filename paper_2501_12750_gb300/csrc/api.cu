@@ -69,6 +69,10 @@ struct vtx_ctx {
   };
   std::vector<Tune> tunes;
   int last_tw = 0, last_th = 0, last_splat = 0;
+  long long soft_sized[4] = {-1, -1, -1, -1};  // (atoms, views, W, H) of the last soft run that synchronised cleanly
+  // failure-injection hooks (vtx_debug_hooks)
+  int dbg_first_wait = -1;
+  bool dbg_corrupt_key = false;
   // output planes last checked by visible_outputs (caller pointers -> device-visible aliases)
   vtx_outputs out_in{}, out_dev{};
   std::string err;
@@ -113,7 +117,8 @@ static void drop_graphs(vtx_ctx *c) {
   c->graphs.clear();
 }
 
-static ViewParams make_view(const vtx_camera &cam) {
+namespace vtx {
+ViewParams make_view(const vtx_camera &cam) {
   ViewParams v;
   for (int k = 0; k < 3; ++k) {
     v.eye[k] = cam.eye[k];
@@ -139,7 +144,7 @@ static ViewParams make_view(const vtx_camera &cam) {
   return v;
 }
 
-static bool cam_ok(const vtx_camera *c) {
+bool cam_ok(const vtx_camera *c) {
   if (!c) return false;
   if (c->width < 1 || c->height < 1 || c->width > 16384 || c->height > 16384) return false;
   if (!(c->tan_half_fovy > 0.0f) || !std::isfinite(c->tan_half_fovy)) return false;
@@ -150,6 +155,7 @@ static bool cam_ok(const vtx_camera *c) {
       return false;
   return true;
 }
+}  // namespace vtx
 
 static vtx_status settings_ok(vtx_ctx *c, const vtx_settings *s) {
   if (!s) return fail(c, VTX_ERR_INVALID_ARG, "settings is NULL");
@@ -218,6 +224,7 @@ static void base_geometry(Geometry &g, const vtx_camera *cams, int n_views, int 
   g.tiles_y = (g.H + tile_h - 1) / tile_h;
   g.tiles_per_img = g.tiles_x * g.tiles_y;
   g.pix_per_img = (long long)g.W * g.H;
+  g.dbg_first_wait = -1;
 }
 
 // Size the arena for a launch; records/entries grow only through overflow reports.
@@ -295,6 +302,10 @@ static vtx_status check_status(vtx_ctx *c) {
   if (s.overflow & 16u) {
     cudaMemsetAsync(c->status.p, 0, sizeof(Status), c->stream);
     return fail(c, VTX_ERR_TIMEOUT, "a device-side wait for a bulk copy gave up; the frame is invalid");
+  }
+  if (s.overflow & 32u) {
+    cudaMemsetAsync(c->status.p, 0, sizeof(Status), c->stream);
+    return fail(c, VTX_ERR_BOUNDS, "a decoded primitive id was out of range (drawn as background); the frame is invalid");
   }
   std::string msg = "scratch capacity exceeded:";
   if (s.overflow & 2u) {
@@ -557,7 +568,9 @@ static vtx_status render_once(vtx_ctx *c, const vtx_settings *s, const vtx_outpu
   g.surv_cap = c->n_atoms + g.n_bonds + cull_survivor_slack(c->n_atoms);
   vtx_status st = prepare(c, g, false, 0);
   if (st) return st;
+  g.dbg_first_wait = c->dbg_first_wait;
   Scene sc{c->xyzr, nullptr, c->elem, g.n_bonds ? c->bonds : nullptr, nullptr};
+  sc.dbg_corrupt_key = c->dbg_corrupt_key;
   // host-resident atoms: the cull copies its survivors into device memory (when there is room), so setup and
   // resolve gather them from HBM instead of over the host link (bonds need their end atoms: not staged)
   if (c->atoms_on_host && g.n_bonds == 0 && c->n_atoms > 0) {
@@ -748,7 +761,9 @@ static vtx_status batch_once(vtx_ctx *c, const float *frames, int64_t stride, co
   if (st) return st;
   const long long ppi = g.pix_per_img;
   const long long img0 = (long long)f0 * n_views;
+  g.dbg_first_wait = c->dbg_first_wait;
   Scene sc{(const float4 *)frames + (long long)f0 * stride, d_counts + f0, c->elem, nullptr, nullptr};
+  sc.dbg_corrupt_key = c->dbg_corrupt_key;
   Outputs o{out->depth + img0 * ppi, out->id + img0 * ppi, out->normal + img0 * 3 * ppi, out->rgb + img0 * 3 * ppi,
             out->ao ? out->ao + img0 * ppi : nullptr};
   ShadeParams sh = make_shade(c, s);
@@ -946,24 +961,35 @@ static vtx_status soft_common(vtx_ctx *c, const float *xyzr, int64_t n, const vt
   g.stride = n;
   g.n_atoms = n;
   g.surv_cap = n;
+  g.dbg_first_wait = c->dbg_first_wait;
   return prepare(c, g, true, n);
 }
 
+// Soft calls: with VTX_FLAG_SYNC (and always for the first call of a problem size on a context) the call
+// synchronises, grows the arena on a capacity overflow and renders again; otherwise it only enqueues and a
+// device-side error is reported by the next synchronising call.
 static vtx_status soft_run(vtx_ctx *c, const float *xyzr, int64_t n, const vtx_camera *cams, int32_t n_views,
-                           float sigma, float *cov, float *depth, float *normal, const float *gc, const float *gd,
-                           const float *gn, float *grad) {
+                           float sigma, uint32_t flags, float *cov, float *depth, float *normal, const float *gc,
+                           const float *gd, const float *gn, float *grad, uint32_t *state) {
   if (!c) return VTX_ERR_INVALID_ARG;
   cudaSetDevice(c->device);
+  if (((uintptr_t)state & 7u) != 0) return fail(c, VTX_ERR_INVALID_ARG, "state must be 8-byte aligned");
+  const long long key[4] = {(long long)n, n_views, n_views >= 1 && cams ? cams[0].width : 0,
+                            n_views >= 1 && cams ? cams[0].height : 0};
+  const bool sized = std::equal(key, key + 4, c->soft_sized);
+  const bool sync = (flags & VTX_FLAG_SYNC) != 0 || !sized;
   vtx_status st = VTX_OK;
   for (int attempt = 0; attempt < 4; ++attempt) {
     Geometry g;
     st = soft_common(c, xyzr, n, cams, n_views, sigma, g);
     if (st) return st;
     Scene sc{(const float4 *)xyzr, nullptr, nullptr, nullptr, nullptr};
-    cudaError_t e =
-        run_soft_pipeline(g, sc, scratch_of(c), cov, depth, normal, gc, gd, gn, grad, c->stream, nullptr);
+    cudaError_t e = run_soft_pipeline(g, sc, scratch_of(c), cov, depth, normal, gc, gd, gn, grad, (uint2 *)state,
+                                      c->stream, nullptr);
     if (e != cudaSuccess) return cuda_fail(c, e, "soft launch");
+    if (!sync) return VTX_OK;
     st = check_status(c);
+    if (st == VTX_OK) std::copy(key, key + 4, c->soft_sized);
     if (st != VTX_ERR_CAPACITY) return st;
     if (c->h_status->overflow & 8u) return st;
     c->err.clear();
@@ -971,17 +997,47 @@ static vtx_status soft_run(vtx_ctx *c, const float *xyzr, int64_t n, const vtx_c
   return st;
 }
 
+vtx_status vtx_render_soft_fwd_ex(vtx_ctx *c, const float *xyzr, int64_t n, const vtx_camera *cams,
+                                  int32_t n_views, float sigma_px, uint32_t flags, float *cov, float *depth,
+                                  float *normal, uint32_t *state) {
+  if (!cov || !depth || !normal) return fail(c, VTX_ERR_INVALID_ARG, "soft outputs are required");
+  return soft_run(c, xyzr, n, cams, n_views, sigma_px, flags, cov, depth, normal, nullptr, nullptr, nullptr,
+                  nullptr, state);
+}
+
+vtx_status vtx_render_soft_bwd_ex(vtx_ctx *c, const float *xyzr, int64_t n, const vtx_camera *cams,
+                                  int32_t n_views, float sigma_px, uint32_t flags, const float *g_cov,
+                                  const float *g_depth, const float *g_normal, const uint32_t *state,
+                                  float *grad_xyzr) {
+  if (!grad_xyzr || ((uintptr_t)grad_xyzr & 15u)) return fail(c, VTX_ERR_INVALID_ARG, "grad_xyzr: NULL or unaligned");
+  return soft_run(c, xyzr, n, cams, n_views, sigma_px, flags, nullptr, nullptr, nullptr, g_cov, g_depth, g_normal,
+                  grad_xyzr, const_cast<uint32_t *>(state));
+}
+
 vtx_status vtx_render_soft_fwd(vtx_ctx *c, const float *xyzr, int64_t n, const vtx_camera *cams, int32_t n_views,
                                float sigma_px, float *cov, float *depth, float *normal) {
-  if (!cov || !depth || !normal) return fail(c, VTX_ERR_INVALID_ARG, "soft outputs are required");
-  return soft_run(c, xyzr, n, cams, n_views, sigma_px, cov, depth, normal, nullptr, nullptr, nullptr, nullptr);
+  return vtx_render_soft_fwd_ex(c, xyzr, n, cams, n_views, sigma_px, VTX_FLAG_SYNC, cov, depth, normal, nullptr);
 }
 
 vtx_status vtx_render_soft_bwd(vtx_ctx *c, const float *xyzr, int64_t n, const vtx_camera *cams, int32_t n_views,
                                float sigma_px, const float *g_cov, const float *g_depth, const float *g_normal,
                                float *grad_xyzr) {
-  if (!grad_xyzr || ((uintptr_t)grad_xyzr & 15u)) return fail(c, VTX_ERR_INVALID_ARG, "grad_xyzr: NULL or unaligned");
-  return soft_run(c, xyzr, n, cams, n_views, sigma_px, nullptr, nullptr, nullptr, g_cov, g_depth, g_normal, grad_xyzr);
+  return vtx_render_soft_bwd_ex(c, xyzr, n, cams, n_views, sigma_px, VTX_FLAG_SYNC, g_cov, g_depth, g_normal,
+                                nullptr, grad_xyzr);
+}
+
+vtx_status vtx_soft_terms(vtx_ctx *c, uint64_t *n_terms) {
+  if (!c || !n_terms) return VTX_ERR_INVALID_ARG;
+  cudaSetDevice(c->device);
+  if (!c->status.p) {
+    *n_terms = 0;
+    return VTX_OK;
+  }
+  cudaError_t e = cudaMemcpyAsync(c->h_status, c->status.p, sizeof(Status), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "soft terms");
+  *n_terms = (uint64_t)c->h_status->n_terms;
+  return VTX_OK;
 }
 
 vtx_status vtx_sync_status(vtx_ctx *c) {
@@ -1164,6 +1220,17 @@ vtx_status vtx_ses_mesh(vtx_ctx *c, const float *xyzr, int64_t n_atoms, const vt
   if (e != cudaSuccess) return cuda_fail(c, e, "ses mesh");
   *n_tris = (int64_t)total;
   if ((long long)total > max_tris) return fail(c, VTX_ERR_CAPACITY, "ses: more triangles than max_tris");
+  return VTX_OK;
+}
+
+vtx_status vtx_debug_hooks(vtx_ctx *c, int32_t first_wait_polls, uint32_t cap_records, uint64_t cap_entries,
+                           int32_t corrupt_key) {
+  if (!c) return VTX_ERR_INVALID_ARG;
+  c->dbg_first_wait = first_wait_polls < 0 ? -1 : first_wait_polls;
+  c->dbg_corrupt_key = corrupt_key != 0;
+  if (cap_records > 0) c->cap_rec = cap_records;
+  if (cap_entries > 0) c->cap_entries = cap_entries;
+  drop_graphs(c);
   return VTX_OK;
 }
 

@@ -77,6 +77,7 @@ __global__ __launch_bounds__(256) void k_clear(ImageState *st, int n_img, Status
   if (tid == 0) {
     status->n_rec = 0u;
     status->n_entries = 0ull;
+    status->n_terms = 0ull;
     status->n_list = 0u;
     status->n_cov = 0u;
   }
@@ -113,6 +114,8 @@ __device__ __forceinline__ void warp_minmax(float &lo, float &hi) {
 // memory and appended with one global atomic per 1,024 atoms.
 // ONE_VIEW: a single camera, whose constants are then compile-time indexed
 // kernel parameters; otherwise the views are read from a shared-memory copy.
+// blockIdx.z splits the views into gridDim.z groups (each CTA tests its
+// group only): a few atoms seen from many views then still fill the GPU.
 template <bool ONE_VIEW>
 __global__ __launch_bounds__(kCullThreads, 5) void k_cull_atoms(Geometry g, const float4 *__restrict__ frames,
                                                                 const long long *__restrict__ counts, ImageState *st,
@@ -139,7 +142,9 @@ __global__ __launch_bounds__(kCullThreads, 5) void k_cull_atoms(Geometry g, cons
     s_zhi[threadIdx.x] = 0u;
     if (!ONE_VIEW && threadIdx.x < g.n_views) s_views[threadIdx.x] = g.views[threadIdx.x];
   }
-  const int n_views = ONE_VIEW ? 1 : g.n_views;
+  const int vper = ONE_VIEW ? 1 : (g.n_views + (int)gridDim.z - 1) / (int)gridDim.z;
+  const int v_begin = ONE_VIEW ? 0 : min((int)blockIdx.z * vper, g.n_views);
+  const int v_end = ONE_VIEW ? 1 : min(v_begin + vper, g.n_views);
   if (threadIdx.x == 0) {
     s_fail = 0;
     s_cnt[0] = 0;
@@ -170,7 +175,9 @@ __global__ __launch_bounds__(kCullThreads, 5) void k_cull_atoms(Geometry g, cons
   long long k = 0;
   for (; k < mine; ++k) {
     // stage k % kStages, parity (k / kStages) & 1
-    if (!mbar_wait_bounded(&s_bar[stg], phase, kWaitLimit)) {
+    // the normal poll limit, except for a test hook that shortens the first wait (the drain below keeps it)
+    const uint32_t lim = (k == 0 && g.dbg_first_wait >= 0) ? (uint32_t)g.dbg_first_wait : kWaitLimit;
+    if (!mbar_wait_bounded(&s_bar[stg], phase, lim)) {
       s_fail = 1;
       atomicOr(&status->overflow, 16u);
     }
@@ -182,7 +189,7 @@ __global__ __launch_bounds__(kCullThreads, 5) void k_cull_atoms(Geometry g, cons
       const int i = j * kCullThreads + threadIdx.x;
       a[j] = i < cnt ? s_atoms[stg * kChunk + i] : make_float4(0.0f, 0.0f, 0.0f, -1.0f);
     }
-    for (int v = 0; v < n_views; ++v, ub = ub == 2 ? 0 : ub + 1) {
+    for (int v = v_begin; v < v_end; ++v, ub = ub == 2 ? 0 : ub + 1) {
       const int b = ub;
       const ViewParams &vp = ONE_VIEW ? g.views[0] : s_views[v];
       float zlo = __int_as_float(0x7f800000), zhi = 0.0f;
@@ -228,7 +235,7 @@ __global__ __launch_bounds__(kCullThreads, 5) void k_cull_atoms(Geometry g, cons
         pend_cnt = c;
         pend_img = img;
         s_cnt[(b + 1) % 3] = 0;
-        if (v == 0 && issued < mine) {  // the stage is free again: refill it
+        if (v == v_begin && issued < mine) {  // the stage is free again: refill it
           fence_proxy_async();
           const long long b0 = ((long long)blockIdx.x + issued * gridDim.x) * kChunk;
           const uint32_t bytes = (uint32_t)min((long long)kChunk, n - b0) * 16u;
@@ -272,7 +279,7 @@ __global__ __launch_bounds__(kCullThreads, 5) void k_cull_atoms(Geometry g, cons
       mbar_wait_bounded(&s_bar[q % kStages], (uint32_t)((q / kStages) & 1), kWaitLimit);
   }
   __syncthreads();
-  if (threadIdx.x < n_views && s_zhi[threadIdx.x] != 0u) {
+  if ((int)threadIdx.x >= v_begin && (int)threadIdx.x < v_end && s_zhi[threadIdx.x] != 0u) {
     const int img = frame * g.n_views + threadIdx.x;
     atomicMin(&st[img].zlo_bits, s_zlo[threadIdx.x]);
     atomicMax(&st[img].zhi_bits, s_zhi[threadIdx.x]);
@@ -594,14 +601,17 @@ __global__ __launch_bounds__(256, VTX_SETUP_MINB) void k_setup(Geometry g, const
   unsigned long long *K = keys + (long long)img * g.pix_per_img;
   const int lane = threadIdx.x & 31;
   const long long stride = (long long)gridDim.x * blockDim.x;
-  const long long n_pad = (n + 31) & ~31LL;
+  // binned records are reserved once per CTA and iteration (a shared count, then one global atomic)
+  __shared__ unsigned s_blk_cnt, s_blk_base;
+  if (threadIdx.x == 0) s_blk_cnt = 0u;
+  __syncthreads();
   // two-stage prefetch: the id two iterations ahead, the atom record one ahead
   const long long k0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   uint32_t id_cur = k0 < n ? sv[k0] : 0u;
   uint32_t id_nxt = k0 + stride < n ? sv[k0 + stride] : 0u;
   float4 a_cur = (k0 < n && (long long)id_cur < g.n_atoms) ? X[id_cur] : zero4;
-  for (long long k = k0; k < n_pad; k += stride) {
+  for (long long k = k0; k - threadIdx.x < n; k += stride) {  // same trip count for every thread of a CTA
     const float4 a_nxt = (k + stride < n && (long long)id_nxt < g.n_atoms) ? X[id_nxt] : zero4;
     const uint32_t id_nn = k + 2 * stride < n ? sv[k + 2 * stride] : 0u;
     bool binned = false;
@@ -670,26 +680,41 @@ __global__ __launch_bounds__(256, VTX_SETUP_MINB) void k_setup(Geometry g, const
         }
       }
     }
-    unsigned m = __ballot_sync(0xffffffffu, binned);
-    if (m) {
-      int leader = __ffs(m) - 1;
-      unsigned base = 0;
-      if (lane == leader) base = atomicAdd(&status->n_rec, (unsigned)__popc(m));
-      base = __shfl_sync(0xffffffffu, base, leader);
-      if (binned) {
-        unsigned slot = base + __popc(m & ((1u << lane) - 1u));
-        if (slot < cap_rec) {
-          recs[slot] = rec;
-          rec_img[slot] = (uint32_t)img;
-          rec_box[slot] = rbox;
-          if (SOFT) rec_of[(long long)img * g.n_atoms + rec.id] = slot;
-          int tx0 = rbox.x & 0xffff, ty0 = rbox.x >> 16, tx1 = rbox.y & 0xffff, ty1 = rbox.y >> 16;
-          uint32_t *tc = tile_count + (long long)img * g.tiles_per_img;
-          for (int ty = ty0; ty <= ty1; ++ty)
-            for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(tc + ty * g.tiles_x + tx, 1u);
-        } else {
-          atomicOr(&status->overflow, 2u);
-        }
+    const unsigned m = __ballot_sync(0xffffffffu, binned);
+    unsigned woff = 0u;
+    if (m && lane == __ffs(m) - 1) woff = atomicAdd(&s_blk_cnt, (unsigned)__popc(m));
+    woff = __shfl_sync(0xffffffffu, woff, m ? __ffs(m) - 1 : 0);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const unsigned c = s_blk_cnt;
+      s_blk_base = c ? atomicAdd(&status->n_rec, c) : 0u;
+      s_blk_cnt = 0u;
+    }
+    __syncthreads();
+    bool counted = false;
+    if (binned) {
+      const unsigned slot = s_blk_base + woff + __popc(m & ((1u << lane) - 1u));
+      if (slot < cap_rec) {
+        recs[slot] = rec;
+        rec_img[slot] = (uint32_t)img;
+        rec_box[slot] = rbox;
+        if (SOFT) rec_of[(long long)img * g.n_atoms + rec.id] = slot;
+        counted = true;
+      } else {
+        atomicOr(&status->overflow, 2u);
+      }
+    }
+    // per-tile counts: lanes adding to the same tile in the same step are merged (neighbouring survivors
+    // share tiles), so a busy tile's counter takes one atomic per warp and step instead of one per record
+    if (__any_sync(0xffffffffu, counted)) {
+      const int tx0 = rbox.x & 0xffff, ty0 = rbox.x >> 16, tx1 = rbox.y & 0xffff, ty1 = rbox.y >> 16;
+      const int nx = tx1 - tx0 + 1, nt = counted ? nx * (ty1 - ty0 + 1) : 0;
+      const int maxnt = (int)__reduce_max_sync(0xffffffffu, (unsigned)nt);
+      uint32_t *tc = tile_count + (long long)img * g.tiles_per_img;
+      for (int q = 0; q < maxnt; ++q) {
+        const int tile = q < nt ? (ty0 + q / nx) * g.tiles_x + tx0 + q % nx : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, tile);
+        if (tile >= 0 && lane == __ffs(peers) - 1) atomicAdd(tc + tile, (unsigned)__popc(peers));
       }
     }
   }
@@ -1066,6 +1091,29 @@ __device__ __forceinline__ bool raster_keep(const PrimRec &p, unsigned x0, unsig
   return !(dx * dx + dy * dy > rt * rt);
 }
 
+// Dynamic shared memory of the raster: the segment's ordered entries, then per warp two 32-record windows
+// (the one being tested and the next one, filled by cp.async meanwhile), which also hold the bucket offsets
+// while a segment is ordered.
+template <int NT>
+constexpr size_t raster_smem() {
+  return kListCap * sizeof(unsigned long long) +
+         (NT * 2 * sizeof(PrimRec) > kListCap * 2 ? NT * 2 * sizeof(PrimRec) : kListCap * 2);
+}
+
+// Copy the 64-byte records of window entries [c0, c0 + 32) into this warp's window w (one record per lane,
+// four 16-byte asynchronous copies) and close the lane's commit group (an empty group past the end, so every
+// lane always has the same number of groups in flight).
+__device__ __forceinline__ void raster_stage(const PrimRec *__restrict__ recs, const unsigned long long *s_e, int m,
+                                             int c0, PrimRec *w, int lane) {
+  if (c0 + lane < m) {
+    const char *src = reinterpret_cast<const char *>(recs + (uint32_t)s_e[c0 + lane]);
+    char *dst = reinterpret_cast<char *>(w + lane);
+#pragma unroll
+    for (int b = 0; b < 64; b += 16) cp_async16(dst + b, src + b);
+  }
+  cp_async_commit();
+}
+
 template <int TW, int TH>
 __global__ __launch_bounds__(TW *TH) void k_raster(Geometry g, const PrimRec *__restrict__ recs,
                                                    const unsigned long long *__restrict__ entries,
@@ -1077,13 +1125,11 @@ __global__ __launch_bounds__(TW *TH) void k_raster(Geometry g, const PrimRec *__
   pdl_enter();
   constexpr int NT = TW * TH;
   static_assert(NT % 32 == 0, "whole warps per tile");
-  __shared__ unsigned long long s_e[kListCap];
-  // the warps' record windows, which also hold the bucket offsets while a segment is ordered
-  constexpr int kRawBytes = NT * (int)sizeof(PrimRec) > kListCap * 2 ? NT * (int)sizeof(PrimRec) : kListCap * 2;
-  __shared__ __align__(16) unsigned char s_raw[kRawBytes];
+  extern __shared__ __align__(16) unsigned char raster_smem_raw[];
+  unsigned long long *s_e = reinterpret_cast<unsigned long long *>(raster_smem_raw);
+  unsigned char *s_raw = raster_smem_raw + kListCap * sizeof(unsigned long long);
   __shared__ uint32_t s_cnt[kRasterBuckets], s_lo[kRasterBuckets], s_red[2];
-  PrimRec *s_r = reinterpret_cast<PrimRec *>(s_raw);
-  PrimRec *s_w = s_r + (threadIdx.x & ~31u);  // this warp's 32-entry window
+  PrimRec *s_w = reinterpret_cast<PrimRec *>(s_raw) + 2 * (threadIdx.x & ~31u);  // this warp's two windows
   const int lane = threadIdx.x & 31;
   const uint32_t n_list = status->n_list;
   for (uint32_t li = blockIdx.x; li < n_list; li += gridDim.x) {  // only the non-empty tiles
@@ -1108,25 +1154,25 @@ __global__ __launch_bounds__(TW *TH) void k_raster(Geometry g, const PrimRec *__
   for (uint32_t seg = 0; seg < cnt; seg += kListCap) {
     const int m = (int)min((uint32_t)kListCap, cnt - seg);
     bucket_order<NT>(entries + start + seg, m, s_e, reinterpret_cast<uint16_t *>(s_raw), s_cnt, s_lo, s_red);
-    // each warp walks the sorted segment on its own, 32 entries at a time; a
-    // pixel is finished once its hit is nearer than the next entry's nearest
-    // possible depth
+    // each warp walks the sorted segment on its own, 32 entries at a time, the next window's records
+    // arriving by cp.async while the current one is tested; a pixel is finished once its hit is nearer
+    // than the next entry's nearest possible depth
     bool done = !inside;
-    for (int c0 = 0; c0 < m; c0 += 32) {
+    int wb = 0;
+    raster_stage(recs, s_e, m, 0, s_w, lane);
+    for (int c0 = 0; c0 < m; c0 += 32, wb ^= 32) {
       if (!done && (uint32_t)(best >> 32) < (uint32_t)(s_e[c0] >> 32)) done = true;
       if (__all_sync(0xffffffffu, done)) break;
+      raster_stage(recs, s_e, m, c0 + 32, s_w + (wb ^ 32), lane);
+      cp_async_wait<1>();  // this window's copies have landed (the next window's may still be in flight)
+      __syncwarp();
+      const PrimRec *win = s_w + wb;
       const unsigned x0 = __reduce_min_sync(0xffffffffu, done ? 0xffffffffu : (unsigned)px);
       const unsigned x1 = __reduce_max_sync(0xffffffffu, done ? 0u : (unsigned)px);
       const unsigned y0 = __reduce_min_sync(0xffffffffu, done ? 0xffffffffu : (unsigned)py);
       const unsigned y1 = __reduce_max_sync(0xffffffffu, done ? 0u : (unsigned)py);
-      bool keep = false;
-      if (c0 + lane < m) {
-        const PrimRec p = recs[(uint32_t)s_e[c0 + lane]];
-        s_w[lane] = p;
-        keep = raster_keep(p, x0, x1, y0, y1, uu_max);
-      }
+      const bool keep = c0 + lane < m && raster_keep(win[lane], x0, x1, y0, y1, uu_max);
       const unsigned kept = __ballot_sync(0xffffffffu, keep);
-      __syncwarp();
       for (unsigned b = kept; b != 0u; b &= b - 1u) {
         const int q = __ffs(b) - 1;
         if (done) continue;
@@ -1134,7 +1180,7 @@ __global__ __launch_bounds__(TW *TH) void k_raster(Geometry g, const PrimRec *__
           done = true;
           continue;
         }
-        const PrimRec &p = s_w[q];
+        const PrimRec &p = win[q];
         float3 o = local_o(p.u0h, p.u0l, p.v0h, p.v0l, p.k, p.dz, r);
         float s;
         bool hit;
@@ -1150,8 +1196,9 @@ __global__ __launch_bounds__(TW *TH) void k_raster(Geometry g, const PrimRec *__
           best = key < best ? key : best;
         }
       }
-      __syncwarp();
+      __syncwarp();  // every lane is done with this window before it is refilled
     }
+    cp_async_wait<0>();  // no copy may still target the windows when the next segment reuses them
     __syncthreads();
   }
   if (inside) *K = best;
@@ -1185,14 +1232,19 @@ __device__ __forceinline__ void resolve_pixel(const Geometry &g, const ShadePara
                                               const uint8_t *__restrict__ elem, const uint2 *__restrict__ bonds,
                                               const ImageState *__restrict__ st,
                                               const unsigned long long *__restrict__ keys, const Outputs &out,
-                                              int do_ssao, int img, int px, int py, unsigned long long key) {
+                                              int do_ssao, int img, int px, int py, unsigned long long key, Status *status) {
   const long long ppi = g.pix_per_img;
   {
     const long long p = (long long)py * g.W + px;
     const long long q = (long long)img * ppi + p;
-    const uint32_t id = (uint32_t)key;
+    uint32_t id = (uint32_t)key;
     float *nrm = out.normal + (long long)img * 3 * ppi + p;
     float *rgb = out.rgb + (long long)img * 3 * ppi + p;
+    // bounds check of the decoded id (a corrupted key): recorded in the status word, drawn as background
+    if (id != kNoId && (long long)id >= g.n_atoms + g.n_bonds) {
+      atomicOr(&status->overflow, 32u);
+      id = kNoId;
+    }
     if (id == kNoId) {
       out.depth[q] = __int_as_float(0x7f800000);
       out.id[q] = kNoId;
@@ -1337,7 +1389,7 @@ __global__ __launch_bounds__(256, VTX_RESOLVE_MINB) void k_resolve(Geometry g, S
                                                  const uint8_t *__restrict__ elem, const uint2 *__restrict__ bonds,
                                                  const ImageState *__restrict__ st,
                                                  const unsigned long long *__restrict__ keys, Outputs out,
-                                                 int do_ssao) {
+                                                 int do_ssao, Status *status) {
   pdl_enter();
   const int px = blockIdx.x * 32 + (threadIdx.x & 31);
   const int py0 = blockIdx.y * 32 + (threadIdx.x >> 5);
@@ -1355,7 +1407,7 @@ __global__ __launch_bounds__(256, VTX_RESOLVE_MINB) void k_resolve(Geometry g, S
     k1 = k2;
     k2 = k3;
     const int py = py0 + 8 * i;
-    if (py < g.H) resolve_pixel(g, sh, frames, elem, bonds, st, keys, out, do_ssao, img, px, py, key);
+    if (py < g.H) resolve_pixel(g, sh, frames, elem, bonds, st, keys, out, do_ssao, img, px, py, key, status);
   }
 }
 
@@ -1427,7 +1479,7 @@ __global__ __launch_bounds__(256, VTX_RESOLVE_MINB) void k_resolve_split(
     Geometry g, ShadeParams sh, const float4 *__restrict__ frames, const uint8_t *__restrict__ elem,
     const uint2 *__restrict__ bonds, const ImageState *__restrict__ st, const unsigned long long *__restrict__ keys,
     Outputs out, int do_ssao, const uint32_t *__restrict__ cov, const uint32_t *__restrict__ mask,
-    const Status *__restrict__ status, int n_shade) {
+    Status *status, int n_shade) {
   pdl_enter();
   const long long ppi = g.pix_per_img;
   if ((int)blockIdx.x < n_shade) {
@@ -1437,7 +1489,7 @@ __global__ __launch_bounds__(256, VTX_RESOLVE_MINB) void k_resolve_split(
       const int img = (int)(q / ppi);
       const long long p = q - (long long)img * ppi;
       const int py = (int)(p / g.W), px = (int)(p - (long long)py * g.W);
-      resolve_pixel(g, sh, frames, elem, bonds, st, keys, out, do_ssao, img, px, py, keys[q]);
+      resolve_pixel(g, sh, frames, elem, bonds, st, keys, out, do_ssao, img, px, py, keys[q], status);
     }
     return;
   }
@@ -1536,7 +1588,9 @@ cudaError_t run_binning(const Geometry &g, const Scene &sc, const Scratch &s, cu
     long long want = (5LL * sms + g.n_frames - 1) / g.n_frames;
     if (want < 1) want = 1;
     int bx = (int)(chunks < want ? (chunks > 0 ? chunks : 1) : want);
-    dim3 grid(bx, g.n_frames);
+    // few chunks (a small system seen from many views): one view per CTA
+    const int vg = (g.n_views > 1 && (long long)bx * g.n_frames < 2LL * sms) ? g.n_views : 1;
+    dim3 grid(bx, g.n_frames, vg);
     if (g.n_views == 1 && g.n_frames == 1 && sc.counts == nullptr && !g.soft) {
       const int b1 = (int)cull_one_ctas(g.n_atoms);
       const bool plain = g.mode == 0 && !g.clip_on;
@@ -1612,16 +1666,24 @@ cudaError_t run_frame_pipeline(const Geometry &g, const ShadeParams &sh, const S
   const long long n_tiles = (long long)g.n_img * g.tiles_per_img;
   const unsigned rgrid = (unsigned)(n_tiles < (long long)VTX_RASTER_GRID * sm_count() ? n_tiles
                                                                           : (long long)VTX_RASTER_GRID * sm_count());
+  static bool rattr = false;
+  if (!rattr) {
+    cudaFuncSetAttribute(k_raster<16, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)raster_smem<256>());
+    cudaFuncSetAttribute(k_raster<32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)raster_smem<256>());
+    cudaFuncSetAttribute(k_raster<8, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)raster_smem<64>());
+    rattr = true;
+  }
   if (g.tile_w == 16 && g.tile_h == 16)
-    launch_pdl(k_raster<16, 16>, rgrid, 256, 0, st, g, s.recs, s.entries, s.cap_entries, s.tile_count,
-                                                        s.tile_start, s.state, s.keys, s.tile_list, s.status);
+    launch_pdl(k_raster<16, 16>, rgrid, 256, raster_smem<256>(), st, g, s.recs, s.entries, s.cap_entries,
+               s.tile_count, s.tile_start, s.state, s.keys, s.tile_list, s.status);
   else if (g.tile_w == 32 && g.tile_h == 8)
-    launch_pdl(k_raster<32, 8>, rgrid, 256, 0, st, g, s.recs, s.entries, s.cap_entries, s.tile_count,
-                                                       s.tile_start, s.state, s.keys, s.tile_list, s.status);
+    launch_pdl(k_raster<32, 8>, rgrid, 256, raster_smem<256>(), st, g, s.recs, s.entries, s.cap_entries,
+               s.tile_count, s.tile_start, s.state, s.keys, s.tile_list, s.status);
   else
-    launch_pdl(k_raster<8, 8>, rgrid, 64, 0, st, g, s.recs, s.entries, s.cap_entries, s.tile_count,
-                                                     s.tile_start, s.state, s.keys, s.tile_list, s.status);
+    launch_pdl(k_raster<8, 8>, rgrid, 64, raster_smem<64>(), st, g, s.recs, s.entries, s.cap_entries,
+               s.tile_count, s.tile_start, s.state, s.keys, s.tile_list, s.status);
   ev_rec(evs, 5, st);
+  if (sc.dbg_corrupt_key && s.keys) cudaMemsetAsync(s.keys, 0x7f, sizeof(unsigned long long), st);  // test hook
   if (VTX_RESOLVE_2PASS && s.cov_list) {
     const int sms = sm_count();
     const long long total = g.pix_per_img * g.n_img;
@@ -1646,7 +1708,8 @@ cudaError_t run_frame_pipeline(const Geometry &g, const ShadeParams &sh, const S
     }
   } else {
     dim3 grid((g.W + 31) / 32, (g.H + 31) / 32, g.n_img);
-    launch_pdl(k_resolve, grid, 256, 0, st, g, sh, Xr, sc.elem, sc.bonds, s.state, s.keys, out, ssao ? 1 : 0);
+    launch_pdl(k_resolve, grid, 256, 0, st, g, sh, Xr, sc.elem, sc.bonds, s.state, s.keys, out, ssao ? 1 : 0,
+               s.status);
     ev_rec(evs, 6, st);
   }
   ev_rec(evs, 7, st);

@@ -42,8 +42,10 @@ struct __align__(16) SoftPrim {
   float u0h, u0l, v0h, v0l;   // projected reference point (pixels), double-float
   float k, dz, zr, rad;       // A per pixel at zr, zr - centre depth, reference depth, radius
   float fz, inv_rad, eta, rej2;  // f / centre depth, 1 / rad, 0.05 rad, bound on rho^2 of a used sphere
+  float rpx2;                 // rej2 / k^2 (px^2) when dz = 0, else +inf: the pixel-distance pre-test
+  float pad[3];
 };
-static_assert(sizeof(SoftPrim) == 48, "SoftPrim is three 16-byte words");
+static_assert(sizeof(SoftPrim) == 64, "SoftPrim is four 16-byte words");
 static_assert(kSoftNT * sizeof(SoftPrim) >= kSoftCap * sizeof(uint16_t), "the record windows hold the sort's offsets");
 
 constexpr size_t kSoftSmem = kSoftCap * sizeof(unsigned long long) + kSoftNT * sizeof(SoftPrim);
@@ -65,6 +67,11 @@ __device__ __forceinline__ SoftPrim soft_prim(const PrimRec &p, float f) {
   // 0.05 % so that rounding never drops a sphere the exact test keeps.
   const float reach = p.rad + 4.0f / s.fz;
   s.rej2 = reach * reach * 1.001f + 1e-6f;
+  // with dz = 0 the offset is o = k (dx, -dy, 0) and rho^2 >= |o|^2 / |u|^2 (Cauchy-Schwarz on its x, y part),
+  // so d^2 > rej2 |u|^2 / k^2 (d: pixel distance to the projected centre) rejects the sphere; the 0.1 % in
+  // rej2 covers the FP32 rounding of this quotient
+  s.rpx2 = p.dz == 0.0f ? s.rej2 / (p.k * p.k) : __int_as_float(0x7f800000);
+  s.pad[0] = s.pad[1] = s.pad[2] = 0.0f;
   return s;
 }
 
@@ -90,18 +97,24 @@ struct SoftTerm {
 };
 
 // The soft term of one sphere for one pixel; false when delta < -4 px.
-__device__ __forceinline__ bool soft_term(const SoftPrim &p, const SoftPix &x, float inv_sigma, SoftTerm &o) {
+// nl2s = -log2(e) / sigma, so that exp(-delta / sigma) = 2^(delta nl2s).
+__device__ __forceinline__ bool soft_term(const SoftPrim &p, const SoftPix &x, float nl2s, SoftTerm &o) {
   const PixRay &r = x.r;
-  o.ov = local_o(p.u0h, p.u0l, p.v0h, p.v0l, p.k, p.dz, r);
+  const float ox = __fsub_rn(__fsub_rn(r.pxc, p.u0h), p.u0l);
+  const float oy = __fsub_rn(__fsub_rn(r.pyc, p.v0h), p.v0l);
+  if (fmaf(ox, ox, oy * oy) > p.rpx2 * r.uu) return false;  // pixel-distance pre-test
+  o.ov = make_float3(__fmul_rn(p.k, ox), __fmul_rn(-p.k, oy), p.dz);  // local_o
   const float ou = fmaf(o.ov.x, r.a, fmaf(o.ov.y, r.b, o.ov.z));
   const float oo = fmaf(o.ov.x, o.ov.x, fmaf(o.ov.y, o.ov.y, o.ov.z * o.ov.z));
   o.sst = -ou * x.inv_uu;
   o.rho2 = fmaxf(fmaf(ou, o.sst, oo), 0.0f);  // |o|^2 - (o.u)^2 / |u|^2
   if (o.rho2 > p.rej2) return false;
   o.rho2s = o.rho2 + 1e-12f;
-  o.delta = (p.rad - sqrtf(o.rho2s)) * p.fz;
+  // hardware approximations (relative errors near 1e-7; the outputs' tolerance is 5e-5): sqrt as x rsqrt(x),
+  // the sigmoid through ex2.approx and rcp.approx
+  o.delta = (p.rad - o.rho2s * rsqrtf(o.rho2s)) * p.fz;
   if (!(o.delta >= -4.0f)) return false;
-  o.sg = __frcp_rn(1.0f + expf(-o.delta * inv_sigma));
+  o.sg = rcp_approx(1.0f + exp2_approx(o.delta * nl2s));
   o.alpha = fminf(kAMax, o.sg);
   o.m = fmaxf(fmaf(p.rad, p.rad, -o.rho2), 0.0f);
   const float m2 = fmaf(p.eta, p.eta, o.m);
@@ -229,8 +242,10 @@ __device__ __forceinline__ bool soft_load(const Geometry &g, const unsigned long
   const int tx = t % g.tiles_x, ty = t / g.tiles_x;
   T.px0 = tx * 16;
   T.py0 = ty * 16;
-  T.px = T.px0 + (threadIdx.x & 15);
-  T.py = T.py0 + (threadIdx.x >> 4);
+  // warp w covers the 8x4 block (w & 1, w >> 1) of the tile; lane l its pixel (l & 7, l >> 3)
+  const int w = (int)(threadIdx.x >> 5), l = (int)(threadIdx.x & 31);
+  T.px = T.px0 + 8 * (w & 1) + (l & 7);
+  T.py = T.py0 + 4 * (w >> 1) + (l >> 3);
   T.inside = T.px < g.W && T.py < g.H;
   uint32_t cnt = tile_count[gt];
   T.start = tile_start[gt];
@@ -252,8 +267,9 @@ __device__ __forceinline__ bool soft_load(const Geometry &g, const unsigned long
 // pixels): it stages 32 entries at a time, lane i converting entry c0 + i, in
 // its private 32-slot window of shared memory.
 //
-// Staging also culls the window for the warp.  The warp covers two 16-pixel
-// rows; `am` marks the lanes still compositing.  For a sphere whose reference
+// Staging also culls the window for the warp.  The warp covers an 8x4 pixel
+// block (lane l at column l & 7, row l >> 3); `am` marks the lanes still
+// compositing.  For a sphere whose reference
 // point is its centre (dz = 0) the offset at the reference depth is
 // o = k (du, -dv, 0) with (du, dv) the pixel offset from the projected centre,
 // and rho^2 = |o|^2 - (o.u)^2 / |u|^2 >= |o|^2 / |u|^2 (Cauchy-Schwarz on the
@@ -271,9 +287,11 @@ __device__ __forceinline__ unsigned soft_stage(const Geometry &g, const PrimRec 
   if (j < T.m) {
     const SoftPrim sp = soft_prim(recs[rec_of[(long long)T.img * g.n_atoms + (uint32_t)s_e[j]]], f);
     s_w[lane] = sp;
-    const unsigned cols = (am | (am >> 16)) & 0xffffu;
+    const unsigned cols = (am | (am >> 8) | (am >> 16) | (am >> 24)) & 0xffu;
+    const unsigned rows = ((am & 0xffu) ? 1u : 0u) | ((am & 0xff00u) ? 2u : 0u) | ((am & 0xff0000u) ? 4u : 0u) |
+                          ((am & 0xff000000u) ? 8u : 0u);
     const float rx0 = col0 + (float)(__ffs(cols) - 1), rx1 = col0 + (float)(31 - __clz(cols));
-    const float ry0 = row0 + ((am & 0xffffu) ? 0.0f : 1.0f), ry1 = row0 + ((am >> 16) ? 1.0f : 0.0f);
+    const float ry0 = row0 + (float)(__ffs(rows) - 1), ry1 = row0 + (float)(31 - __clz(rows));
     const float cu = sp.u0h + sp.u0l, cv = sp.v0h + sp.v0l;
     const float dx = fmaxf(fmaxf(rx0 - cu, cu - rx1), 0.0f);
     const float dy = fmaxf(fmaxf(ry0 - cv, cv - ry1), 0.0f);
@@ -284,13 +302,19 @@ __device__ __forceinline__ unsigned soft_stage(const Geometry &g, const PrimRec 
   return __ballot_sync(0xffffffffu, keep);
 }
 
-__global__ __launch_bounds__(kSoftNT) void k_soft_fwd(Geometry g, const PrimRec *__restrict__ recs,
+// state (optional, [n_img][H][W]): per pixel the final transmittance (float
+// bits) and 1 + the sorted-list position of its last contributor (0: none),
+// which lets the backward pass start its back-to-front walk directly.
+#ifndef VTX_SOFT_FWD_MINB
+#define VTX_SOFT_FWD_MINB 4
+#endif
+__global__ __launch_bounds__(kSoftNT, VTX_SOFT_FWD_MINB) void k_soft_fwd(Geometry g, const PrimRec *__restrict__ recs,
                                                       const uint32_t *__restrict__ rec_of,
                                                       const unsigned long long *__restrict__ entries,
                                                       unsigned long long cap_entries,
                                                       const uint32_t *__restrict__ tile_count,
                                                       const uint32_t *__restrict__ tile_start, Status *status,
-                                                      float *cov, float *dep, float *nrm) {
+                                                      float *cov, float *dep, float *nrm, uint2 *state) {
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned long long *s_e = reinterpret_cast<unsigned long long *>(smem);
   SoftPrim *s_w = reinterpret_cast<SoftPrim *>(smem + kSoftCap * sizeof(unsigned long long)) + (threadIdx.x & ~31);
@@ -300,9 +324,13 @@ __global__ __launch_bounds__(kSoftNT) void k_soft_fwd(Geometry g, const PrimRec 
   const ViewParams &v = g.views[T.img % g.n_views];
   const SoftPix x = soft_pix(v, T.px, T.py);
   const float inv_sigma = 1.0f / g.sigma;
+  const float nl2s = -1.4426950408889634f * inv_sigma;  // exp(-delta / sigma) = 2^(delta nl2s)
   const float uu_max = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(x.r.uu)));
-  const float col0 = (float)T.px0 + 0.5f, row0 = (float)(T.py0 + 2 * (int)(threadIdx.x >> 5)) + 0.5f;
+  const float col0 = (float)(T.px0 + 8 * (int)((threadIdx.x >> 5) & 1)) + 0.5f;
+  const float row0 = (float)(T.py0 + 4 * (int)(threadIdx.x >> 6)) + 0.5f;
   float A = 0.0f, D = 0.0f, N0 = 0.0f, N1 = 0.0f, N2 = 0.0f, Tr = 1.0f;
+  int last = -1;
+  unsigned used = 0u;
   bool done = !T.inside;
   if (any) {
     for (int c0 = 0; c0 < T.m; c0 += 32) {
@@ -312,8 +340,9 @@ __global__ __launch_bounds__(kSoftNT) void k_soft_fwd(Geometry g, const PrimRec 
       __syncwarp();
       for (unsigned b = keep; b != 0u; b &= b - 1u) {
         if (done) continue;
+        const int q = __ffs(b) - 1;
         SoftTerm o;
-        if (!soft_term(s_w[__ffs(b) - 1], x, inv_sigma, o)) continue;
+        if (!soft_term(s_w[q], x, nl2s, o)) continue;
         const float w = o.alpha * Tr;
         A += w;
         D = fmaf(w, o.t, D);
@@ -321,12 +350,20 @@ __global__ __launch_bounds__(kSoftNT) void k_soft_fwd(Geometry g, const PrimRec 
         N1 = fmaf(w, o.n.y, N1);
         N2 = fmaf(-w, o.n.z, N2);
         Tr *= 1.0f - o.alpha;
+        last = c0 + q;
+        ++used;
         if (Tr < kTStop) done = true;
       }
       __syncwarp();
     }
   }
+  // composited terms, one atomic per warp (the algorithmic work of the pass)
+  const unsigned wused = __reduce_add_sync(0xffffffffu, used);
+  if ((threadIdx.x & 31) == 0 && wused) atomicAdd(&status->n_terms, (unsigned long long)wused);
   if (T.inside) {
+    if (state)
+      state[(long long)T.img * g.pix_per_img + (long long)T.py * g.W + T.px] =
+          make_uint2(__float_as_uint(Tr), (uint32_t)(last + 1));
     const long long ppi = g.pix_per_img;
     const long long p = (long long)T.py * g.W + T.px;
     cov[(long long)T.img * ppi + p] = A;
@@ -362,7 +399,7 @@ __global__ __launch_bounds__(kSoftNT) void k_soft_bwd(Geometry g, const PrimRec 
                                                       const uint32_t *__restrict__ tile_count,
                                                       const uint32_t *__restrict__ tile_start, Status *status,
                                                       const float *gcov, const float *gdep, const float *gnrm,
-                                                      float *grad) {
+                                                      const uint2 *__restrict__ state, float *grad) {
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned long long *s_e = reinterpret_cast<unsigned long long *>(smem);
   SoftPrim *s_w = reinterpret_cast<SoftPrim *>(smem + kSoftCap * sizeof(unsigned long long)) + (threadIdx.x & ~31);
@@ -374,6 +411,7 @@ __global__ __launch_bounds__(kSoftNT) void k_soft_bwd(Geometry g, const PrimRec 
   const SoftPix x = soft_pix(v, T.px, T.py);
   const PixRay &r = x.r;
   const float inv_sigma = 1.0f / g.sigma;
+  const float nl2s = -1.4426950408889634f * inv_sigma;
   const long long ppi = g.pix_per_img;
   const long long p = (long long)T.py * g.W + T.px;
   float gA = 0.0f, gD = 0.0f;
@@ -388,13 +426,23 @@ __global__ __launch_bounds__(kSoftNT) void k_soft_bwd(Geometry g, const PrimRec 
     }
   }
   const bool need = T.inside && (gA != 0.0f || gD != 0.0f || gN.x != 0.0f || gN.y != 0.0f || gN.z != 0.0f);
-  // pass 1: front to back, last contributor and final transmittance
+  // pass 1: front to back, last contributor and final transmittance (read from the forward call's state
+  // when it left one)
   const float uu_max = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(r.uu)));
-  const float col0 = (float)T.px0 + 0.5f, row0 = (float)(T.py0 + 2 * (int)(threadIdx.x >> 5)) + 0.5f;
+  const float col0 = (float)(T.px0 + 8 * (int)((threadIdx.x >> 5) & 1)) + 0.5f;
+  const float row0 = (float)(T.py0 + 4 * (int)(threadIdx.x >> 6)) + 0.5f;
   float Tr = 1.0f;
   int last = -1;
   bool done = !need;
-  for (int c0 = 0; c0 < T.m; c0 += 32) {
+  if (state) {
+    if (need) {
+      const uint2 sv = state[(long long)T.img * ppi + p];
+      Tr = __uint_as_float(sv.x);
+      last = min((int)sv.y - 1, T.m - 1);
+    }
+    done = true;
+  }
+  for (int c0 = 0; c0 < T.m && !__all_sync(0xffffffffu, done); c0 += 32) {
     const unsigned am = __ballot_sync(0xffffffffu, !done);
     if (am == 0u) break;
     const unsigned keep = soft_stage(g, recs, rec_of, s_e, T, c0, v.f, s_w, am, col0, row0, uu_max);
@@ -403,7 +451,7 @@ __global__ __launch_bounds__(kSoftNT) void k_soft_bwd(Geometry g, const PrimRec 
       if (done) continue;
       const int q = __ffs(b) - 1;
       SoftTerm o;
-      if (!soft_term(s_w[q], x, inv_sigma, o)) continue;
+      if (!soft_term(s_w[q], x, nl2s, o)) continue;
       Tr *= 1.0f - o.alpha;
       last = c0 + q;
       if (Tr < kTStop) done = true;
@@ -429,7 +477,7 @@ __global__ __launch_bounds__(kSoftNT) void k_soft_bwd(Geometry g, const PrimRec 
       const SoftPrim &pr = s_w[q];
       float gx = 0.0f, gy = 0.0f, gz = 0.0f, grr = 0.0f;
       SoftTerm o;
-      if (c0 + q <= last && soft_term(pr, x, inv_sigma, o)) {
+      if (c0 + q <= last && soft_term(pr, x, nl2s, o)) {
         const float Ti = Tc / (1.0f - o.alpha);
         const float w = o.alpha * Ti;
         const float ci = gA + gD * o.t + gN.x * o.n.x + gN.y * o.n.y + gN.z * o.n.z;
@@ -485,7 +533,7 @@ __global__ __launch_bounds__(kSoftNT) void k_soft_bwd(Geometry g, const PrimRec 
 
 cudaError_t run_soft_pipeline(const Geometry &g, const Scene &sc, const Scratch &s, float *cov, float *depth,
                               float *normal, const float *g_cov, const float *g_depth, const float *g_normal,
-                              float *grad, cudaStream_t st, StageEvents *evs) {
+                              float *grad, uint2 *state, cudaStream_t st, StageEvents *evs) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_soft_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSoftSmem);
@@ -498,12 +546,12 @@ cudaError_t run_soft_pipeline(const Geometry &g, const Scene &sc, const Scratch 
   if (grad == nullptr) {
     k_soft_fwd<<<(unsigned)n_tiles, kSoftNT, kSoftSmem, st>>>(g, s.recs, s.rec_of, s.entries, s.cap_entries,
                                                              s.tile_count, s.tile_start, s.status, cov, depth,
-                                                             normal);
+                                                             normal, state);
   } else {
     cudaMemsetAsync(grad, 0, sizeof(float) * 4 * (size_t)g.n_atoms, st);
     k_soft_bwd<<<(unsigned)n_tiles, kSoftNT, kSoftSmem, st>>>(g, s.recs, s.rec_of, s.entries, s.cap_entries,
                                                              s.tile_count, s.tile_start, s.status, g_cov, g_depth,
-                                                             g_normal, grad);
+                                                             g_normal, state, grad);
   }
   if (evs && evs->ev && evs->n > 5) cudaEventRecord(evs->ev[5], st);
   if (evs && evs->ev && evs->n > 6) cudaEventRecord(evs->ev[6], st);

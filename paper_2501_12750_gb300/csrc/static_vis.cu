@@ -9,10 +9,11 @@
 // allocates nothing.  The caller passes device inputs and outputs.
 //
 // The kernels here are a compact variant of the frame pipeline: the same
-// conservative cull test, precise double-float setup and 64-bit atomicMin
-// merge as the main path, but every surviving sphere is ray-cast directly
-// over its whole candidate pixel box (no tile binning), which suits the
-// small images this entry point is limited to.
+// camera check and per-camera constants, conservative cull test, precise
+// double-float setup and 64-bit atomicMin merge as the main path, but every
+// surviving sphere is ray-cast directly over its candidate pixel box (no
+// tile binning), which suits the small images this entry point is limited
+// to; a box of more than 64 pixels is shared by the 32 lanes of a warp.
 #include <mutex>
 
 #include "../../include/vtx.h"
@@ -92,29 +93,69 @@ __global__ void k_static_finalize(ViewParams v, unsigned long long *scratch) {
   h->valid = 1u;
 }
 
+// Candidate boxes of more than kStaticBig pixels are ray-cast by the whole warp (lane l takes pixels
+// l, l + 32, ...), so no thread tests more than ceil(W H / 32) pixels for one sphere, however close it is.
+constexpr long long kStaticBig = 64;
+
+__device__ __forceinline__ void static_hit(const ViewParams &v, int W, const Setup &su, float rad, uint32_t id,
+                                           float S, int px, int py, unsigned long long *K) {
+  const PixRay r = pix_ray(v, px, py);
+  const float3 o = local_o(su.u0.hi, su.u0.lo, su.v0.hi, su.v0.lo, su.k, su.dz, r);
+  float s;
+  if (sphere_local(o, r, rad, s) && su.zr + s >= v.znear)
+    atomicMin(K + (long long)py * W + px, pack_key(su.keyc, s, S, id));
+}
+
 __global__ void k_static_splat(ViewParams v, int W, int H, const float4 *__restrict__ X, long long n,
                                unsigned long long *scratch) {
   const StaticHead *h = reinterpret_cast<const StaticHead *>(scratch);
   if (!h->valid) return;
   const float zlo = h->zlo, S = h->S;
   unsigned long long *K = scratch + kStaticHead;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const float4 a = X[i];
-    float vx, vy, vz, Rm;
-    if (!static_cull(v, a, vx, vy, vz, Rm)) continue;
-    PixBox b;
-    if (!lean_box(v, W, H, vx, vy, vz, Rm, b)) continue;
-    df dx, dy, dz;
-    eye_offset(v, a, dx, dy, dz);
-    const Setup su = precise_setup(v, dx, dy, dz, a.w, zlo, S);
-    for (int py = b.y0; py <= b.y1; ++py)
-      for (int px = b.x0; px <= b.x1; ++px) {
-        const PixRay r = pix_ray(v, px, py);
-        const float3 o = local_o(su.u0.hi, su.u0.lo, su.v0.hi, su.v0.lo, su.k, su.dz, r);
-        float s;
-        if (sphere_local(o, r, a.w, s) && su.zr + s >= v.znear)
-          atomicMin(K + (long long)py * W + px, pack_key(su.keyc, s, S, (uint32_t)i));
+  const int lane = threadIdx.x & 31;
+  const long long n_warps = ((long long)gridDim.x * blockDim.x) >> 5;
+  // one atom per lane; the trip count is the same for all lanes of a warp
+  for (long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w * 32 < n; w += n_warps) {
+    const long long i = w * 32 + lane;
+    bool have = false;
+    PixBox b{0, -1, 0, -1};
+    Setup su;
+    float rad = 0.0f;
+    if (i < n) {
+      const float4 a = X[i];
+      float vx, vy, vz, Rm;
+      if (static_cull(v, a, vx, vy, vz, Rm) && lean_box(v, W, H, vx, vy, vz, Rm, b)) {
+        df dx, dy, dz;
+        eye_offset(v, a, dx, dy, dz);
+        su = precise_setup(v, dx, dy, dz, a.w, zlo, S);
+        rad = a.w;
+        have = true;
       }
+    }
+    const long long npx = have ? (long long)(b.x1 - b.x0 + 1) * (long long)(b.y1 - b.y0 + 1) : 0;
+    const bool big = npx > kStaticBig;
+    if (have && !big)
+      for (int py = b.y0; py <= b.y1; ++py)
+        for (int px = b.x0; px <= b.x1; ++px) static_hit(v, W, su, rad, (uint32_t)i, S, px, py, K);
+    for (unsigned bigm = __ballot_sync(0xffffffffu, big); bigm != 0u; bigm &= bigm - 1u) {
+      const int src = __ffs(bigm) - 1;
+      Setup sb;
+      sb.u0.hi = __shfl_sync(0xffffffffu, su.u0.hi, src);
+      sb.u0.lo = __shfl_sync(0xffffffffu, su.u0.lo, src);
+      sb.v0.hi = __shfl_sync(0xffffffffu, su.v0.hi, src);
+      sb.v0.lo = __shfl_sync(0xffffffffu, su.v0.lo, src);
+      sb.zr = __shfl_sync(0xffffffffu, su.zr, src);
+      sb.dz = __shfl_sync(0xffffffffu, su.dz, src);
+      sb.k = __shfl_sync(0xffffffffu, su.k, src);
+      sb.keyc = __shfl_sync(0xffffffffu, su.keyc, src);
+      const float rb = __shfl_sync(0xffffffffu, rad, src);
+      const int x0 = __shfl_sync(0xffffffffu, b.x0, src), x1 = __shfl_sync(0xffffffffu, b.x1, src);
+      const int y0 = __shfl_sync(0xffffffffu, b.y0, src), y1 = __shfl_sync(0xffffffffu, b.y1, src);
+      const long long bw = x1 - x0 + 1, total = bw * (long long)(y1 - y0 + 1);
+      const uint32_t id = (uint32_t)(w * 32 + src);
+      for (long long q = lane; q < total; q += 32)
+        static_hit(v, W, sb, rb, id, S, x0 + (int)(q % bw), y0 + (int)(q / bw), K);
+    }
   }
 }
 
@@ -159,8 +200,7 @@ extern "C" vtx_status vtx_render_visibility_static(const float *xyzr, int64_t n_
   if (!cam || !depth || !id || n_atoms < 0 || n_atoms > 2147483647LL || (n_atoms > 0 && !xyzr))
     return VTX_ERR_INVALID_ARG;
   if (((uintptr_t)xyzr & 15u) != 0) return VTX_ERR_INVALID_ARG;
-  if (cam->width < 1 || cam->height < 1 || !(cam->tan_half_fovy > 0.0f) || !(cam->znear > 0.0f))
-    return VTX_ERR_INVALID_ARG;
+  if (!cam_ok(cam)) return VTX_ERR_INVALID_ARG;  // the same camera check as vtx_set_camera
   const long long n_px = (long long)cam->width * cam->height;
   if (n_px > VTX_STATIC_MAX_PIXELS) return VTX_ERR_CAPACITY;
   int dev = 0;
@@ -183,31 +223,7 @@ extern "C" vtx_status vtx_render_visibility_static(const float *xyzr, int64_t n_
     scratch = g_static_ptr[dev];
   }
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  ViewParams v;
-  {
-    // the same per-camera constants as the main path
-    for (int k = 0; k < 3; ++k) {
-      v.eye[k] = cam->eye[k];
-      v.R[k] = cam->right[k];
-      v.U[k] = cam->up[k];
-      v.F[k] = cam->forward[k];
-    }
-    const double f = (double)cam->height / (2.0 * (double)cam->tan_half_fovy);
-    v.f_hi = (float)f;
-    v.f_lo = (float)(f - (double)v.f_hi);
-    v.f = v.f_hi;
-    v.inv_f = (float)(1.0 / f);
-    v.cx = 0.5f * (float)cam->width;
-    v.cy = 0.5f * (float)cam->height;
-    v.znear = cam->znear;
-    v.pad0 = 0.0f;
-    v.hc = (float)(f * (1.0 + 4e-6));
-    v.e0 = (float)(1e-4 + 1e-6 * ((double)cam->width + (double)cam->height));
-    v.cxm = v.cx - 0.5f;
-    v.cym = v.cy - 0.5f;
-    v.wm1 = (float)(cam->width - 1);
-    v.hm1 = (float)(cam->height - 1);
-  }
+  const ViewParams v = make_view(*cam);  // the per-camera constants of the main path
   const int sms = sm_count();
   const float4 *X = (const float4 *)xyzr;
   const int ga = (int)(n_atoms / 256 + 1 < 8LL * sms ? n_atoms / 256 + 1 : 8LL * sms);

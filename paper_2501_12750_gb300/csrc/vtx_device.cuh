@@ -63,6 +63,7 @@ struct Geometry {
   float clip[4];         // clip plane (n, d); clip_on = n != 0
   int clip_on;
   int splat_max;         // max candidate pixels for the direct splat path
+  int dbg_first_wait;    // test hook: polls allowed for the multi-view cull's first stage wait (-1: normal limit)
   int soft;              // 1 = soft-edge binning (dilated bounds, no splat, every survivor binned)
   float sigma;           // soft: sigmoid width in pixels
   long long stride;      // atom records per frame slot
@@ -101,12 +102,14 @@ struct ImageState {
 // Launch-wide status (device memory, read back by the host).
 struct Status {
   unsigned int n_rec;           // binned records requested
-  unsigned int overflow;        // bit 0 survivors, 1 records, 2 entries, 3 soft tile list too long
+  unsigned int overflow;        // bit 0 survivors, 1 records, 2 entries, 3 soft tile list too long,
+                                // 4 a bounded wait gave up, 5 a decoded primitive id out of range
   unsigned long long n_entries; // binned (tile, primitive) entries requested
   unsigned int max_list;        // longest tile list seen by the raster stage
   unsigned int n_list;          // non-empty tiles listed by the scan (raster work list)
   unsigned int n_cov;           // covered pixels listed by the resolve's list pass
   unsigned int pad;
+  unsigned long long n_terms;   // soft forward: sigmoid terms composited (sum over pixels)
 };
 
 // A binned primitive staged through shared memory (64 bytes).  Its tile box
@@ -462,6 +465,13 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return r;
 }
 
+// 2^x by the hardware approximation (relative error near 2^-22, flushes subnormals).
+__device__ __forceinline__ float exp2_approx(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // The same test as cull_fast with its rounding margins folded into per-view
 // constants (ViewParams::hc, e0) and a 1-ulp approximate reciprocal:
 //   reciprocal and products: <= 3.6e-7 relative on the slopes, i.e. at most
@@ -587,6 +597,18 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
   for (uint32_t i = 0; i < limit; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
+}
+
+// 16-byte asynchronous copies global -> shared (sm_80+ PTX), completed per thread in commit groups; the
+// L2-only variant (.cg) leaves L1 to the kernel's other loads.
+__device__ __forceinline__ void cp_async16(void *dst_smem, const void *src_gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst_smem)), "l"(src_gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// Wait until at most N of the calling thread's commit groups are still in flight.
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 // Plain (non-transaction) arrival of the calling thread.

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/vtx.h"
 #include "vtx_device.cuh"
 
 namespace vtx {
@@ -37,6 +38,7 @@ struct Scene {
   const uint2 *bonds;         // [n_bonds] or null
   float4 *stage;              // single view, no bonds: device copy of the surviving records, written by the cull
                               // and read by setup and resolve instead of frames (frames in host memory), or null
+  bool dbg_corrupt_key = false;  // test hook: overwrite the first depth key with an out-of-range id after the raster
 };
 
 struct Outputs {
@@ -58,9 +60,11 @@ cudaError_t run_frame_pipeline(const Geometry &g, const ShadeParams &sh, const S
                                const Outputs &out, bool ssao, cudaStream_t st, StageEvents *evs);
 
 // Soft-edge pipeline (binning shared with the hard path); backward when grad != null.
+// state: optional per-pixel (final transmittance, 1 + last contributor) planes, written by the forward
+// call and read by the backward call (which then skips its front-to-back walk).
 cudaError_t run_soft_pipeline(const Geometry &g, const Scene &sc, const Scratch &s, float *cov, float *depth,
                               float *normal, const float *g_cov, const float *g_depth, const float *g_normal,
-                              float *grad, cudaStream_t st, StageEvents *evs);
+                              float *grad, uint2 *state, cudaStream_t st, StageEvents *evs);
 
 // Interleaved RGBA8 of n_img images of ppi pixels from the rgb and id planes (background alpha bg_a).
 cudaError_t run_export_rgba8(const float *rgb, const uint32_t *id, long long ppi, long long n_img, unsigned char bg_a,
@@ -90,6 +94,11 @@ long long ses_blocks(const int32_t dims[3]);
 int ses_window(float probe, float h);
 
 int sm_count();
+
+// Per-camera constants of the kernels (FP64-derived focal length, cull margins) and the host-side camera check
+// (sizes 1..16384, finite eye and basis, finite tan_half_fovy > 0 and znear > 0), shared by every entry point.
+ViewParams make_view(const vtx_camera &cam);
+bool cam_ok(const vtx_camera *c);
 
 // Extra survivor slots the single-view cull may leave as holes (per-warp slabs).
 long long cull_survivor_slack(long long n_atoms);
