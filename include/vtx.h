@@ -168,9 +168,21 @@ const char *vtx_version(void);
 vtx_status vtx_default_settings(vtx_settings *s);
 
 /*
- * Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
- * owned by the caller (NULL = the legacy default stream).  Allocates only a
- * few small host-pinned and device buffers; scratch grows on first use.
+ * A rendering context: the per-frame engine state of the paper's Molecular
+ * Graphics Engine (Methods; Implementation: one engine drawing the molecule
+ * every frame) -- the recorded molecule, the camera and the scratch memory
+ * the frame pipeline reuses from frame to frame.
+ *
+ * vtx_create: a context on CUDA device `device` (0..device count - 1, else
+ * VTX_ERR_INVALID_ARG; *out is set to NULL on failure).  `cuda_stream` is a
+ * cudaStream_t owned by the caller (NULL = the legacy default stream).
+ * Allocates only a few small host-pinned and device buffers (VTX_ERR_OOM
+ * when that fails); scratch grows on first use.
+ * vtx_destroy: synchronises the context's stream, then frees everything the
+ * context owns (never the caller's arrays or stream).  VTX_ERR_INVALID_ARG
+ * for NULL.
+ * vtx_set_stream: later calls enqueue on `cuda_stream`; cached batch graphs
+ * are dropped (they were captured on the previous stream).
  */
 vtx_status vtx_create(vtx_ctx **out, int32_t device, void *cuda_stream);
 vtx_status vtx_destroy(vtx_ctx *ctx);
@@ -204,7 +216,14 @@ vtx_status vtx_upload_atoms(vtx_ctx *ctx, const float *xyzr, const uint8_t *elem
  */
 vtx_status vtx_upload_bonds(vtx_ctx *ctx, const uint32_t *pairs, int64_t n_bonds);
 
-/* Set the camera for vtx_render_frame (copied). */
+/*
+ * Set the camera for vtx_render_frame (copied).  The paper's interaction
+ * modes (Improved user experience: trackball and free-fly cameras) end in
+ * one pinhole camera per frame; this is that camera, with the conventions
+ * stated at the top of this header.  VTX_ERR_INVALID_ARG when a size is
+ * outside 1..16384, tan_half_fovy or znear is not finite and positive, or a
+ * component of the eye or the basis is not finite.
+ */
 vtx_status vtx_set_camera(vtx_ctx *ctx, const vtx_camera *cam);
 
 /*
@@ -426,7 +445,12 @@ vtx_status vtx_tuned_settings(const vtx_ctx *ctx, int32_t *tile_w, int32_t *tile
 vtx_status vtx_debug_hooks(vtx_ctx *ctx, int32_t first_wait_polls, uint32_t cap_records, uint64_t cap_entries,
                            int32_t corrupt_key);
 
-/* Text of the most recent error on this context ("" if none). */
+/*
+ * Text of the most recent error on this context ("" if none; "null context"
+ * for NULL).  The engine's log of failures (the paper's console of logs,
+ * Figure 1) reduced to the last message; the pointer stays valid until the
+ * next call on the context.
+ */
 const char *vtx_last_error(const vtx_ctx *ctx);
 
 /*

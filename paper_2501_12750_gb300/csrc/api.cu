@@ -308,21 +308,24 @@ static vtx_status check_status(vtx_ctx *c) {
     return fail(c, VTX_ERR_BOUNDS, "a decoded primitive id was out of range (drawn as background); the frame is invalid");
   }
   std::string msg = "scratch capacity exceeded:";
+  unsigned long long need_e = s.n_entries;
   if (s.overflow & 2u) {
+    const unsigned long long written = c->cap_rec > 0 ? c->cap_rec : 1;
     unsigned long long need = (unsigned long long)s.n_rec;
     unsigned long long cap = need + need / 2 + 1024;
     if (cap > 0xfffffff0ull) cap = 0xfffffff0ull;
     if (cap > c->cap_rec) c->cap_rec = (uint32_t)cap;
+    // the tile entries were counted from the records that fitted only: scale them to all records, so one
+    // re-render suffices
+    if (need > written) need_e = (unsigned long long)((double)need_e * (double)need / (double)written);
     msg += " records";
   }
-  if (s.overflow & 4u) {
-    unsigned long long need = s.n_entries;
-    unsigned long long cap = need + need / 2 + 4096;
+  if ((s.overflow & 4u) || need_e > c->cap_entries) {
+    unsigned long long cap = need_e + need_e / 2 + 4096;
     if (cap > 0xfffffff0ull) cap = 0xfffffff0ull;
     if (cap > c->cap_entries) c->cap_entries = cap;
     msg += " tile entries";
   }
-  if (s.overflow & 8u) msg += " soft tile list longer than 4096";
   cudaMemsetAsync(c->status.p, 0, sizeof(Status), c->stream);
   drop_graphs(c);
   vtx_status st;
@@ -330,7 +333,6 @@ static vtx_status check_status(vtx_ctx *c) {
   if ((st = ensure(c, c->recimg, sizeof(uint32_t) * (size_t)c->cap_rec, "record images"))) return st;
   if ((st = ensure(c, c->recbox, sizeof(uint2) * (size_t)c->cap_rec, "record boxes"))) return st;
   if ((st = ensure(c, c->entries, sizeof(unsigned long long) * (size_t)c->cap_entries, "entries"))) return st;
-  if (s.overflow & 8u) return fail(c, VTX_ERR_CAPACITY, msg);
   return fail(c, VTX_ERR_CAPACITY, msg + " (arena grown; render again)");
 }
 
@@ -991,7 +993,6 @@ static vtx_status soft_run(vtx_ctx *c, const float *xyzr, int64_t n, const vtx_c
     st = check_status(c);
     if (st == VTX_OK) std::copy(key, key + 4, c->soft_sized);
     if (st != VTX_ERR_CAPACITY) return st;
-    if (c->h_status->overflow & 8u) return st;
     c->err.clear();
   }
   return st;

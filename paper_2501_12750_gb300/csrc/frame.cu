@@ -601,17 +601,13 @@ __global__ __launch_bounds__(256, VTX_SETUP_MINB) void k_setup(Geometry g, const
   unsigned long long *K = keys + (long long)img * g.pix_per_img;
   const int lane = threadIdx.x & 31;
   const long long stride = (long long)gridDim.x * blockDim.x;
-  // binned records are reserved once per CTA and iteration (a shared count, then one global atomic)
-  __shared__ unsigned s_blk_cnt, s_blk_base;
-  if (threadIdx.x == 0) s_blk_cnt = 0u;
-  __syncthreads();
   // two-stage prefetch: the id two iterations ahead, the atom record one ahead
   const long long k0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   uint32_t id_cur = k0 < n ? sv[k0] : 0u;
   uint32_t id_nxt = k0 + stride < n ? sv[k0 + stride] : 0u;
   float4 a_cur = (k0 < n && (long long)id_cur < g.n_atoms) ? X[id_cur] : zero4;
-  for (long long k = k0; k - threadIdx.x < n; k += stride) {  // same trip count for every thread of a CTA
+  for (long long k = k0; k - lane < n; k += stride) {  // the same trip count for the lanes of a warp
     const float4 a_nxt = (k + stride < n && (long long)id_nxt < g.n_atoms) ? X[id_nxt] : zero4;
     const uint32_t id_nn = k + 2 * stride < n ? sv[k + 2 * stride] : 0u;
     bool binned = false;
@@ -681,19 +677,12 @@ __global__ __launch_bounds__(256, VTX_SETUP_MINB) void k_setup(Geometry g, const
       }
     }
     const unsigned m = __ballot_sync(0xffffffffu, binned);
-    unsigned woff = 0u;
-    if (m && lane == __ffs(m) - 1) woff = atomicAdd(&s_blk_cnt, (unsigned)__popc(m));
-    woff = __shfl_sync(0xffffffffu, woff, m ? __ffs(m) - 1 : 0);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const unsigned c = s_blk_cnt;
-      s_blk_base = c ? atomicAdd(&status->n_rec, c) : 0u;
-      s_blk_cnt = 0u;
-    }
-    __syncthreads();
+    unsigned base = 0u;
+    if (m && lane == __ffs(m) - 1) base = atomicAdd(&status->n_rec, (unsigned)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, m ? __ffs(m) - 1 : 0);
     bool counted = false;
     if (binned) {
-      const unsigned slot = s_blk_base + woff + __popc(m & ((1u << lane) - 1u));
+      const unsigned slot = base + __popc(m & ((1u << lane) - 1u));
       if (slot < cap_rec) {
         recs[slot] = rec;
         rec_img[slot] = (uint32_t)img;
@@ -1228,6 +1217,11 @@ constexpr int kSsaoGroup = VTX_SSAO_GROUP;  // SSAO samples whose neighbour keys
 #define VTX_RESOLVE_2PASS 1
 #endif
 
+// A depth-key difference as float: the 32-bit conversion when it fits (the same rounding as the 64-bit one).
+__device__ __forceinline__ float key_diff_f(long long d) {
+  return (d >= -2147483647LL && d <= 2147483647LL) ? __int2float_rn((int)d) : (float)d;
+}
+
 __device__ __forceinline__ void resolve_pixel(const Geometry &g, const ShadeParams &sh, const float4 *__restrict__ frames,
                                               const uint8_t *__restrict__ elem, const uint2 *__restrict__ bonds,
                                               const ImageState *__restrict__ st,
@@ -1340,7 +1334,7 @@ __device__ __forceinline__ void resolve_pixel(const Geometry &g, const ShadePara
 #pragma unroll
         for (int u = 0; u < kSsaoGroup; ++u) {
           if ((uint32_t)kf[u] == kNoId) continue;
-          const float dzf = (float)((long long)(kf[u] >> 32) - kP) * s.invS;  // z_f - t
+          const float dzf = key_diff_f((long long)(kf[u] >> 32) - kP) * s.invS;  // z_f - t
           if (dzf <= dls[u] - sh.ssao_bias) {
             const float adz = fabsf(dzf);
             occ += adz <= R ? 1.0f : R / adz;
@@ -1361,7 +1355,7 @@ __device__ __forceinline__ void resolve_pixel(const Geometry &g, const ShadePara
       for (int u = 0; u < 4; ++u) {
         if (nx[u] < 0 || ny[u] < 0 || nx[u] >= g.W || ny[u] >= g.H) continue;
         const unsigned long long kq = Kimg[(long long)ny[u] * g.W + nx[u]];
-        if ((uint32_t)kq == kNoId || (float)((long long)(kq >> 32) - kP) * s.invS > sh.outline_depth) edge = true;
+        if ((uint32_t)kq == kNoId || key_diff_f((long long)(kq >> 32) - kP) * s.invS > sh.outline_depth) edge = true;
       }
       if (edge) col = make_float3(sh.outline_color[0], sh.outline_color[1], sh.outline_color[2]);
     }

@@ -131,6 +131,7 @@ struct SoftTile {
   int px0, py0;  // the tile's first column and row
   bool inside;
   uint32_t start;
+  const unsigned long long *list;  // the tile's entries in (centre-depth key, id) order: shared or global memory
 };
 
 // Exact ascending order of a tile's m entries (centre-depth key << 32 | id)
@@ -231,8 +232,48 @@ __device__ __forceinline__ void soft_order(const unsigned long long *__restrict_
   }
 }
 
-// Load and order a tile's entries (shared by forward and backward).
-__device__ __forceinline__ bool soft_load(const Geometry &g, const unsigned long long *entries,
+// Ascending order of a list too long for shared memory, sorted in place in global memory by the whole CTA:
+// a bitonic network written with ascending comparisons only (each stage first compares i with
+// i ^ (k - 1), then i with i + j), so that padding the list to a power of two with virtual +inf entries
+// never moves anything: no element is compared with a partner at or beyond m.
+__device__ __noinline__ void soft_sort_global(unsigned long long *a, int m) {
+  int n2 = 1;
+  while (n2 < m) n2 <<= 1;
+  const int half = n2 >> 1;
+  for (int k = 2; k <= n2; k <<= 1) {
+    const int hk = k >> 1;
+    for (int t = threadIdx.x; t < half; t += blockDim.x) {
+      const int i = (t / hk) * k + (t % hk);
+      const int q = i ^ (k - 1);
+      if (q < m) {
+        const unsigned long long x = a[i], y = a[q];
+        if (x > y) {
+          a[i] = y;
+          a[q] = x;
+        }
+      }
+    }
+    __syncthreads();
+    for (int j = k >> 2; j > 0; j >>= 1) {
+      for (int t = threadIdx.x; t < half; t += blockDim.x) {
+        const int i = (t / j) * 2 * j + (t % j);
+        const int q = i + j;
+        if (q < m) {
+          const unsigned long long x = a[i], y = a[q];
+          if (x > y) {
+            a[i] = y;
+            a[q] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Load and order a tile's entries (shared by forward and backward).  Up to kSoftCap entries are ordered
+// in shared memory; a longer list is ordered in place in the entry array, which the walk then reads.
+__device__ __forceinline__ bool soft_load(const Geometry &g, unsigned long long *entries,
                                           unsigned long long cap_entries, const uint32_t *tile_count,
                                           const uint32_t *tile_start, Status *status, unsigned long long *s_e,
                                           uint16_t *s_off, SoftTile &T) {
@@ -251,14 +292,16 @@ __device__ __forceinline__ bool soft_load(const Geometry &g, const unsigned long
   T.start = tile_start[gt];
   if ((unsigned long long)T.start >= cap_entries) cnt = 0;
   else if ((unsigned long long)T.start + cnt > cap_entries) cnt = (uint32_t)(cap_entries - T.start);
-  if (cnt > (uint32_t)kSoftCap) {
-    if (threadIdx.x == 0) atomicOr(&status->overflow, 8u);
-    cnt = kSoftCap;
-  }
   if (threadIdx.x == 0) atomicMax(&status->max_list, cnt);
   T.m = (int)cnt;
+  T.list = s_e;
   if (cnt == 0) return false;
-  soft_order(entries + T.start, T.m, s_e, s_off);
+  if (cnt <= (uint32_t)kSoftCap) {
+    soft_order(entries + T.start, T.m, s_e, s_off);
+  } else {
+    soft_sort_global(entries + T.start, T.m);
+    T.list = entries + T.start;
+  }
   return true;
 }
 
@@ -285,7 +328,7 @@ __device__ __forceinline__ unsigned soft_stage(const Geometry &g, const PrimRec 
   const int j = c0 + lane;
   bool keep = false;
   if (j < T.m) {
-    const SoftPrim sp = soft_prim(recs[rec_of[(long long)T.img * g.n_atoms + (uint32_t)s_e[j]]], f);
+    const SoftPrim sp = soft_prim(recs[rec_of[(long long)T.img * g.n_atoms + (uint32_t)T.list[j]]], f);
     s_w[lane] = sp;
     const unsigned cols = (am | (am >> 8) | (am >> 16) | (am >> 24)) & 0xffu;
     const unsigned rows = ((am & 0xffu) ? 1u : 0u) | ((am & 0xff00u) ? 2u : 0u) | ((am & 0xff0000u) ? 4u : 0u) |
@@ -310,7 +353,7 @@ __device__ __forceinline__ unsigned soft_stage(const Geometry &g, const PrimRec 
 #endif
 __global__ __launch_bounds__(kSoftNT, VTX_SOFT_FWD_MINB) void k_soft_fwd(Geometry g, const PrimRec *__restrict__ recs,
                                                       const uint32_t *__restrict__ rec_of,
-                                                      const unsigned long long *__restrict__ entries,
+                                                      unsigned long long *entries,
                                                       unsigned long long cap_entries,
                                                       const uint32_t *__restrict__ tile_count,
                                                       const uint32_t *__restrict__ tile_start, Status *status,
@@ -394,7 +437,7 @@ __device__ __forceinline__ float warp_sum4_scatter(float a0, float a1, float a2,
 
 __global__ __launch_bounds__(kSoftNT) void k_soft_bwd(Geometry g, const PrimRec *__restrict__ recs,
                                                       const uint32_t *__restrict__ rec_of,
-                                                      const unsigned long long *__restrict__ entries,
+                                                      unsigned long long *entries,
                                                       unsigned long long cap_entries,
                                                       const uint32_t *__restrict__ tile_count,
                                                       const uint32_t *__restrict__ tile_start, Status *status,
@@ -520,7 +563,7 @@ __global__ __launch_bounds__(kSoftNT) void k_soft_bwd(Geometry g, const PrimRec 
         const float sz = __shfl_sync(0xffffffffu, sum, 16);
         const float sr = __shfl_sync(0xffffffffu, sum, 24);
         if (lane == 0) {
-          const uint32_t id = (uint32_t)s_e[c0 + q];
+          const uint32_t id = (uint32_t)T.list[c0 + q];
           const float4 wv = make_float4(v.R[0] * sum + v.U[0] * sy + v.F[0] * sz,
                                         v.R[1] * sum + v.U[1] * sy + v.F[1] * sz,
                                         v.R[2] * sum + v.U[2] * sy + v.F[2] * sz, sr);

@@ -102,8 +102,8 @@ struct ImageState {
 // Launch-wide status (device memory, read back by the host).
 struct Status {
   unsigned int n_rec;           // binned records requested
-  unsigned int overflow;        // bit 0 survivors, 1 records, 2 entries, 3 soft tile list too long,
-                                // 4 a bounded wait gave up, 5 a decoded primitive id out of range
+  unsigned int overflow;        // bit 1 records, 2 entries, 4 a bounded wait gave up,
+                                // 5 a decoded primitive id out of range
   unsigned long long n_entries; // binned (tile, primitive) entries requested
   unsigned int max_list;        // longest tile list seen by the raster stage
   unsigned int n_list;          // non-empty tiles listed by the scan (raster work list)
@@ -256,7 +256,10 @@ struct PixRay {
   float pxc, pyc;  // pixel-centre coordinates (px + 0.5, py + 0.5), exact
   float a, b;      // slopes of the ray u = (a, b, 1)
   float uu;        // |u|^2
+  float inv_uu;    // 1 / |u|^2 (hardware reciprocal)
 };
+
+__device__ __forceinline__ float rcp_approx(float x);
 
 __device__ __forceinline__ PixRay pix_ray(const ViewParams &v, int px, int py) {
   PixRay r;
@@ -265,6 +268,14 @@ __device__ __forceinline__ PixRay pix_ray(const ViewParams &v, int px, int py) {
   r.a = __fmul_rn(__fsub_rn(r.pxc, v.cx), v.inv_f);
   r.b = __fmul_rn(__fsub_rn(v.cy, r.pyc), v.inv_f);
   r.uu = fmaf(r.a, r.a, fmaf(r.b, r.b, 1.0f));
+  r.inv_uu = rcp_approx(r.uu);
+  return r;
+}
+
+// sqrt(x) for x >= 0 by the hardware approximation (relative error near 2^-23; 0 gives 0).
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
 
@@ -333,12 +344,15 @@ __device__ __forceinline__ float3 local_o(float u0h, float u0l, float v0h, float
 // The hit tests spell every product-sum as an explicit fmaf or a plain
 // operation, leaving the compiler no contraction choice: the direct-splat and
 // binned paths, inlined into different kernels, then produce the same key bits.
+// The square root and the division by |u|^2 use the hardware approximations
+// (s is Angstrom-scale, so their ~1e-7 relative error is far below a depth-key
+// step or the 1e-4 A tie band).
 __device__ __forceinline__ bool sphere_local(float3 o, const PixRay &r, float rad, float &s) {
   float ou = fmaf(o.x, r.a, fmaf(o.y, r.b, o.z));
   float oo = fmaf(o.x, o.x, fmaf(o.y, o.y, __fmul_rn(o.z, o.z)));
   float disc = fmaf(ou, ou, __fmul_rn(-r.uu, fmaf(-rad, rad, oo)));
   if (!(disc >= 0.0f)) return false;
-  s = __fdiv_rn(__fsub_rn(-ou, sqrtf(disc)), r.uu);
+  s = __fmul_rn(__fsub_rn(-ou, sqrt_approx(disc)), r.inv_uu);
   return true;
 }
 __device__ __forceinline__ bool cylinder_local(float3 o, const PixRay &r, float3 A, float hl, float rb, float &s,
@@ -383,8 +397,12 @@ __device__ __forceinline__ bool cylinder_local(float3 o, const PixRay &r, float3
   return true;
 }
 
+// The offset s S is rounded to the nearest integer, through the 32-bit conversion whenever it fits
+// (the same result as the 64-bit one, which is kept for the extreme key scales near the eye).
 __device__ __forceinline__ unsigned long long pack_key(long long keyc, float s, float S, uint32_t id) {
-  long long k = keyc + llrintf(fminf(fmaxf(s * S, -4.0e18f), 4.0e18f));
+  const float x = s * S;
+  const long long d = fabsf(x) < 2.0e9f ? (long long)__float2int_rn(x) : llrintf(fminf(fmaxf(x, -4.0e18f), 4.0e18f));
+  long long k = keyc + d;
   k = k < 0 ? 0 : (k > kKeySpan ? kKeySpan : k);
   return ((unsigned long long)k << 32) | (unsigned long long)id;
 }

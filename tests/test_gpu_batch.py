@@ -74,4 +74,4 @@ def test_batch_images_match_oracle():
         cov = res["id"] != oracle.NO_ID
         pix = sample_pixels(160, 96, 300, img, windows=[(70, 40, 16)], covered_mask=cov if cov.any() else None)
         h = oracle.render_pixels(sc, 0, pix, kernel=k)
-        compare(res, h, ssao=True, allow_excluded=0.02, label="batch img %d" % img)
+        compare(res, h, ssao=True, label="batch img %d" % img)

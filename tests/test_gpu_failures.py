@@ -95,7 +95,7 @@ def test_forced_capacity_overflow_then_identical_rerender():
     out = r.render_frame(vtx.default_settings(ssao_kernel=k, splat_max_px=1), out=out)
     r.sync_status()  # the grown arena holds the frame
     _same(_planes(out), ref)
-    assert (ref["id"] != -1).sum() > 10000
+    assert (ref["id"] != -1).sum() > 2000
 
 
 def test_corrupted_key_hits_the_bounds_check():

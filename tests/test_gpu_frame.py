@@ -38,7 +38,8 @@ def test_random_tiny_scenes(seed):
     res = gpu_render(s, ssao=scenes.ssao_kernel())
     h = oracle.render_pixels(s, 0, oracle.all_pixels(s.cameras[0].width, s.cameras[0].height),
                              kernel=scenes.ssao_kernel())
-    compare(res, h, ssao=True, allow_excluded=0.02, label="tiny%d" % seed)
+    # 1,100-2,500 covered pixels: 0-4 of them flagged (measured at most 0.21 %)
+    compare(res, h, ssao=True, allow_excluded=0.0025, label="tiny%d" % seed)
 
 
 def test_near_plane_and_eye_inside():
@@ -51,7 +52,7 @@ def test_near_plane_and_eye_inside():
     s = scenes.Scene("near", xyzr, np.array([0, 1, 2, 3], np.uint8), [cam], ssao=False)
     res = gpu_render(s)
     h = oracle.render_pixels(s, 0, oracle.all_pixels(97, 81))
-    compare(res, h, ssao=False, allow_excluded=0.05, label="near")
+    compare(res, h, ssao=False, label="near")
 
 
 def test_empty_and_all_culled():
@@ -94,7 +95,7 @@ def test_config3_full_size_sampled():
     j = len(xs) // 2
     pix = sample_pixels(3840, 2160, 240, 11, windows=[(xs[j] - 6, ys[j] - 6, 12)], covered_mask=cov)
     h = oracle.render_pixels(s, 0, pix, kernel=k)
-    st = compare(res, h, ssao=True, allow_excluded=0.02, label="config3 V1")
+    st = compare(res, h, ssao=True, label="config3 V1")
     assert st["covered"] > 150
 
 
@@ -110,7 +111,7 @@ def test_ball_and_stick_subset():
     assert ((res["id"] >= s.xyzr.shape[0]) & (res["id"] != oracle.NO_ID)).sum() > 500  # bonds visible
     pix = sample_pixels(320, 240, 1200, 3, windows=[(150, 110, 24)], covered_mask=res["id"] != oracle.NO_ID)
     h = oracle.render_pixels(s, 0, pix, kernel=k)
-    compare(res, h, ssao=True, allow_excluded=0.01, label="ball-and-stick")
+    compare(res, h, ssao=True, allow_excluded=0.0015, label="ball-and-stick")  # measured 2 of 1,799
 
 
 def test_permutation_relabels_ids():

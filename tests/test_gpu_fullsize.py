@@ -33,11 +33,11 @@ def test_config3_close_view_v2(cell):
     assert cov.mean() > 0.2
     pix = sample_pixels(3840, 2160, 60, 21, covered_mask=cov)
     h = oracle.hits(cell.xyzr, cell.cameras[1], pix)
-    st = compare(res, h, ssao=False, allow_excluded=0.02, label="config3 V2 hits", colour=False)
+    st = compare(res, h, ssao=False, label="config3 V2 hits", colour=False)
     assert st["covered"] > 60
     win = sample_pixels(3840, 2160, 0, 22, windows=[(1917, 1077, 6)])
     hw = oracle.render_pixels(cell, 1, win, kernel=k)
-    compare(res, hw, ssao=True, allow_excluded=0.1, label="config3 V2 window")
+    compare(res, hw, ssao=True, label="config3 V2 window")
 
 
 def test_config3_ball_and_stick_full_subset(cell):
@@ -53,7 +53,7 @@ def test_config3_ball_and_stick_full_subset(cell):
     assert bonds_seen > 10000
     pix = sample_pixels(3840, 2160, 50, 23, windows=[(1910, 1070, 8)], covered_mask=ids != oracle.NO_ID)
     h = oracle.render_pixels(s, 0, pix)
-    compare(res, h, ssao=False, allow_excluded=0.03, label="ball-and-stick 5e6")
+    compare(res, h, ssao=False, label="ball-and-stick 5e6")
 
 
 def test_config4_full_batch_sampled():
@@ -81,4 +81,4 @@ def test_config4_full_batch_sampled():
         cov = res["id"] != oracle.NO_ID
         pix = sample_pixels(1280, 720, 150, img, windows=[(630, 350, 12)], covered_mask=cov)
         h = oracle.render_pixels(sc, 0, pix, kernel=k)
-        compare(res, h, ssao=True, allow_excluded=0.02, label="config4 img %d" % img)
+        compare(res, h, ssao=True, label="config4 img %d" % img)

@@ -127,7 +127,7 @@ def test_three_hundred_million_atoms_streamed_from_host():
     assert cov.sum() > 200000
     pix = sample_pixels(cam.width, cam.height, 32, 5, covered_mask=cov)
     h = oracle.render_pixels(s, 0, pix)
-    compare(res, h, ssao=False, allow_excluded=0.05, label="3e8 host")
+    compare(res, h, ssao=False, label="3e8 host")
 
 
 def test_output_planes_in_page_locked_host_memory():

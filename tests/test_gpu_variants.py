@@ -38,7 +38,7 @@ def _clear_plane(xyzr, n, d, margin=0.01):
 def test_sas_config1_full_frame_with_ssao():
     s = scenes.config1()
     res, h = _both(s, oracle.all_pixels(256, 256), kernel=scenes.ssao_kernel(), mode=3, probe=1.4)
-    st = compare(res, h, ssao=True, allow_excluded=0.02, label="SAS")
+    st = compare(res, h, ssao=True, allow_excluded=0.0015, label="SAS")  # measured 10 of 8,798
     assert st["covered"] > 8000
 
 
@@ -46,7 +46,7 @@ def test_sas_random_tiny_probe_sizes():
     for seed, probe in [(3, 0.5), (4, 1.4), (5, 3.0)]:
         s = scenes.random_tiny(seed, n=50, width=61, height=47, distance=24.0)
         res, h = _both(s, oracle.all_pixels(61, 47), kernel=scenes.ssao_kernel(), mode=3, probe=probe)
-        compare(res, h, ssao=True, allow_excluded=0.03, label="SAS p=%g" % probe)
+        compare(res, h, ssao=True, allow_excluded=0.0025, label="SAS p=%g" % probe)  # at most 3 of 1,432
 
 
 def test_sticks_close_view():
@@ -62,7 +62,7 @@ def test_sticks_close_view():
     assert ((res["id"] >= s.xyzr.shape[0]) & cov).sum() > 500
     pix = sample_pixels(256, 192, 1000, 5, windows=[(120, 90, 20)], covered_mask=cov)
     h = oracle.render_pixels(s, 0, pix, kernel=k, mode=2)
-    compare(res, h, ssao=True, allow_excluded=0.04, label="sticks")
+    compare(res, h, ssao=True, allow_excluded=0.0025, label="sticks")  # measured 3 of 1,528
 
 
 def test_clip_plane_vdw_full_frame():
@@ -88,21 +88,21 @@ def test_clip_plane_ball_and_stick_with_ssao():
     cov = res["id"] != oracle.NO_ID
     pix = sample_pixels(240, 180, 800, 9, windows=[(110, 80, 20)], covered_mask=cov)
     h = oracle.render_pixels(s, 0, pix, kernel=k, clip=plane)
-    compare(res, h, ssao=True, allow_excluded=0.02, label="clip b&s")
+    compare(res, h, ssao=True, label="clip b&s")
 
 
 @pytest.mark.parametrize("model,levels", [(1, 4), (2, 4), (3, 2), (3, 4), (3, 7)])
 def test_shading_models_config1(model, levels):
     s = scenes.config1()
     res, h = _both(s, oracle.all_pixels(256, 256), model=model, toon_levels=levels)
-    compare(res, h, ssao=False, allow_excluded=0.01, label="shading %d/%d" % (model, levels))
+    compare(res, h, ssao=False, allow_excluded=0.0025, label="shading %d/%d" % (model, levels))  # toon band flags: at most 15 of 7,530
 
 
 def test_toon_with_ssao_random_tiny():
     for seed in range(3):
         s = scenes.random_tiny(200 + seed, n=60, width=64, height=52, distance=18.0)
         res, h = _both(s, oracle.all_pixels(64, 52), kernel=scenes.ssao_kernel(), model=3, toon_levels=5)
-        compare(res, h, ssao=True, allow_excluded=0.03, label="toon tiny%d" % seed)
+        compare(res, h, ssao=True, allow_excluded=0.0035, label="toon tiny%d" % seed)  # at most 4 of 1,368
 
 
 @pytest.mark.parametrize("density", [0.6, 1.0])
@@ -116,7 +116,7 @@ def test_outline_config1_with_ssao():
     s = scenes.config1()
     res, h = _both(s, oracle.all_pixels(256, 256), kernel=scenes.ssao_kernel(), outline_depth=1.0,
                    outline_color=(0.1, 0.0, 0.3))
-    st = compare(res, h, ssao=True, allow_excluded=0.02, label="outline")
+    st = compare(res, h, ssao=True, allow_excluded=0.0025, label="outline")  # measured 17 of 7,530
     col = np.array([0.1, 0.0, 0.3], np.float32)
     rgb = res["rgb"].transpose(1, 2, 0)
     outlined = np.all(rgb == col, axis=2)
@@ -138,7 +138,7 @@ def test_all_variants_together_config2_sampled():
     pix = sample_pixels(1920, 1080, 1200, 21, windows=[(cx - 16, cy - 16, 32), (xs.min(), cy, 24)],
                         covered_mask=cov)
     h = oracle.render_pixels(s, 0, pix, kernel=k, **kw)
-    compare(res, h, ssao=True, allow_excluded=0.02, label="config2 variants")
+    compare(res, h, ssao=True, allow_excluded=0.0025, label="config2 variants")  # 6 of 2,600
 
 
 def test_batch_sas_clip_matches_per_frame():
