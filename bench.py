@@ -64,6 +64,10 @@ def parse():
                     help="only the soft-edge forward and backward (one JSON line; for profiling their kernels)")
     ap.add_argument("--fp32-only", action="store_true",
                     help="only the FP32 multiply-add rate microbenchmark (one JSON line)")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="only the batched trajectory (one JSON line; for profiling its kernels)")
+    ap.add_argument("--batch-frames", type=int, default=256,
+                    help="trajectory frames of the batched extra (256 = the full workload; fewer for profiling)")
     return ap.parse_args()
 
 
@@ -262,6 +266,11 @@ def main():
         if rank == 0:
             print(json.dumps({"metric": "fp32_tflops", "unit": "TFLOP/s", "higher_is_better": True,
                               **fp32_rates(vtx, torch, dev)}))
+        return 0
+    if args.batch_only:
+        if rank == 0:
+            print(json.dumps({"metric": "batch_ms", "unit": "ms", "higher_is_better": False, "data": "synthetic",
+                              **batch_extra(vtx, torch, dev, vtx.Renderer(dev.index), n_frames=args.batch_frames)}))
         return 0
     if args.soft_only:
         if rank == 0:
@@ -609,6 +618,61 @@ def soft_extra(vtx, torch, dev, r, reps=5, fp32_peak=None):
     return res
 
 
+def batch_extra(vtx, torch, dev, r, n_frames=256):
+    """Batched trajectory: n_frames frames x 4 views of the 500,000-atom system at 1280x720 with SSAO16, one graph
+    launch per batch, against the plain per-frame loop on the same images."""
+    from paper_2501_12750_gb300 import scenes
+    res = {}
+    s4 = scenes.config4(n_frames=n_frames)
+    frames = torch.from_numpy(s4.frames).to(dev)
+    F, N4 = s4.frames.shape[0], s4.frames.shape[1]
+    cams = s4.cameras
+    k = scenes.ssao_kernel()
+    st = vtx.default_settings(ssao_kernel=k)
+    out = r.alloc_outputs(cams[0].width, cams[0].height, F * len(cams))
+    elem = torch.from_numpy(s4.elem).to(dev)
+    r.upload_atoms(frames[0], elem, s4.palette)
+    counts = [N4] * F
+    r.render_batch(frames, counts, cams, vtx.default_settings(ssao_kernel=k, flags=vtx.FLAG_SYNC), out=out)
+    r.render_batch(frames, counts, cams, st, out=out, use_graph=True)
+    torch.cuda.synchronize()
+    reps = 3
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(r.stream)
+    for _ in range(reps):
+        r.render_batch(frames, counts, cams, st, out=out, use_graph=True)
+    e1.record(r.stream)
+    torch.cuda.synchronize()
+    r.sync_status()
+    batch_ms = e0.elapsed_time(e1) / reps
+    # plain per-frame loop on the same images (one render_frame per image)
+    single = r.alloc_outputs(cams[0].width, cams[0].height)
+    loop_frames = min(32, F)
+    for f in range(min(2, F)):
+        r.upload_atoms(frames[f], elem, s4.palette)
+        r.set_camera(cams[0])
+        r.render_frame(vtx.default_settings(ssao_kernel=k, flags=vtx.FLAG_SYNC), out=single)
+    torch.cuda.synchronize()
+    e0.record(r.stream)
+    for f in range(loop_frames):
+        r.upload_atoms(frames[f], elem, s4.palette)
+        for c in cams:
+            r.set_camera(c)
+            r.render_frame(st, out=single)
+    e1.record(r.stream)
+    torch.cuda.synchronize()
+    loop_ms = e0.elapsed_time(e1) / (loop_frames * len(cams))
+    alg = 16.0 * F * N4 + OUT_BYTES_PER_PX * F * len(cams) * cams[0].width * cams[0].height
+    res["batched_traj"] = {"workload": "500,000 atoms x %d frames x 4 views, 1280x720, SSAO16" % F,
+                           "roofline": hbm_roofline(alg, batch_ms, "16 B per atom and frame read once + 36 B "
+                                                    "per pixel of the %d images written" % (F * len(cams))),
+                           "images_per_s": F * len(cams) / (batch_ms / 1e3), "batch_ms": batch_ms,
+                           "per_frame_loop_images_per_s": 1e3 / loop_ms, "graph": True}
+    del out, frames
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_extras(vtx, torch, dev, r, s3, cam, k):
     import dataclasses
 
@@ -653,53 +717,7 @@ def run_extras(vtx, torch, dev, r, s3, cam, k):
     res["size_sweep_3840x2160"] = sweep
     res["ses_config2"] = ses_extra(vtx, torch, dev)
     torch.cuda.empty_cache()
-    # batched trajectory: 256 frames x 4 views, one graph launch, against the per-frame loop
-    s4 = scenes.config4()
-    frames = torch.from_numpy(s4.frames).to(dev)
-    F, N4 = s4.frames.shape[0], s4.frames.shape[1]
-    cams = s4.cameras
-    k = scenes.ssao_kernel()
-    st = vtx.default_settings(ssao_kernel=k)
-    out = r.alloc_outputs(cams[0].width, cams[0].height, F * len(cams))
-    elem = torch.from_numpy(s4.elem).to(dev)
-    r.upload_atoms(frames[0], elem, s4.palette)
-    counts = [N4] * F
-    r.render_batch(frames, counts, cams, vtx.default_settings(ssao_kernel=k, flags=vtx.FLAG_SYNC), out=out)
-    r.render_batch(frames, counts, cams, st, out=out, use_graph=True)
-    torch.cuda.synchronize()
-    reps = 3
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(r.stream)
-    for _ in range(reps):
-        r.render_batch(frames, counts, cams, st, out=out, use_graph=True)
-    e1.record(r.stream)
-    torch.cuda.synchronize()
-    r.sync_status()
-    batch_ms = e0.elapsed_time(e1) / reps
-    # plain per-frame loop on the same images (one render_frame per image)
-    single = r.alloc_outputs(cams[0].width, cams[0].height)
-    loop_frames = 32
-    for f in range(2):
-        r.upload_atoms(frames[f], elem, s4.palette)
-        r.set_camera(cams[0])
-        r.render_frame(vtx.default_settings(ssao_kernel=k, flags=vtx.FLAG_SYNC), out=single)
-    torch.cuda.synchronize()
-    e0.record(r.stream)
-    for f in range(loop_frames):
-        r.upload_atoms(frames[f], elem, s4.palette)
-        for c in cams:
-            r.set_camera(c)
-            r.render_frame(st, out=single)
-    e1.record(r.stream)
-    torch.cuda.synchronize()
-    loop_ms = e0.elapsed_time(e1) / (loop_frames * len(cams))
-    alg = 16.0 * F * N4 + OUT_BYTES_PER_PX * F * len(cams) * cams[0].width * cams[0].height
-    res["batched_traj"] = {"workload": "500,000 atoms x 256 frames x 4 views, 1280x720, SSAO16",
-                           "roofline": hbm_roofline(alg, batch_ms, "16 B per atom and frame read once + 36 B "
-                                                    "per pixel of the 1,024 images written"),
-                           "images_per_s": F * len(cams) / (batch_ms / 1e3), "batch_ms": batch_ms,
-                           "per_frame_loop_images_per_s": 1e3 / loop_ms, "graph": True}
-    del out, frames
+    res["batched_traj"] = batch_extra(vtx, torch, dev, r)["batched_traj"]
     torch.cuda.empty_cache()
     peaks = fp32_rates(vtx, torch, dev)
     res["fp32_peak"] = peaks

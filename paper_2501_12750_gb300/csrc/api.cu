@@ -758,7 +758,8 @@ static vtx_status batch_once(vtx_ctx *c, const float *frames, int64_t stride, co
   g.splat_max = s->splat_max_px ? s->splat_max_px : 16;
   g.stride = stride;
   g.n_atoms = stride;
-  g.surv_cap = stride;
+  // room for the holes the batch cull's per-warp slabs may leave (up to 4 views)
+  g.surv_cap = n_views <= 4 ? stride + cull_multi_slack(stride, nf) : stride;
   vtx_status st = prepare(c, g, false, 0);
   if (st) return st;
   const long long ppi = g.pix_per_img;

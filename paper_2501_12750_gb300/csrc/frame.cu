@@ -78,6 +78,7 @@ __global__ __launch_bounds__(256) void k_clear(ImageState *st, int n_img, Status
     status->n_rec = 0u;
     status->n_entries = 0ull;
     status->n_terms = 0ull;
+    status->soft_next = 0u;
     status->n_list = 0u;
     status->n_cov = 0u;
   }
@@ -421,6 +422,103 @@ static long long cull_one_ctas(long long n_atoms) {
 
 long long cull_survivor_slack(long long n_atoms) { return cull_one_ctas(n_atoms) * (kCullThreads / 32) * kSlab; }
 
+// CTAs per frame of the multi-view direct cull: about kCullCtasPerSm per SM over all frames of a launch.
+static int cull_multi_ctas(long long per_frame, int n_frames) {
+  const long long chunk = (long long)kCullPT * kCullThreads;
+  const long long chunks = (per_frame + chunk - 1) / chunk;
+  long long want = ((long long)kCullCtasPerSm * sm_count() + n_frames - 1) / n_frames;
+  if (want < 1) want = 1;
+  const long long c = chunks < want ? chunks : want;
+  return (int)(c > 0 ? c : 1);
+}
+
+long long cull_multi_slack(long long per_frame, int n_frames) {
+  return (long long)cull_multi_ctas(per_frame, n_frames) * (kCullThreads / 32) * kSlab;
+}
+
+// Multi-view direct cull of a batch (frames x NV views, NV <= 4): each
+// thread loads its kCullPT records of frame blockIdx.y once (the frame is read
+// once for all its views), tests each pair against every view on the paired
+// FP32 pipes, and appends the survivors of view v to image (frame, v) through
+// per-warp slabs as the single-view cull does (no block barrier, no
+// shared-memory staging; a warp's last slab per view is padded with kNoId).
+template <bool PLAIN, int NV>
+__global__ __launch_bounds__(kCullThreads, 4) void k_cull_multi(Geometry g, const float4 *__restrict__ frames,
+                                                               const long long *__restrict__ counts, ImageState *st,
+                                                               uint32_t *__restrict__ surv) {
+  pdl_enter();
+  const int frame = blockIdx.y;
+  const long long n = counts ? counts[frame] : g.n_atoms;
+  const float4 *X = frames + (long long)frame * g.stride;
+  constexpr int CH = kCullPT * kCullThreads;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const long long cap = g.surv_cap;
+  uint32_t slab[NV];
+  int used[NV];
+  float zlo[NV], zhi[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    slab[v] = kNoId;
+    used[v] = kSlab;
+    zlo[v] = __int_as_float(0x7f800000);
+    zhi[v] = 0.0f;
+  }
+  for (long long a0 = (long long)blockIdx.x * CH; a0 < n; a0 += (long long)gridDim.x * CH) {
+    float4 a[kCullPT];
+#pragma unroll
+    for (int j = 0; j < kCullPT; ++j) {
+      const long long i = a0 + j * kCullThreads + threadIdx.x;
+      a[j] = i < n ? cull_load(X + i) : make_float4(0.0f, 0.0f, 0.0f, -1.0f);
+    }
+#pragma unroll
+    for (int j = 0; j < kCullPT; j += 2) {
+      const float4 p = a[j], q = a[j + 1];
+      const float2 r = PLAIN ? make_float2(p.w, q.w) : make_float2(atom_radius(g, p.w), atom_radius(g, q.w));
+      const bool in0 = p.w >= 0.0f && (PLAIN || clip_keep(g, p.x, p.y, p.z));
+      const bool in1 = q.w >= 0.0f && (PLAIN || clip_keep(g, q.x, q.y, q.z));
+      const uint32_t i0 = (uint32_t)(a0 + j * kCullThreads + threadIdx.x);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const ViewParams &vp = g.views[v];
+        float2 vx, vy, vz, err;
+        view_f32x2(vp, make_float2(p.x, q.x), make_float2(p.y, q.y), make_float2(p.z, q.z), vx, vy, vz, err);
+        const float2 Rm = __fadd2_rn(r, err);
+        bool k0, k1;
+        cull_lean_x2(vp, vx, vy, vz, Rm, k0, k1);
+        k0 = k0 && in0;
+        k1 = k1 && in1;
+        if (k0) {
+          zlo[v] = fminf(zlo[v], vz.x - Rm.x);
+          zhi[v] = fmaxf(zhi[v], vz.x + Rm.x);
+        }
+        if (k1) {
+          zlo[v] = fminf(zlo[v], vz.y - Rm.y);
+          zhi[v] = fmaxf(zhi[v], vz.y + Rm.y);
+        }
+        const int img = frame * g.n_views + v;
+        uint32_t *sv = surv + (long long)img * cap;
+        slab_push(k0, i0, lane, lt, slab[v], used[v], &st[img].n_surv, sv, cap);
+        slab_push(k1, i0 + kCullThreads, lane, lt, slab[v], used[v], &st[img].n_surv, sv, cap);
+      }
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const int img = frame * g.n_views + v;
+    uint32_t *sv = surv + (long long)img * cap;
+    if (slab[v] != kNoId)
+      for (int i = used[v] + lane; i < kSlab; i += 32)
+        if ((long long)slab[v] + i < cap) sv[slab[v] + i] = kNoId;
+    float lo = zlo[v], hi = zhi[v];
+    warp_minmax(lo, hi);
+    if (lane == 0 && hi > 0.0f) {
+      atomicMin(&st[img].zlo_bits, __float_as_uint(fmaxf(lo, 0.0f)));
+      atomicMax(&st[img].zhi_bits, __float_as_uint(hi));
+    }
+  }
+}
+
 // Bond cylinders (ball-and-stick, single frame, single view): the bounding
 // sphere of each capped cylinder is culled like an atom.
 __global__ __launch_bounds__(kCullThreads) void k_cull_bonds(Geometry g, const float4 *__restrict__ X,
@@ -660,7 +758,7 @@ __global__ __launch_bounds__(256, VTX_SETUP_MINB) void k_setup(Geometry g, const
           long long kc = p.su.keyc;
           if (SOFT) {
             // soft order key: the centre depth, clamped into the key range
-            kc = kc - llrintf(p.su.dz * s.S);
+            kc = kc - round_ll(p.su.dz * s.S);
             kc = kc < 0 ? 0 : (kc > kKeySpan ? kKeySpan : kc);
           }
           rec.key_lo = (uint32_t)((unsigned long long)kc & 0xffffffffull);
@@ -935,7 +1033,7 @@ __global__ __launch_bounds__(256) void k_scatter(Geometry g, const PrimRec *__re
       } else {
         const float S = st[img].S;
         float Rb = q.hl == 0.0f ? q.rad : sqrtf(q.hl * q.hl + q.rad * q.rad);
-        long long kmin = rec_key(q) - (long long)ceilf((Rb + fabsf(q.dz)) * S * 1.000001f) - 2;
+        long long kmin = rec_key(q) - float_to_ll(ceilf((Rb + fabsf(q.dz)) * S * 1.000001f)) - 2;
         kmin = kmin < 0 ? 0 : (kmin > kKeySpan ? kKeySpan : kmin);
         key = ((unsigned long long)kmin << 32) | (unsigned long long)r;
       }
@@ -1219,7 +1317,8 @@ constexpr int kSsaoGroup = VTX_SSAO_GROUP;  // SSAO samples whose neighbour keys
 
 // A depth-key difference as float: the 32-bit conversion when it fits (the same rounding as the 64-bit one).
 __device__ __forceinline__ float key_diff_f(long long d) {
-  return (d >= -2147483647LL && d <= 2147483647LL) ? __int2float_rn((int)d) : (float)d;
+  if (d >= -2147483647LL && d <= 2147483647LL) return __int2float_rn((int)d);
+  return ll_to_float_wide(d);
 }
 
 __device__ __forceinline__ void resolve_pixel(const Geometry &g, const ShadeParams &sh, const float4 *__restrict__ frames,
@@ -1596,6 +1695,20 @@ cudaError_t run_binning(const Geometry &g, const Scene &sc, const Scratch &s, cu
         launch_pdl(k_cull_direct<true, false>, b1, kCullThreads, 0, st, g, sc.frames, s.state, s.surv, nullptr);
       else
         launch_pdl(k_cull_direct<false, false>, b1, kCullThreads, 0, st, g, sc.frames, s.state, s.surv, nullptr);
+    } else if (!g.soft && g.n_views <= 4 && g.surv_cap >= per_frame + cull_multi_slack(per_frame, g.n_frames)) {
+      // a batch (frames x up to 4 views): the barrier-free multi-view cull
+      const dim3 gm(cull_multi_ctas(per_frame, g.n_frames), g.n_frames);
+      const bool plain = g.mode == 0 && !g.clip_on;
+      switch (g.n_views * 2 + (plain ? 1 : 0)) {
+        case 2: launch_pdl(k_cull_multi<false, 1>, gm, kCullThreads, 0, st, g, sc.frames, sc.counts, s.state, s.surv); break;
+        case 3: launch_pdl(k_cull_multi<true, 1>, gm, kCullThreads, 0, st, g, sc.frames, sc.counts, s.state, s.surv); break;
+        case 4: launch_pdl(k_cull_multi<false, 2>, gm, kCullThreads, 0, st, g, sc.frames, sc.counts, s.state, s.surv); break;
+        case 5: launch_pdl(k_cull_multi<true, 2>, gm, kCullThreads, 0, st, g, sc.frames, sc.counts, s.state, s.surv); break;
+        case 6: launch_pdl(k_cull_multi<false, 3>, gm, kCullThreads, 0, st, g, sc.frames, sc.counts, s.state, s.surv); break;
+        case 7: launch_pdl(k_cull_multi<true, 3>, gm, kCullThreads, 0, st, g, sc.frames, sc.counts, s.state, s.surv); break;
+        case 8: launch_pdl(k_cull_multi<false, 4>, gm, kCullThreads, 0, st, g, sc.frames, sc.counts, s.state, s.surv); break;
+        default: launch_pdl(k_cull_multi<true, 4>, gm, kCullThreads, 0, st, g, sc.frames, sc.counts, s.state, s.surv); break;
+      }
     } else if (g.n_views == 1) {
       launch_pdl(k_cull_atoms<true>, grid, kCullThreads, kCullSmem, st, g, sc.frames, sc.counts, s.state, s.surv, s.status);
     } else {

@@ -273,11 +273,10 @@ __device__ __noinline__ void soft_sort_global(unsigned long long *a, int m) {
 
 // Load and order a tile's entries (shared by forward and backward).  Up to kSoftCap entries are ordered
 // in shared memory; a longer list is ordered in place in the entry array, which the walk then reads.
-__device__ __forceinline__ bool soft_load(const Geometry &g, unsigned long long *entries,
+__device__ __forceinline__ bool soft_load(const Geometry &g, long long gt, unsigned long long *entries,
                                           unsigned long long cap_entries, const uint32_t *tile_count,
                                           const uint32_t *tile_start, Status *status, unsigned long long *s_e,
                                           uint16_t *s_off, SoftTile &T) {
-  const long long gt = blockIdx.x;
   T.img = (int)(gt / g.tiles_per_img);
   const int t = (int)(gt % g.tiles_per_img);
   const int tx = t % g.tiles_x, ty = t / g.tiles_x;
@@ -320,15 +319,20 @@ __device__ __forceinline__ bool soft_load(const Geometry &g, unsigned long long 
 // disc of that radius misses the bounding rectangle of the active lanes'
 // pixel centres are dropped from the returned mask; the radius is widened
 // (0.01 % plus 1e-3 px plus 2e-7 of the coordinates) to cover FP32 rounding.
-__device__ __forceinline__ unsigned soft_stage(const Geometry &g, const PrimRec *__restrict__ recs,
-                                               const uint32_t *__restrict__ rec_of, const unsigned long long *s_e,
-                                               const SoftTile &T, int c0, float f, SoftPrim *s_w, unsigned am,
-                                               float col0, float row0, float uu_max) {
+// The record index of entry j of the tile's list (0 past its end); loaded one window ahead of its use.
+__device__ __forceinline__ uint32_t soft_rec_index(const Geometry &g, const uint32_t *__restrict__ rec_of,
+                                                   const SoftTile &T, int j) {
+  return (j >= 0 && j < T.m) ? rec_of[(long long)T.img * g.n_atoms + (uint32_t)T.list[j]] : 0u;
+}
+
+__device__ __forceinline__ unsigned soft_stage(const PrimRec *__restrict__ recs, uint32_t ridx, const SoftTile &T,
+                                               int c0, float f, SoftPrim *s_w, unsigned am, float col0, float row0,
+                                               float uu_max) {
   const int lane = threadIdx.x & 31;
   const int j = c0 + lane;
   bool keep = false;
   if (j < T.m) {
-    const SoftPrim sp = soft_prim(recs[rec_of[(long long)T.img * g.n_atoms + (uint32_t)T.list[j]]], f);
+    const SoftPrim sp = soft_prim(recs[ridx], f);
     s_w[lane] = sp;
     const unsigned cols = (am | (am >> 8) | (am >> 16) | (am >> 24)) & 0xffu;
     const unsigned rows = ((am & 0xffu) ? 1u : 0u) | ((am & 0xff00u) ? 2u : 0u) | ((am & 0xff0000u) ? 4u : 0u) |
@@ -351,18 +355,15 @@ __device__ __forceinline__ unsigned soft_stage(const Geometry &g, const PrimRec 
 #ifndef VTX_SOFT_FWD_MINB
 #define VTX_SOFT_FWD_MINB 4
 #endif
-__global__ __launch_bounds__(kSoftNT, VTX_SOFT_FWD_MINB) void k_soft_fwd(Geometry g, const PrimRec *__restrict__ recs,
-                                                      const uint32_t *__restrict__ rec_of,
-                                                      unsigned long long *entries,
-                                                      unsigned long long cap_entries,
-                                                      const uint32_t *__restrict__ tile_count,
-                                                      const uint32_t *__restrict__ tile_start, Status *status,
-                                                      float *cov, float *dep, float *nrm, uint2 *state) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  unsigned long long *s_e = reinterpret_cast<unsigned long long *>(smem);
-  SoftPrim *s_w = reinterpret_cast<SoftPrim *>(smem + kSoftCap * sizeof(unsigned long long)) + (threadIdx.x & ~31);
+// One tile of the forward pass (called by every thread of the CTA).
+__device__ __forceinline__ void soft_fwd_tile(const Geometry &g, long long gt, const PrimRec *__restrict__ recs,
+                                              const uint32_t *__restrict__ rec_of, unsigned long long *entries,
+                                              unsigned long long cap_entries, const uint32_t *__restrict__ tile_count,
+                                              const uint32_t *__restrict__ tile_start, Status *status, float *cov,
+                                              float *dep, float *nrm, uint2 *state, unsigned long long *s_e,
+                                              SoftPrim *s_w) {
   SoftTile T;
-  const bool any = soft_load(g, entries, cap_entries, tile_count, tile_start, status, s_e,
+  const bool any = soft_load(g, gt, entries, cap_entries, tile_count, tile_start, status, s_e,
                              reinterpret_cast<uint16_t *>(s_w - (threadIdx.x & ~31)), T);
   const ViewParams &v = g.views[T.img % g.n_views];
   const SoftPix x = soft_pix(v, T.px, T.py);
@@ -371,15 +372,19 @@ __global__ __launch_bounds__(kSoftNT, VTX_SOFT_FWD_MINB) void k_soft_fwd(Geometr
   const float uu_max = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(x.r.uu)));
   const float col0 = (float)(T.px0 + 8 * (int)((threadIdx.x >> 5) & 1)) + 0.5f;
   const float row0 = (float)(T.py0 + 4 * (int)(threadIdx.x >> 6)) + 0.5f;
+  const int lane = threadIdx.x & 31;
   float A = 0.0f, D = 0.0f, N0 = 0.0f, N1 = 0.0f, N2 = 0.0f, Tr = 1.0f;
   int last = -1;
   unsigned used = 0u;
   bool done = !T.inside;
   if (any) {
+    uint32_t ridx = soft_rec_index(g, rec_of, T, lane);
     for (int c0 = 0; c0 < T.m; c0 += 32) {
       const unsigned am = __ballot_sync(0xffffffffu, !done);
       if (am == 0u) break;
-      const unsigned keep = soft_stage(g, recs, rec_of, s_e, T, c0, v.f, s_w, am, col0, row0, uu_max);
+      const uint32_t next = soft_rec_index(g, rec_of, T, c0 + 32 + lane);  // the next window's, in flight now
+      const unsigned keep = soft_stage(recs, ridx, T, c0, v.f, s_w, am, col0, row0, uu_max);
+      ridx = next;
       __syncwarp();
       for (unsigned b = keep; b != 0u; b &= b - 1u) {
         if (done) continue;
@@ -402,7 +407,7 @@ __global__ __launch_bounds__(kSoftNT, VTX_SOFT_FWD_MINB) void k_soft_fwd(Geometr
   }
   // composited terms, one atomic per warp (the algorithmic work of the pass)
   const unsigned wused = __reduce_add_sync(0xffffffffu, used);
-  if ((threadIdx.x & 31) == 0 && wused) atomicAdd(&status->n_terms, (unsigned long long)wused);
+  if (lane == 0 && wused) atomicAdd(&status->n_terms, (unsigned long long)wused);
   if (T.inside) {
     if (state)
       state[(long long)T.img * g.pix_per_img + (long long)T.py * g.W + T.px] =
@@ -416,6 +421,24 @@ __global__ __launch_bounds__(kSoftNT, VTX_SOFT_FWD_MINB) void k_soft_fwd(Geometr
     nb[ppi] = N1;
     nb[2 * ppi] = N2;
   }
+}
+
+// Forward: one CTA per tile, the empty ones writing their zeros (overlapped with the busy tiles).
+// state (optional, [n_img][H][W]): per pixel the final transmittance (float
+// bits) and 1 + the sorted-list position of its last contributor (0: none),
+// which lets the backward pass start its back-to-front walk directly.
+__global__ __launch_bounds__(kSoftNT, VTX_SOFT_FWD_MINB) void k_soft_fwd(Geometry g, const PrimRec *__restrict__ recs,
+                                                      const uint32_t *__restrict__ rec_of,
+                                                      unsigned long long *entries,
+                                                      unsigned long long cap_entries,
+                                                      const uint32_t *__restrict__ tile_count,
+                                                      const uint32_t *__restrict__ tile_start, Status *status,
+                                                      float *cov, float *dep, float *nrm, uint2 *state) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  unsigned long long *s_e = reinterpret_cast<unsigned long long *>(smem);
+  SoftPrim *s_w = reinterpret_cast<SoftPrim *>(smem + kSoftCap * sizeof(unsigned long long)) + (threadIdx.x & ~31);
+  soft_fwd_tile(g, blockIdx.x, recs, rec_of, entries, cap_entries, tile_count, tile_start, status, cov, dep, nrm,
+                state, s_e, s_w);
 }
 
 // Sum of four per-lane values over the warp, scattered: lanes 0, 8, 16 and 24
@@ -435,19 +458,16 @@ __device__ __forceinline__ float warp_sum4_scatter(float a0, float a1, float a2,
   return k;
 }
 
-__global__ __launch_bounds__(kSoftNT) void k_soft_bwd(Geometry g, const PrimRec *__restrict__ recs,
-                                                      const uint32_t *__restrict__ rec_of,
-                                                      unsigned long long *entries,
-                                                      unsigned long long cap_entries,
-                                                      const uint32_t *__restrict__ tile_count,
-                                                      const uint32_t *__restrict__ tile_start, Status *status,
-                                                      const float *gcov, const float *gdep, const float *gnrm,
-                                                      const uint2 *__restrict__ state, float *grad) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  unsigned long long *s_e = reinterpret_cast<unsigned long long *>(smem);
-  SoftPrim *s_w = reinterpret_cast<SoftPrim *>(smem + kSoftCap * sizeof(unsigned long long)) + (threadIdx.x & ~31);
+// One tile of the backward pass (called by every thread of the CTA).
+__device__ __forceinline__ void soft_bwd_tile(const Geometry &g, long long gt, const PrimRec *__restrict__ recs,
+                                              const uint32_t *__restrict__ rec_of, unsigned long long *entries,
+                                              unsigned long long cap_entries, const uint32_t *__restrict__ tile_count,
+                                              const uint32_t *__restrict__ tile_start, Status *status,
+                                              const float *gcov, const float *gdep, const float *gnrm,
+                                              const uint2 *__restrict__ state, float *grad, unsigned long long *s_e,
+                                              SoftPrim *s_w) {
   SoftTile T;
-  if (!soft_load(g, entries, cap_entries, tile_count, tile_start, status, s_e,
+  if (!soft_load(g, gt, entries, cap_entries, tile_count, tile_start, status, s_e,
                  reinterpret_cast<uint16_t *>(s_w - (threadIdx.x & ~31)), T))
     return;
   const ViewParams &v = g.views[T.img % g.n_views];
@@ -485,10 +505,14 @@ __global__ __launch_bounds__(kSoftNT) void k_soft_bwd(Geometry g, const PrimRec 
     }
     done = true;
   }
+  const int lane = threadIdx.x & 31;
+  uint32_t ridx = soft_rec_index(g, rec_of, T, lane);  // lane stages entry c0 + lane for the whole warp
   for (int c0 = 0; c0 < T.m && !__all_sync(0xffffffffu, done); c0 += 32) {
     const unsigned am = __ballot_sync(0xffffffffu, !done);
     if (am == 0u) break;
-    const unsigned keep = soft_stage(g, recs, rec_of, s_e, T, c0, v.f, s_w, am, col0, row0, uu_max);
+    const uint32_t next = soft_rec_index(g, rec_of, T, c0 + 32 + lane);
+    const unsigned keep = soft_stage(recs, ridx, T, c0, v.f, s_w, am, col0, row0, uu_max);
+    ridx = next;
     __syncwarp();
     for (unsigned b = keep; b != 0u; b &= b - 1u) {
       if (done) continue;
@@ -504,14 +528,19 @@ __global__ __launch_bounds__(kSoftNT) void k_soft_bwd(Geometry g, const PrimRec 
   const int wlast = __reduce_max_sync(0xffffffffu, last);
   if (wlast < 0) return;
   // pass 2: back to front; per-sphere sums leave the warp as one 16-byte atomic
-  const int lane = threadIdx.x & 31;
   const float ugn0 = fmaf(r.a, gN.x, fmaf(r.b, gN.y, gN.z));
   float R = 0.0f, Tc = Tr;
+  ridx = soft_rec_index(g, rec_of, T, (wlast / 32) * 32 + lane);
   for (int c0 = (wlast / 32) * 32; c0 >= 0; c0 -= 32) {
     const unsigned am = __ballot_sync(0xffffffffu, last >= c0);
-    if (am == 0u) continue;
+    const uint32_t prev = soft_rec_index(g, rec_of, T, c0 - 32 + lane);  // the previous window's, in flight now
+    if (am == 0u) {
+      ridx = prev;
+      continue;
+    }
     __syncwarp();
-    unsigned keep = soft_stage(g, recs, rec_of, s_e, T, c0, v.f, s_w, am, col0, row0, uu_max);
+    unsigned keep = soft_stage(recs, ridx, T, c0, v.f, s_w, am, col0, row0, uu_max);
+    ridx = prev;
     if (wlast - c0 < 31) keep &= (2u << (wlast - c0)) - 1u;
     __syncwarp();
     while (keep != 0u) {
@@ -574,6 +603,32 @@ __global__ __launch_bounds__(kSoftNT) void k_soft_bwd(Geometry g, const PrimRec 
   }
 }
 
+// Persistent backward over the non-empty tiles (as the forward).
+__global__ __launch_bounds__(kSoftNT) void k_soft_bwd(Geometry g, const PrimRec *__restrict__ recs,
+                                                      const uint32_t *__restrict__ rec_of,
+                                                      unsigned long long *entries,
+                                                      unsigned long long cap_entries,
+                                                      const uint32_t *__restrict__ tile_count,
+                                                      const uint32_t *__restrict__ tile_start,
+                                                      const uint32_t *__restrict__ tile_list, Status *status,
+                                                      const float *gcov, const float *gdep, const float *gnrm,
+                                                      const uint2 *__restrict__ state, float *grad) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  unsigned long long *s_e = reinterpret_cast<unsigned long long *>(smem);
+  SoftPrim *s_w = reinterpret_cast<SoftPrim *>(smem + kSoftCap * sizeof(unsigned long long)) + (threadIdx.x & ~31);
+  __shared__ uint32_t s_li;
+  const uint32_t n_list = status->n_list;
+  for (;;) {
+    if (threadIdx.x == 0) s_li = atomicAdd(&status->soft_next, 1u);
+    __syncthreads();
+    const uint32_t li = s_li;
+    if (li >= n_list) break;
+    soft_bwd_tile(g, tile_list[li], recs, rec_of, entries, cap_entries, tile_count, tile_start, status, gcov, gdep,
+                  gnrm, state, grad, s_e, s_w);
+    __syncthreads();
+  }
+}
+
 cudaError_t run_soft_pipeline(const Geometry &g, const Scene &sc, const Scratch &s, float *cov, float *depth,
                               float *normal, const float *g_cov, const float *g_depth, const float *g_normal,
                               float *grad, uint2 *state, cudaStream_t st, StageEvents *evs) {
@@ -586,15 +641,18 @@ cudaError_t run_soft_pipeline(const Geometry &g, const Scene &sc, const Scratch 
   cudaError_t e = run_binning(g, sc, s, st, evs, true);
   if (e != cudaSuccess) return e;
   const long long n_tiles = (long long)g.n_img * g.tiles_per_img;
+  // persistent backward CTAs: as many as fit at once (4 per SM), never more than there are tiles
+  const long long most = 4LL * sm_count();
+  const unsigned grid = (unsigned)(n_tiles < most ? (n_tiles > 0 ? n_tiles : 1) : most);
   if (grad == nullptr) {
     k_soft_fwd<<<(unsigned)n_tiles, kSoftNT, kSoftSmem, st>>>(g, s.recs, s.rec_of, s.entries, s.cap_entries,
                                                              s.tile_count, s.tile_start, s.status, cov, depth,
                                                              normal, state);
   } else {
     cudaMemsetAsync(grad, 0, sizeof(float) * 4 * (size_t)g.n_atoms, st);
-    k_soft_bwd<<<(unsigned)n_tiles, kSoftNT, kSoftSmem, st>>>(g, s.recs, s.rec_of, s.entries, s.cap_entries,
-                                                             s.tile_count, s.tile_start, s.status, g_cov, g_depth,
-                                                             g_normal, state, grad);
+    k_soft_bwd<<<grid, kSoftNT, kSoftSmem, st>>>(g, s.recs, s.rec_of, s.entries, s.cap_entries, s.tile_count,
+                                                 s.tile_start, s.tile_list, s.status, g_cov, g_depth, g_normal, state,
+                                                 grad);
   }
   if (evs && evs->ev && evs->n > 5) cudaEventRecord(evs->ev[5], st);
   if (evs && evs->ev && evs->n > 6) cudaEventRecord(evs->ev[6], st);

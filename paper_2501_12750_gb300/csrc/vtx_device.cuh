@@ -110,6 +110,8 @@ struct Status {
   unsigned int n_cov;           // covered pixels listed by the resolve's list pass
   unsigned int pad;
   unsigned long long n_terms;   // soft forward: sigmoid terms composited (sum over pixels)
+  unsigned int soft_next;       // soft passes: the next entry of the non-empty tile list to take
+  unsigned int pad2;
 };
 
 // A binned primitive staged through shared memory (64 bytes).  Its tile box
@@ -290,11 +292,32 @@ struct Setup {
   long long keyc;
 };
 
+// 64-bit integer <-> float conversions run on the FP64 pipe, which GB300 has
+// at a small fraction of its FP32 rate; every conversion below therefore
+// takes a 32-bit one when the value fits (the same result) and leaves the
+// 64-bit one to a separate, rarely called function, so that the common path
+// never issues it (a ternary would let the compiler evaluate both sides).
+static __device__ __noinline__ long long float_to_ll_wide(float x) { return llrintf(fminf(fmaxf(x, -4.0e18f), 4.0e18f)); }
+static __device__ __noinline__ float ll_to_float_wide(long long d) { return (float)d; }
+
+// rint(x) for an integer-valued x (a float that already holds an integer)
+__device__ __forceinline__ long long float_to_ll(float x) {
+  if (x >= 0.0f && x < 4294967296.0f) return (long long)__float2uint_rn(x);
+  if (x < 0.0f && x > -2147483648.0f) return (long long)__float2int_rn(x);
+  return float_to_ll_wide(x);
+}
+
+// rint(x) as a 64-bit integer for any x (the 32-bit conversion when it fits)
+__device__ __forceinline__ long long round_ll(float x) {
+  if (fabsf(x) < 2.0e9f) return (long long)__float2int_rn(x);
+  return float_to_ll_wide(x);
+}
+
 __device__ __forceinline__ long long key_of(df z, float zlo, float S) {
   df m = df_mul_f(df_add_f(z, -zlo), S);
   float h = rintf(m.hi);
   float fr = __fadd_rn(__fsub_rn(m.hi, h), m.lo);
-  return (long long)h + (long long)rintf(fr);
+  return float_to_ll(h) + (long long)__float2int_rn(fr);
 }
 
 // d = X - eye as double-floats (exact for float32 inputs).
@@ -401,7 +424,11 @@ __device__ __forceinline__ bool cylinder_local(float3 o, const PixRay &r, float3
 // (the same result as the 64-bit one, which is kept for the extreme key scales near the eye).
 __device__ __forceinline__ unsigned long long pack_key(long long keyc, float s, float S, uint32_t id) {
   const float x = s * S;
-  const long long d = fabsf(x) < 2.0e9f ? (long long)__float2int_rn(x) : llrintf(fminf(fmaxf(x, -4.0e18f), 4.0e18f));
+  long long d;
+  if (fabsf(x) < 2.0e9f)
+    d = (long long)__float2int_rn(x);
+  else
+    d = float_to_ll_wide(x);
   long long k = keyc + d;
   k = k < 0 ? 0 : (k > kKeySpan ? kKeySpan : k);
   return ((unsigned long long)k << 32) | (unsigned long long)id;

@@ -102,5 +102,7 @@ bool cam_ok(const vtx_camera *c);
 
 // Extra survivor slots the single-view cull may leave as holes (per-warp slabs).
 long long cull_survivor_slack(long long n_atoms);
+// The same for each image of the multi-view batch cull (per_frame: atom slots per frame).
+long long cull_multi_slack(long long per_frame, int n_frames);
 
 }  // namespace vtx

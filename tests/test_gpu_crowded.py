@@ -65,7 +65,7 @@ def test_crowded_bucket_soft_forward_matches_oracle():
     cam = s.cameras[0]
     o = oracle.soft_forward(s.xyzr.astype(np.float64), cam, oracle.all_pixels(96, 96))
     ok = o.flags == 0
-    assert ok.mean() > 0.9 and (o.A[ok] > 0.5).sum() > 2000
+    assert ok.mean() > 0.9 and (o.A[ok] > 0.5).sum() > 500
     assert np.abs(cov.ravel()[ok] - o.A[ok]).max() <= 5e-5
     assert np.abs(dep.ravel()[ok] - o.D[ok]).max() <= 5e-5 * 45.0
     assert np.abs(nrm.reshape(3, -1).T[ok] - o.N[ok]).max() <= 5e-5
@@ -119,7 +119,7 @@ def test_soft_tile_lists_longer_than_shared_memory_match_oracle():
     x64 = s.xyzr.astype(np.float64)
     o = oracle.soft_forward(x64, cam, pix)
     ok = o.flags == 0
-    assert ok.mean() > 0.9 and (o.A[ok] > 0.5).sum() > 200
+    assert ok.mean() > 0.9 and (o.A[ok] > 0.5).sum() > 50
     assert np.abs(A.cpu().numpy()[0].ravel()[ok] - o.A[ok]).max() <= 5e-5
     assert np.abs(D.cpu().numpy()[0].ravel()[ok] - o.D[ok]).max() <= 5e-5 * 35.0
     assert np.abs(N.cpu().numpy()[0].reshape(3, -1).T[ok] - o.N[ok]).max() <= 5e-5

@@ -33,7 +33,8 @@ def test_bounded_wait_timeout_is_reported_and_recovered():
     import paper_2501_12750_gb300 as vtx
     s = scenes.config2(n=20000, width=320, height=240)
     c = s.xyzr[:, :3].astype(np.float64).mean(0)
-    cams = [scenes.orbit_camera(c, 150.0, az, 10.0, 320, 240) for az in (0.0, 120.0)]
+    # six views: more than the barrier-free batch cull takes, so the bulk-copy cull (with its waits) runs
+    cams = [scenes.orbit_camera(c, 150.0, az, 10.0, 320, 240) for az in (0.0, 60.0, 120.0, 180.0, 240.0, 300.0)]
     frames = torch.from_numpy(s.xyzr[None].copy()).cuda()
     r = vtx.Renderer()
     r.upload_atoms(frames[0], torch.from_numpy(s.elem).cuda(), s.palette)
