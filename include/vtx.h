@@ -95,9 +95,11 @@ enum {
   VTX_FLAG_SYNC = 1u,     /* synchronise at the end of the call and report device-side errors */
   VTX_FLAG_PROFILE = 2u,  /* record per-stage CUDA events (read with vtx_stage_times) */
   VTX_FLAG_NO_SSAO = 4u,  /* skip ambient occlusion even if ssao_samples > 0 */
-  VTX_FLAG_PROFILE_CULL = 8u /* record CUDA events around the cull stage only (vtx_stage_times reports its
+  VTX_FLAG_PROFILE_CULL = 8u, /* record CUDA events around the cull stage only (vtx_stage_times reports its
                                 time, the other stages 0): two events per frame instead of nine, so the
                                 other kernels keep their overlapped launches */
+  VTX_FLAG_SOFT_REUSE = 16u   /* soft backward only: the caller vouches that the contents of xyzr are those
+                                of the latest soft forward call on this context (see vtx_render_soft_bwd_ex) */
 };
 
 /* Pinhole camera, 64 bytes.  forward/right/up: the view basis (float32 as passed). */
@@ -282,8 +284,9 @@ vtx_status vtx_render_soft_fwd(vtx_ctx *ctx, const float *xyzr, int64_t n, const
  * VTX_ERR_INVALID_ARG when NULL or unaligned, before any launch)
  * = d/d(x,y,z,r) of sum over views and pixels of
  *   g_cov*cov + g_depth*depth + g_normal . normal.
- * Tile lists are rebuilt (not stored by the forward call).  Gradient
- * planes have the layout of the forward outputs; any may be NULL (zero).
+ * Tile lists are rebuilt (vtx_render_soft_bwd_ex can reuse the forward
+ * call's lists).  Gradient planes have the layout of the forward outputs;
+ * any may be NULL (zero).
  */
 vtx_status vtx_render_soft_bwd(vtx_ctx *ctx, const float *xyzr, int64_t n, const vtx_camera *cams,
                                int32_t n_views, float sigma_px, const float *g_cov, const float *g_depth,
@@ -302,8 +305,17 @@ vtx_status vtx_render_soft_bwd(vtx_ctx *ctx, const float *xyzr, int64_t n, const
  * The forward call writes per pixel the final transmittance (float bits)
  * and 1 + the position of its last contributor in the tile's sorted list;
  * a backward call given the state of the forward call made with the SAME
- * xyzr, cams and sigma_px skips its front-to-back walk (the tile lists are
- * still rebuilt).  Any other state gives wrong gradients.
+ * xyzr, cams and sigma_px skips its front-to-back walk.  Any other state
+ * gives wrong gradients.
+ * The forward call leaves its tile lists, in their sorted order, in the
+ * context's arena.  A backward call with VTX_FLAG_SOFT_REUSE reuses them
+ * (no cull, binning or sort) when that forward call was the context's latest
+ * call to use the arena, with the same xyzr pointer, n, cams (compared byte
+ * for byte) and sigma_px, and no context buffer has been reallocated since;
+ * otherwise it rebuilds them, as without the flag.  The flag is the caller's
+ * promise that the CONTENTS of xyzr have not changed since that forward call
+ * (the library compares only the pointer); a broken promise gives wrong
+ * gradients.  The flag is ignored by forward calls.
  */
 vtx_status vtx_render_soft_fwd_ex(vtx_ctx *ctx, const float *xyzr, int64_t n, const vtx_camera *cams,
                                   int32_t n_views, float sigma_px, uint32_t flags, float *cov, float *depth,

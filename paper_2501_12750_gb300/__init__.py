@@ -30,6 +30,7 @@ FLAG_SYNC = 1
 FLAG_PROFILE = 2
 FLAG_NO_SSAO = 4
 FLAG_PROFILE_CULL = 8
+FLAG_SOFT_REUSE = 16
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "CAPACITY", 5: "TIMEOUT", 6: "BOUNDS", 7: "STATE"}
 
@@ -282,9 +283,11 @@ class Renderer:
         return cov, dep, nrm
 
     def render_soft_bwd(self, xyzr, cams: List, g_cov, g_depth, g_normal, sigma_px: float = 0.5, state=None,
-                        sync: bool = True):
+                        sync: bool = True, reuse_lists: bool = False):
         """d/d(x, y, z, r) of sum(g_cov cov + g_depth depth + g_normal . normal); state from the matching
-        forward call (same xyzr, cams, sigma) skips the backward's front-to-back walk."""
+        forward call (same xyzr, cams, sigma) skips the backward's front-to-back walk.  reuse_lists promises
+        that xyzr's contents are those of the latest soft forward call on this renderer: its tile lists are
+        then reused when nothing else has used the renderer's scratch since (else they are rebuilt)."""
         torch = self._torch
         V = len(cams)
         grad = torch.empty_like(xyzr)
@@ -293,8 +296,9 @@ class Renderer:
         gd = None if g_depth is None else g_depth.contiguous()
         gn = None if g_normal is None else g_normal.contiguous()
         self._check(self.lib.vtx_render_soft_bwd_ex(self.ctx, _ptr(xyzr), xyzr.shape[0], carr, V, sigma_px,
-                                                    FLAG_SYNC if sync else 0, _ptr(gc), _ptr(gd), _ptr(gn),
-                                                    _ptr(state), _ptr(grad)))
+                                                    (FLAG_SYNC if sync else 0) |
+                                                    (FLAG_SOFT_REUSE if reuse_lists else 0),
+                                                    _ptr(gc), _ptr(gd), _ptr(gn), _ptr(state), _ptr(grad)))
         return grad
 
     def soft_terms(self) -> int:
@@ -348,9 +352,11 @@ def _soft_function():
 
         @staticmethod
         def backward(ctx, g_cov, g_dep, g_nrm):
+            # saved tensors are checked against in-place changes, so x still holds the forward's contents and
+            # the forward's tile lists may be reused (the library rebuilds them if another call intervened)
             x, state = ctx.saved_tensors
             grad = ctx.renderer.render_soft_bwd(x, ctx.cams, g_cov, g_dep, g_nrm, ctx.sigma, state=state,
-                                                sync=False)
+                                                sync=False, reuse_lists=True)
             ctx.renderer.sync_status()  # a capacity overflow in either call surfaces here
             return grad, None, None, None
 

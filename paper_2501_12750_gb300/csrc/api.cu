@@ -70,6 +70,17 @@ struct vtx_ctx {
   std::vector<Tune> tunes;
   int last_tw = 0, last_th = 0, last_splat = 0;
   long long soft_sized[4] = {-1, -1, -1, -1};  // (atoms, views, W, H) of the last soft run that synchronised cleanly
+  // every run that sizes or replays the arena takes a new generation; a soft forward records the generation
+  // and inputs of the tile lists it leaves behind, which a backward call may then reuse
+  uint64_t arena_gen = 0;
+  uint64_t alloc_gen = 0;  // bumped by every (re)allocation of a context buffer
+  struct SoftLists {
+    uint64_t gen = ~0ull;
+    const float *xyzr = nullptr;
+    int64_t n = 0;
+    float sigma = 0.0f;
+    std::vector<vtx_camera> cams;
+  } soft_lists;
   // failure-injection hooks (vtx_debug_hooks)
   int dbg_first_wait = -1;
   bool dbg_corrupt_key = false;
@@ -94,6 +105,7 @@ static vtx_status ensure(vtx_ctx *c, Buf &b, size_t bytes, const char *what) {
   b.p = nullptr;
   b.bytes = 0;
   size_t want = bytes + bytes / 8;
+  ++c->alloc_gen;
   cudaError_t e = cudaMalloc(&b.p, want);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -229,6 +241,7 @@ static void base_geometry(Geometry &g, const vtx_camera *cams, int n_views, int 
 
 // Size the arena for a launch; records/entries grow only through overflow reports.
 static vtx_status prepare(vtx_ctx *c, const Geometry &g, bool soft, long long stride_for_recof) {
+  ++c->arena_gen;
   const long long n_img = g.n_img;
   const long long n_tiles = n_img * g.tiles_per_img;
   vtx_status st;
@@ -842,6 +855,7 @@ vtx_status vtx_render_batch(vtx_ctx *c, const float *frames_xyzr, int64_t frame_
     push(&c->elem, sizeof(void *));
     for (auto &ge : c->graphs)
       if (ge.key == key) {
+        ++c->arena_gen;
         cudaError_t e = cudaGraphLaunch(ge.exec, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphLaunch");
         return VTX_OK;
@@ -939,6 +953,7 @@ vtx_status vtx_render_batch(vtx_ctx *c, const float *frames_xyzr, int64_t frame_
     return cuda_fail(c, e, "cudaGraphInstantiate");
   }
   c->graphs.push_back(ge);
+  ++c->arena_gen;
   e = cudaGraphLaunch(ge.exec, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphLaunch");
   return VTX_OK;
@@ -981,15 +996,34 @@ static vtx_status soft_run(vtx_ctx *c, const float *xyzr, int64_t n, const vtx_c
                             n_views >= 1 && cams ? cams[0].height : 0};
   const bool sized = std::equal(key, key + 4, c->soft_sized);
   const bool sync = (flags & VTX_FLAG_SYNC) != 0 || !sized;
+  // a backward call may reuse the lists of the latest forward call when nothing has used the arena since and
+  // the inputs are the same (the caller vouches, with the flag, that the contents of xyzr are unchanged)
+  const auto &L = c->soft_lists;
+  bool reuse = grad != nullptr && (flags & VTX_FLAG_SOFT_REUSE) != 0 && L.gen == c->arena_gen && L.xyzr == xyzr &&
+               L.n == n && L.sigma == sigma && cams && n_views >= 1 && L.cams.size() == (size_t)n_views &&
+               std::memcmp(L.cams.data(), cams, sizeof(vtx_camera) * (size_t)n_views) == 0;
   vtx_status st = VTX_OK;
   for (int attempt = 0; attempt < 4; ++attempt) {
     Geometry g;
+    const uint64_t gen0 = c->arena_gen, alloc0 = c->alloc_gen;
     st = soft_common(c, xyzr, n, cams, n_views, sigma, g);
     if (st) return st;
+    if (reuse && c->alloc_gen == alloc0)
+      c->arena_gen = gen0;  // sizing an arena that already fits the lists leaves them in place
+    else
+      reuse = false;
     Scene sc{(const float4 *)xyzr, nullptr, nullptr, nullptr, nullptr};
     cudaError_t e = run_soft_pipeline(g, sc, scratch_of(c), cov, depth, normal, gc, gd, gn, grad, (uint2 *)state,
-                                      c->stream, nullptr);
+                                      reuse, c->stream, nullptr);
     if (e != cudaSuccess) return cuda_fail(c, e, "soft launch");
+    if (grad == nullptr) {
+      c->soft_lists.gen = c->arena_gen;
+      c->soft_lists.xyzr = xyzr;
+      c->soft_lists.n = n;
+      c->soft_lists.sigma = sigma;
+      c->soft_lists.cams.assign(cams, cams + n_views);
+    }
+    reuse = false;  // a retry after an overflow rebuilds everything
     if (!sync) return VTX_OK;
     st = check_status(c);
     if (st == VTX_OK) std::copy(key, key + 4, c->soft_sized);

@@ -666,6 +666,21 @@ __device__ __forceinline__ bool prim_hit(const PrimGeom &p, float3 o, const PixR
   return cylinder_local(o, r, p.A, p.hl, p.rad, s, kind, axial);
 }
 
+// Ray-cast primitive p at every pixel of its candidate box, merging hits into the key plane K (one lane).
+__device__ __forceinline__ void splat_box(const Geometry &g, const ViewParams &v, const PrimGeom &p, const PixBox &box,
+                                          float S, uint32_t id, unsigned long long *K) {
+  for (int py = box.y0; py <= box.y1; ++py)
+    for (int px = box.x0; px <= box.x1; ++px) {
+      PixRay r = pix_ray(v, px, py);
+      float3 o = local_o(p.su.u0.hi, p.su.u0.lo, p.su.v0.hi, p.su.v0.lo, p.su.k, p.su.dz, r);
+      float sh;
+      int kind;
+      float axial;
+      if (prim_hit(p, o, r, sh, kind, axial) && p.su.zr + sh >= v.znear)
+        atomicMin(K + (long long)py * g.W + px, pack_key(p.su.keyc, sh, S, id));
+    }
+}
+
 // Setup occupancy: 4 CTAs per SM (63 registers, a few bytes spilled) and 8
 // CTAs per SM of grid, measured best against 2 and 3 per SM and a 4-per-SM
 // grid (4K overview 0.072 -> 0.065 ms, close view 0.97 -> 0.76 ms).
@@ -735,16 +750,7 @@ __global__ __launch_bounds__(256, VTX_SETUP_MINB) void k_setup(Geometry g, const
       if (any) {
         const long long npx = (long long)(box.x1 - box.x0 + 1) * (long long)(box.y1 - box.y0 + 1);
         if (!SOFT && npx <= g.splat_max) {
-          for (int py = box.y0; py <= box.y1; ++py)
-            for (int px = box.x0; px <= box.x1; ++px) {
-              PixRay r = pix_ray(v, px, py);
-              float3 o = local_o(p.su.u0.hi, p.su.u0.lo, p.su.v0.hi, p.su.v0.lo, p.su.k, p.su.dz, r);
-              float sh;
-              int kind;
-              float axial;
-              if (prim_hit(p, o, r, sh, kind, axial) && p.su.zr + sh >= v.znear)
-                atomicMin(K + (long long)py * g.W + px, pack_key(p.su.keyc, sh, s.S, id));
-            }
+          splat_box(g, v, p, box, s.S, id, K);
         } else {
           binned = true;
           rec.u0h = p.su.u0.hi;
@@ -861,7 +867,7 @@ __global__ __launch_bounds__(1024) void k_scan_blocks(const uint32_t *__restrict
 }
 
 constexpr int kScanRounds = 32;                                 // values per lane in the one-CTA scan
-constexpr long long kScanSingleMax = 32LL * 32 * kScanRounds;   // 32 warps x 32 lanes x rounds
+static_assert(kScanSingleMax == 32LL * 32 * kScanRounds, "32 warps x 32 lanes x rounds");
 
 // Exclusive scan of every tile count in one CTA (up to 1024 R tiles), listing
 // the non-empty tiles for the raster stage on the way.  Warp w owns the
@@ -869,22 +875,30 @@ constexpr long long kScanSingleMax = 32LL * 32 * kScanRounds;   // 32 warps x 32
 // up front (coalesced rows of 32), warps scan their rows with shuffles, and
 // one pass over the 32 warp totals links the segments.  The launch picks the
 // smallest R in {8, 16, 32} that covers the tiles: a 1080p frame's 8,160
-// tiles take 8 rounds instead of the 32 a 4K frame needs.
+// tiles take 8 rounds instead of the 32 a 4K frame needs.  The list is ordered
+// longest first by classes of equal bit length of the count (a counting sort
+// on the count's leading zeros), so that the kernels walking it start the
+// longest tiles first and the short ones fill in behind them; the order
+// within a class, like the order of the lists themselves, affects only
+// scheduling.
 template <int R>
 __global__ __launch_bounds__(1024) void k_scan_single(const uint32_t *__restrict__ cnt, long long n,
                                                       uint32_t *__restrict__ start, uint32_t *__restrict__ cursor,
                                                       uint32_t *__restrict__ list, Status *status,
-                                                      unsigned long long cap_entries, int skip_if_empty) {
+                                                      unsigned long long cap_entries, int skip_if_empty,
+                                                      int list_empty) {
   pdl_enter();
   // hard edges: with no binned record every tile is empty; the raster reads
   // only the tile list (left empty by the set-up kernel) and the scatter has
   // nothing to place, so the scan has nothing to do
   if (skip_if_empty && status->n_rec == 0u) return;
   __shared__ unsigned long long s_wsum[32];
-  __shared__ unsigned int s_n;
+  // [0, 32): tiles per class (leading zeros of the count), then the class cursors; [32]: non-empty tiles;
+  // [33]: cursor of the empty tiles, listed after all others when list_empty is set
+  __shared__ unsigned int s_cls[34];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const long long seg = (long long)wid * 32 * R;
-  if (threadIdx.x == 0) s_n = 0u;
+  if (threadIdx.x < 34) s_cls[threadIdx.x] = 0u;
   uint32_t v[R];
   unsigned long long wsum = 0;
 #pragma unroll
@@ -894,6 +908,13 @@ __global__ __launch_bounds__(1024) void k_scan_single(const uint32_t *__restrict
   }
 #pragma unroll
   for (int r = 0; r < R; ++r) wsum += v[r];
+  __syncthreads();  // class counters cleared
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int c = v[r] ? __clz(v[r]) : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, c);
+    if (c >= 0 && lane == __ffs(peers) - 1) atomicAdd(&s_cls[c], (unsigned)__popc(peers));
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
   if (lane == 0) s_wsum[wid] = wsum;
@@ -910,6 +931,20 @@ __global__ __launch_bounds__(1024) void k_scan_single(const uint32_t *__restrict
       status->n_entries = x;
       start[n] = (uint32_t)(x > cap_entries ? cap_entries : x);
       if (x > cap_entries) atomicOr(&status->overflow, 4u);
+    }
+  } else if (wid == 1) {
+    // class c starts after every class with fewer leading zeros (longer counts); s_cls[32] = tiles listed
+    const unsigned c = s_cls[lane];
+    unsigned y = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned t = __shfl_up_sync(0xffffffffu, y, o);
+      if (lane >= o) y += t;
+    }
+    s_cls[lane] = y - c;
+    if (lane == 31) {
+      s_cls[32] = y;
+      s_cls[33] = y;
     }
   }
   __syncthreads();
@@ -930,17 +965,16 @@ __global__ __launch_bounds__(1024) void k_scan_single(const uint32_t *__restrict
       start[i] = w;
       cursor[i] = w;
     }
-    const unsigned m = __ballot_sync(0xffffffffu, ne);
-    if (m) {
-      unsigned base = 0u;
-      if (lane == 0) base = atomicAdd(&s_n, (unsigned)__popc(m));
-      base = __shfl_sync(0xffffffffu, base, 0);
-      if (ne) list[base + __popc(m & ((1u << lane) - 1u))] = (uint32_t)i;
-    }
+    const int c = ne ? __clz(v[r]) : (list_empty && i < n ? 33 : -1);
+    const unsigned peers = __match_any_sync(0xffffffffu, c);
+    const int leader = __ffs(peers) - 1;
+    unsigned base = 0u;
+    if (c >= 0 && lane == leader) base = atomicAdd(&s_cls[c], (unsigned)__popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (c >= 0) list[base + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)i;
     carry += __shfl_sync(0xffffffffu, x, 31);
   }
-  __syncthreads();
-  if (threadIdx.x == 0) status->n_list = s_n;
+  if (threadIdx.x == 0) status->n_list = s_cls[32];
 }
 
 // Scan of the block totals (one CTA, loops when there are more than 1,024 blocks).
@@ -1738,13 +1772,13 @@ cudaError_t run_binning(const Geometry &g, const Scene &sc, const Scratch &s, cu
       const int skip = soft ? 0 : 1;
       if (n_tiles <= 1024LL * 8)
         launch_pdl(k_scan_single<8>, 1, 1024, 0, st, s.tile_count, n_tiles, s.tile_start, s.tile_cursor, s.tile_list,
-                                             s.status, s.cap_entries, skip);
+                                             s.status, s.cap_entries, skip, 1 - skip);
       else if (n_tiles <= 1024LL * 16)
         launch_pdl(k_scan_single<16>, 1, 1024, 0, st, s.tile_count, n_tiles, s.tile_start, s.tile_cursor, s.tile_list,
-                                              s.status, s.cap_entries, skip);
+                                              s.status, s.cap_entries, skip, 1 - skip);
       else
         launch_pdl(k_scan_single<kScanRounds>, 1, 1024, 0, st, s.tile_count, n_tiles, s.tile_start, s.tile_cursor,
-                                                       s.tile_list, s.status, s.cap_entries, skip);
+                                                       s.tile_list, s.status, s.cap_entries, skip, 1 - skip);
     } else {
       int nb = (int)((n_tiles + kScanItems - 1) / kScanItems);
       unsigned long long *bs = reinterpret_cast<unsigned long long *>(s.block_sums);

@@ -273,10 +273,12 @@ __device__ __noinline__ void soft_sort_global(unsigned long long *a, int m) {
 
 // Load and order a tile's entries (shared by forward and backward).  Up to kSoftCap entries are ordered
 // in shared memory; a longer list is ordered in place in the entry array, which the walk then reads.
+// The forward writes the ordered list back to the entry array (store_back), so a backward call on the
+// same lists loads it already ordered (presorted) instead of sorting it again.
 __device__ __forceinline__ bool soft_load(const Geometry &g, long long gt, unsigned long long *entries,
                                           unsigned long long cap_entries, const uint32_t *tile_count,
                                           const uint32_t *tile_start, Status *status, unsigned long long *s_e,
-                                          uint16_t *s_off, SoftTile &T) {
+                                          uint16_t *s_off, SoftTile &T, bool store_back, bool presorted) {
   T.img = (int)(gt / g.tiles_per_img);
   const int t = (int)(gt % g.tiles_per_img);
   const int tx = t % g.tiles_x, ty = t / g.tiles_x;
@@ -295,11 +297,16 @@ __device__ __forceinline__ bool soft_load(const Geometry &g, long long gt, unsig
   T.m = (int)cnt;
   T.list = s_e;
   if (cnt == 0) return false;
-  if (cnt <= (uint32_t)kSoftCap) {
-    soft_order(entries + T.start, T.m, s_e, s_off);
-  } else {
-    soft_sort_global(entries + T.start, T.m);
+  if (cnt > (uint32_t)kSoftCap) {
+    if (!presorted) soft_sort_global(entries + T.start, T.m);
     T.list = entries + T.start;
+  } else if (presorted) {
+    for (int i = threadIdx.x; i < T.m; i += kSoftNT) s_e[i] = entries[T.start + i];
+    __syncthreads();
+  } else {
+    soft_order(entries + T.start, T.m, s_e, s_off);
+    if (store_back)
+      for (int i = threadIdx.x; i < T.m; i += kSoftNT) entries[T.start + i] = s_e[i];
   }
   return true;
 }
@@ -364,7 +371,7 @@ __device__ __forceinline__ void soft_fwd_tile(const Geometry &g, long long gt, c
                                               SoftPrim *s_w) {
   SoftTile T;
   const bool any = soft_load(g, gt, entries, cap_entries, tile_count, tile_start, status, s_e,
-                             reinterpret_cast<uint16_t *>(s_w - (threadIdx.x & ~31)), T);
+                             reinterpret_cast<uint16_t *>(s_w - (threadIdx.x & ~31)), T, true, false);
   const ViewParams &v = g.views[T.img % g.n_views];
   const SoftPix x = soft_pix(v, T.px, T.py);
   const float inv_sigma = 1.0f / g.sigma;
@@ -432,13 +439,16 @@ __global__ __launch_bounds__(kSoftNT, VTX_SOFT_FWD_MINB) void k_soft_fwd(Geometr
                                                       unsigned long long *entries,
                                                       unsigned long long cap_entries,
                                                       const uint32_t *__restrict__ tile_count,
-                                                      const uint32_t *__restrict__ tile_start, Status *status,
+                                                      const uint32_t *__restrict__ tile_start,
+                                                      const uint32_t *__restrict__ tile_list, Status *status,
                                                       float *cov, float *dep, float *nrm, uint2 *state) {
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned long long *s_e = reinterpret_cast<unsigned long long *>(smem);
   SoftPrim *s_w = reinterpret_cast<SoftPrim *>(smem + kSoftCap * sizeof(unsigned long long)) + (threadIdx.x & ~31);
-  soft_fwd_tile(g, blockIdx.x, recs, rec_of, entries, cap_entries, tile_count, tile_start, status, cov, dep, nrm,
-                state, s_e, s_w);
+  // every tile, longest list first when the scan listed them all (empty tiles last), else in index order
+  const long long gt = tile_list ? (long long)tile_list[blockIdx.x] : (long long)blockIdx.x;
+  soft_fwd_tile(g, gt, recs, rec_of, entries, cap_entries, tile_count, tile_start, status, cov, dep, nrm, state, s_e,
+                s_w);
 }
 
 // Sum of four per-lane values over the warp, scattered: lanes 0, 8, 16 and 24
@@ -465,10 +475,10 @@ __device__ __forceinline__ void soft_bwd_tile(const Geometry &g, long long gt, c
                                               const uint32_t *__restrict__ tile_start, Status *status,
                                               const float *gcov, const float *gdep, const float *gnrm,
                                               const uint2 *__restrict__ state, float *grad, unsigned long long *s_e,
-                                              SoftPrim *s_w) {
+                                              SoftPrim *s_w, bool presorted) {
   SoftTile T;
   if (!soft_load(g, gt, entries, cap_entries, tile_count, tile_start, status, s_e,
-                 reinterpret_cast<uint16_t *>(s_w - (threadIdx.x & ~31)), T))
+                 reinterpret_cast<uint16_t *>(s_w - (threadIdx.x & ~31)), T, false, presorted))
     return;
   const ViewParams &v = g.views[T.img % g.n_views];
   const SoftPix x = soft_pix(v, T.px, T.py);
@@ -612,7 +622,7 @@ __global__ __launch_bounds__(kSoftNT) void k_soft_bwd(Geometry g, const PrimRec 
                                                       const uint32_t *__restrict__ tile_start,
                                                       const uint32_t *__restrict__ tile_list, Status *status,
                                                       const float *gcov, const float *gdep, const float *gnrm,
-                                                      const uint2 *__restrict__ state, float *grad) {
+                                                      const uint2 *__restrict__ state, float *grad, int presorted) {
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned long long *s_e = reinterpret_cast<unsigned long long *>(smem);
   SoftPrim *s_w = reinterpret_cast<SoftPrim *>(smem + kSoftCap * sizeof(unsigned long long)) + (threadIdx.x & ~31);
@@ -624,35 +634,43 @@ __global__ __launch_bounds__(kSoftNT) void k_soft_bwd(Geometry g, const PrimRec 
     const uint32_t li = s_li;
     if (li >= n_list) break;
     soft_bwd_tile(g, tile_list[li], recs, rec_of, entries, cap_entries, tile_count, tile_start, status, gcov, gdep,
-                  gnrm, state, grad, s_e, s_w);
+                  gnrm, state, grad, s_e, s_w, presorted != 0);
     __syncthreads();
   }
 }
 
 cudaError_t run_soft_pipeline(const Geometry &g, const Scene &sc, const Scratch &s, float *cov, float *depth,
                               float *normal, const float *g_cov, const float *g_depth, const float *g_normal,
-                              float *grad, uint2 *state, cudaStream_t st, StageEvents *evs) {
+                              float *grad, uint2 *state, bool reuse_lists, cudaStream_t st, StageEvents *evs) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_soft_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSoftSmem);
     cudaFuncSetAttribute(k_soft_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSoftSmem);
     attr = true;
   }
-  cudaError_t e = run_binning(g, sc, s, st, evs, true);
-  if (e != cudaSuccess) return e;
+  const bool reuse = reuse_lists && grad != nullptr;
+  if (reuse) {
+    // the lists, records and tile order of the forward call are still in place; only the backward's tile
+    // queue counter (which the forward leaves untouched) is reset
+    cudaMemsetAsync(&s.status->soft_next, 0, sizeof(s.status->soft_next), st);
+  } else {
+    cudaError_t e = run_binning(g, sc, s, st, evs, true);
+    if (e != cudaSuccess) return e;
+  }
   const long long n_tiles = (long long)g.n_img * g.tiles_per_img;
   // persistent backward CTAs: as many as fit at once (4 per SM), never more than there are tiles
   const long long most = 4LL * sm_count();
   const unsigned grid = (unsigned)(n_tiles < most ? (n_tiles > 0 ? n_tiles : 1) : most);
   if (grad == nullptr) {
     k_soft_fwd<<<(unsigned)n_tiles, kSoftNT, kSoftSmem, st>>>(g, s.recs, s.rec_of, s.entries, s.cap_entries,
-                                                             s.tile_count, s.tile_start, s.status, cov, depth,
-                                                             normal, state);
+                                                             s.tile_count, s.tile_start,
+                                                             n_tiles <= kScanSingleMax ? s.tile_list : nullptr,
+                                                             s.status, cov, depth, normal, state);
   } else {
     cudaMemsetAsync(grad, 0, sizeof(float) * 4 * (size_t)g.n_atoms, st);
     k_soft_bwd<<<grid, kSoftNT, kSoftSmem, st>>>(g, s.recs, s.rec_of, s.entries, s.cap_entries, s.tile_count,
                                                  s.tile_start, s.tile_list, s.status, g_cov, g_depth, g_normal, state,
-                                                 grad);
+                                                 grad, reuse ? 1 : 0);
   }
   if (evs && evs->ev && evs->n > 5) cudaEventRecord(evs->ev[5], st);
   if (evs && evs->ev && evs->n > 6) cudaEventRecord(evs->ev[6], st);

@@ -9,6 +9,10 @@
 
 namespace vtx {
 
+// Tile counts that the one-CTA scan covers (32 warps x 32 lanes x 32 values); more take the three-kernel scan,
+// whose tile list is unordered and holds the non-empty tiles only.
+constexpr long long kScanSingleMax = 32LL * 32 * 32;
+
 // Device buffers of one pipeline run (all owned by the context).
 struct Scratch {
   unsigned long long *keys;   // [n_img][H][W] packed (depth key << 32 | id)
@@ -18,7 +22,8 @@ struct Scratch {
   uint32_t *tile_start;       // [n_tiles + 1] exclusive prefix (tile_start[n_tiles] = total, clamped)
   uint32_t *tile_cursor;      // [n_tiles]
   uint32_t *block_sums;       // [ceil(n_tiles / 4096) + 1]
-  uint32_t *tile_list;        // [n_tiles] indices of the non-empty tiles
+  uint32_t *tile_list;        // [n_tiles] indices of the non-empty tiles, longest list first (one-CTA scan);
+                              // the soft path's one-CTA scan lists the empty tiles after them
   PrimRec *recs;              // [cap_rec]
   uint32_t *rec_img;          // [cap_rec] image of each record
   uint2 *rec_box;             // [cap_rec] tile box of each record: (x0 | y0 << 16, x1 | y1 << 16)
@@ -62,9 +67,11 @@ cudaError_t run_frame_pipeline(const Geometry &g, const ShadeParams &sh, const S
 // Soft-edge pipeline (binning shared with the hard path); backward when grad != null.
 // state: optional per-pixel (final transmittance, 1 + last contributor) planes, written by the forward
 // call and read by the backward call (which then skips its front-to-back walk).
+// reuse_lists (backward only): the scratch still holds the tile lists, records and tile order that the
+// forward call on the same inputs built and ordered; the backward skips the binning and the sort.
 cudaError_t run_soft_pipeline(const Geometry &g, const Scene &sc, const Scratch &s, float *cov, float *depth,
                               float *normal, const float *g_cov, const float *g_depth, const float *g_normal,
-                              float *grad, uint2 *state, cudaStream_t st, StageEvents *evs);
+                              float *grad, uint2 *state, bool reuse_lists, cudaStream_t st, StageEvents *evs);
 
 // Interleaved RGBA8 of n_img images of ppi pixels from the rgb and id planes (background alpha bg_a).
 cudaError_t run_export_rgba8(const float *rgb, const uint32_t *id, long long ppi, long long n_img, unsigned char bg_a,

@@ -133,3 +133,10 @@ def test_soft_tile_lists_longer_than_shared_memory_match_oracle():
                           torch.from_numpy(gN.T.reshape(1, 3, 64, 64).astype(np.float32)).cuda())
     g = g.cpu().numpy().astype(np.float64)
     assert np.linalg.norm(g - ref) <= 1e-4 * np.linalg.norm(ref)
+    # the forward leaves the long list sorted in place; a backward reusing it skips the global sort
+    r.render_soft_fwd(x, [cam])
+    g2 = r.render_soft_bwd(x, [cam], torch.from_numpy(gA.reshape(1, 64, 64).astype(np.float32)).cuda(),
+                           torch.from_numpy(gD.reshape(1, 64, 64).astype(np.float32)).cuda(),
+                           torch.from_numpy(gN.T.reshape(1, 3, 64, 64).astype(np.float32)).cuda(), reuse_lists=True)
+    g2 = g2.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(g2 - g) <= 1e-6 * np.linalg.norm(g)

@@ -319,3 +319,38 @@ def test_soft_state_and_async_paths_match_the_plain_calls(config5_run):
     assert np.linalg.norm(g - config5_run["g"]) <= 1e-6 * np.linalg.norm(config5_run["g"])
     r.render_soft_fwd(x, s.cameras, state=st, sync=False)
     assert r.soft_terms() > 100000
+
+
+def test_soft_backward_reuses_the_forward_lists_only_when_valid(config5_run):
+    """A backward call with the reuse flag takes the forward call's tile lists (no binning, no sort) and gives
+    the rebuilt-list gradients up to the order of the float atomics.  It is repeated (the tile queue restarts),
+    and the flag is refused, with the lists rebuilt, after another soft forward on other atoms and after a hard
+    frame render on the same context."""
+    import torch
+
+    import paper_2501_12750_gb300 as vtx
+    s, r, x = config5_run["s"], config5_run["r"], config5_run["x"]
+    gA, gD, gN = config5_run["gA_t"], config5_run["gD_t"], config5_run["gN_t"]
+    ref = config5_run["g"]
+
+    def close(g):
+        g = g.cpu().numpy().astype(np.float64)
+        return np.linalg.norm(g - ref) <= 1e-6 * np.linalg.norm(ref)
+
+    st = r.soft_state(s.cameras)
+    r.render_soft_fwd(x, s.cameras, state=st, sync=False)
+    assert close(r.render_soft_bwd(x, s.cameras, gA, gD, gN, state=st, sync=False, reuse_lists=True))
+    assert close(r.render_soft_bwd(x, s.cameras, gA, gD, gN, state=st, sync=False, reuse_lists=True))
+    r.sync_status()
+    # another forward (other atoms, other pointer) in between: the lists are those of the other atoms
+    other = torch.from_numpy(s.extra["target"]).cuda()
+    r.render_soft_fwd(x, s.cameras, state=st, sync=False)
+    r.render_soft_fwd(other, s.cameras, sync=False)
+    assert close(r.render_soft_bwd(x, s.cameras, gA, gD, gN, state=st, sync=False, reuse_lists=True))
+    # a hard frame on the same context in between overwrites the scratch
+    r.render_soft_fwd(x, s.cameras, state=st, sync=False)
+    r.upload_atoms(other, None, None)
+    r.set_camera(s.cameras[0])
+    r.render_frame(vtx.default_settings(), width=512, height=512)
+    assert close(r.render_soft_bwd(x, s.cameras, gA, gD, gN, state=st, sync=False, reuse_lists=True))
+    r.sync_status()
