@@ -71,7 +71,11 @@ __global__ __launch_bounds__(256) void k_clear(ImageState *st, int n_img, Status
     s.zlo = 0.0f;
     s.S = 0.0f;
     s.invS = 0.0f;
-    s.pad = 0.0f;
+    s.zsplit = 0.0f;
+    s.occl = 0u;
+    s.n_def = 0u;
+    s.n_vis = 0u;
+    s.n_near = 0u;
     st[tid] = s;
   }
   if (tid == 0) {
@@ -79,6 +83,7 @@ __global__ __launch_bounds__(256) void k_clear(ImageState *st, int n_img, Status
     status->n_entries = 0ull;
     status->n_terms = 0ull;
     status->soft_next = 0u;
+    status->tile_next = 0u;
     status->n_list = 0u;
     status->n_cov = 0u;
   }
@@ -577,6 +582,15 @@ __global__ __launch_bounds__(kCullThreads) void k_cull_bonds(Geometry g, const f
   }
 }
 
+#ifndef VTX_OCCL_SPLIT
+#define VTX_OCCL_SPLIT 0.25f
+#endif
+#ifndef VTX_OCCL_PIXELS
+#define VTX_OCCL_PIXELS 4
+#endif
+constexpr float kOcclSplit = VTX_OCCL_SPLIT;  // near-pass share of the image's depth range
+constexpr long long kOcclPixels = VTX_OCCL_PIXELS;  // occlusion pass from one survivor per this many pixels
+
 // Depth-key range per image: [zlo, zhi] of the survivors, widened past the
 // FP32 error of the cull and clamped to half the near plane.
 // Depth-key range of image img from its survivors' range (the cull's
@@ -596,6 +610,10 @@ __device__ __forceinline__ ImageState finalize_state(const Geometry &g, int img,
   s.S = kKeySpanF / (hi - lo);
   s.invS = (hi - lo) / kKeySpanF;
   s.valid = 1u;
+  // occlusion pass: images with at least one survivor per kOcclPixels pixels (a depth complexity at which
+  // most survivors are hidden); the near pass takes the survivors reaching the front kOcclSplit of the range
+  s.occl = (g.occl && !g.soft && (long long)s.n_surv * kOcclPixels >= g.pix_per_img) ? 1u : 0u;
+  s.zsplit = lo + (hi - lo) * kOcclSplit;
   return s;
 }
 
@@ -667,18 +685,25 @@ __device__ __forceinline__ bool prim_hit(const PrimGeom &p, float3 o, const PixR
 }
 
 // Ray-cast primitive p at every pixel of its candidate box, merging hits into the key plane K (one lane).
+// One flat loop over the box's pixels: the lanes of a warp, whose boxes differ in shape, then run for the
+// largest box's pixel count rather than for the most rows times the most columns.
 __device__ __forceinline__ void splat_box(const Geometry &g, const ViewParams &v, const PrimGeom &p, const PixBox &box,
                                           float S, uint32_t id, unsigned long long *K) {
-  for (int py = box.y0; py <= box.y1; ++py)
-    for (int px = box.x0; px <= box.x1; ++px) {
-      PixRay r = pix_ray(v, px, py);
-      float3 o = local_o(p.su.u0.hi, p.su.u0.lo, p.su.v0.hi, p.su.v0.lo, p.su.k, p.su.dz, r);
-      float sh;
-      int kind;
-      float axial;
-      if (prim_hit(p, o, r, sh, kind, axial) && p.su.zr + sh >= v.znear)
-        atomicMin(K + (long long)py * g.W + px, pack_key(p.su.keyc, sh, S, id));
+  const int npix = (box.x1 - box.x0 + 1) * (box.y1 - box.y0 + 1);
+  int px = box.x0, py = box.y0;
+  for (int i = 0; i < npix; ++i) {
+    PixRay r = pix_ray(v, px, py);
+    float3 o = local_o(p.su.u0.hi, p.su.u0.lo, p.su.v0.hi, p.su.v0.lo, p.su.k, p.su.dz, r);
+    float sh;
+    int kind;
+    float axial;
+    if (prim_hit(p, o, r, sh, kind, axial) && p.su.zr + sh >= v.znear)
+      atomicMin(K + (long long)py * g.W + px, pack_key(p.su.keyc, sh, S, id));
+    if (++px > box.x1) {
+      px = box.x0;
+      ++py;
     }
+  }
 }
 
 // Setup occupancy: 4 CTAs per SM (63 registers, a few bytes spilled) and 8
@@ -695,22 +720,29 @@ __global__ __launch_bounds__(256, VTX_SETUP_MINB) void k_setup(Geometry g, const
                                                const uint2 *__restrict__ bonds, ImageState *st,
                                                const uint32_t *__restrict__ surv, unsigned long long *keys,
                                                PrimRec *recs, uint32_t *rec_img, uint2 *rec_box, uint32_t *rec_of,
-                                               uint32_t *tile_count, Status *status, uint32_t cap_rec) {
+                                               uint32_t *tile_count, Status *status, uint32_t cap_rec,
+                                               const uint32_t *near, int pass) {
   pdl_enter();
   const int img = blockIdx.y;
   const ImageState s = finalize_state(g, img, st[img]);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (pass <= 1 && blockIdx.x == 0 && threadIdx.x == 0) {
     st[img].zlo = s.zlo;
     st[img].S = s.S;
     st[img].invS = s.invS;
     st[img].valid = s.valid;
   }
   if (!s.valid) return;
+  // pass 0: every survivor (no occlusion pass).  An occlusion image takes its near survivors in pass 1 and the
+  // deferred ones the occlusion test kept (written over its survivor list) in pass 2; any other image takes
+  // all its survivors in pass 1.
+  if (pass == 2 && !s.occl) return;
+  const bool near_list = pass == 1 && s.occl;
   const ViewParams &v = g.views[img % g.n_views];
   const int frame = img / g.n_views;
   const float4 *X = frames + (long long)frame * g.stride;
-  const long long n = min((long long)s.n_surv, g.surv_cap);
-  const uint32_t *sv = surv + (long long)img * g.surv_cap;
+  const ImageState cnt = st[img];  // the counts written by the occlusion kernels
+  const long long n = min((long long)(near_list ? cnt.n_near : (pass == 2 ? cnt.n_vis : s.n_surv)), g.surv_cap);
+  const uint32_t *sv = (near_list ? near : surv) + (long long)img * g.surv_cap;
   unsigned long long *K = keys + (long long)img * g.pix_per_img;
   const int lane = threadIdx.x & 31;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -810,6 +842,203 @@ __global__ __launch_bounds__(256, VTX_SETUP_MINB) void k_setup(Geometry g, const
         if (tile >= 0 && lane == __ffs(peers) - 1) atomicAdd(tc + tile, (unsigned)__popc(peers));
       }
     }
+  }
+}
+
+// ------------------------------------------------------- occlusion pass --
+// Images with many survivors per pixel (a trajectory blob seen whole) spend most of their setup on spheres
+// that lose every depth test.  k_occl_split lists an occlusion image's survivors in two compact lists: those
+// reaching the front kOcclSplit of the depth range (from the start of the image's deferred slots) and the
+// rest (from the end); setup pass 1 takes the near list; k_occl_test drops a deferred sphere when the
+// smallest depth key any of its hits could have exceeds the depth key every pixel of its candidate box
+// already holds (each of its atomicMin calls would then leave the key unchanged: keys only decrease) and
+// lists the others over the survivor list, which setup pass 2 takes.  Lists are compacted so that setup
+// warps stay converged.
+// Exact: the planes are those of the plain pass, bit for bit.
+
+// Survivors per lane per step of the occlusion kernels: a warp takes 128 consecutive list entries (coalesced
+// loads of four independent items in flight) and reserves its output slots with one atomic per list.
+constexpr int kOcclItems = 4;
+
+// Warp-wide placement of up to kOcclItems flagged items per lane: one atomicAdd on *counter for the warp's
+// total; returns each item's slot in the list, in item-major order of the flags.
+__device__ __forceinline__ void occl_slots(const bool (&f)[kOcclItems], unsigned *counter, int lane,
+                                           unsigned (&slot)[kOcclItems]) {
+  unsigned m[kOcclItems], tot = 0u;
+#pragma unroll
+  for (int j = 0; j < kOcclItems; ++j) {
+    m[j] = __ballot_sync(0xffffffffu, f[j]);
+    tot += (unsigned)__popc(m[j]);
+  }
+  unsigned base = 0u;
+  if (lane == 0 && tot) base = atomicAdd(counter, tot);
+  base = __shfl_sync(0xffffffffu, base, 0);
+  const unsigned below = (1u << lane) - 1u;
+#pragma unroll
+  for (int j = 0; j < kOcclItems; ++j) {
+    slot[j] = base + (unsigned)__popc(m[j] & below);
+    base += (unsigned)__popc(m[j]);
+  }
+}
+
+__global__ __launch_bounds__(256) void k_occl_split(Geometry g, const float4 *__restrict__ frames, ImageState *st,
+                                                    const uint32_t *__restrict__ surv, uint32_t *lists) {
+  pdl_enter();
+  const int img = blockIdx.y;
+  const ImageState s = finalize_state(g, img, st[img]);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st[img].zsplit = s.zsplit;
+    st[img].occl = s.occl;
+  }
+  if (!s.valid || !s.occl) return;
+  const long long n = min((long long)s.n_surv, g.surv_cap);
+  const ViewParams &v = g.views[img % g.n_views];
+  const float4 *X = frames + (long long)(img / g.n_views) * g.stride;
+  const uint32_t *sv = surv + (long long)img * g.surv_cap;
+  uint32_t *L = lists + (long long)img * g.surv_cap;
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long base = warp * 32 * kOcclItems; base < n; base += warps * 32 * kOcclItems) {
+    uint32_t id[kOcclItems];
+    bool near[kOcclItems], far[kOcclItems];
+#pragma unroll
+    for (int j = 0; j < kOcclItems; ++j) {
+      const long long k = base + j * 32 + lane;
+      id[j] = k < n ? sv[k] : kNoId;
+    }
+#pragma unroll
+    for (int j = 0; j < kOcclItems; ++j) {
+      near[j] = far[j] = false;
+      if (id[j] != kNoId && (long long)id[j] >= g.n_atoms) {
+        near[j] = true;  // not an atom record (the occlusion pass is for atoms): setup takes it as usual
+      } else if (id[j] != kNoId) {
+        const float4 a = X[id[j]];
+        const float r = atom_radius(g, a.w);
+        float vx, vy, vz, err;
+        view_f32(v, a.x, a.y, a.z, vx, vy, vz, err);
+        PixBox box;
+        if (lean_box(v, g.W, g.H, vx, vy, vz, r + err, box)) {  // an empty box can change no pixel
+          far[j] = vz - r - err > s.zsplit;
+          near[j] = !far[j];
+        }
+      }
+    }
+    unsigned sn[kOcclItems], sf[kOcclItems];
+    occl_slots(near, &st[img].n_near, lane, sn);
+    occl_slots(far, &st[img].n_def, lane, sf);
+    // near + far <= n <= surv_cap: the two lists never meet
+#pragma unroll
+    for (int j = 0; j < kOcclItems; ++j) {
+      if (near[j]) L[sn[j]] = id[j];
+      if (far[j]) L[g.surv_cap - 1 - sf[j]] = id[j];
+    }
+  }
+}
+
+// Most pixels a deferred sphere's box may have and still be tested (larger boxes are kept).
+constexpr int kOcclMaxPixels = 64;
+
+// A 16-bit depth plane of the keys after the near pass: q = (depth key) >> 16, so the pixel's key is below
+// (q + 1) * 65536 (the background key gives q = 65535, which no sphere is behind).  2 bytes per pixel instead
+// of 8: the test's scattered reads of all the images in flight then stay in L2.  Four pixels per thread.
+__global__ __launch_bounds__(256) void k_occl_depth(Geometry g, const ImageState *__restrict__ st,
+                                                    const unsigned long long *__restrict__ keys, uint16_t *plane) {
+  pdl_enter();
+  const int img = blockIdx.y;
+  const ImageState s = st[img];
+  if (!s.valid || !s.occl || s.n_def == 0u) return;
+  const unsigned long long *K = keys + (long long)img * g.pix_per_img;
+  uint16_t *P = plane + (long long)img * g.pix_per_img;
+  const long long quads = (g.pix_per_img + 3) / 4;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < quads; q += (long long)gridDim.x * blockDim.x) {
+    const long long p0 = q * 4;
+    if (p0 + 4 <= g.pix_per_img) {
+      const ulonglong2 a = __ldcs(reinterpret_cast<const ulonglong2 *>(K + p0));
+      const ulonglong2 b = __ldcs(reinterpret_cast<const ulonglong2 *>(K + p0) + 1);
+      const ushort4 w = make_ushort4((unsigned short)(a.x >> 48), (unsigned short)(a.y >> 48),
+                                     (unsigned short)(b.x >> 48), (unsigned short)(b.y >> 48));
+      *reinterpret_cast<ushort4 *>(P + p0) = w;
+    } else {
+      for (long long p = p0; p < g.pix_per_img; ++p) P[p] = (uint16_t)(K[p] >> 48);
+    }
+  }
+}
+
+// Is the sphere at FP32 view position (vz, err) with radius r, candidate box `box`, hidden in every pixel of
+// its box by the keys already there (read from the 16-bit depth plane P)?  lb: the smallest depth key any of its hits could have -- its front (vz - r,
+// widened by the view error and by 2e-7 of the depths for the FP32 rounding of these differences) mapped to
+// keys, less 4e-6 relative plus 4096 keys for the rounding of the product, of the reference key and of the
+// hit offset (tens of keys); compared in FP32 with the pixels' depth keys (rounded to nearest, within 256
+// keys of the integers).  Boxes of at most 4 x 4 pixels (the common case) load all their depth words at once.
+__device__ __forceinline__ bool occl_hidden(const Geometry &g, const ViewParams &v, const ImageState &s,
+                                            const uint16_t *P, float vz, float err, float r, const PixBox &box) {
+  if (!(vz > 2.0f * (r + err) + v.znear)) return false;
+  float lb = (vz - err - r * 1.000002f - s.zlo - 2e-7f * (fabsf(vz) + fabsf(s.zlo))) * s.S;
+  lb = lb - fabsf(lb) * 4e-6f - 4096.0f;
+  // hidden at a pixel when (q + 1) * 65536 <= lb: exact in FP32 (q + 1 <= 65536 times a power of two)
+  const float qmax = lb * (1.0f / 65536.0f) - 1.0f;  // q + 1 <= lb / 65536 (the scaling is exact)
+  const int w = box.x1 - box.x0 + 1, h = box.y1 - box.y0 + 1;
+  const uint16_t *Pb = P + (long long)box.y0 * g.W + box.x0;
+  if (w <= 4 && h <= 4) {
+    unsigned short kd[16];
+#pragma unroll
+    for (int dy = 0; dy < 4; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 4; ++dx) kd[dy * 4 + dx] = (dx < w && dy < h) ? Pb[(long long)dy * g.W + dx] : 0;
+    bool hidden = true;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) hidden = hidden && (float)kd[q] <= qmax;
+    return hidden;
+  }
+  if (w * h > kOcclMaxPixels) return false;
+  for (int dy = 0; dy < h; ++dy)
+    for (int dx = 0; dx < w; ++dx)
+      if (!((float)Pb[(long long)dy * g.W + dx] <= qmax)) return false;
+  return true;
+}
+
+__global__ __launch_bounds__(256) void k_occl_test(Geometry g, const float4 *__restrict__ frames, ImageState *st,
+                                                   const uint32_t *__restrict__ lists,
+                                                   const uint16_t *__restrict__ plane, uint32_t *surv) {
+  pdl_enter();
+  const int img = blockIdx.y;
+  const ImageState s = st[img];
+  if (!s.valid || !s.occl) return;
+  const long long n = min((long long)s.n_def, g.surv_cap);
+  const ViewParams &v = g.views[img % g.n_views];
+  const float4 *X = frames + (long long)(img / g.n_views) * g.stride;
+  const uint32_t *D = lists + (long long)img * g.surv_cap + (g.surv_cap - n);  // the deferred list's n slots
+  const uint16_t *P = plane + (long long)img * g.pix_per_img;
+  uint32_t *vis = surv + (long long)img * g.surv_cap;
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long base = warp * 32 * kOcclItems; base < n; base += warps * 32 * kOcclItems) {
+    uint32_t id[kOcclItems];
+    bool keep[kOcclItems];
+#pragma unroll
+    for (int j = 0; j < kOcclItems; ++j) {
+      const long long k = base + j * 32 + lane;
+      id[j] = k < n ? D[k] : kNoId;
+    }
+#pragma unroll
+    for (int j = 0; j < kOcclItems; ++j) {
+      keep[j] = false;
+      if (id[j] != kNoId) {
+        const float4 a = X[id[j]];
+        const float r = atom_radius(g, a.w);
+        float vx, vy, vz, err;
+        view_f32(v, a.x, a.y, a.z, vx, vy, vz, err);
+        PixBox box;
+        keep[j] = lean_box(v, g.W, g.H, vx, vy, vz, r + err, box) && !occl_hidden(g, v, s, P, vz, err, r, box);
+      }
+    }
+    unsigned sk[kOcclItems];
+    occl_slots(keep, &st[img].n_vis, lane, sk);
+#pragma unroll
+    for (int j = 0; j < kOcclItems; ++j)
+      if (keep[j]) vis[sk[j]] = id[j];
   }
 }
 
@@ -1115,10 +1344,17 @@ __global__ __launch_bounds__(256) void k_scatter(Geometry g, const PrimRec *__re
 // after the first).
 constexpr int kRasterBuckets = 256;
 
-template <int NT>
+template <int TW, int TH>
+__device__ __forceinline__ uint32_t entry_box(const PrimRec *__restrict__ recs, uint32_t ri, int tx0, int ty0,
+                                              float uu_max);
+
+// While placing each entry, the final pass also stores its 16-bit pixel box (entry_box) beside it in s_box.
+template <int TW, int TH>
 __device__ __forceinline__ void bucket_order(const unsigned long long *__restrict__ src, int m,
                                              unsigned long long *s_e, uint16_t *s_off, uint32_t *s_cnt,
-                                             uint32_t *s_lo, uint32_t *s_red) {
+                                             uint32_t *s_lo, uint32_t *s_red, const PrimRec *__restrict__ recs,
+                                             uint16_t *s_box, int tx0, int ty0, float uu_tile) {
+  constexpr int NT = TW * TH;
   constexpr int NB = kRasterBuckets;
   static_assert(NB % NT == 0 && NT <= NB, "buckets per thread");
   constexpr int PER = NB / NT;
@@ -1184,7 +1420,9 @@ __device__ __forceinline__ void bucket_order(const unsigned long long *__restric
     const unsigned long long e = src[i];
     const uint32_t k = (uint32_t)(e >> 32);
     const int b = min(NB - 1, (int)((float)(k - lo) * scale));
-    s_e[s_cnt[b] + s_off[i]] = ((unsigned long long)s_lo[b] << 32) | (e & 0xffffffffull);
+    const uint32_t pos = s_cnt[b] + s_off[i];
+    s_e[pos] = ((unsigned long long)s_lo[b] << 32) | (e & 0xffffffffull);
+    s_box[pos] = (uint16_t)entry_box<TW, TH>(recs, (uint32_t)e, tx0, ty0, uu_tile);
   }
   __syncthreads();
 }
@@ -1200,41 +1438,130 @@ constexpr int kListCap = 2048;
 // pixel distance d from the projected centre exceeds Rb |u|_max / k.  The
 // radius is widened (0.1 % plus 0.01 px plus 2e-7 of the coordinates) so that
 // FP32 rounding never drops an entry the hit test would accept.
+// Pixel radius about (cu, cv) outside which no ray with |u|^2 <= uu_max meets the bounding sphere.
+__device__ __forceinline__ float raster_reach(float hl, float rad, float k, float cu, float cv, float uu_max) {
+  const float rb2 = fmaf(hl, hl, rad * rad);
+  const float rb = hl == 0.0f ? rad : rb2 * rsqrtf(rb2);
+  return __fdividef(rb * uu_max * rsqrtf(uu_max), k) * 1.001f + 0.01f + 2e-7f * (fabsf(cu) + fabsf(cv));
+}
+
 __device__ __forceinline__ bool raster_keep(const PrimRec &p, unsigned x0, unsigned x1, unsigned y0, unsigned y1,
                                             float uu_max) {
   if (p.dz != 0.0f) return true;
-  const float rb2 = fmaf(p.hl, p.hl, p.rad * p.rad);
-  const float rb = p.hl == 0.0f ? p.rad : rb2 * rsqrtf(rb2);
   const float cu = p.u0h + p.u0l, cv = p.v0h + p.v0l;
   const float dx = fmaxf(fmaxf((float)x0 + 0.5f - cu, cu - ((float)x1 + 0.5f)), 0.0f);
   const float dy = fmaxf(fmaxf((float)y0 + 0.5f - cv, cv - ((float)y1 + 0.5f)), 0.0f);
-  const float rt = __fdividef(rb * uu_max * rsqrtf(uu_max), p.k) * 1.001f + 0.01f + 2e-7f * (fabsf(cu) + fabsf(cv));
+  const float rt = raster_reach(p.hl, p.rad, p.k, cu, cv, uu_max);
   return !(dx * dx + dy * dy > rt * rt);
+}
+
+// The tile pixels an entry can reach, as a 16-bit box of tile-local indices (x0, x1, y0, y1 in XB, XB, YB, YB
+// bits; x0 > x1 when it reaches none).  A pixel whose centre lies farther than the reach from the projected
+// centre along x or along y is farther than the reach in the plane, so its ray cannot meet the bounding
+// sphere; the box keeps every other pixel.  uu_max bounds |u|^2 over the whole tile.  Computed once per
+// entry while the tile is ordered, it lets a warp skip, without loading their records, the entries that
+// cannot reach any of its still-searching pixels.
+template <int TW, int TH>
+__device__ __forceinline__ uint32_t entry_box(const PrimRec *__restrict__ recs, uint32_t ri, int tx0, int ty0,
+                                              float uu_max) {
+  constexpr int XB = TW == 32 ? 5 : (TW == 16 ? 4 : 3), YB = TH == 16 ? 4 : 3;
+  static_assert((1 << XB) == TW && (1 << YB) == TH && 2 * (XB + YB) <= 16, "tile shape");
+  const PrimRec *pr = recs + ri;
+  const float4 uv = __ldg(reinterpret_cast<const float4 *>(pr));      // u0h, u0l, v0h, v0l
+  const float4 zk = __ldg(reinterpret_cast<const float4 *>(pr) + 1);  // zr, k, dz, rad
+  const float hl = __ldg(&pr->hl);
+  int x0 = 0, x1 = TW - 1, y0 = 0, y1 = TH - 1;
+  if (zk.z == 0.0f) {
+    const float cu = uv.x + uv.y, cv = uv.z + uv.w;
+    const float rt = raster_reach(hl, zk.w, zk.y, cu, cv, uu_max);
+    // pixel px is kept when |px + 0.5 - cu| <= rt; clamped to the tile in float first (no int overflow)
+    const float lo_x = fmaxf(ceilf(cu - rt - 0.5f) - (float)tx0, 0.0f);
+    const float hi_x = fminf(floorf(cu + rt - 0.5f) - (float)tx0, (float)(TW - 1));
+    const float lo_y = fmaxf(ceilf(cv - rt - 0.5f) - (float)ty0, 0.0f);
+    const float hi_y = fminf(floorf(cv + rt - 0.5f) - (float)ty0, (float)(TH - 1));
+    if (!(lo_x <= hi_x && lo_y <= hi_y)) return (uint32_t)(TW - 1);  // x0 = TW - 1 > x1 = 0: no pixel
+    x0 = (int)lo_x;
+    x1 = (int)hi_x;
+    y0 = (int)lo_y;
+    y1 = (int)hi_y;
+  }
+  return (uint32_t)x0 | ((uint32_t)x1 << XB) | ((uint32_t)y0 << (2 * XB)) | ((uint32_t)y1 << (2 * XB + YB));
+}
+
+// Does the box meet the rectangle [x0, x1] x [y0, y1] (tile-local; empty when x0 > x1)?
+template <int TW, int TH>
+__device__ __forceinline__ bool box_meets(uint32_t b, int x0, int x1, int y0, int y1) {
+  constexpr int XB = TW == 32 ? 5 : (TW == 16 ? 4 : 3), YB = TH == 16 ? 4 : 3;
+  const int bx0 = (int)(b & (TW - 1)), bx1 = (int)((b >> XB) & (TW - 1));
+  const int by0 = (int)((b >> (2 * XB)) & (TH - 1)), by1 = (int)((b >> (2 * XB + YB)) & (TH - 1));
+  return bx0 <= bx1 && bx0 <= x1 && x0 <= bx1 && by0 <= y1 && y0 <= by1;
 }
 
 // Dynamic shared memory of the raster: the segment's ordered entries, then per warp two 32-record windows
 // (the one being tested and the next one, filled by cp.async meanwhile), which also hold the bucket offsets
-// while a segment is ordered.
+// while a segment is ordered, then the entries' 16-bit pixel boxes.
 template <int NT>
-constexpr size_t raster_smem() {
-  return kListCap * sizeof(unsigned long long) +
-         (NT * 2 * sizeof(PrimRec) > kListCap * 2 ? NT * 2 * sizeof(PrimRec) : kListCap * 2);
+__host__ __device__ constexpr size_t raster_windows() {
+  return NT * 2 * sizeof(PrimRec) > kListCap * 2 ? NT * 2 * sizeof(PrimRec) : kListCap * 2;
+}
+template <int NT>
+__host__ __device__ constexpr size_t raster_smem() {
+  return kListCap * sizeof(unsigned long long) + raster_windows<NT>() + kListCap * sizeof(uint16_t);
 }
 
-// Copy the 64-byte records of window entries [c0, c0 + 32) into this warp's window w (one record per lane,
-// four 16-byte asynchronous copies) and close the lane's commit group (an empty group past the end, so every
-// lane always has the same number of groups in flight).
-__device__ __forceinline__ void raster_stage(const PrimRec *__restrict__ recs, const unsigned long long *s_e, int m,
-                                             int c0, PrimRec *w, int lane) {
-  if (c0 + lane < m) {
+// Copy the 64-byte records of the window entries [c0, c0 + 32) whose pixel boxes meet the rectangle
+// [x0, x1] x [y0, y1] of the warp's still-searching pixels into this warp's window w (one record per lane,
+// four 16-byte asynchronous copies) and close the lane's commit group (an empty group when the lane copies
+// nothing, so every lane always has the same number of groups in flight).  Returns the warp's mask of copied
+// entries: the others are neither loaded nor read, and a window with none is skipped without a wait.
+template <int TW, int TH>
+__device__ __forceinline__ unsigned raster_stage(const PrimRec *__restrict__ recs, const unsigned long long *s_e,
+                                                 const uint16_t *s_box, int m, int c0, PrimRec *w, int lane, int x0,
+                                                 int x1, int y0, int y1) {
+  const bool take = c0 + lane < m && box_meets<TW, TH>(s_box[c0 + lane], x0, x1, y0, y1);
+  if (take) {
     const char *src = reinterpret_cast<const char *>(recs + (uint32_t)s_e[c0 + lane]);
     char *dst = reinterpret_cast<char *>(w + lane);
 #pragma unroll
     for (int b = 0; b < 64; b += 16) cp_async16(dst + b, src + b);
   }
   cp_async_commit();
+  return __ballot_sync(0xffffffffu, take);
 }
 
+// |u|^2 bound over a whole tile: the ray slopes of its extreme columns and rows (pix_ray's operations, and
+// every rounded step is monotone, so no pixel of the tile has a larger |u|^2).
+template <int TW, int TH>
+__device__ __forceinline__ float tile_uu_max(const ViewParams &v, int tx, int ty) {
+  const float a0 = fabsf(__fmul_rn(__fsub_rn((float)(tx * TW) + 0.5f, v.cx), v.inv_f));
+  const float a1 = fabsf(__fmul_rn(__fsub_rn((float)(tx * TW + TW - 1) + 0.5f, v.cx), v.inv_f));
+  const float b0 = fabsf(__fmul_rn(__fsub_rn(v.cy, (float)(ty * TH) + 0.5f), v.inv_f));
+  const float b1 = fabsf(__fmul_rn(__fsub_rn(v.cy, (float)(ty * TH + TH - 1) + 0.5f), v.inv_f));
+  const float am = fmaxf(a0, a1), bm = fmaxf(b0, b1);
+  return fmaf(am, am, fmaf(bm, bm, 1.0f));
+}
+
+#ifndef VTX_RASTER_PAIR
+#define VTX_RASTER_PAIR 1  // test two window entries per step
+#endif
+
+// The packed key of record p's hit at pixel ray r, or the background key when the ray misses it.
+__device__ __forceinline__ unsigned long long raster_hit(const PrimRec &p, const PixRay &r, float znear, float S) {
+  const float3 o = local_o(p.u0h, p.u0l, p.v0h, p.v0l, p.k, p.dz, r);
+  float s;
+  bool hit;
+  if (p.hl == 0.0f) {
+    hit = sphere_local(o, r, p.rad, s);
+  } else {
+    int kind;
+    float axial;
+    hit = cylinder_local(o, r, make_float3(p.ax, p.ay, p.az), p.hl, p.rad, s, kind, axial);
+  }
+  return (hit && p.zr + s >= znear) ? pack_key(rec_key(p), s, S, p.id) : kBgKey;
+}
+
+// One CTA per tile at a time, the non-empty tiles longest first from a queue (as many CTAs as are resident):
+// the tile's list is ordered by depth bucket with every entry's pixel box; then each warp walks it on its own.
 template <int TW, int TH>
 __global__ __launch_bounds__(TW *TH) void k_raster(Geometry g, const PrimRec *__restrict__ recs,
                                                    const unsigned long long *__restrict__ entries,
@@ -1249,80 +1576,97 @@ __global__ __launch_bounds__(TW *TH) void k_raster(Geometry g, const PrimRec *__
   extern __shared__ __align__(16) unsigned char raster_smem_raw[];
   unsigned long long *s_e = reinterpret_cast<unsigned long long *>(raster_smem_raw);
   unsigned char *s_raw = raster_smem_raw + kListCap * sizeof(unsigned long long);
+  uint16_t *s_box = reinterpret_cast<uint16_t *>(s_raw + raster_windows<NT>());
   __shared__ uint32_t s_cnt[kRasterBuckets], s_lo[kRasterBuckets], s_red[2];
+  __shared__ uint32_t s_li;
   PrimRec *s_w = reinterpret_cast<PrimRec *>(s_raw) + 2 * (threadIdx.x & ~31u);  // this warp's two windows
   const int lane = threadIdx.x & 31;
+  const int lx = (int)(threadIdx.x % TW), ly = (int)(threadIdx.x / TW);  // tile-local pixel
   const uint32_t n_list = status->n_list;
-  for (uint32_t li = blockIdx.x; li < n_list; li += gridDim.x) {  // only the non-empty tiles
-  const long long gt = tile_list[li];
-  const int img = (int)(gt / g.tiles_per_img);
-  const int t = (int)(gt % g.tiles_per_img);
-  uint32_t cnt = tile_count[gt];
-  if (cnt == 0u) continue;
-  const uint32_t start = tile_start[gt];
-  if ((unsigned long long)start >= cap_entries) continue;
-  if ((unsigned long long)start + cnt > cap_entries) cnt = (uint32_t)(cap_entries - start);
-  const ViewParams &v = g.views[img % g.n_views];
-  const float S = st[img].S;
-  const int tx = t % g.tiles_x, ty = t / g.tiles_x;
-  const int px = tx * TW + (threadIdx.x % TW), py = ty * TH + (threadIdx.x / TW);
-  const bool inside = px < g.W && py < g.H;
-  const PixRay r = pix_ray(v, px, py);
-  const float uu_max = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(r.uu)));
-  unsigned long long *K = keys + (long long)img * g.pix_per_img + (long long)py * g.W + px;
-  unsigned long long best = inside ? *K : kBgKey;
-  if (threadIdx.x == 0) atomicMax(&status->max_list, cnt);
-  for (uint32_t seg = 0; seg < cnt; seg += kListCap) {
-    const int m = (int)min((uint32_t)kListCap, cnt - seg);
-    bucket_order<NT>(entries + start + seg, m, s_e, reinterpret_cast<uint16_t *>(s_raw), s_cnt, s_lo, s_red);
-    // each warp walks the sorted segment on its own, 32 entries at a time, the next window's records
-    // arriving by cp.async while the current one is tested; a pixel is finished once its hit is nearer
-    // than the next entry's nearest possible depth
-    bool done = !inside;
-    int wb = 0;
-    raster_stage(recs, s_e, m, 0, s_w, lane);
-    for (int c0 = 0; c0 < m; c0 += 32, wb ^= 32) {
-      if (!done && (uint32_t)(best >> 32) < (uint32_t)(s_e[c0] >> 32)) done = true;
-      if (__all_sync(0xffffffffu, done)) break;
-      raster_stage(recs, s_e, m, c0 + 32, s_w + (wb ^ 32), lane);
-      cp_async_wait<1>();  // this window's copies have landed (the next window's may still be in flight)
-      __syncwarp();
-      const PrimRec *win = s_w + wb;
-      const unsigned x0 = __reduce_min_sync(0xffffffffu, done ? 0xffffffffu : (unsigned)px);
-      const unsigned x1 = __reduce_max_sync(0xffffffffu, done ? 0u : (unsigned)px);
-      const unsigned y0 = __reduce_min_sync(0xffffffffu, done ? 0xffffffffu : (unsigned)py);
-      const unsigned y1 = __reduce_max_sync(0xffffffffu, done ? 0u : (unsigned)py);
-      const bool keep = c0 + lane < m && raster_keep(win[lane], x0, x1, y0, y1, uu_max);
-      const unsigned kept = __ballot_sync(0xffffffffu, keep);
-      for (unsigned b = kept; b != 0u; b &= b - 1u) {
-        const int q = __ffs(b) - 1;
-        if (done) continue;
-        if ((uint32_t)(best >> 32) < (uint32_t)(s_e[c0 + q] >> 32)) {
-          done = true;
+  for (;;) {
+    __syncthreads();  // every thread has read the previous tile's index
+    if (threadIdx.x == 0) s_li = atomicAdd(&status->tile_next, 1u);
+    __syncthreads();
+    const uint32_t li = s_li;
+    if (li >= n_list) break;
+    const long long gt = tile_list[li];
+    const int img = (int)(gt / g.tiles_per_img);
+    const int t = (int)(gt % g.tiles_per_img);
+    uint32_t cnt = tile_count[gt];
+    if (cnt == 0u) continue;
+    const uint32_t start = tile_start[gt];
+    if ((unsigned long long)start >= cap_entries) continue;
+    if ((unsigned long long)start + cnt > cap_entries) cnt = (uint32_t)(cap_entries - start);
+    const ViewParams &v = g.views[img % g.n_views];
+    const float S = st[img].S;
+    const int tx = t % g.tiles_x, ty = t / g.tiles_x;
+    const int px = tx * TW + lx, py = ty * TH + ly;
+    const bool inside = px < g.W && py < g.H;
+    const PixRay r = pix_ray(v, px, py);
+    const float uu_max = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(r.uu)));
+    const float uu_tile = tile_uu_max<TW, TH>(v, tx, ty);
+    unsigned long long *K = keys + (long long)img * g.pix_per_img + (long long)py * g.W + px;
+    unsigned long long best = inside ? *K : kBgKey;
+    if (threadIdx.x == 0) atomicMax(&status->max_list, cnt);
+    for (uint32_t seg = 0; seg < cnt; seg += kListCap) {
+      const int m = (int)min((uint32_t)kListCap, cnt - seg);
+      bucket_order<TW, TH>(entries + start + seg, m, s_e, reinterpret_cast<uint16_t *>(s_raw), s_cnt, s_lo, s_red,
+                           recs, s_box, tx * TW, ty * TH, uu_tile);
+      // each warp walks the sorted segment on its own, 32 entries at a time, the next window's records
+      // arriving by cp.async while the current one is tested; only the entries whose pixel boxes meet the
+      // rectangle of the warp's still-searching pixels are loaded; a pixel is finished once its hit is nearer
+      // than the next entry's nearest possible depth
+      bool done = !inside;
+      int wb = 0;
+      int rx0 = __reduce_min_sync(0xffffffffu, done ? TW : lx), rx1 = __reduce_max_sync(0xffffffffu, done ? -1 : lx);
+      int ry0 = __reduce_min_sync(0xffffffffu, done ? TH : ly), ry1 = __reduce_max_sync(0xffffffffu, done ? -1 : ly);
+      unsigned cur = raster_stage<TW, TH>(recs, s_e, s_box, m, 0, s_w, lane, rx0, rx1, ry0, ry1);
+      for (int c0 = 0; c0 < m; c0 += 32, wb ^= 32) {
+        if (!done && (uint32_t)(best >> 32) < (uint32_t)(s_e[c0] >> 32)) done = true;
+        if (__all_sync(0xffffffffu, done)) break;
+        rx0 = __reduce_min_sync(0xffffffffu, done ? TW : lx);
+        rx1 = __reduce_max_sync(0xffffffffu, done ? -1 : lx);
+        ry0 = __reduce_min_sync(0xffffffffu, done ? TH : ly);
+        ry1 = __reduce_max_sync(0xffffffffu, done ? -1 : ly);
+        const unsigned nxt = raster_stage<TW, TH>(recs, s_e, s_box, m, c0 + 32, s_w + (wb ^ 32), lane, rx0, rx1, ry0,
+                                                  ry1);
+        if (cur == 0u) {  // nothing of this window can reach the warp's pixels: no record was loaded
+          cur = nxt;
           continue;
         }
-        const PrimRec &p = win[q];
-        float3 o = local_o(p.u0h, p.u0l, p.v0h, p.v0l, p.k, p.dz, r);
-        float s;
-        bool hit;
-        if (p.hl == 0.0f) {
-          hit = sphere_local(o, r, p.rad, s);
-        } else {
-          int kind;
-          float axial;
-          hit = cylinder_local(o, r, make_float3(p.ax, p.ay, p.az), p.hl, p.rad, s, kind, axial);
+        cp_async_wait<1>();  // this window's copies have landed (the next window's may still be in flight)
+        __syncwarp();
+        const PrimRec *win = s_w + wb;
+        const unsigned x0 = (unsigned)(tx * TW + rx0), x1 = (unsigned)(tx * TW + rx1);
+        const unsigned y0 = (unsigned)(ty * TH + ry0), y1 = (unsigned)(ty * TH + ry1);
+        const bool keep = ((cur >> lane) & 1u) && raster_keep(win[lane], x0, x1, y0, y1, uu_max);
+        const unsigned kept = __ballot_sync(0xffffffffu, keep);
+        // two entries per step: their hit tests are independent chains the scheduler can interleave.  The
+        // second is tested even when the first's bound would have finished the pixel after the first's
+        // hit: one more candidate leaves the minimum unchanged, and the next step checks the bound again.
+        for (unsigned b = kept; b != 0u;) {
+          const int q1 = __ffs(b) - 1;
+          b &= b - 1u;
+          const int q2 = b != 0u ? __ffs(b) - 1 : -1;
+          if (b != 0u) b &= b - 1u;
+          if (done) continue;
+          if ((uint32_t)(best >> 32) < (uint32_t)(s_e[c0 + q1] >> 32)) {
+            done = true;
+            continue;
+          }
+          const unsigned long long k1 = raster_hit(win[q1], r, v.znear, S);
+          const unsigned long long k2 = (VTX_RASTER_PAIR && q2 >= 0) ? raster_hit(win[q2], r, v.znear, S) : kBgKey;
+          if (!VTX_RASTER_PAIR && q2 >= 0) b |= 1u << q2;  // one entry per step: the second waits for the next
+          best = k1 < best ? k1 : best;
+          best = k2 < best ? k2 : best;
         }
-        if (hit && p.zr + s >= v.znear) {
-          unsigned long long key = pack_key(rec_key(p), s, S, p.id);
-          best = key < best ? key : best;
-        }
+        __syncwarp();  // every lane is done with this window before it is refilled
+        cur = nxt;
       }
-      __syncwarp();  // every lane is done with this window before it is refilled
+      cp_async_wait<0>();  // no copy may still target the windows when the next segment reuses them
+      __syncthreads();
     }
-    cp_async_wait<0>();  // no copy may still target the windows when the next segment reuses them
-    __syncthreads();
-  }
-  if (inside) *K = best;
+    if (inside) *K = best;
   }
 }
 
@@ -1336,14 +1680,9 @@ __global__ __launch_bounds__(TW *TH) void k_raster(Geometry g, const PrimRec *__
 #endif
 constexpr int kSsaoGroup = VTX_SSAO_GROUP;  // SSAO samples whose neighbour keys are fetched together
 // Measured: 3 shading CTAs per SM beat 2 and 4 (2 starves the close view and
-// the batch, 4 leaves too few CTAs for the background writes of the batch);
-// 16 raster CTAs per SM beat 4 and 8 on the close view (0.23 -> 0.20 ms) and
-// tie elsewhere.
+// the batch, 4 leaves too few CTAs for the background writes of the batch).
 #ifndef VTX_SHADE_PER_SM
 #define VTX_SHADE_PER_SM 3
-#endif
-#ifndef VTX_RASTER_GRID
-#define VTX_RASTER_GRID 16
 #endif
 #ifndef VTX_RESOLVE_2PASS
 #define VTX_RESOLVE_2PASS 1
@@ -1760,11 +2099,25 @@ cudaError_t run_binning(const Geometry &g, const Scene &sc, const Scratch &s, cu
     dim3 grid(bx, g.n_img);
     if (soft)
       launch_pdl(k_setup<true>, grid, 256, 0, st, g, sc.frames, sc.bonds, s.state, s.surv, s.keys, s.recs, s.rec_img,
-                                          s.rec_box, s.rec_of, s.tile_count, s.status, s.cap_rec);
-    else
+                                          s.rec_box, s.rec_of, s.tile_count, s.status, s.cap_rec, nullptr, 0);
+    else if (!(g.occl && s.defer && s.dplane))
       launch_pdl(k_setup<false>, grid, 256, 0, st, g, sc.stage ? sc.stage : sc.frames, sc.bonds, s.state, s.surv, s.keys,
                                            s.recs, s.rec_img, s.rec_box, s.rec_of, s.tile_count, s.status,
-                                           s.cap_rec);
+                                           s.cap_rec, nullptr, 0);
+    else {
+      // occlusion pass (images that do not take it run all their survivors in setup pass 1): split, near
+      // setup, 16-bit depth plane, test, setup of the kept deferred survivors
+      const float4 *Xs = sc.stage ? sc.stage : sc.frames;
+      launch_pdl(k_occl_split, grid, 256, 0, st, g, Xs, s.state, s.surv, s.defer);
+      launch_pdl(k_setup<false>, grid, 256, 0, st, g, Xs, sc.bonds, s.state, s.surv, s.keys, s.recs, s.rec_img,
+                 s.rec_box, s.rec_of, s.tile_count, s.status, s.cap_rec, s.defer, 1);
+      const long long quads = (g.pix_per_img + 3) / 4;
+      const int bq = (int)((quads + 255) / 256 < 64 ? (quads + 255) / 256 : 64);
+      launch_pdl(k_occl_depth, dim3(bq, g.n_img), 256, 0, st, g, s.state, s.keys, s.dplane);
+      launch_pdl(k_occl_test, grid, 256, 0, st, g, Xs, s.state, s.defer, s.dplane, s.surv);
+      launch_pdl(k_setup<false>, grid, 256, 0, st, g, Xs, sc.bonds, s.state, s.surv, s.keys, s.recs, s.rec_img,
+                 s.rec_box, s.rec_of, s.tile_count, s.status, s.cap_rec, s.defer, 2);
+    }
   }
   ev_rec(evs, 2, st);
   {
@@ -1805,19 +2158,26 @@ cudaError_t run_frame_pipeline(const Geometry &g, const ShadeParams &sh, const S
   if (e != cudaSuccess) return e;
   const float4 *Xr = sc.stage ? sc.stage : sc.frames;  // winners are survivors: staged when staging is on
   const long long n_tiles = (long long)g.n_img * g.tiles_per_img;
-  const unsigned rgrid = (unsigned)(n_tiles < (long long)VTX_RASTER_GRID * sm_count() ? n_tiles
-                                                                          : (long long)VTX_RASTER_GRID * sm_count());
+  // raster CTAs: as many as are resident at once (the tile queue balances them), never more than tiles
+  static int per_sm[3] = {0, 0, 0};
   static bool rattr = false;
   if (!rattr) {
     cudaFuncSetAttribute(k_raster<16, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)raster_smem<256>());
     cudaFuncSetAttribute(k_raster<32, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)raster_smem<256>());
     cudaFuncSetAttribute(k_raster<8, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)raster_smem<64>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], k_raster<16, 16>, 256, raster_smem<256>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], k_raster<32, 8>, 256, raster_smem<256>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[2], k_raster<8, 8>, 64, raster_smem<64>());
+    for (int &q : per_sm) q = q > 0 ? q : 1;
     rattr = true;
   }
-  if (g.tile_w == 16 && g.tile_h == 16)
+  const int shape = (g.tile_w == 16 && g.tile_h == 16) ? 0 : ((g.tile_w == 32 && g.tile_h == 8) ? 1 : 2);
+  const long long resident = (long long)per_sm[shape] * sm_count();
+  const unsigned rgrid = (unsigned)(n_tiles < resident ? (n_tiles > 0 ? n_tiles : 1) : resident);
+  if (shape == 0)
     launch_pdl(k_raster<16, 16>, rgrid, 256, raster_smem<256>(), st, g, s.recs, s.entries, s.cap_entries,
                s.tile_count, s.tile_start, s.state, s.keys, s.tile_list, s.status);
-  else if (g.tile_w == 32 && g.tile_h == 8)
+  else if (shape == 1)
     launch_pdl(k_raster<32, 8>, rgrid, 256, raster_smem<256>(), st, g, s.recs, s.entries, s.cap_entries,
                s.tile_count, s.tile_start, s.state, s.keys, s.tile_list, s.status);
   else

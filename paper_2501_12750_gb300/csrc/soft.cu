@@ -475,11 +475,14 @@ __device__ __forceinline__ void soft_bwd_tile(const Geometry &g, long long gt, c
                                               const uint32_t *__restrict__ tile_start, Status *status,
                                               const float *gcov, const float *gdep, const float *gnrm,
                                               const uint2 *__restrict__ state, float *grad, unsigned long long *s_e,
-                                              SoftPrim *s_w, bool presorted) {
-  SoftTile T;
-  if (!soft_load(g, gt, entries, cap_entries, tile_count, tile_start, status, s_e,
-                 reinterpret_cast<uint16_t *>(s_w - (threadIdx.x & ~31)), T, false, presorted))
-    return;
+                                              SoftPrim *s_w, bool presorted);
+
+// The backward of one warp: its 8x4 pixel block wblk of tile T, whose sorted list T.list is in shared or
+// global memory; s_w is the warp's 32-entry window.
+__device__ __forceinline__ void soft_bwd_walk(const Geometry &g, const SoftTile &T, int wblk,
+                                              const PrimRec *__restrict__ recs, const uint32_t *__restrict__ rec_of,
+                                              const float *gcov, const float *gdep, const float *gnrm,
+                                              const uint2 *__restrict__ state, float *grad, SoftPrim *s_w) {
   const ViewParams &v = g.views[T.img % g.n_views];
   const SoftPix x = soft_pix(v, T.px, T.py);
   const PixRay &r = x.r;
@@ -502,8 +505,8 @@ __device__ __forceinline__ void soft_bwd_tile(const Geometry &g, long long gt, c
   // pass 1: front to back, last contributor and final transmittance (read from the forward call's state
   // when it left one)
   const float uu_max = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(r.uu)));
-  const float col0 = (float)(T.px0 + 8 * (int)((threadIdx.x >> 5) & 1)) + 0.5f;
-  const float row0 = (float)(T.py0 + 4 * (int)(threadIdx.x >> 6)) + 0.5f;
+  const float col0 = (float)(T.px0 + 8 * (wblk & 1)) + 0.5f;
+  const float row0 = (float)(T.py0 + 4 * (wblk >> 1)) + 0.5f;
   float Tr = 1.0f;
   int last = -1;
   bool done = !need;
@@ -613,6 +616,20 @@ __device__ __forceinline__ void soft_bwd_tile(const Geometry &g, long long gt, c
   }
 }
 
+__device__ __forceinline__ void soft_bwd_tile(const Geometry &g, long long gt, const PrimRec *__restrict__ recs,
+                                              const uint32_t *__restrict__ rec_of, unsigned long long *entries,
+                                              unsigned long long cap_entries, const uint32_t *__restrict__ tile_count,
+                                              const uint32_t *__restrict__ tile_start, Status *status,
+                                              const float *gcov, const float *gdep, const float *gnrm,
+                                              const uint2 *__restrict__ state, float *grad, unsigned long long *s_e,
+                                              SoftPrim *s_w, bool presorted) {
+  SoftTile T;
+  if (!soft_load(g, gt, entries, cap_entries, tile_count, tile_start, status, s_e,
+                 reinterpret_cast<uint16_t *>(s_w - (threadIdx.x & ~31)), T, false, presorted))
+    return;
+  soft_bwd_walk(g, T, (int)(threadIdx.x >> 5), recs, rec_of, gcov, gdep, gnrm, state, grad, s_w);
+}
+
 // Persistent backward over the non-empty tiles (as the forward).
 __global__ __launch_bounds__(kSoftNT) void k_soft_bwd(Geometry g, const PrimRec *__restrict__ recs,
                                                       const uint32_t *__restrict__ rec_of,
@@ -636,6 +653,49 @@ __global__ __launch_bounds__(kSoftNT) void k_soft_bwd(Geometry g, const PrimRec 
     soft_bwd_tile(g, tile_list[li], recs, rec_of, entries, cap_entries, tile_count, tile_start, status, gcov, gdep,
                   gnrm, state, grad, s_e, s_w, presorted != 0);
     __syncthreads();
+  }
+}
+
+// Backward on the forward call's lists, already sorted in the entry array: each warp takes (tile, 8x4 block)
+// items from a queue -- the non-empty tiles longest first, eight blocks each -- and walks the tile's list in
+// global memory on its own.  No step needs the whole tile, so there is no block barrier: a warp that finishes
+// its block early takes the next item instead of waiting for the tile's slowest warp.
+__global__ __launch_bounds__(kSoftNT, 4) void k_soft_bwd_warps(Geometry g, const PrimRec *__restrict__ recs,
+                                                            const uint32_t *__restrict__ rec_of,
+                                                            const unsigned long long *__restrict__ entries,
+                                                            unsigned long long cap_entries,
+                                                            const uint32_t *__restrict__ tile_count,
+                                                            const uint32_t *__restrict__ tile_start,
+                                                            const uint32_t *__restrict__ tile_list, Status *status,
+                                                            const float *gcov, const float *gdep, const float *gnrm,
+                                                            const uint2 *__restrict__ state, float *grad) {
+  __shared__ SoftPrim s_win[kSoftNT];  // a 32-entry window per warp
+  SoftPrim *s_w = s_win + (threadIdx.x & ~31);
+  const int lane = threadIdx.x & 31;
+  const uint32_t n_items = status->n_list * 8u;
+  for (;;) {
+    uint32_t item = 0u;
+    if (lane == 0) item = atomicAdd(&status->soft_next, 1u);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= n_items) break;
+    const long long gt = tile_list[item >> 3];
+    const int wblk = (int)(item & 7u);
+    SoftTile T;
+    T.img = (int)(gt / g.tiles_per_img);
+    const int t = (int)(gt % g.tiles_per_img);
+    T.px0 = (t % g.tiles_x) * 16;
+    T.py0 = (t / g.tiles_x) * 16;
+    T.px = T.px0 + 8 * (wblk & 1) + (lane & 7);
+    T.py = T.py0 + 4 * (wblk >> 1) + (lane >> 3);
+    T.inside = T.px < g.W && T.py < g.H;
+    uint32_t cnt = tile_count[gt];
+    T.start = tile_start[gt];
+    if ((unsigned long long)T.start >= cap_entries) cnt = 0;
+    else if ((unsigned long long)T.start + cnt > cap_entries) cnt = (uint32_t)(cap_entries - T.start);
+    T.m = (int)cnt;
+    T.list = entries + T.start;
+    if (cnt > 0) soft_bwd_walk(g, T, wblk, recs, rec_of, gcov, gdep, gnrm, state, grad, s_w);
+    __syncwarp();
   }
 }
 
@@ -668,9 +728,14 @@ cudaError_t run_soft_pipeline(const Geometry &g, const Scene &sc, const Scratch 
                                                              s.status, cov, depth, normal, state);
   } else {
     cudaMemsetAsync(grad, 0, sizeof(float) * 4 * (size_t)g.n_atoms, st);
-    k_soft_bwd<<<grid, kSoftNT, kSoftSmem, st>>>(g, s.recs, s.rec_of, s.entries, s.cap_entries, s.tile_count,
-                                                 s.tile_start, s.tile_list, s.status, g_cov, g_depth, g_normal, state,
-                                                 grad, reuse ? 1 : 0);
+    if (reuse)
+      k_soft_bwd_warps<<<(unsigned)most, kSoftNT, 0, st>>>(g, s.recs, s.rec_of, s.entries, s.cap_entries,
+                                                           s.tile_count, s.tile_start, s.tile_list, s.status, g_cov,
+                                                           g_depth, g_normal, state, grad);
+    else
+      k_soft_bwd<<<grid, kSoftNT, kSoftSmem, st>>>(g, s.recs, s.rec_of, s.entries, s.cap_entries, s.tile_count,
+                                                   s.tile_start, s.tile_list, s.status, g_cov, g_depth, g_normal,
+                                                   state, grad, 0);
   }
   if (evs && evs->ev && evs->n > 5) cudaEventRecord(evs->ev[5], st);
   if (evs && evs->ev && evs->n > 6) cudaEventRecord(evs->ev[6], st);
