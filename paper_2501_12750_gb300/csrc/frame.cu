@@ -2027,13 +2027,26 @@ static cudaError_t launch_pdl(void (*k)(P...), dim3 grid, int block, size_t smem
   return cudaLaunchKernelEx(&cfg, k, static_cast<P>(args)...);
 }
 
+#ifndef VTX_CLEAR_MEMSET
+#define VTX_CLEAR_MEMSET 1  // clear a batch's key planes with a memset instead of the clear kernel's stores
+#endif
+
 // Shared binning front end: init, cull, finalize, setup (+splat), scan, scatter.
 cudaError_t run_binning(const Geometry &g, const Scene &sc, const Scratch &s, cudaStream_t st, StageEvents *evs,
                         bool soft) {
   const int sms = sm_count();
   const long long n_tiles = (long long)g.n_img * g.tiles_per_img;
   {
-    const long long n_keys = soft ? 0 : g.pix_per_img * g.n_img;
+    // the background key has every bit set, so the key planes of a batch are cleared by a byte memset
+    // (batch 30.9 -> 29.3 ms) instead of the clear kernel's stores; a single frame keeps the kernel, whose
+    // launch overlaps its neighbours' (the memset slowed the 1e5-atom 1080p frame 0.081 -> 0.083 ms)
+    const long long all_keys = soft ? 0 : g.pix_per_img * g.n_img;
+    const bool fill = VTX_CLEAR_MEMSET && g.n_img > 1 && all_keys > 0;
+    const long long n_keys = fill ? 0 : all_keys;
+    if (fill) {
+      static_assert(kBgKey == ~0ull, "a byte fill of 0xff gives the background key");
+      cudaMemsetAsync(s.keys, 0xff, sizeof(unsigned long long) * (size_t)all_keys, st);
+    }
     long long want = n_keys / 2 > n_tiles ? n_keys / 2 : n_tiles;
     want = want > g.n_img ? want : g.n_img;
     const long long blocks = (want + 255) / 256;
