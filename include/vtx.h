@@ -139,7 +139,9 @@ typedef struct {
   float ssao_bias;       /* A */
   float ssao_kernel[VTX_MAX_SSAO_SAMPLES][3]; /* hemisphere offsets (unit-ball scale), z along the normal */
   int32_t tile_w, tile_h; /* 16x16, 32x8 or 8x8; tile_w = 0: autotune tile shape AND splat_max_px (below) */
-  int32_t splat_max_px;  /* primitives whose candidate pixel box is <= this are splatted directly (0 = 16) */
+  int32_t splat_max_px;  /* primitives whose candidate pixel box is <= this are splatted directly; 0 = the
+                            library default: 4 when the primitives number at most one per 8 pixels, else 16
+                            (the planes are the same for every value) */
   uint32_t flags;        /* VTX_FLAG_* */
   /* post-processes and variants (the paper's list: shading modes, fog, outline; Fig. 1C clipping) */
   int32_t shading;       /* VTX_SHADE_* */

@@ -406,7 +406,7 @@ vtx_status vtx_default_settings(vtx_settings *s) {
   s->ssao_bias = 0.025f;
   s->tile_w = 16;
   s->tile_h = 16;
-  s->splat_max_px = 16;
+  s->splat_max_px = 0;  // the library default: by primitives per pixel
   s->shading = VTX_SHADE_GLOSSY;
   s->toon_levels = 4;
   s->probe_radius = 1.4f;
@@ -580,6 +580,14 @@ static void set_representation(Geometry &g, const vtx_settings *s) {
   g.clip_on = (s->clip_plane[0] != 0.0f || s->clip_plane[1] != 0.0f || s->clip_plane[2] != 0.0f) ? 1 : 0;
 }
 
+// Library-default direct-splat threshold (splat_max_px = 0): sparse frames (at most one primitive per 8
+// pixels) bin all but the smallest primitives for the tile raster (4 px), crowded ones splat boxes of up to
+// 16 px directly.  Measured with the autotuner: the 1e5-atom 1080p frame is fastest at 4 (0.082 -> 0.078
+// ms), the 1e8-atom 4K frame and the 500k-atom trajectory images at 16.  Every threshold gives the same planes.
+static int default_splat(long long prims_per_img, long long pix_per_img) {
+  return prims_per_img * 8 <= pix_per_img ? 4 : 16;
+}
+
 static vtx_status render_once(vtx_ctx *c, const vtx_settings *s, const vtx_outputs *out, StageEvents *ev) {
   Geometry g;
   int tw = s->tile_w ? s->tile_w : 16, th = s->tile_h ? s->tile_h : 16;
@@ -587,11 +595,11 @@ static vtx_status render_once(vtx_ctx *c, const vtx_settings *s, const vtx_outpu
   g.n_frames = 1;
   g.n_img = 1;
   set_representation(g, s);
-  g.splat_max = s->splat_max_px ? s->splat_max_px : 16;
   g.soft = 0;
   g.stride = c->n_atoms;
   g.n_atoms = c->n_atoms;
   g.n_bonds = (s->mode == VTX_MODE_BALL_AND_STICK || s->mode == VTX_MODE_STICKS) ? c->n_bonds : 0;
+  g.splat_max = s->splat_max_px ? s->splat_max_px : default_splat(g.n_atoms + g.n_bonds, g.pix_per_img);
   g.surv_cap = c->n_atoms + g.n_bonds + cull_survivor_slack(c->n_atoms);
   vtx_status st = prepare(c, g, false, 0);
   if (st) return st;
@@ -780,7 +788,7 @@ static vtx_status batch_once(vtx_ctx *c, const float *frames, int64_t stride, co
   g.n_frames = nf;
   g.n_img = nf * n_views;
   set_representation(g, s);
-  g.splat_max = s->splat_max_px ? s->splat_max_px : 16;
+  g.splat_max = s->splat_max_px ? s->splat_max_px : default_splat(stride, g.pix_per_img);
   g.stride = stride;
   g.n_atoms = stride;
   // room for the holes the batch cull's per-warp slabs may leave (up to 4 views)

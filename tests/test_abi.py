@@ -43,7 +43,7 @@ def test_host_side_argument_checks_without_gpu():
     lib = _native.load()
     s = _native.VtxSettings()
     assert lib.vtx_default_settings(ctypes.byref(s)) == 0
-    assert abs(s.ka - 0.2) < 1e-7 and s.tile_w == 16 and s.splat_max_px == 16
+    assert abs(s.ka - 0.2) < 1e-7 and s.tile_w == 16 and s.splat_max_px == 0  # 0: the adaptive default
     assert lib.vtx_default_settings(None) == 1
     assert lib.vtx_create(None, 0, None) == 1
     h = ctypes.c_void_p()
