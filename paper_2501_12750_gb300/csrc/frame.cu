@@ -6,8 +6,10 @@
 // occlusion ("High Quality Rendering").  Here the same per-pixel result --
 // the nearest ray/primitive hit -- is computed without a graphics API:
 //
-//   k_clear      resets image states and counters, tile counts and keys;
-//   k_cull_direct / k_cull_atoms / k_cull_bonds  stream every record once,
+//   k_clear      resets image states and counters, tile counts and (single
+//        frames) keys; a batch's key planes are cleared by a byte memset;
+//   k_cull_direct / k_cull_multi / k_cull_atoms / k_cull_bonds  stream every
+//        record once (one view; a batch of up to four views; more views),
 //        reject what cannot cover a pixel centre, append survivors through
 //        per-warp slabs or per-block runs;
 //   k_setup      fixes each image's depth-key range from the survivors, then
@@ -15,15 +17,20 @@
 //        most splat_max candidate pixels are ray-cast right there and
 //        merged with a 64-bit atomicMin of (depth key << 32 | id); larger
 //        ones become 64-byte records counted per screen tile;
-//   k_scan_*     exclusive scan of the per-tile counts (counting sort by tile);
+//   k_occl_split / k_occl_depth / k_occl_test  (crowded batch images) setup
+//        takes the survivors near the front first, then only the deferred
+//        ones that the keys already there do not hide at every box pixel;
+//   k_scan_*     exclusive scan of the per-tile counts (counting sort by tile),
+//        listing the non-empty tiles longest first;
 //   k_scatter    writes (min depth key << 32 | record) entries per tile;
-//   k_raster     one CTA per tile: orders its entries front to back by depth
-//        bucket in shared memory (one-pass counting sort); then each warp
-//        walks the ordered list on its own, staging 32 records at a time,
-//        dropping those whose bounding sphere misses every ray of its
-//        still-searching pixels, ray-casting the rest, and stopping once
-//        every pixel's hit is nearer than the next entry's nearest possible
-//        depth;
+//   k_raster     resident CTAs take tiles from a queue: each orders its tile's
+//        entries front to back by depth bucket in shared memory (one-pass
+//        counting sort) with a pixel box per entry; then each warp walks the
+//        ordered list on its own, staging 32 records at a time (only those
+//        whose boxes meet its still-searching pixels), dropping those whose
+//        bounding sphere misses every ray of those pixels, ray-casting the
+//        rest two at a time, and stopping once every pixel's hit is nearer
+//        than the next entry's nearest possible depth;
 //   k_resolve_list / k_resolve_split  list the covered pixels, then shade
 //        them (id decoded, hit recomputed -> depth, normal, colour, SSAO
 //        from neighbouring depth keys, outline, fog) beside CTAs that write

@@ -11,14 +11,18 @@
 //   w_i = alpha_i T_i, T_{i+1} = T_i (1 - alpha_i), stop once T < 1e-4;
 //   coverage = sum w_i, depth = sum w_i t_i, normal = sum w_i n_i.
 // Binning (cull with 4 px dilation, precise setup, per-tile counting sort)
-// is shared with the hard-edge path; each tile CTA sorts its list by
-// (centre depth key, id) in shared memory (bucket pass plus per-bucket
-// insertion sort), then each warp walks the sorted
-// list on its own, staging 32 entries at a time with their per-sphere
-// constants (f / z_c, 1 / r and a bound on rho^2 that rejects most entries
-// before any square root or division).  The backward kernel rebuilds the
-// lists, re-walks each pixel front to back for its last contributor and final
-// transmittance, then walks back to front with the carry
+// is shared with the hard-edge path; each tile CTA (tiles longest first)
+// sorts its list by (centre depth key, id) in shared memory (bucket pass plus
+// per-bucket insertion sort; in global memory for lists longer than shared
+// memory holds) and writes it back, then each warp walks the sorted list on
+// its own, staging 32 entries at a time with their per-sphere constants
+// (f / z_c, 1 / r and a bound on rho^2 that rejects most entries before any
+// square root or division).  The forward can leave per pixel its final
+// transmittance and last contributor (the state).  The backward either
+// reuses the forward's sorted lists (warps taking (tile, block) items from a
+// queue) or rebuilds them; it takes the last contributor and final
+// transmittance from the state, or re-walks each pixel front to back for
+// them, then walks back to front with the carry
 // R_i = alpha_{i+1} c_{i+1} + (1 - alpha_{i+1}) R_{i+1}, recovering T_i from
 // T_{i+1} / (1 - alpha_i) (alpha <= 0.99 keeps this safe), and accumulates
 // d/d(x, y, z, r) per sphere as a warp sum (a six-shuffle reduce-scatter)

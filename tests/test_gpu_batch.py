@@ -75,3 +75,33 @@ def test_batch_images_match_oracle():
         pix = sample_pixels(160, 96, 300, img, windows=[(70, 40, 16)], covered_mask=cov if cov.any() else None)
         h = oracle.render_pixels(sc, 0, pix, kernel=k)
         compare(res, h, ssao=True, label="batch img %d" % img)
+
+
+@pytest.mark.parametrize("n_views", [1, 2, 3, 5])
+def test_batch_view_counts_bit_exact_with_per_frame(n_views):
+    """Batches of one to three views take the barrier-free multi-view cull with that many views per atom, five
+    views the bulk-copy cull; every image equals the per-frame renderer's, plane for plane."""
+    import torch
+
+    import paper_2501_12750_gb300 as vtx
+    s, counts = _small_traj()
+    c = np.array([scenes.box_edge(20000) / 2] * 3)
+    cams = [scenes.orbit_camera(c, 3.0 * scenes.box_edge(20000), 360.0 * v / n_views + 10.0, 20.0 * v - 15.0, 160, 96)
+            for v in range(n_views)]
+    k = scenes.ssao_kernel()
+    r = vtx.Renderer()
+    frames = torch.from_numpy(s.frames).cuda()
+    elem = torch.from_numpy(s.elem).cuda()
+    r.upload_atoms(frames[0], elem, s.palette)
+    st = vtx.default_settings(ssao_kernel=k, flags=vtx.FLAG_SYNC)
+    b = _np(r.render_batch(frames, counts, cams, st))
+    single = r.alloc_outputs(160, 96)
+    for f in (0, 3, 5):
+        r.upload_atoms(frames[f, :counts[f]], elem[:counts[f]], s.palette)
+        for v, cam in enumerate(cams):
+            r.set_camera(cam)
+            r.render_frame(st, out=single)
+            one = _np(single)
+            for key in one:
+                assert np.array_equal(one[key], b[key][f * n_views + v], equal_nan=True), (n_views, f, v, key)
+    assert (b["id"] != oracle.NO_ID).sum() > 1000
