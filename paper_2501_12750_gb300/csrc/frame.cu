@@ -17,9 +17,10 @@
 //        most splat_max candidate pixels are ray-cast right there and
 //        merged with a 64-bit atomicMin of (depth key << 32 | id); larger
 //        ones become 64-byte records counted per screen tile;
-//   k_occl_split / k_occl_depth / k_occl_test  (crowded batch images) setup
-//        takes the survivors near the front first, then only the deferred
-//        ones that the keys already there do not hide at every box pixel;
+//   k_occl_upper / k_occl_test  (crowded batch images) every survivor
+//        writes FP32 upper bounds of its entry depth at the pixels it
+//        certainly covers; setup then takes only the survivors that these
+//        bounds do not hide at every pixel of their boxes;
 //   k_scan_*     exclusive scan of the per-tile counts (counting sort by tile),
 //        listing the non-empty tiles longest first;
 //   k_scatter    writes (min depth key << 32 | record) entries per tile;
@@ -78,11 +79,8 @@ __global__ __launch_bounds__(256) void k_clear(ImageState *st, int n_img, Status
     s.zlo = 0.0f;
     s.S = 0.0f;
     s.invS = 0.0f;
-    s.zsplit = 0.0f;
     s.occl = 0u;
-    s.n_def = 0u;
     s.n_vis = 0u;
-    s.n_near = 0u;
     st[tid] = s;
   }
   if (tid == 0) {
@@ -589,13 +587,9 @@ __global__ __launch_bounds__(kCullThreads) void k_cull_bonds(Geometry g, const f
   }
 }
 
-#ifndef VTX_OCCL_SPLIT
-#define VTX_OCCL_SPLIT 0.25f
-#endif
 #ifndef VTX_OCCL_PIXELS
 #define VTX_OCCL_PIXELS 4
 #endif
-constexpr float kOcclSplit = VTX_OCCL_SPLIT;  // near-pass share of the image's depth range
 constexpr long long kOcclPixels = VTX_OCCL_PIXELS;  // occlusion pass from one survivor per this many pixels
 
 // Depth-key range per image: [zlo, zhi] of the survivors, widened past the
@@ -618,9 +612,8 @@ __device__ __forceinline__ ImageState finalize_state(const Geometry &g, int img,
   s.invS = (hi - lo) / kKeySpanF;
   s.valid = 1u;
   // occlusion pass: images with at least one survivor per kOcclPixels pixels (a depth complexity at which
-  // most survivors are hidden); the near pass takes the survivors reaching the front kOcclSplit of the range
+  // most survivors are hidden)
   s.occl = (g.occl && !g.soft && (long long)s.n_surv * kOcclPixels >= g.pix_per_img) ? 1u : 0u;
-  s.zsplit = lo + (hi - lo) * kOcclSplit;
   return s;
 }
 
@@ -728,28 +721,25 @@ __global__ __launch_bounds__(256, VTX_SETUP_MINB) void k_setup(Geometry g, const
                                                const uint32_t *__restrict__ surv, unsigned long long *keys,
                                                PrimRec *recs, uint32_t *rec_img, uint2 *rec_box, uint32_t *rec_of,
                                                uint32_t *tile_count, Status *status, uint32_t cap_rec,
-                                               const uint32_t *near, int pass) {
+                                               const uint32_t *kept) {
   pdl_enter();
   const int img = blockIdx.y;
   const ImageState s = finalize_state(g, img, st[img]);
-  if (pass <= 1 && blockIdx.x == 0 && threadIdx.x == 0) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
     st[img].zlo = s.zlo;
     st[img].S = s.S;
     st[img].invS = s.invS;
     st[img].valid = s.valid;
   }
   if (!s.valid) return;
-  // pass 0: every survivor (no occlusion pass).  An occlusion image takes its near survivors in pass 1 and the
-  // deferred ones the occlusion test kept (written over its survivor list) in pass 2; any other image takes
-  // all its survivors in pass 1.
-  if (pass == 2 && !s.occl) return;
-  const bool near_list = pass == 1 && s.occl;
+  // with the occlusion pass (kept != null) an occlusion image takes the survivors its test kept; every other
+  // image takes all its survivors
+  const bool kept_list = kept != nullptr && s.occl;
   const ViewParams &v = g.views[img % g.n_views];
   const int frame = img / g.n_views;
   const float4 *X = frames + (long long)frame * g.stride;
-  const ImageState cnt = st[img];  // the counts written by the occlusion kernels
-  const long long n = min((long long)(near_list ? cnt.n_near : (pass == 2 ? cnt.n_vis : s.n_surv)), g.surv_cap);
-  const uint32_t *sv = (near_list ? near : surv) + (long long)img * g.surv_cap;
+  const long long n = min((long long)(kept_list ? st[img].n_vis : s.n_surv), g.surv_cap);
+  const uint32_t *sv = (kept_list ? kept : surv) + (long long)img * g.surv_cap;
   unsigned long long *K = keys + (long long)img * g.pix_per_img;
   const int lane = threadIdx.x & 31;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -854,17 +844,19 @@ __global__ __launch_bounds__(256, VTX_SETUP_MINB) void k_setup(Geometry g, const
 
 // ------------------------------------------------------- occlusion pass --
 // Images with many survivors per pixel (a trajectory blob seen whole) spend most of their setup on spheres
-// that lose every depth test.  k_occl_split lists an occlusion image's survivors in two compact lists: those
-// reaching the front kOcclSplit of the depth range (from the start of the image's deferred slots) and the
-// rest (from the end); setup pass 1 takes the near list; k_occl_test drops a deferred sphere when the
-// smallest depth key any of its hits could have exceeds the depth key every pixel of its candidate box
-// already holds (each of its atomicMin calls would then leave the key unchanged: keys only decrease) and
-// lists the others over the survivor list, which setup pass 2 takes.  Lists are compacted so that setup
-// warps stay converged.
-// Exact: the planes are those of the plain pass, bit for bit.
+// that lose every depth test.  The pass proves most of them hidden before their precise setup, from an FP32
+// plane U of upper bounds of the nearest hit depth:
+//   k_occl_upper: every survivor in the front share of the image's depth range writes, at each pixel whose ray
+//     certainly meets its sphere, an upper bound of its entry depth there (atomicMin on the FP32 bits).  The
+//     nearest hit at that pixel over all survivors is then at most U, whichever survivors are processed later.
+//   k_occl_test: a survivor is dropped when every pixel of its candidate box holds a bound below the smallest
+//     depth any of its hits could have, less the rounding of depth to key; the others are listed for setup.
+// Exact: a dropped sphere's key at every pixel of its box is above the final key there, so it is never the
+// minimum of any pixel and the key planes are those of the plain pass, bit for bit.  (The sphere that holds a
+// pixel's minimum is never dropped, as its key there would have to be above itself.)
 
 // Survivors per lane per step of the occlusion kernels: a warp takes 128 consecutive list entries (coalesced
-// loads of four independent items in flight) and reserves its output slots with one atomic per list.
+// loads of four independent items in flight) and reserves its output slots with one atomic per warp.
 constexpr int kOcclItems = 4;
 
 // Warp-wide placement of up to kOcclItems flagged items per lane: one atomicAdd on *counter for the warp's
@@ -888,136 +880,136 @@ __device__ __forceinline__ void occl_slots(const bool (&f)[kOcclItems], unsigned
   }
 }
 
-__global__ __launch_bounds__(256) void k_occl_split(Geometry g, const float4 *__restrict__ frames, ImageState *st,
-                                                    const uint32_t *__restrict__ surv, uint32_t *lists) {
+// Most pixels a sphere's box may have and still be tested, or write its bounds (larger ones are kept and
+// write none: the bounds stay valid, only weaker).
+constexpr int kOcclMaxPixels = 64;
+// Share of the image's depth range whose spheres (by their front) write bounds.  Spheres farther back seldom
+// hold a pixel's smallest bound; leaving them out halves the writer's work.  Measured on the 1,024-image
+// trajectory batch: every sphere 29.7 ms, front 70 % 27.5, 50 % 25.9, 35 % 25.1, 25 % 25.6 ms.
+#ifndef VTX_OCCL_UPPER_FRONT
+#define VTX_OCCL_UPPER_FRONT 0.35f
+#endif
+constexpr float kOcclUpperFront = VTX_OCCL_UPPER_FRONT;
+
+// Upper bounds of the entry depth of the sphere at FP32 view position (vx, vy, vz) (error err per component)
+// with radius r, at the pixels whose rays certainly meet it, merged into the plane Ui.  At pixel ray
+// u = (a, b, 1) and w = (vx - a vz, vy - b vz) (the centre's offset from the ray at the centre's depth), the
+// centre's squared distance to the ray is d2 = |w|^2 - (w.u)^2 / |u|^2, the ray's closest point to the centre
+// lies at depth tc = vz + (w.u) / |u|^2 and it enters the sphere at depth tc - sqrt((r^2 - d2) / |u|^2).
+// With del = 2 err + 1e-6 vz covering the FP32 errors of w, d2 and tc, a pixel is written when d2 <= rr^2,
+// rr = 0.999 r - 2 del: the ray's true distance is then below 0.999 r - del, so the hit test meets the sphere
+// there whatever its own rounding, and the bound tc - sqrt((rr^2 - d2) / |u|^2) + 2 del + 1e-4 exceeds the true
+// entry depth by at least 1e-4 A (rr^2 - d2 is below the true r^2 - d^2).
+__device__ __forceinline__ void occl_upper_splat(const Geometry &g, const ViewParams &v, uint32_t *Ui, float vx,
+                                                 float vy, float vz, float err, float r) {
+  if (!(vz > 2.0f * (r + err) + v.znear)) return;  // no sphere near the eye plane (its reference depth moves)
+  const float del = 2.0f * err + 1e-6f * vz;
+  const float rr = fmaf(r, 0.999f, -2.0f * del);
+  if (!(rr > 0.0f)) return;
+  PixBox box;
+  {
+    // the pixel centres within rr f / vz of the projected centre (there |w| <= rr in exact arithmetic): any
+    // box is valid, since every written pixel passes the distance test below
+    const float rz = 1.0f / vz, Rs = rr * v.f * rz;
+    const float ux = fmaf(v.f, vx * rz, v.cxm), uy = fmaf(-v.f, vy * rz, v.cym);
+    box.x0 = (int)fmaxf(ceilf(ux - Rs), 0.0f);
+    box.x1 = (int)fminf(floorf(ux + Rs), (float)(g.W - 1));
+    box.y0 = (int)fmaxf(ceilf(uy - Rs), 0.0f);
+    box.y1 = (int)fminf(floorf(uy + Rs), (float)(g.H - 1));
+    if (!(box.x0 <= box.x1 && box.y0 <= box.y1)) return;
+  }
+  const int npix = (box.x1 - box.x0 + 1) * (box.y1 - box.y0 + 1);
+  if (npix > kOcclMaxPixels) return;
+  const float rr2 = rr * rr, dU = fmaf(2.0f, del, 1e-4f);
+  int px = box.x0, py = box.y0;
+  for (int i = 0; i < npix; ++i) {
+    const PixRay q = pix_ray(v, px, py);
+    const float wx = fmaf(-q.a, vz, vx), wy = fmaf(-q.b, vz, vy);
+    const float wu = fmaf(wx, q.a, wy * q.b);
+    const float d2 = fmaf(-wu * wu, q.inv_uu, fmaf(wx, wx, wy * wy));
+    if (d2 <= rr2) {
+      const float tc = fmaf(wu, q.inv_uu, vz);
+      const float sq = sqrt_approx((rr2 - d2) * q.inv_uu);
+      atomicMin(Ui + (long long)py * g.W + px, __float_as_uint(fmaf(-0.99999f, sq, tc) + dU));
+    }
+    if (++px > box.x1) {
+      px = box.x0;
+      ++py;
+    }
+  }
+}
+
+__global__ __launch_bounds__(256) void k_occl_upper(Geometry g, const float4 *__restrict__ frames, ImageState *st,
+                                                    const uint32_t *__restrict__ surv, uint32_t *U) {
   pdl_enter();
   const int img = blockIdx.y;
   const ImageState s = finalize_state(g, img, st[img]);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    st[img].zsplit = s.zsplit;
-    st[img].occl = s.occl;
-  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) st[img].occl = s.occl;
   if (!s.valid || !s.occl) return;
   const long long n = min((long long)s.n_surv, g.surv_cap);
   const ViewParams &v = g.views[img % g.n_views];
   const float4 *X = frames + (long long)(img / g.n_views) * g.stride;
   const uint32_t *sv = surv + (long long)img * g.surv_cap;
-  uint32_t *L = lists + (long long)img * g.surv_cap;
-  const int lane = threadIdx.x & 31;
-  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long base = warp * 32 * kOcclItems; base < n; base += warps * 32 * kOcclItems) {
-    uint32_t id[kOcclItems];
-    bool near[kOcclItems], far[kOcclItems];
-#pragma unroll
-    for (int j = 0; j < kOcclItems; ++j) {
-      const long long k = base + j * 32 + lane;
-      id[j] = k < n ? sv[k] : kNoId;
-    }
-#pragma unroll
-    for (int j = 0; j < kOcclItems; ++j) {
-      near[j] = far[j] = false;
-      if (id[j] != kNoId && (long long)id[j] >= g.n_atoms) {
-        near[j] = true;  // not an atom record (the occlusion pass is for atoms): setup takes it as usual
-      } else if (id[j] != kNoId) {
-        const float4 a = X[id[j]];
-        const float r = atom_radius(g, a.w);
-        float vx, vy, vz, err;
-        view_f32(v, a.x, a.y, a.z, vx, vy, vz, err);
-        PixBox box;
-        if (lean_box(v, g.W, g.H, vx, vy, vz, r + err, box)) {  // an empty box can change no pixel
-          far[j] = vz - r - err > s.zsplit;
-          near[j] = !far[j];
-        }
-      }
-    }
-    unsigned sn[kOcclItems], sf[kOcclItems];
-    occl_slots(near, &st[img].n_near, lane, sn);
-    occl_slots(far, &st[img].n_def, lane, sf);
-    // near + far <= n <= surv_cap: the two lists never meet
-#pragma unroll
-    for (int j = 0; j < kOcclItems; ++j) {
-      if (near[j]) L[sn[j]] = id[j];
-      if (far[j]) L[g.surv_cap - 1 - sf[j]] = id[j];
-    }
+  uint32_t *Ui = U + (long long)img * g.pix_per_img;
+  const float zf = s.zlo + kOcclUpperFront * (kKeySpanF * s.invS);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+    const uint32_t id = sv[k];
+    if (id == kNoId || (long long)id >= g.n_atoms) continue;
+    const float4 a = X[id];
+    float vx, vy, vz, err;
+    view_f32(v, a.x, a.y, a.z, vx, vy, vz, err);
+    const float r = atom_radius(g, a.w);
+    if (vz - r - err > zf) continue;
+    occl_upper_splat(g, v, Ui, vx, vy, vz, err, r);
   }
 }
 
-// Most pixels a deferred sphere's box may have and still be tested (larger boxes are kept).
-constexpr int kOcclMaxPixels = 64;
-
-// A 16-bit depth plane of the keys after the near pass: q = (depth key) >> 16, so the pixel's key is below
-// (q + 1) * 65536 (the background key gives q = 65535, which no sphere is behind).  2 bytes per pixel instead
-// of 8: the test's scattered reads of all the images in flight then stay in L2.  Four pixels per thread.
-__global__ __launch_bounds__(256) void k_occl_depth(Geometry g, const ImageState *__restrict__ st,
-                                                    const unsigned long long *__restrict__ keys, uint16_t *plane) {
-  pdl_enter();
-  const int img = blockIdx.y;
-  const ImageState s = st[img];
-  if (!s.valid || !s.occl || s.n_def == 0u) return;
-  const unsigned long long *K = keys + (long long)img * g.pix_per_img;
-  uint16_t *P = plane + (long long)img * g.pix_per_img;
-  const long long quads = (g.pix_per_img + 3) / 4;
-  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < quads; q += (long long)gridDim.x * blockDim.x) {
-    const long long p0 = q * 4;
-    if (p0 + 4 <= g.pix_per_img) {
-      const ulonglong2 a = __ldcs(reinterpret_cast<const ulonglong2 *>(K + p0));
-      const ulonglong2 b = __ldcs(reinterpret_cast<const ulonglong2 *>(K + p0) + 1);
-      const ushort4 w = make_ushort4((unsigned short)(a.x >> 48), (unsigned short)(a.y >> 48),
-                                     (unsigned short)(b.x >> 48), (unsigned short)(b.y >> 48));
-      *reinterpret_cast<ushort4 *>(P + p0) = w;
-    } else {
-      for (long long p = p0; p < g.pix_per_img; ++p) P[p] = (uint16_t)(K[p] >> 48);
-    }
-  }
-}
-
-// Is the sphere at FP32 view position (vz, err) with radius r, candidate box `box`, hidden in every pixel of
-// its box by the keys already there (read from the 16-bit depth plane P)?  lb: the smallest depth key any of its hits could have -- its front (vz - r,
-// widened by the view error and by 2e-7 of the depths for the FP32 rounding of these differences) mapped to
-// keys, less 4e-6 relative plus 4096 keys for the rounding of the product, of the reference key and of the
-// hit offset (tens of keys); compared in FP32 with the pixels' depth keys (rounded to nearest, within 256
-// keys of the integers).  Boxes of at most 4 x 4 pixels (the common case) load all their depth words at once.
+// Is the sphere at FP32 view position (vx, vy, vz) (error err) with radius r, candidate box `box`, hidden at
+// every pixel of its box by the bounds in Ui?  Its hits lie at depth >= vz - r - err (per component error, so
+// 2 err covers the distance), and its keys at or above that depth's key less the rounding of the key (tens of
+// keys, so 1024 keys, less 2e-6 relative and 1e-4 A for the FP32 evaluation of the threshold); a bound below
+// the threshold means the pixel's final key is below every key of the sphere.  The bits of positive floats
+// compare like the floats; the cleared value (all ones) keeps the sphere.
 __device__ __forceinline__ bool occl_hidden(const Geometry &g, const ViewParams &v, const ImageState &s,
-                                            const uint16_t *P, float vz, float err, float r, const PixBox &box) {
+                                            const uint32_t *Ui, float vz, float err, float r, const PixBox &box) {
   if (!(vz > 2.0f * (r + err) + v.znear)) return false;
-  float lb = (vz - err - r * 1.000002f - s.zlo - 2e-7f * (fabsf(vz) + fabsf(s.zlo))) * s.S;
-  lb = lb - fabsf(lb) * 4e-6f - 4096.0f;
-  // hidden at a pixel when (q + 1) * 65536 <= lb: exact in FP32 (q + 1 <= 65536 times a power of two)
-  const float qmax = lb * (1.0f / 65536.0f) - 1.0f;  // q + 1 <= lb / 65536 (the scaling is exact)
+  const float thr = vz - 2.0f * err - r * 1.000002f - 2e-6f * vz - 1e-4f - 1024.0f * s.invS;
+  if (!(thr > 0.0f)) return false;
+  const uint32_t tb = __float_as_uint(thr);
   const int w = box.x1 - box.x0 + 1, h = box.y1 - box.y0 + 1;
-  const uint16_t *Pb = P + (long long)box.y0 * g.W + box.x0;
-  if (w <= 4 && h <= 4) {
-    unsigned short kd[16];
+  const uint32_t *Ub = Ui + (long long)box.y0 * g.W + box.x0;
+  if (w <= 4 && h <= 4) {  // the common case: all the box's bounds loaded at once
+    uint32_t ub[16];
 #pragma unroll
     for (int dy = 0; dy < 4; ++dy)
 #pragma unroll
-      for (int dx = 0; dx < 4; ++dx) kd[dy * 4 + dx] = (dx < w && dy < h) ? Pb[(long long)dy * g.W + dx] : 0;
+      for (int dx = 0; dx < 4; ++dx) ub[dy * 4 + dx] = (dx < w && dy < h) ? Ub[(long long)dy * g.W + dx] : 0u;
     bool hidden = true;
 #pragma unroll
-    for (int q = 0; q < 16; ++q) hidden = hidden && (float)kd[q] <= qmax;
+    for (int q = 0; q < 16; ++q) hidden = hidden && ub[q] < tb;
     return hidden;
   }
   if (w * h > kOcclMaxPixels) return false;
   for (int dy = 0; dy < h; ++dy)
     for (int dx = 0; dx < w; ++dx)
-      if (!((float)Pb[(long long)dy * g.W + dx] <= qmax)) return false;
+      if (!(Ub[(long long)dy * g.W + dx] < tb)) return false;
   return true;
 }
 
 __global__ __launch_bounds__(256) void k_occl_test(Geometry g, const float4 *__restrict__ frames, ImageState *st,
-                                                   const uint32_t *__restrict__ lists,
-                                                   const uint16_t *__restrict__ plane, uint32_t *surv) {
+                                                   const uint32_t *__restrict__ surv, const uint32_t *__restrict__ U,
+                                                   uint32_t *kept) {
   pdl_enter();
   const int img = blockIdx.y;
-  const ImageState s = st[img];
+  const ImageState s = finalize_state(g, img, st[img]);
   if (!s.valid || !s.occl) return;
-  const long long n = min((long long)s.n_def, g.surv_cap);
+  const long long n = min((long long)s.n_surv, g.surv_cap);
   const ViewParams &v = g.views[img % g.n_views];
   const float4 *X = frames + (long long)(img / g.n_views) * g.stride;
-  const uint32_t *D = lists + (long long)img * g.surv_cap + (g.surv_cap - n);  // the deferred list's n slots
-  const uint16_t *P = plane + (long long)img * g.pix_per_img;
-  uint32_t *vis = surv + (long long)img * g.surv_cap;
+  const uint32_t *sv = surv + (long long)img * g.surv_cap;
+  const uint32_t *Ui = U + (long long)img * g.pix_per_img;
+  uint32_t *L = kept + (long long)img * g.surv_cap;
   const int lane = threadIdx.x & 31;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -1027,25 +1019,27 @@ __global__ __launch_bounds__(256) void k_occl_test(Geometry g, const float4 *__r
 #pragma unroll
     for (int j = 0; j < kOcclItems; ++j) {
       const long long k = base + j * 32 + lane;
-      id[j] = k < n ? D[k] : kNoId;
+      id[j] = k < n ? sv[k] : kNoId;
     }
 #pragma unroll
     for (int j = 0; j < kOcclItems; ++j) {
       keep[j] = false;
-      if (id[j] != kNoId) {
+      if (id[j] != kNoId && (long long)id[j] >= g.n_atoms) {
+        keep[j] = true;  // not an atom record (the occlusion pass is for atoms): setup takes it as usual
+      } else if (id[j] != kNoId) {
         const float4 a = X[id[j]];
         const float r = atom_radius(g, a.w);
         float vx, vy, vz, err;
         view_f32(v, a.x, a.y, a.z, vx, vy, vz, err);
-        PixBox box;
-        keep[j] = lean_box(v, g.W, g.H, vx, vy, vz, r + err, box) && !occl_hidden(g, v, s, P, vz, err, r, box);
+        PixBox box;  // an empty box can change no pixel
+        keep[j] = lean_box(v, g.W, g.H, vx, vy, vz, r + err, box) && !occl_hidden(g, v, s, Ui, vz, err, r, box);
       }
     }
     unsigned sk[kOcclItems];
     occl_slots(keep, &st[img].n_vis, lane, sk);
 #pragma unroll
     for (int j = 0; j < kOcclItems; ++j)
-      if (keep[j]) vis[sk[j]] = id[j];
+      if (keep[j]) L[sk[j]] = id[j];
   }
 }
 
@@ -2043,6 +2037,7 @@ cudaError_t run_binning(const Geometry &g, const Scene &sc, const Scratch &s, cu
                         bool soft) {
   const int sms = sm_count();
   const long long n_tiles = (long long)g.n_img * g.tiles_per_img;
+  const bool occl = g.occl && !soft && s.defer && s.uplane;
   {
     // the background key has every bit set, so the key planes of a batch are cleared by a byte memset
     // (batch 30.9 -> 29.3 ms) instead of the clear kernel's stores; a single frame keeps the kernel, whose
@@ -2054,6 +2049,8 @@ cudaError_t run_binning(const Geometry &g, const Scene &sc, const Scratch &s, cu
       static_assert(kBgKey == ~0ull, "a byte fill of 0xff gives the background key");
       cudaMemsetAsync(s.keys, 0xff, sizeof(unsigned long long) * (size_t)all_keys, st);
     }
+    // the occlusion pass's depth bounds start at all ones, above the bits of every finite float
+    if (occl) cudaMemsetAsync(s.uplane, 0xff, sizeof(uint32_t) * (size_t)(g.pix_per_img * g.n_img), st);
     long long want = n_keys / 2 > n_tiles ? n_keys / 2 : n_tiles;
     want = want > g.n_img ? want : g.n_img;
     const long long blocks = (want + 255) / 256;
@@ -2119,24 +2116,19 @@ cudaError_t run_binning(const Geometry &g, const Scene &sc, const Scratch &s, cu
     dim3 grid(bx, g.n_img);
     if (soft)
       launch_pdl(k_setup<true>, grid, 256, 0, st, g, sc.frames, sc.bonds, s.state, s.surv, s.keys, s.recs, s.rec_img,
-                                          s.rec_box, s.rec_of, s.tile_count, s.status, s.cap_rec, nullptr, 0);
-    else if (!(g.occl && s.defer && s.dplane))
+                                          s.rec_box, s.rec_of, s.tile_count, s.status, s.cap_rec, nullptr);
+    else if (!occl)
       launch_pdl(k_setup<false>, grid, 256, 0, st, g, sc.stage ? sc.stage : sc.frames, sc.bonds, s.state, s.surv, s.keys,
                                            s.recs, s.rec_img, s.rec_box, s.rec_of, s.tile_count, s.status,
-                                           s.cap_rec, nullptr, 0);
+                                           s.cap_rec, nullptr);
     else {
-      // occlusion pass (images that do not take it run all their survivors in setup pass 1): split, near
-      // setup, 16-bit depth plane, test, setup of the kept deferred survivors
+      // occlusion pass (images that do not take it run all their survivors in setup): depth bounds, test,
+      // setup of the kept survivors
       const float4 *Xs = sc.stage ? sc.stage : sc.frames;
-      launch_pdl(k_occl_split, grid, 256, 0, st, g, Xs, s.state, s.surv, s.defer);
+      launch_pdl(k_occl_upper, grid, 256, 0, st, g, Xs, s.state, s.surv, s.uplane);
+      launch_pdl(k_occl_test, grid, 256, 0, st, g, Xs, s.state, s.surv, s.uplane, s.defer);
       launch_pdl(k_setup<false>, grid, 256, 0, st, g, Xs, sc.bonds, s.state, s.surv, s.keys, s.recs, s.rec_img,
-                 s.rec_box, s.rec_of, s.tile_count, s.status, s.cap_rec, s.defer, 1);
-      const long long quads = (g.pix_per_img + 3) / 4;
-      const int bq = (int)((quads + 255) / 256 < 64 ? (quads + 255) / 256 : 64);
-      launch_pdl(k_occl_depth, dim3(bq, g.n_img), 256, 0, st, g, s.state, s.keys, s.dplane);
-      launch_pdl(k_occl_test, grid, 256, 0, st, g, Xs, s.state, s.defer, s.dplane, s.surv);
-      launch_pdl(k_setup<false>, grid, 256, 0, st, g, Xs, sc.bonds, s.state, s.surv, s.keys, s.recs, s.rec_img,
-                 s.rec_box, s.rec_of, s.tile_count, s.status, s.cap_rec, s.defer, 2);
+                 s.rec_box, s.rec_of, s.tile_count, s.status, s.cap_rec, s.defer);
     }
   }
   ev_rec(evs, 2, st);

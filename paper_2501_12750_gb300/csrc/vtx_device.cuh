@@ -65,7 +65,7 @@ struct Geometry {
   int splat_max;         // max candidate pixels for the direct splat path
   int dbg_first_wait;    // test hook: polls allowed for the multi-view cull's first stage wait (-1: normal limit)
   int soft;              // 1 = soft-edge binning (dilated bounds, no splat, every survivor binned)
-  int occl;              // 1 = occlusion pass allowed: near survivors first, the rest tested against their keys
+  int occl;              // 1 = occlusion pass allowed: survivors proven hidden by FP32 depth bounds skip setup
   float sigma;           // soft: sigmoid width in pixels
   long long stride;      // atom records per frame slot
   long long n_atoms;     // atoms of frame 0 (single frame) -- primitive ids of bonds start here
@@ -97,11 +97,8 @@ struct ImageState {
   unsigned int n_surv;    // survivors appended (may exceed the capacity)
   unsigned int valid;     // set by finalize when there is at least one survivor
   float zlo, S, invS;     // key = (depth - zlo) * S
-  float zsplit;           // occlusion pass: survivors wholly behind this depth are tested after the others
   unsigned int occl;      // 1: this image runs the occlusion pass (many survivors per pixel)
-  unsigned int n_def;     // survivors deferred behind zsplit (listed from the end of the image's deferred slots)
-  unsigned int n_vis;     // deferred survivors that the depth pyramid could not reject
-  unsigned int n_near;    // survivors reaching the front of the range (listed from the start of those slots)
+  unsigned int n_vis;     // occlusion pass: survivors its test could not prove hidden (the kept list)
 };
 
 // Launch-wide status (device memory, read back by the host).
