@@ -939,9 +939,14 @@ __device__ __forceinline__ void occl_upper_splat(const Geometry &g, const ViewPa
   }
 }
 
+// A warp reads 128 consecutive survivors (four independent loads per lane in flight), keeps the writers in
+// shared memory and then spreads their pixel loops over all 32 lanes: about a third of the survivors write,
+// so a lane per survivor would leave most lanes idle during the loops.
 __global__ __launch_bounds__(256) void k_occl_upper(Geometry g, const float4 *__restrict__ frames, ImageState *st,
                                                     const uint32_t *__restrict__ surv, uint32_t *U) {
   pdl_enter();
+  __shared__ float4 s_c[8][32 * kOcclItems];  // per warp: the writers' (vx, vy, vz, err)
+  __shared__ float s_r[8][32 * kOcclItems];   // and radii
   const int img = blockIdx.y;
   const ImageState s = finalize_state(g, img, st[img]);
   if (blockIdx.x == 0 && threadIdx.x == 0) st[img].occl = s.occl;
@@ -952,16 +957,49 @@ __global__ __launch_bounds__(256) void k_occl_upper(Geometry g, const float4 *__
   const uint32_t *sv = surv + (long long)img * g.surv_cap;
   uint32_t *Ui = U + (long long)img * g.pix_per_img;
   const float zf = s.zlo + kOcclUpperFront * (kKeySpanF * s.invS);
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
-    const uint32_t id = sv[k];
-    if (id == kNoId || (long long)id >= g.n_atoms) continue;
-    const float4 a = X[id];
-    float vx, vy, vz, err;
-    view_f32(v, a.x, a.y, a.z, vx, vy, vz, err);
-    const float r = atom_radius(g, a.w);
-    if (vz - r - err > zf) continue;
-    occl_upper_splat(g, v, Ui, vx, vy, vz, err, r);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long base = warp * 32 * kOcclItems; base < n; base += warps * 32 * kOcclItems) {
+    uint32_t id[kOcclItems];
+#pragma unroll
+    for (int j = 0; j < kOcclItems; ++j) {
+      const long long k = base + j * 32 + lane;
+      id[j] = k < n ? sv[k] : kNoId;
+    }
+    float4 a[kOcclItems];
+#pragma unroll
+    for (int j = 0; j < kOcclItems; ++j)
+      a[j] = (id[j] != kNoId && (long long)id[j] < g.n_atoms) ? X[id[j]] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    bool wr[kOcclItems];
+    float4 c[kOcclItems];
+    float rad[kOcclItems];
+#pragma unroll
+    for (int j = 0; j < kOcclItems; ++j) {
+      float vx, vy, vz, err;
+      view_f32(v, a[j].x, a[j].y, a[j].z, vx, vy, vz, err);
+      rad[j] = atom_radius(g, a[j].w);
+      c[j] = make_float4(vx, vy, vz, err);
+      wr[j] = id[j] != kNoId && (long long)id[j] < g.n_atoms && !(vz - rad[j] - err > zf);
+    }
+    unsigned total = 0u;
+    const unsigned below = (1u << lane) - 1u;
+#pragma unroll
+    for (int j = 0; j < kOcclItems; ++j) {
+      const unsigned m = __ballot_sync(0xffffffffu, wr[j]);
+      if (wr[j]) {
+        const unsigned slot = total + (unsigned)__popc(m & below);
+        s_c[wid][slot] = c[j];
+        s_r[wid][slot] = rad[j];
+      }
+      total += (unsigned)__popc(m);
+    }
+    __syncwarp();
+    for (unsigned t = lane; t < total; t += 32) {
+      const float4 q = s_c[wid][t];
+      occl_upper_splat(g, v, Ui, q.x, q.y, q.z, q.w, s_r[wid][t]);
+    }
+    __syncwarp();  // the slots are read before the next step refills them
   }
 }
 
