@@ -587,10 +587,6 @@ __global__ __launch_bounds__(kCullThreads) void k_cull_bonds(Geometry g, const f
   }
 }
 
-#ifndef VTX_OCCL_PIXELS
-#define VTX_OCCL_PIXELS 4
-#endif
-constexpr long long kOcclPixels = VTX_OCCL_PIXELS;  // occlusion pass from one survivor per this many pixels
 
 // Depth-key range per image: [zlo, zhi] of the survivors, widened past the
 // FP32 error of the cull and clamped to half the near plane.

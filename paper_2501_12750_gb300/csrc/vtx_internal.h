@@ -9,6 +9,11 @@
 
 namespace vtx {
 
+#ifndef VTX_OCCL_PIXELS
+#define VTX_OCCL_PIXELS 4
+#endif
+constexpr long long kOcclPixels = VTX_OCCL_PIXELS;  // occlusion pass from one survivor per this many pixels
+
 // Tile counts that the one-CTA scan covers (32 warps x 32 lanes x 32 values); more take the three-kernel scan,
 // whose tile list is unordered and holds the non-empty tiles only.
 constexpr long long kScanSingleMax = 32LL * 32 * 32;
