@@ -59,10 +59,10 @@ def test_config3_ball_and_stick_full_subset(cell):
 def test_config4_full_batch_sampled():
     """All 1,024 images (500k atoms x 256 frames x 4 views, 1280x720, SSAO) in one graph launch.
 
-    Every image has ~500k survivors on ~5 % of its pixels, so the batch takes its exact occlusion pass (near
-    survivors first, deferred ones dropped when every pixel of their box already holds a nearer key): three
-    images are compared bit for bit with the per-frame renderer, which has no occlusion pass, and sampled
-    pixels of the same images with the FP64 oracle."""
+    Every image has ~500k survivors on ~5 % of its pixels, so the batch takes its exact occlusion pass (a
+    survivor is dropped when FP32 upper bounds of the nearest depth, written by the front survivors, lie in
+    front of it at every pixel of its box): three images are compared bit for bit with the per-frame renderer, which has no occlusion pass, and
+    sampled pixels of the same images with the FP64 oracle."""
     import torch
 
     import paper_2501_12750_gb300 as vtx
