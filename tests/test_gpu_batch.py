@@ -105,3 +105,36 @@ def test_batch_view_counts_bit_exact_with_per_frame(n_views):
             for key in one:
                 assert np.array_equal(one[key], b[key][f * n_views + v], equal_nan=True), (n_views, f, v, key)
     assert (b["id"] != oracle.NO_ID).sum() > 1000
+
+
+def test_batch_sas_close_clipped_bit_exact_with_per_frame():
+    """SAS radii, one camera close to the system (spheres cut by the near plane and boxes wider than the
+    occlusion pass writes or tests) and a clip plane through the middle: the batch, whose crowded images take
+    the occlusion pass, equals the per-frame renderer image for image, plane for plane."""
+    import torch
+
+    import paper_2501_12750_gb300 as vtx
+    s, counts = _small_traj()
+    L = scenes.box_edge(20000)
+    c = np.array([L / 2] * 3)
+    cams = [scenes.orbit_camera(c, 0.6 * L, 30.0, 10.0, 160, 96),
+            scenes.orbit_camera(c, 1.4 * L, 200.0, -20.0, 160, 96)]
+    k = scenes.ssao_kernel()
+    r = vtx.Renderer()
+    frames = torch.from_numpy(s.frames).cuda()
+    elem = torch.from_numpy(s.elem).cuda()
+    r.upload_atoms(frames[0], elem, s.palette)
+    st = vtx.default_settings(ssao_kernel=k, flags=vtx.FLAG_SYNC, mode=vtx.MODE_SAS, probe_radius=1.4,
+                              clip_plane=(1.0, 0.0, 0.0, -float(c[0])))
+    b = _np(r.render_batch(frames, counts, cams, st))
+    single = r.alloc_outputs(160, 96)
+    for f in (0, 2, 3):
+        r.upload_atoms(frames[f, :counts[f]], elem[:counts[f]], s.palette)
+        for v, cam in enumerate(cams):
+            r.set_camera(cam)
+            r.render_frame(st, out=single)
+            one = _np(single)
+            for key in one:
+                assert np.array_equal(one[key], b[key][f * len(cams) + v], equal_nan=True), (f, v, key)
+    for v in range(len(cams)):
+        assert (b["id"][v] != oracle.NO_ID).sum() > 500, v
