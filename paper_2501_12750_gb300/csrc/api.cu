@@ -47,7 +47,7 @@ struct vtx_ctx {
   bool has_cam = false;
   // scratch
   Buf keys, surv, state, tcount, tstart, tcursor, tlist, bsums, recs, recimg, recbox, recof, entries, status, counts, hostin_x,
-      hostin_e, hostout, covlist, covmask, stage, defer, uplane;
+      hostin_e, hostout, covlist, covmask, stage, defer;
   bool cov_ok = false;  // the covered-pixel list of the last prepared launch fits (two-pass resolve)
   bool occl_ok = false;  // the occlusion pass's buffers of the last prepared launch fit
   Buf ses_sas, ses_a, ses_b, ses_edt, ses_blk, ses_base, ses_total, ses_bbox, ses_case;
@@ -271,12 +271,10 @@ static vtx_status prepare(vtx_ctx *c, const Geometry &g, bool soft, long long st
     if ((st = ensure(c, c->status, sizeof(Status), "status"))) return st;
     cudaMemsetAsync(c->status.p, 0, sizeof(Status), c->stream);
   }
-  // occlusion pass: the kept survivors' list and the upper-bound depth plane (no room: the plain setup does
-  // without)
+  // occlusion pass: the kept survivors' list (no room: the plain setup does without)
   c->occl_ok = false;
   if (g.occl && !soft) {
-    if (ensure(c, c->defer, sizeof(uint32_t) * (size_t)(n_img * g.surv_cap), "kept survivors") == VTX_OK &&
-        ensure(c, c->uplane, sizeof(uint32_t) * (size_t)(n_img * g.pix_per_img), "depth bound plane") == VTX_OK)
+    if (ensure(c, c->defer, sizeof(uint32_t) * (size_t)(n_img * g.surv_cap), "kept survivors") == VTX_OK)
       c->occl_ok = true;
     else
       c->err.clear();
@@ -314,7 +312,6 @@ static Scratch scratch_of(vtx_ctx *c) {
   s.cov_list = c->cov_ok ? (uint32_t *)c->covlist.p : nullptr;
   s.cov_mask = c->cov_ok ? (uint32_t *)c->covmask.p : nullptr;
   s.defer = c->occl_ok ? (uint32_t *)c->defer.p : nullptr;
-  s.uplane = c->occl_ok ? (uint32_t *)c->uplane.p : nullptr;
   return s;
 }
 
@@ -449,7 +446,7 @@ vtx_status vtx_destroy(vtx_ctx *c) {
   drop_graphs(c);
   Buf *bufs[] = {&c->keys,   &c->surv,   &c->state,  &c->tcount,   &c->tstart,   &c->tcursor,  &c->tlist,
                  &c->bsums,  &c->recs,   &c->recimg, &c->recbox,   &c->recof,    &c->entries,  &c->status,
-                 &c->counts, &c->hostin_x, &c->hostin_e, &c->hostout, &c->covlist, &c->covmask, &c->stage, &c->defer, &c->uplane, &c->ses_sas, &c->ses_a, &c->ses_b,
+                 &c->counts, &c->hostin_x, &c->hostin_e, &c->hostout, &c->covlist, &c->covmask, &c->stage, &c->defer, &c->ses_sas, &c->ses_a, &c->ses_b,
                  &c->ses_edt, &c->ses_blk, &c->ses_base, &c->ses_total, &c->ses_bbox, &c->ses_case};
   for (Buf *b : bufs)
     if (b->p) cudaFree(b->p);
@@ -814,11 +811,11 @@ static vtx_status batch_once(vtx_ctx *c, const float *frames, int64_t stride, co
   return VTX_OK;
 }
 
-// Frames per pipeline pass: bounded so the per-image scratch (keys, coverage list and depth-bound plane per
-// pixel; survivor and kept-survivor slots per atom) stays near 8 GB, and the images of a pass within the 65,535
+// Frames per pipeline pass: bounded so the per-image scratch (keys and coverage list per pixel; survivor and
+// kept-survivor slots per atom) stays near 8 GB, and the images of a pass within the 65,535
 // blocks of a launch's second grid dimension.
 static int batch_chunk(const vtx_camera *cams, int n_views, long long stride, int n_frames) {
-  double per_frame = (double)n_views * ((double)cams[0].width * cams[0].height * 16.0 + (double)stride * 8.0);
+  double per_frame = (double)n_views * ((double)cams[0].width * cams[0].height * 12.0 + (double)stride * 8.0);
   int fc = (int)(8e9 / (per_frame > 1.0 ? per_frame : 1.0));
   if (fc > 65535 / n_views) fc = 65535 / n_views;
   if (fc < 1) fc = 1;

@@ -17,10 +17,10 @@
 //        most splat_max candidate pixels are ray-cast right there and
 //        merged with a 64-bit atomicMin of (depth key << 32 | id); larger
 //        ones become 64-byte records counted per screen tile;
-//   k_occl_upper / k_occl_test  (crowded batch images) every survivor
-//        writes FP32 upper bounds of its entry depth at the pixels it
-//        certainly covers; setup then takes only the survivors that these
-//        bounds do not hide at every pixel of their boxes;
+//   k_occl_upper / k_occl_test  (crowded batch images) the front survivors
+//        write bound keys (FP32 upper bounds of their entry depth, as keys)
+//        at the pixels they certainly cover; setup then takes only the
+//        survivors that these keys do not hide at every pixel of their boxes;
 //   k_scan_*     exclusive scan of the per-tile counts (counting sort by tile),
 //        listing the non-empty tiles longest first;
 //   k_scatter    writes (min depth key << 32 | record) entries per tile;
@@ -840,13 +840,15 @@ __global__ __launch_bounds__(256, VTX_SETUP_MINB) void k_setup(Geometry g, const
 
 // ------------------------------------------------------- occlusion pass --
 // Images with many survivors per pixel (a trajectory blob seen whole) spend most of their setup on spheres
-// that lose every depth test.  The pass proves most of them hidden before their precise setup, from an FP32
-// plane U of upper bounds of the nearest hit depth:
+// that lose every depth test.  The pass proves most of them hidden before their precise setup, from bound keys
+// written into the (still clear) key plane itself:
 //   k_occl_upper: every survivor in the front share of the image's depth range writes, at each pixel whose ray
-//     certainly meets its sphere, an upper bound of its entry depth there (atomicMin on the FP32 bits).  The
-//     nearest hit at that pixel over all survivors is then at most U, whichever survivors are processed later.
-//   k_occl_test: a survivor is dropped when every pixel of its candidate box holds a bound below the smallest
-//     depth any of its hits could have, less the rounding of depth to key; the others are listed for setup.
+//     certainly meets its sphere, a key above every key its hit there can have: the depth key of an FP32
+//     upper bound of its entry depth, raised past the key rounding, with the id of no primitive (atomicMin).
+//     The final key of that pixel, over all survivors, is then below the bound key, whichever survivors are
+//     processed later, and it is a primitive's key: the bound keys never survive to the resolve.
+//   k_occl_test: a survivor is dropped when every pixel of its candidate box holds a key whose depth part is
+//     below the smallest depth key any of its hits could have; the others are listed for setup.
 // Exact: a dropped sphere's key at every pixel of its box is above the final key there, so it is never the
 // minimum of any pixel and the key planes are those of the plain pass, bit for bit.  (The sphere that holds a
 // pixel's minimum is never dropped, as its key there would have to be above itself.)
@@ -880,7 +882,7 @@ __device__ __forceinline__ void occl_slots(const bool (&f)[kOcclItems], unsigned
   }
 }
 
-// Most pixels a sphere's box may have and still be tested, or write its bounds (larger ones are kept and
+// Most pixels a sphere's box may have and still be tested, or write its bound keys (larger ones are kept and
 // write none: the bounds stay valid, only weaker).
 constexpr int kOcclMaxPixels = 64;
 // Share of the image's depth range whose spheres (by their front) write bounds.  Spheres farther back seldom
@@ -891,8 +893,19 @@ constexpr int kOcclMaxPixels = 64;
 #endif
 constexpr float kOcclUpperFront = VTX_OCCL_UPPER_FRONT;
 
+// The bound key of a hit depth bound ub: the depth key of ub, raised past every rounding of the key of a hit at
+// a depth below ub (the FP32 difference and product here, ~2e-7 of the key, and the hit's own key rounding,
+// tens of keys: 4e-6 of the key plus 8192 keys), with the id of no primitive, so that a primitive's key with
+// the same depth part is still below it.  Beyond the key range: the background key (no bound).
+__device__ __forceinline__ unsigned long long bound_key(float ub, float zlo, float S) {
+  float kf = fmaxf((ub - zlo) * S, 0.0f);
+  kf = fmaf(kf, 4e-6f, kf) + 8192.0f;
+  if (!(kf < 4294967040.0f)) return kBgKey;
+  return ((unsigned long long)(uint32_t)ceilf(kf) << 32) | (unsigned long long)kNoId;
+}
+
 // Upper bounds of the entry depth of the sphere at FP32 view position (vx, vy, vz) (error err per component)
-// with radius r, at the pixels whose rays certainly meet it, merged into the plane Ui.  At pixel ray
+// with radius r, at the pixels whose rays certainly meet it, merged as bound keys into the key plane Ki.  At pixel ray
 // u = (a, b, 1) and w = (vx - a vz, vy - b vz) (the centre's offset from the ray at the centre's depth), the
 // centre's squared distance to the ray is d2 = |w|^2 - (w.u)^2 / |u|^2, the ray's closest point to the centre
 // lies at depth tc = vz + (w.u) / |u|^2 and it enters the sphere at depth tc - sqrt((r^2 - d2) / |u|^2).
@@ -900,8 +913,8 @@ constexpr float kOcclUpperFront = VTX_OCCL_UPPER_FRONT;
 // rr = 0.999 r - 2 del: the ray's true distance is then below 0.999 r - del, so the hit test meets the sphere
 // there whatever its own rounding, and the bound tc - sqrt((rr^2 - d2) / |u|^2) + 2 del + 1e-4 exceeds the true
 // entry depth by at least 1e-4 A (rr^2 - d2 is below the true r^2 - d^2).
-__device__ __forceinline__ void occl_upper_splat(const Geometry &g, const ViewParams &v, uint32_t *Ui, float vx,
-                                                 float vy, float vz, float err, float r) {
+__device__ __forceinline__ void occl_upper_splat(const Geometry &g, const ViewParams &v, unsigned long long *Ki,
+                                                 float vx, float vy, float vz, float err, float r, float zlo, float S) {
   if (!(vz > 2.0f * (r + err) + v.znear)) return;  // no sphere near the eye plane (its reference depth moves)
   const float del = 2.0f * err + 1e-6f * vz;
   const float rr = fmaf(r, 0.999f, -2.0f * del);
@@ -930,7 +943,7 @@ __device__ __forceinline__ void occl_upper_splat(const Geometry &g, const ViewPa
     if (d2 <= rr2) {
       const float tc = fmaf(wu, q.inv_uu, vz);
       const float sq = sqrt_approx((rr2 - d2) * q.inv_uu);
-      atomicMin(Ui + (long long)py * g.W + px, __float_as_uint(fmaf(-0.99999f, sq, tc) + dU));
+      atomicMin(Ki + (long long)py * g.W + px, bound_key(fmaf(-0.99999f, sq, tc) + dU, zlo, S));
     }
     if (++px > box.x1) {
       px = box.x0;
@@ -943,7 +956,7 @@ __device__ __forceinline__ void occl_upper_splat(const Geometry &g, const ViewPa
 // shared memory and then spreads their pixel loops over all 32 lanes: about a third of the survivors write,
 // so a lane per survivor would leave most lanes idle during the loops.
 __global__ __launch_bounds__(256) void k_occl_upper(Geometry g, const float4 *__restrict__ frames, ImageState *st,
-                                                    const uint32_t *__restrict__ surv, uint32_t *U) {
+                                                    const uint32_t *__restrict__ surv, unsigned long long *keys) {
   pdl_enter();
   __shared__ float4 s_c[8][32 * kOcclItems];  // per warp: the writers' (vx, vy, vz, err)
   __shared__ float s_r[8][32 * kOcclItems];   // and radii
@@ -955,7 +968,7 @@ __global__ __launch_bounds__(256) void k_occl_upper(Geometry g, const float4 *__
   const ViewParams &v = g.views[img % g.n_views];
   const float4 *X = frames + (long long)(img / g.n_views) * g.stride;
   const uint32_t *sv = surv + (long long)img * g.surv_cap;
-  uint32_t *Ui = U + (long long)img * g.pix_per_img;
+  unsigned long long *Ki = keys + (long long)img * g.pix_per_img;
   const float zf = s.zlo + kOcclUpperFront * (kKeySpanF * s.invS);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -997,47 +1010,51 @@ __global__ __launch_bounds__(256) void k_occl_upper(Geometry g, const float4 *__
     __syncwarp();
     for (unsigned t = lane; t < total; t += 32) {
       const float4 q = s_c[wid][t];
-      occl_upper_splat(g, v, Ui, q.x, q.y, q.z, q.w, s_r[wid][t]);
+      occl_upper_splat(g, v, Ki, q.x, q.y, q.z, q.w, s_r[wid][t], s.zlo, s.S);
     }
     __syncwarp();  // the slots are read before the next step refills them
   }
 }
 
 // Is the sphere at FP32 view position (vx, vy, vz) (error err) with radius r, candidate box `box`, hidden at
-// every pixel of its box by the bounds in Ui?  Its hits lie at depth >= vz - r - err (per component error, so
-// 2 err covers the distance), and its keys at or above that depth's key less the rounding of the key (tens of
-// keys, so 1024 keys, less 2e-6 relative and 1e-4 A for the FP32 evaluation of the threshold); a bound below
-// the threshold means the pixel's final key is below every key of the sphere.  The bits of positive floats
-// compare like the floats; the cleared value (all ones) keeps the sphere.
+// every pixel of its box by the keys in Ki (bound keys or the background)?  lb: the smallest depth key any of its
+// hits could have -- its front (vz - r, widened by the view error and by 2e-7 of the depths for the FP32
+// rounding of these differences) mapped to keys, less 4e-6 relative plus 4096 keys for the rounding of the
+// product, of the reference key and of the hit offset (tens of keys).  A pixel whose key's depth part is below
+// lb can take no key of this sphere.  Only the depth words (the upper halves of the keys) are read; boxes of at
+// most 4 x 4 pixels (the common case) load all of theirs at once.
 __device__ __forceinline__ bool occl_hidden(const Geometry &g, const ViewParams &v, const ImageState &s,
-                                            const uint32_t *Ui, float vz, float err, float r, const PixBox &box) {
+                                            const unsigned long long *Ki, float vz, float err, float r,
+                                            const PixBox &box) {
   if (!(vz > 2.0f * (r + err) + v.znear)) return false;
-  const float thr = vz - 2.0f * err - r * 1.000002f - 2e-6f * vz - 1e-4f - 1024.0f * s.invS;
-  if (!(thr > 0.0f)) return false;
-  const uint32_t tb = __float_as_uint(thr);
+  float lb = (vz - err - r * 1.000002f - s.zlo - 2e-7f * (fabsf(vz) + fabsf(s.zlo))) * s.S;
+  lb = lb - fabsf(lb) * 4e-6f - 4096.0f;
+  if (!(lb > 0.0f)) return false;
+  const uint32_t lbi = (uint32_t)fminf(floorf(lb), 4294967040.0f);  // lbi <= lb
   const int w = box.x1 - box.x0 + 1, h = box.y1 - box.y0 + 1;
-  const uint32_t *Ub = Ui + (long long)box.y0 * g.W + box.x0;
-  if (w <= 4 && h <= 4) {  // the common case: all the box's bounds loaded at once
-    uint32_t ub[16];
+  // the depth word of a key: its upper 32 bits (little-endian)
+  const uint32_t *Db = reinterpret_cast<const uint32_t *>(Ki + (long long)box.y0 * g.W + box.x0) + 1;
+  if (w <= 4 && h <= 4) {
+    uint32_t kd[16];
 #pragma unroll
     for (int dy = 0; dy < 4; ++dy)
 #pragma unroll
-      for (int dx = 0; dx < 4; ++dx) ub[dy * 4 + dx] = (dx < w && dy < h) ? Ub[(long long)dy * g.W + dx] : 0u;
+      for (int dx = 0; dx < 4; ++dx) kd[dy * 4 + dx] = (dx < w && dy < h) ? Db[2 * ((long long)dy * g.W + dx)] : 0u;
     bool hidden = true;
 #pragma unroll
-    for (int q = 0; q < 16; ++q) hidden = hidden && ub[q] < tb;
+    for (int q = 0; q < 16; ++q) hidden = hidden && kd[q] < lbi;
     return hidden;
   }
   if (w * h > kOcclMaxPixels) return false;
   for (int dy = 0; dy < h; ++dy)
     for (int dx = 0; dx < w; ++dx)
-      if (!(Ub[(long long)dy * g.W + dx] < tb)) return false;
+      if (!(Db[2 * ((long long)dy * g.W + dx)] < lbi)) return false;
   return true;
 }
 
 __global__ __launch_bounds__(256) void k_occl_test(Geometry g, const float4 *__restrict__ frames, ImageState *st,
-                                                   const uint32_t *__restrict__ surv, const uint32_t *__restrict__ U,
-                                                   uint32_t *kept) {
+                                                   const uint32_t *__restrict__ surv,
+                                                   const unsigned long long *__restrict__ keys, uint32_t *kept) {
   pdl_enter();
   const int img = blockIdx.y;
   const ImageState s = finalize_state(g, img, st[img]);
@@ -1046,7 +1063,7 @@ __global__ __launch_bounds__(256) void k_occl_test(Geometry g, const float4 *__r
   const ViewParams &v = g.views[img % g.n_views];
   const float4 *X = frames + (long long)(img / g.n_views) * g.stride;
   const uint32_t *sv = surv + (long long)img * g.surv_cap;
-  const uint32_t *Ui = U + (long long)img * g.pix_per_img;
+  const unsigned long long *Ki = keys + (long long)img * g.pix_per_img;
   uint32_t *L = kept + (long long)img * g.surv_cap;
   const int lane = threadIdx.x & 31;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1070,7 +1087,7 @@ __global__ __launch_bounds__(256) void k_occl_test(Geometry g, const float4 *__r
         float vx, vy, vz, err;
         view_f32(v, a.x, a.y, a.z, vx, vy, vz, err);
         PixBox box;  // an empty box can change no pixel
-        keep[j] = lean_box(v, g.W, g.H, vx, vy, vz, r + err, box) && !occl_hidden(g, v, s, Ui, vz, err, r, box);
+        keep[j] = lean_box(v, g.W, g.H, vx, vy, vz, r + err, box) && !occl_hidden(g, v, s, Ki, vz, err, r, box);
       }
     }
     unsigned sk[kOcclItems];
@@ -2075,7 +2092,7 @@ cudaError_t run_binning(const Geometry &g, const Scene &sc, const Scratch &s, cu
                         bool soft) {
   const int sms = sm_count();
   const long long n_tiles = (long long)g.n_img * g.tiles_per_img;
-  const bool occl = g.occl && !soft && s.defer && s.uplane;
+  const bool occl = g.occl && !soft && s.defer;
   {
     // the background key has every bit set, so the key planes of a batch are cleared by a byte memset
     // (batch 30.9 -> 29.3 ms) instead of the clear kernel's stores; a single frame keeps the kernel, whose
@@ -2087,8 +2104,6 @@ cudaError_t run_binning(const Geometry &g, const Scene &sc, const Scratch &s, cu
       static_assert(kBgKey == ~0ull, "a byte fill of 0xff gives the background key");
       cudaMemsetAsync(s.keys, 0xff, sizeof(unsigned long long) * (size_t)all_keys, st);
     }
-    // the occlusion pass's depth bounds start at all ones, above the bits of every finite float
-    if (occl) cudaMemsetAsync(s.uplane, 0xff, sizeof(uint32_t) * (size_t)(g.pix_per_img * g.n_img), st);
     long long want = n_keys / 2 > n_tiles ? n_keys / 2 : n_tiles;
     want = want > g.n_img ? want : g.n_img;
     const long long blocks = (want + 255) / 256;
@@ -2163,8 +2178,8 @@ cudaError_t run_binning(const Geometry &g, const Scene &sc, const Scratch &s, cu
       // occlusion pass (images that do not take it run all their survivors in setup): depth bounds, test,
       // setup of the kept survivors
       const float4 *Xs = sc.stage ? sc.stage : sc.frames;
-      launch_pdl(k_occl_upper, grid, 256, 0, st, g, Xs, s.state, s.surv, s.uplane);
-      launch_pdl(k_occl_test, grid, 256, 0, st, g, Xs, s.state, s.surv, s.uplane, s.defer);
+      launch_pdl(k_occl_upper, grid, 256, 0, st, g, Xs, s.state, s.surv, s.keys);
+      launch_pdl(k_occl_test, grid, 256, 0, st, g, Xs, s.state, s.surv, s.keys, s.defer);
       launch_pdl(k_setup<false>, grid, 256, 0, st, g, Xs, sc.bonds, s.state, s.surv, s.keys, s.recs, s.rec_img,
                  s.rec_box, s.rec_of, s.tile_count, s.status, s.cap_rec, s.defer);
     }

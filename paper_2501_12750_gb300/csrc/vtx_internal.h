@@ -37,8 +37,6 @@ struct Scratch {
   uint32_t *cov_list;         // [n_img * H * W] covered pixels (img * H * W + p), or null: single-pass resolve
   uint32_t *cov_mask;         // [n_img * H * W / 32 + 8] coverage bits written by the list pass
   uint32_t *defer;            // occlusion pass: [n_img][surv_cap] the survivors its test kept, or null
-  uint32_t *uplane;           // occlusion pass: [n_img][H][W] upper bounds of the nearest hit depth (FP32 bits),
-                              // or null
   Status *status;
   uint32_t cap_rec;
   unsigned long long cap_entries;

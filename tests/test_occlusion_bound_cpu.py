@@ -1,4 +1,4 @@
-"""The occlusion pass's two FP32 bounds, checked in FP64 on random spheres, pixel rays and key scales.
+"""The occlusion pass's FP32 bounds and bound keys, checked in FP64 on random spheres, pixel rays and key scales.
 
 Writer (k_occl_upper): at pixel ray u = (a, b, 1) (the FP32 slopes of the pixel centre) the kernel forms, from
 the FP32 view centre (vx, vy, vz) (|error| <= err per component),
@@ -8,12 +8,12 @@ and when d2 <= rr^2 writes U = tc - 0.99999 sqrt((rr^2 - d2) / |u|^2) + 2 del + 
 distance of the centre to that ray is below 0.9995 r (the hit test meets the sphere there), and U exceeds the
 ray's true entry depth by at least 5e-5 A.
 
-Test (k_occl_test): a sphere is dropped when every bound in its box is below
-    thr = vz - 2 err - 1.000002 r - 2e-6 vz - 1e-4 - 1024 / S.
-Claim: thr is below the sphere's nearest possible depth zc - r by more than 256 keys (the depth-to-key rounding
-of both spheres' hits is tens of keys), so a pixel whose bound is below thr ends with a key below every key
-of the dropped sphere.  sqrt and 1/|u|^2 use the hardware approximations in the kernel; here they are
-perturbed by up to 2^-22 relative."""
+Bound keys: the writer stores ceil((U - zlo) S (1 + 4e-6) + 8192) as the depth part of a key with the id of no
+primitive; it must exceed the key of any hit at a depth below U.  Test (k_occl_test): a sphere is dropped when
+the depth part of every key in its box is below floor(lb),
+    lb = (vz - err - 1.000002 r - zlo - 2e-7 (|vz| + |zlo|)) S,  lb -= 4e-6 |lb| + 4096,
+which must lie below the smallest key any of its hits can have.  sqrt and 1/|u|^2 use the hardware
+approximations in the kernel; here they are perturbed by up to 2^-22 relative."""
 import numpy as np
 
 f32 = np.float32
@@ -75,27 +75,57 @@ def test_upper_bound_is_above_the_entry_depth_where_it_is_written():
     assert np.median(slack) < 0.05
 
 
-def test_threshold_is_below_every_hit_depth_by_more_than_the_key_rounding():
+def _bound_key_hi(ub, zlo, S):
+    """Depth part of bound_key(ub, zlo, S) in FP32 (NaN for the background key)."""
+    kf = _f(np.maximum(_f(_f(ub - zlo) * S), 0.0))
+    kf = _f(_fma(kf, _f(4e-6), kf) + 8192.0)
+    return np.where(kf < 4294967040.0, np.ceil(kf), np.nan)
+
+
+def test_bound_key_is_above_every_key_of_a_hit_below_the_bound():
+    """A hit at depth d <= ub has key round((z_r - zlo) S) + round((d - z_r) S) <= (d - zlo) S + 1 + tens of
+    keys (the FP32 hit offset); the bound key's depth part must exceed that by a margin."""
+    rng = np.random.default_rng(16)
+    n = 400000
+    zlo = _f(rng.uniform(1.0, 5.0e3, n))
+    span = rng.uniform(5.0, 3.0e3, n)
+    S = _f(4294966784.0 / span)
+    ub = _f(zlo + rng.uniform(0.0, 1.0, n) * span)
+    hi = _bound_key_hi(ub, zlo, S)
+    ok = ~np.isnan(hi)
+    assert ok.mean() > 0.99
+    assert np.all(hi[ok] > (ub[ok] - zlo[ok]) * S[ok] + 128.0)
+
+
+def test_key_lower_bound_is_below_every_hit_key():
+    """lb = (vz - err - 1.000002 r - zlo - 2e-7 (|vz| + |zlo|)) S, less 4e-6 |lb| + 4096, floored: below the
+    smallest key (zc - r - zlo) S - 66 any hit of the sphere can have."""
     rng = np.random.default_rng(14)
     n = 400000
     zc, r, cx, cy, err, vx, vy, vz, a, b = _case(rng, n)
+    zlo = _f(zc - r - rng.uniform(0.0, 0.9, n) * (zc - r))
     span = rng.uniform(5.0, 3.0e3, n)
-    S = _f(4294967295.0 / span)
-    invS = _f(span / 4294967295.0)
-    thr = _f(_f(_f(_f(_f(vz - _f(2.0 * err)) - _f(r * _f(1.000002))) - _f(_f(2e-6) * vz)) - _f(1e-4)) - _f(1024.0 * invS))
-    assert np.all(thr < zc - r - 256.0 / S)
+    S = _f(4294966784.0 / span)
+    lb = _f(_f(_f(_f(_f(vz - err) - _f(r * _f(1.000002))) - zlo) - _f(_f(2e-7) * _f(np.abs(vz) + np.abs(zlo)))) * S)
+    lb = _f(_f(lb - _f(np.abs(lb) * _f(4e-6))) - 4096.0)
+    lbi = np.floor(np.minimum(lb, 4294967040.0))
+    true_min = (zc - r - zlo.astype(np.float64)) * S - 66.0
+    sel = lb > 0
+    assert sel.mean() > 0.9
+    assert np.all(lbi[sel] < true_min[sel])
 
 
-def test_threshold_rejects_a_sphere_behind_a_surface():
-    """The margins cost little: a bound 0.01 A in front of a sphere's front rejects it at every key scale."""
+def test_key_lower_bound_rejects_a_sphere_behind_a_surface():
+    """The margins cost little: a bound key 0.01 A in front of a sphere's front lies below its lb."""
     rng = np.random.default_rng(15)
     n = 20000
     zc = rng.uniform(100.0, 2000.0, n)
     r = np.full(n, 1.5)
     err = _f(4e-7 * 3.0 * zc)
     vz = _f(zc)
-    invS = _f(400.0 / 4294967295.0)
-    thr = _f(_f(_f(_f(_f(vz - _f(2.0 * err)) - _f(r * _f(1.000002))) - _f(_f(2e-6) * vz)) - _f(1e-4)) - _f(1024.0 * invS))
-    bound = _f(zc - r - 0.01)
-    # the kernel compares FP32 bit patterns; for positive floats that is the float order
-    assert np.all(bound.astype(np.float32).view(np.uint32) < thr.astype(np.float32).view(np.uint32))
+    zlo = _f(zc - rng.uniform(20.0, 90.0, n))
+    S = _f(4294966784.0 / 400.0)
+    lb = _f(_f(_f(_f(_f(vz - err) - _f(r * _f(1.000002))) - zlo) - _f(_f(2e-7) * _f(np.abs(vz) + np.abs(zlo)))) * S)
+    lb = _f(_f(lb - _f(np.abs(lb) * _f(4e-6))) - 4096.0)
+    hi = _bound_key_hi(_f(zc - r - 0.01), zlo, S)
+    assert np.all(hi < np.floor(lb))

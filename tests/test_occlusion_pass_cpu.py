@@ -2,10 +2,10 @@
 
 A sphere blob is ray-cast exactly (FP64 entry depth per pixel centre, ties to the smaller id).  The pass is
 then emulated with the kernels' FP32 formulas: the survivors in the front 35 % of the depth range write upper
-bounds of their entry depth at the pixels their rays certainly meet (k_occl_upper), and every survivor whose
-candidate box holds only bounds below its threshold is dropped (k_occl_test).  Claims: every bound lies above
-the exact nearest depth of its pixel, every threshold below its sphere's nearest depth, no dropped sphere holds
-any pixel of the exact image, the image of the kept spheres alone is the exact image bit for bit, and the pass
+bounds of their entry depth, as bound keys, at the pixels their rays certainly meet (k_occl_upper), and every
+survivor whose candidate box holds only bound keys below its key bound is dropped (k_occl_test).  Claims: every
+bound lies above the exact nearest depth of its pixel and every bound key above that depth's key, every key
+bound below the key of its sphere's nearest depth, no dropped sphere holds any pixel of the exact image, the image of the kept spheres alone is the exact image bit for bit, and the pass
 drops about half of the spheres (so the check is not vacuous)."""
 import numpy as np
 
@@ -96,22 +96,32 @@ def test_occlusion_pass_drops_only_spheres_that_hold_no_pixel():
     fin = np.isfinite(U)
     assert fin.sum() > 0.5 * (owner >= 0).sum()
     assert np.all(U[fin].astype(np.float64) >= depth[fin] + 5e-5)
+    # as bound keys (depth parts): above the exact key of that depth by more than the key rounding
+    S = f32(1.0) / invS
+    kf = np.maximum(f32(f32(U - f32(zlo)) * S), f32(0.0))
+    kf = f32(f32(kf * f32(4e-6) + kf) + f32(8192.0))
+    KB = np.where(fin & (kf < 4294967040.0), np.ceil(kf.astype(np.float64)), np.inf)
+    assert np.all(KB[fin] > (depth[fin] - float(f32(zlo))) * float(S) + 128.0)
     # k_occl_test, with each sphere's exact pixel box widened by a pixel for the candidate box
     dropped = []
     for i in range(n):
         if not (vz[i] > 2 * (r32[i] + err[i])):
             continue
-        thr = f32(f32(f32(f32(f32(vz[i] - f32(2 * err[i])) - f32(r32[i] * f32(1.000002))) - f32(f32(2e-6) * vz[i]))
-                      - f32(1e-4)) - f32(f32(1024.0) * invS))
+        zl = f32(zlo)
+        lb = f32(f32(f32(f32(vz[i] - err[i]) - f32(r32[i] * f32(1.000002))) - zl)
+                 - f32(f32(2e-7) * f32(abs(vz[i]) + abs(zl))))
+        lb = f32(f32(lb * S) - f32(abs(f32(lb * S)) * f32(4e-6))) - f32(4096.0)
+        lbi = np.floor(min(float(lb), 4294967040.0))
         rp = f * rad[i] / c[i, 2] * 1.05 + 1.0
         u0, v0 = W / 2 + f * c[i, 0] / c[i, 2], H / 2 - f * c[i, 1] / c[i, 2]
         x0, x1 = max(int(np.floor(u0 - rp - 0.5)), 0), min(int(np.ceil(u0 + rp - 0.5)), W - 1)
         y0, y1 = max(int(np.floor(v0 - rp - 0.5)), 0), min(int(np.ceil(v0 + rp - 0.5)), H - 1)
         if x0 > x1 or y0 > y1:
             continue
-        # the test's claim: the threshold lies below the sphere's nearest depth by more than the key rounding
-        assert float(thr) < c[i, 2] - rad[i] - 256.0 * float(invS)
-        if thr > 0 and (U[y0:y1 + 1, x0:x1 + 1] < thr).all():
+        # the test's claim: its key bound lies below the key of the sphere's nearest depth by more than the key
+        # rounding
+        assert lbi < (c[i, 2] - rad[i] - float(zl)) * float(S) - 66.0
+        if lb > 0 and (KB[y0:y1 + 1, x0:x1 + 1] < lbi).all():
             dropped.append(i)
     dropped = np.array(dropped)
     assert len(dropped) > 2 * n // 5, len(dropped)  # about half of the 8,000 spheres
