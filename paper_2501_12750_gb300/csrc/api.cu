@@ -600,8 +600,8 @@ static vtx_status render_once(vtx_ctx *c, const vtx_settings *s, const vtx_outpu
   g.splat_max = s->splat_max_px ? s->splat_max_px : default_splat(g.n_atoms + g.n_bonds, g.pix_per_img);
   g.surv_cap = c->n_atoms + g.n_bonds + cull_survivor_slack(c->n_atoms);
   // no occlusion pass for a single frame: measured on the 1e8-atom 4K frame (whose set-up is 0.07 ms of
-  // 0.43) it cost more than it saved (2,331 -> 1,959 frames/s), the bound plane's clear and the two passes
-  // over all survivors outweighing the set-up they remove
+  // 0.43) it cost more than it saved (2,331 -> 1,959 frames/s, with the bounds then in a plane of their own):
+  // its two passes over every survivor outweigh the set-up they remove
   g.occl = 0;
   vtx_status st = prepare(c, g, false, 0);
   if (st) return st;
